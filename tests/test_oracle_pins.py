@@ -1,0 +1,355 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, an exact invariant, a brute-force solve on a tiny lattice, or a
+convergence rate the paper states.  All run on the CPU.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import Oracle, link_flux
+from paper_1907_04732_gb300 import workloads as wl
+import analytic as an
+
+A0 = 1.0 + 2.0 * math.sqrt(2.0)
+
+
+def make(w, **kw):
+    args = dict(tau=w.tau, bjerrum=w.bjerrum, z=w.z, D=w.D, rho_bulk=w.rho_bulk,
+                e_app=w.e_app, flow=w.flow)
+    args.update(kw)
+    o = Oracle(w.shape, w.periodic, **args)
+    o.set_geometry(w.ids, w.n_elec)
+    o.set_voltage(w.psi)
+    return o
+
+
+# ---------------------------------------------------------------------------
+# Eq. DiscreteLaplacian: the stencil is exact on quadratics (sum rules of the
+# lattice, Sec. "Imposing conducting boundary conditions").
+def test_laplacian_exact_on_quadratics():
+    nx, ny, nz = 9, 8, 10
+    ids = wl.plates(nx, ny, nz)
+    o = Oracle((nx, ny, nz), (1, 1, 0))
+    o.set_geometry(ids, 2)
+    rng = np.random.default_rng(1)
+    a = rng.normal(size=10)
+    zz, yy, xx = np.mgrid[0:nz, 0:ny, 0:nx].astype(float)
+    phi = (a[0] * xx * xx + a[1] * yy * yy + a[2] * zz * zz + a[3] * xx * yy + a[4] * xx * zz
+           + a[5] * yy * zz + a[6] * xx + a[7] * yy + a[8] * zz + a[9])
+    lap = o.laplacian(phi)
+    inner = lap[2:nz - 2, 1:ny - 1, 1:nx - 1]   # no wrap, no boundary link
+    np.testing.assert_allclose(inner, 2.0 * (a[0] + a[1] + a[2]), rtol=0, atol=1e-10)
+
+
+# Fig. BC_ConstPot / Eq. DiscreteLaplacianModif: with every boundary link
+# doubled, the Laplace solution between plates is exactly linear and reaches
+# the electrode potential half-way between the last solid and first fluid
+# node; Q(0) is the dielectric capacitor's C_0 = eps/L times the voltage.
+@pytest.mark.parametrize("nx,nz,psi", [(1, 20, (0.1, 0.2)), (3, 33, (-0.3, 0.25)), (2, 64, (0.0, 1.0))])
+def test_plate_laplace_is_linear_with_midplane_interface(nx, nz, psi):
+    w = wl.plate_capacitor(nx, nx, nz, psi=psi)
+    o = make(w)
+    o.init()
+    L = nz - 2
+    zc = np.arange(nz, dtype=float)
+    exact = psi[0] + (psi[1] - psi[0]) * (zc - 0.5) / L
+    phi = o.phi()
+    np.testing.assert_allclose(phi[1:-1], np.broadcast_to(exact[1:-1, None, None], phi[1:-1].shape),
+                               rtol=0, atol=1e-12)
+    q = o.charge()
+    qexp = an.dielectric_plate_charge_per_area(an.eps_of(w.bjerrum), L, psi[1] - psi[0]) * nx * nx
+    np.testing.assert_allclose(q, [-qexp, qexp], rtol=1e-11)
+
+
+# Brute force on a tiny lattice: the oracle's converged potential equals a
+# dense direct solve of the masked modified-Laplacian system, written here
+# from the paper's stencil with numpy rolls.
+def _dense_system(ids, psi, rho_el, lB):
+    nz, ny, nx = ids.shape
+    cvs = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+    cvs += [(sx, sy, 0) for sx in (1, -1) for sy in (1, -1)]
+    cvs += [(sx, 0, sz) for sx in (1, -1) for sz in (1, -1)]
+    cvs += [(0, sy, sz) for sy in (1, -1) for sz in (1, -1)]
+    N = ids.size
+    idx = np.arange(N).reshape(ids.shape)
+    solid = ids > 0
+    fluid_nodes = np.flatnonzero(~solid.reshape(-1))
+    pos = -np.ones(N, dtype=int)
+    pos[fluid_nodes] = np.arange(fluid_nodes.size)
+    A = np.zeros((fluid_nodes.size, fluid_nodes.size))
+    b = 4 * math.pi * lB * rho_el.reshape(-1)[fluid_nodes].copy()
+    phis = np.zeros(N)
+    phis[solid.reshape(-1)] = np.asarray(psi)[ids.reshape(-1)[solid.reshape(-1)] - 1]
+    for c in cvs:
+        coef = 1.0 / 3.0 if sum(abs(t) for t in c) == 1 else 1.0 / 6.0
+        nb = np.roll(idx, shift=(-c[2], -c[1], -c[0]), axis=(0, 1, 2)).reshape(-1)
+        for row, r in enumerate(fluid_nodes):
+            r2 = nb[r]
+            if r2 == r:
+                continue
+            if solid.reshape(-1)[r2]:
+                A[row, row] += 2 * coef
+                b[row] += 2 * coef * phis[r2]
+            else:
+                A[row, row] += coef
+                A[row, pos[r2]] -= coef
+    return A, b, fluid_nodes, phis
+
+
+def test_poisson_matches_dense_solve():
+    ids = wl.random_blobs(6, 5, 7, 2, 0.25, seed=11)
+    psi = (0.13, -0.21)
+    rng = np.random.default_rng(5)
+    rho_el = rng.normal(scale=1e-3, size=ids.shape) * (ids == 0)
+    lB = 0.9
+    o = Oracle((6, 5, 7), (1, 1, 1), bjerrum=lB)
+    o.set_geometry(ids, 2)
+    o.set_voltage(psi)
+    assert o.poisson(rho_el) >= 0
+    A, b, fl, phis = _dense_system(ids, psi, rho_el, lB)
+    x = np.linalg.solve(A, b)
+    phi = o.phi().reshape(-1)
+    np.testing.assert_allclose(phi[fl], x, rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(phi[ids.reshape(-1) > 0], phis[ids.reshape(-1) > 0])
+    # induced charge: Q_e = -eps * sum over electrode-e nodes of the modified
+    # Laplacian restricted to links to fluid (Eq. Qelec)
+    lap = o.laplacian(o.phi())
+    q = o.charge()
+    # total induced charge equals minus the ionic charge (Gauss; symmetric link
+    # weights make the Laplacian sum to zero over the lattice)
+    eps = an.eps_of(lB)
+    np.testing.assert_allclose(q.sum(), -rho_el.sum(), rtol=0, atol=1e-12)
+    # with only electrode-to-fluid links between the electrodes, the electrode
+    # sums of the Laplacian give each charge
+    s1 = -eps * lap[ids == 1].sum()
+    s2 = -eps * lap[ids == 2].sum()
+    touching = False
+    for ax in range(3):
+        for sh in (1, -1):
+            if np.any((ids == 1) & (np.roll(ids, sh, axis=ax) == 2)):
+                touching = True
+    if not touching:
+        np.testing.assert_allclose(q, [s1, s2], rtol=1e-12, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# Eq. LF2: the Boltzmann distribution n_k = A_k exp(-z_k phi) is an exact
+# fixed point of the link fluxes (stated below Eq. LF2).
+def test_boltzmann_is_fixed_point_of_link_flux():
+    ids = wl.random_blobs(7, 6, 5, 2, 0.2, seed=3)
+    o = Oracle((7, 6, 5), (1, 1, 1), bjerrum=1.3, flow=False, rho_bulk=(0.01, 0.01))
+    o.set_geometry(ids, 2)
+    o.set_voltage((0.05, -0.04))
+    o.init()
+    rng = np.random.default_rng(2)
+    phi = o.phi() + rng.normal(scale=0.2, size=ids.shape) * (ids == 0)
+    n = np.stack([0.011 * np.exp(-phi), 0.009 * np.exp(phi)]) * (ids == 0)
+    o.set_state(n=n, phi=phi)
+    o.step(1)
+    np.testing.assert_allclose(o.n(), n, rtol=1e-14, atol=0)
+
+
+def test_link_flux_single_link_values():
+    # closed forms of Eq. LF2 for one link
+    d = 0.05 / A0
+    # no potential: Fickian difference over the link length
+    assert link_flux(d, math.sqrt(2), 1.0, 0.3, 0.3, 0.0, 2.0, 2.5) == pytest.approx(-d * 0.5 / math.sqrt(2), rel=1e-14)
+    # uniform concentration, potential step dphi: j = -d n (e^{dphi} - e^{-dphi})/2
+    dphi = 0.07
+    want = -d * 1.3 * 0.5 * (1 + math.exp(-dphi)) * (math.exp(dphi) - 1.0)
+    assert link_flux(d, 1.0, 1.0, 0.0, dphi, 0.0, 1.3, 1.3) == pytest.approx(want, rel=1e-14)
+    # an applied field E.c acts as minus a potential step
+    assert link_flux(d, 1.0, 1.0, 0.0, 0.0, -dphi, 1.3, 1.3) == pytest.approx(want, rel=1e-14)
+    # antisymmetry of the link flux (local conservation)
+    a = link_flux(d, 1.0, -1.0, 0.11, 0.19, 0.02, 1.0, 1.4)
+    b = link_flux(d, 1.0, -1.0, 0.19, 0.11, -0.02, 1.4, 1.0)
+    assert a == pytest.approx(-b, rel=1e-14)
+
+
+# A0 reading: the update n(t+1) - n = -sum_i j^i with d = D/A0 gives a Fickian
+# diffusivity of exactly D at long wavelength (the paper's D = 0.05 and the
+# charging time ~ L lambda_D / 2D rely on it).  A plane wave decays per step by
+# 1 - d sum_i (1 - cos k.c_i)/|c_i|, which tends to 1 - D k^2.
+@pytest.mark.parametrize("kvec", [(1, 0, 0), (0, 2, 1), (1, 1, 1)])
+def test_diffusion_mode_decay(kvec):
+    nx, ny, nz = 16, 12, 10
+    D = 0.05
+    ids = np.zeros((nz, ny, nx), dtype=np.uint8)
+    o = Oracle((nx, ny, nz), (1, 1, 1), D=(D, D), flow=False, rho_bulk=(0.02, 0.02))
+    o.set_geometry(ids, 0)
+    o.init()
+    zz, yy, xx = np.mgrid[0:nz, 0:ny, 0:nx].astype(float)
+    k = 2 * math.pi * np.array([kvec[0] / nx, kvec[1] / ny, kvec[2] / nz])
+    mode = np.cos(k[0] * xx + k[1] * yy + k[2] * zz)
+    n0 = 0.02 * (1 + 0.1 * mode)
+    o.set_state(n=np.stack([n0, n0]))
+    o.step(1)
+    got = (o.n()[0] - 0.02) / (0.002 * mode)
+    cvs = np.array([(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+                   + [(a, b, 0) for a in (1, -1) for b in (1, -1)]
+                   + [(a, 0, b) for a in (1, -1) for b in (1, -1)]
+                   + [(0, a, b) for a in (1, -1) for b in (1, -1)], dtype=float)
+    lens = np.linalg.norm(cvs, axis=1)
+    factor = 1 - (D / A0) * np.sum((1 - np.cos(cvs @ k)) / lens)
+    sel = np.abs(mode) > 0.3
+    np.testing.assert_allclose(got[sel], factor, rtol=1e-10)
+    # long-wavelength limit: effective diffusivity D (not A0*D)
+    kk = float(k @ k)
+    assert abs((1 - factor) / (D * kk) - 1) < 0.1 * kk + 1e-3
+
+
+# ---------------------------------------------------------------------------
+# Exact conservation: per-species solute amount is conserved by the link
+# fluxes and the advection shares (Sec. "Lattice Boltzmann Electrokinetics";
+# Introduction), and the electrodes carry exactly minus the ionic charge.
+def test_mass_and_charge_conservation_with_flow():
+    ids = wl.random_blobs(10, 9, 8, 2, 0.2, seed=7)
+    w = wl.Workload("blob", ids, 2, (1, 1, 1), (0.0, 0.3), 1.1, 3.0, e_app=(2e-3, -1e-3, 5e-4))
+    o = make(w)
+    o.init()
+    m0 = o.n().sum(axis=(1, 2, 3))
+    for _ in range(4):
+        o.step(5)
+        n = o.n()
+        np.testing.assert_allclose(n.sum(axis=(1, 2, 3)), m0, rtol=1e-13)
+        rho_el = (n[0] - n[1]).sum()
+        assert abs(o.charge().sum() + rho_el) < 1e-12 * max(1.0, abs(o.charge()).max())
+    assert np.abs(o.u()).max() > 1e-8  # the fluid does move
+
+
+# Sec. "Parallel plate capacitor": results do not depend on the absolute
+# potentials, only on their difference; and a one-node-wide periodic column is
+# equivalent to a wider one.
+def test_absolute_potential_and_column_width_independence():
+    base = wl.plate_capacitor(1, 1, 24, debye=3.0, bjerrum=1.0, psi=(0.1, 0.2))
+    res = []
+    for nx, shift in ((1, 0.0), (1, 0.37), (3, 0.0), (4, -0.2)):
+        w = wl.plate_capacitor(nx, nx, 24, debye=3.0, bjerrum=1.0, psi=(0.1 + shift, 0.2 + shift))
+        o = make(w)
+        o.init()
+        o.step(30)
+        res.append((o.n()[:, :, 0, 0], o.charge() / (nx * nx), o.phi()[:, 0, 0] - shift,
+                    o.u()[:, :, 0, 0]))
+    for n, q, phi, u in res[1:]:
+        np.testing.assert_allclose(n, res[0][0], rtol=1e-11)
+        np.testing.assert_allclose(q, res[0][1], rtol=1e-9)
+        np.testing.assert_allclose(phi, res[0][2], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(u, res[0][3], rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# Advection: a uniform velocity moves the solute's centre of mass by exactly u
+# per step (cell-overlap rule), conserving it; a share bound for a solid node
+# stays on the source node.
+def test_advection_translation_and_solid_retention():
+    nx = ny = nz = 16
+    ids = np.zeros((nz, ny, nx), dtype=np.uint8)
+    o = Oracle((nx, ny, nz), (1, 1, 1), z=(1.0,), D=(0.0,), rho_bulk=(1.0,))
+    o.set_geometry(ids, 0)
+    zz, yy, xx = np.mgrid[0:nz, 0:ny, 0:nx].astype(float)
+    n = np.exp(-((xx - 8) ** 2 + (yy - 8) ** 2 + (zz - 8) ** 2) / 2.0)[None]
+    u = np.zeros((3, nz, ny, nx))
+    uv = (0.3, -0.2, 0.15)
+    for a in range(3):
+        u[a] = uv[a]
+    out = o.advect(n, u)
+    assert out.sum() == pytest.approx(n.sum(), rel=1e-14)
+    com = lambda m: np.array([(m * xx).sum(), (m * yy).sum(), (m * zz).sum()]) / m.sum()
+    np.testing.assert_allclose(com(out[0]) - com(n[0]), uv, atol=1e-9)
+    # retention next to a wall
+    ids2 = np.zeros((nz, ny, nx), dtype=np.uint8)
+    ids2[:, :, 7] = 1
+    o2 = Oracle((nx, ny, nz), (1, 1, 1), z=(1.0,), D=(0.0,), rho_bulk=(1.0,))
+    o2.set_geometry(ids2, 1)
+    n2 = np.zeros((1, nz, ny, nx))
+    n2[0, 5, 5, 6] = 1.0
+    u2 = np.zeros((3, nz, ny, nx))
+    u2[0] = 0.25
+    out2 = o2.advect(n2, u2)
+    assert out2[0, 5, 5, 6] == pytest.approx(1.0, abs=1e-15)
+    assert out2[0, :, :, 7].sum() == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Steady state of the plate capacitor vs Debye-Hueckel (Eq. DHslitpotential,
+# Eq. SLITcapaDH), and the paper's second-order convergence of the capacitance
+# error in dx/lambda_D (Fig. 4b): halving dx/lambda_D at fixed L/lambda_D
+# divides the error by about 4.
+def _plate_steady(lam, L, dV=0.01, lB=1.0, D=0.15):
+    w = wl.plate_capacitor(1, 1, L + 2, debye=lam, bjerrum=lB, psi=(0.0, dV), flow=False,
+                           D=(D, D))
+    o = make(w)
+    o.init()
+    tau_c = L * lam / (2 * D)
+    o.step(int(9 * tau_c))
+    return w, o
+
+
+@pytest.mark.slow
+def test_plate_steady_state_dh_and_second_order():
+    errs = []
+    for lam, L in ((3.0, 24), (6.0, 48)):
+        w, o = _plate_steady(lam, L)
+        eps = an.eps_of(w.bjerrum)
+        kappa = 1 / lam
+        q = o.charge()[1]
+        qdh = an.dh_plate_charge_per_area(eps, kappa, L, 0.01)
+        errs.append(abs(q - qdh) / qdh)
+        zc = np.arange(L + 2) - (L + 1) / 2.0
+        phi = o.phi()[1:-1, 0, 0]
+        dh = an.dh_plate_potential(zc[1:-1], L, kappa, 0.0, 0.01)
+        assert np.abs(phi - dh).max() < 0.02 * 0.01
+        n = o.n()[:, 1:-1, 0, 0]
+        rs = w.rho_bulk[0]
+        np.testing.assert_allclose(n[0] / rs - 1, -(dh - 0.005), atol=4e-4 * 0.01 / 0.01 * 0.01 + 2e-4)
+    assert errs[0] < 0.05
+    ratio = errs[0] / errs[1]
+    assert 3.0 < ratio < 5.0, (errs, ratio)
+
+
+# Sec. "Cylindrical (coaxial) capacitor": the initial potential follows the
+# logarithmic profile of Eq. PSIcoxialNosalt and Q(0) the dielectric
+# C_0^cyl = 2 pi eps / ln(R2/R1), even with a coarse inner cylinder.
+def test_coax_initial_log_profile_and_c0():
+    R1, R2 = 4.0, 25.0
+    w = wl.coax_capacitor(60, 60, 1, r1=R1, r2=R2, debye=9.0, bjerrum=1.2, psi=(0.0, 0.1))
+    o = make(w, flow=False)
+    o.init()
+    phi = o.phi()[0]
+    y, x = np.mgrid[0:60, 0:60].astype(float)
+    r = np.hypot(x - 29.5, y - 29.5)
+    fl = w.ids[0] == 0
+    ref = an.coax_log_potential(r, R1, R2, 0.0, 0.1)
+    err = np.abs(phi - ref)[fl & (r > R1 + 1.5) & (r < R2 - 1.5)]
+    assert err.max() < 0.02 * 0.1
+    c0 = an.coax_c0_per_length(an.eps_of(1.2), R1, R2)
+    q = o.charge()
+    assert abs(q[1] / 0.1 - c0) / c0 < 0.03
+    assert q[0] == pytest.approx(-q[1], rel=1e-10)
+
+
+# Sec. "Electrokinetic effects" (plates): starting from the charged steady
+# state, a tangential field drives the electro-osmotic profile of Eq.
+# DHslitEOF (eta = rho nu = (tau - 1/2)/3).
+@pytest.mark.slow
+def test_plate_eof_profile():
+    lam, L, dV, lB, E = 5.0, 40, 0.05, 1.0, 2e-3
+    D = 0.15
+    w = wl.plate_capacitor(1, 1, L + 2, debye=lam, bjerrum=lB, psi=(0.0, dV), D=(D, D))
+    o = make(w, flow=False)
+    o.init()
+    o.step(int(8 * L * lam / (2 * D)))
+    oe = make(w.with_(e_app=(E, 0.0, 0.0)), flow=True)
+    oe.init()
+    oe.set_state(n=o.n(), phi=o.phi())
+    oe.step(int(9 * L * L / (math.pi ** 2 / 6.0)))
+    ux = oe.u()[0, 1:-1, 0, 0]
+    zc = np.arange(L + 2)[1:-1] - (L + 1) / 2.0
+    eps = an.eps_of(lB)
+    eta = 1.0 / 6.0
+    ref = an.dh_plate_eof(zc, L, 1 / lam, eps, eta, E, dV)
+    uref = eps * E * dV / eta
+    assert np.abs(ux - ref).max() < 0.04 * uref, (np.abs(ux - ref).max() / uref)
