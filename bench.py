@@ -1,0 +1,324 @@
+"""Benchmark of the LBE time step (MLUPS and fraction of the HBM roofline).
+
+One "step" is one full LBE time step of the lattice: the fused link-flux +
+collide-stream sweep, the advection sweep and the Poisson solve to tolerance
+(the induced charge is read through the e2e path).  Default workload: the
+64x64x256 electro-osmosis lattice (plates at z = 0 and z = 255, voltage 0.2,
+tangential field 1e-3, Debye length 16, l_B = 1.44, tau = 1), from the
+uncharged capacitor with the voltage applied.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload eof|coax|plates|porous] [--precision fp64]
+
+Under torchrun (N > 1) every rank advances its own replica of the lattice
+(the workload does not shard across GPUs in this build); ``value`` sums the
+lattice updates of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1907_04732_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "MLUPS"
+UNIT = "MLUPS"
+
+
+def make_workload(name: str):
+    if name == "eof":
+        return wl.eof_plates()
+    if name == "coax":
+        return wl.coax_capacitor()
+    if name == "plates":
+        return wl.plate_capacitor()
+    if name == "porous":
+        return wl.porous_electrode()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def section(w, side=16):
+    """Periodic x-y section of a translation-invariant workload (the oracle's
+    bounded sample); None if the workload is not invariant along x and y."""
+    if w.name.startswith(("eof_", "plates_")):
+        nx, ny, nz = w.shape
+        ids = w.ids[:, :min(side, ny), :min(side, nx)].copy()
+        return w.with_(ids=ids, name=w.name + f"_section{ids.shape[2]}x{ids.shape[1]}")
+    return None
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# bytes per fluid node moved by each kernel of the FP64 path (algorithmic:
+# every array element read or written once; neighbour re-reads come from cache)
+BYTES_FP64 = {
+    # 19 populations read + 19 written, n_k read + n*_k written, phi read,
+    # u written (3), link mask read
+    "sweep": lambda ns: 8 * (19 + 19 + 2 * ns + 1 + 3) + 4,
+    # n*_k read, n_k written, u read (3), link mask
+    "advect": lambda ns: 8 * (2 * ns + 3) + 4,
+    # one CG iteration: matvec (p read, q write), update (phi, res, p, q read;
+    # phi, res write), direction (res, p read; p write), mask read thrice
+    "cg_iter": lambda ns: 8 * (2 + 6 + 3) + 3 * 4,
+}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_lattice(w, tol):
+    from oracle import Oracle
+    o = Oracle(w.shape, w.periodic, tau=w.tau, bjerrum=w.bjerrum, z=w.z, D=w.D, rho_bulk=w.rho_bulk,
+               e_app=w.e_app, flow=w.flow, tol=tol)
+    o.set_geometry(w.ids, w.n_elec)
+    o.set_voltage(w.psi)
+    return o
+
+
+def cpu_baseline(w, tol, budget_s=15.0):
+    """Time the FP64 oracle, as it stands, on a bounded sample of the
+    workload: a 16x16 periodic section (or the full lattice when not
+    translation invariant), warm-started from its initial state."""
+    sub = section(w) or w
+    o = oracle_lattice(sub, tol)
+    o.init()
+    o.step(1)  # first step outside the timing (page-in)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        o.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", 0)) or os.cpu_count()
+    return {"value": sub.nodes * steps / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} FP64 oracle steps of the {sub.shape[0]}x{sub.shape[1]}x{sub.shape[2]} "
+                      f"periodic section of {w.name} after its init ({dt:.1f} s, OpenMP)"}
+
+
+def run_reference(args, w):
+    """Reference arm: the plain FP64 oracle (CPU) on the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sub = section(w) or w
+    o = oracle_lattice(sub, args.tol)
+    o.init()
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", 0)) or os.cpu_count()
+    val = sub.nodes * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "sample": sub.name},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} steps of the {sub.shape} section of {w.name}"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="eof")
+    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--tol", type=float, default=1e-12)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    args = ap.parse_args()
+    w = make_workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_1907_04732_gb300 import build as nvbuild
+    from paper_1907_04732_gb300 import lbe
+    nvbuild.build()
+    lbe.load()
+
+    stream = torch.cuda.Stream()
+    params = lbe.params_for(w, tol=args.tol)
+    lat = lbe.Lattice(params, stream=stream.cuda_stream)
+    lat.set_geometry(w.ids, w.n_elec)
+    lat.set_voltage(w.psi)
+    lat.init()
+    fluid = int((w.ids == 0).sum())
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        lat.step(1)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat.profile_begin()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        lat.step(1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    prof = lat.profile_end()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * w.nodes * args.steps / (ms * 1e-3) / 1e6
+
+    # e2e through the public API with host buffers: per step the electrode
+    # potentials go host->device, the induced charges device->host
+    psi = np.asarray(w.psi, dtype=np.float64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        lat.set_voltage(psi)
+        lat.step(1)
+        q = lat.charge()
+    torch.cuda.synchronize()
+    e2e_dt = time.perf_counter() - t0
+    e2e_val = world * w.nodes * args.e2e_steps / e2e_dt / 1e6
+
+    peak, peak_kind = load_peaks()
+    ns = len(w.z)
+    iters = prof.poisson_iters / max(prof.poisson_solves, 1)
+    phases = {"sweep": prof.sweep_ms / max(prof.sweep_launches, 1),
+              "advect": prof.advect_ms / max(prof.advect_launches, 1),
+              "poisson": prof.poisson_ms / max(prof.poisson_solves, 1)}
+    sweep_bytes = BYTES_FP64["sweep"](ns) * fluid
+    sweep_gbs = sweep_bytes / (phases["sweep"] * 1e-3) / 1e9
+    cg_bytes = BYTES_FP64["cg_iter"](ns) * w.nodes
+    cg_gbs = (cg_bytes * iters) / (phases["poisson"] * 1e-3) / 1e9 if phases["poisson"] > 0 else 0.0
+    dominant = max(phases, key=phases.get)
+    if dominant == "poisson":
+        roof = {"kernel": "poisson CG iteration (matvec+update+direction)", "bound": "hbm",
+                "achieved": cg_gbs, "peak": peak, "unit": "GB/s", "frac": cg_gbs / peak, "traffic": None,
+                "bytes_per_node": BYTES_FP64["cg_iter"](ns)}
+    else:
+        roof = {"kernel": "k_sweep (fused link flux + collide-stream)", "bound": "hbm", "achieved": sweep_gbs,
+                "peak": peak, "unit": "GB/s", "frac": sweep_gbs / peak, "traffic": None,
+                "bytes_per_node": BYTES_FP64["sweep"](ns)}
+    roof["peak_source"] = peak_kind
+    step_bytes = sweep_bytes + BYTES_FP64["advect"](ns) * fluid + cg_bytes * iters
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "lattice": list(w.shape), "nodes": w.nodes, "fluid_nodes": fluid,
+                   "precision": "fp64", "poisson_tol": args.tol,
+                   "l2": "inputs larger than L2 (FP64 populations %.0f MB)" % (w.nodes * 19 * 8 * 2 / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roof,
+        "step_hbm_frac": step_bytes / (ms_step * 1e-3) / 1e9 / peak,
+        "phases_ms": phases, "poisson_iters_per_step": iters,
+        "sweep_gbs": sweep_gbs, "cg_gbs": cg_gbs,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * w.n_elec,
+                "d2h_bytes_per_step": 8 * w.n_elec},
+        "gpu_launches": int(prof.kernel_launches),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.tol)
+    lat.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

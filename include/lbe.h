@@ -1,0 +1,173 @@
+/*
+ * lbe.h -- C ABI of the GB300 Lattice Boltzmann Electrokinetics library with
+ * constant-potential (metallic) electrodes.
+ *
+ * Method: Asta, Palaia, Trizac, Levesque, Rotenberg, "Lattice Boltzmann
+ * Electrokinetics simulation of nanocapacitors", arXiv:1907.04732.
+ *
+ * Units are lattice units: spacing = time step = 1, k_B T = e = 1.  Potentials
+ * are reduced (phi = beta e psi), concentrations are solute amounts per node
+ * (n_k = rho_k dx^3), charges are in units of e.
+ *
+ * Lattice layout: node r = x + nx*(y + ny*z), 0 <= x < nx etc.  Per-node
+ * fields are arrays of N = nx*ny*nz values; multi-component fields are
+ * component-major ([k][r] for species, [a][r] for vector components).
+ *
+ * Ownership: a handle owns all of its device state (allocated in lbe_create /
+ * lbe_set_geometry, freed in lbe_destroy).  Every buffer passed in or out is
+ * owned by the caller; a flag says whether it lives in host or device memory.
+ * All work is ordered on the CUDA stream given to lbe_create (NULL = the
+ * legacy default stream).  Calls that return data to host memory synchronise
+ * that stream; lbe_step synchronises only to test Poisson convergence.
+ *
+ * Errors: every function returns LBE_OK (0) or a negative LBE_ERR_* code; the
+ * message of the last error on a handle is lbe_last_error(handle).  No call
+ * aborts the process.  A CUDA error is reported as LBE_ERR_CUDA and leaves
+ * the handle unusable except for lbe_destroy.
+ */
+#ifndef LBE_H
+#define LBE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBE_OK 0
+#define LBE_ERR_ARG (-1)        /* invalid argument or size */
+#define LBE_ERR_CUDA (-2)       /* a CUDA call failed */
+#define LBE_ERR_NOCONVERGE (-3) /* Poisson solve hit poisson_max_iter */
+#define LBE_ERR_NONFINITE (-4)  /* NaN/Inf met in a reduction */
+#define LBE_ERR_STATE (-5)      /* call out of order (e.g. step before init) */
+#define LBE_ERR_GEOMETRY (-6)   /* fluid node on a non-periodic face, bad id */
+
+#define LBE_FP64 0 /* all state and arithmetic in FP64 */
+#define LBE_FP32 1 /* FP32 deviations from the rest state, FP64 Poisson
+                      residual/refinement and FP64 reductions */
+
+#define LBE_MAX_SPECIES 4
+#define LBE_MAX_ELECTRODES 16
+
+/* lbe_fields selectors */
+#define LBE_FIELD_PHI 0 /* reduced potential, N doubles */
+#define LBE_FIELD_N 1   /* solute amounts, nspecies*N doubles */
+#define LBE_FIELD_RHO 2 /* solvent density, N doubles (0 on solid nodes) */
+#define LBE_FIELD_U 3   /* solvent velocity (sum f c + F/2)/rho, 3*N doubles */
+#define LBE_FIELD_F 4   /* populations after streaming, 19*N doubles, in the
+                           velocity order c_0 = (0,0,0);
+                           c_1..c_9 = (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,-1,0)
+                           (1,0,1) (1,0,-1) (0,1,1) (0,1,-1); c_{i+9} = -c_i */
+
+typedef struct lbe_handle lbe_handle;
+
+typedef struct {
+  int nx, ny, nz;       /* lattice size (Sec. "Parallel plate capacitor") */
+  int periodic[3];      /* 1 = periodic along x/y/z; a non-periodic face must
+                           be solid (its nodes are electrode nodes) */
+  double tau;           /* BGK relaxation time, Eq. LBpop (nu = (tau-1/2)/3) */
+  double bjerrum;       /* Bjerrum length l_B in lattice units, Eq. lambda */
+  int nspecies;         /* ionic species, 1..LBE_MAX_SPECIES */
+  double z[LBE_MAX_SPECIES];        /* valencies z_k (integers, |z| <= 4) */
+  double D[LBE_MAX_SPECIES];        /* diffusivities D_k, Eq. NP */
+  double rho_bulk[LBE_MAX_SPECIES]; /* initial uniform concentrations */
+  double e_app[3];      /* applied field beta e E dx (Sec. "Electrokinetic
+                           effects"), enters the link chemical-potential
+                           differences */
+  int flow;             /* 1: solvent evolves (LB + advection);
+                           0: solvent at rest (pure Poisson-Nernst-Planck) */
+  int precision;        /* LBE_FP64 or LBE_FP32 */
+  double poisson_tol;   /* stop when max_r |residual(r)|/diag(r) <= tol */
+  int poisson_max_iter; /* iteration cap per Poisson solve */
+} lbe_params;
+
+/* Defaults: 1x1x1, periodic, tau 1, l_B 1, 1:1 salt with D = 0.05 and
+ * rho = 0.01, no field, flow on, FP64, tol 1e-13, 100000 iterations. */
+void lbe_default_params(lbe_params *p);
+
+/* Create a lattice.  cuda_stream is a cudaStream_t (may be NULL).  On
+ * success *out receives the handle. */
+int lbe_create(const lbe_params *p, void *cuda_stream, lbe_handle **out);
+
+/* Free all device state of the handle (NULL is accepted). */
+int lbe_destroy(lbe_handle *h);
+
+/* Message of the last error on h (static string if h is NULL). */
+const char *lbe_last_error(const lbe_handle *h);
+
+/* Geometry (Sec. "Imposing conducting boundary conditions": chi_s, and the
+ * electrode regions of Figs. 2 and 7).  node_id has N bytes: 0 = fluid node,
+ * e in 1..n_electrodes = solid node of electrode e.  on_device selects where
+ * node_id lives.  Fails with LBE_ERR_GEOMETRY if an id exceeds n_electrodes
+ * or a fluid node lies on a non-periodic face. */
+int lbe_set_geometry(lbe_handle *h, const uint8_t *node_id, int n_electrodes, int on_device);
+
+/* Electrode potentials psi_e (reduced, host array of n_electrodes doubles).
+ * Only differences matter (Sec. "Parallel plate capacitor").  After lbe_init
+ * the potential is re-solved at once so that the state stays consistent. */
+int lbe_set_voltage(lbe_handle *h, const double *psi);
+
+/* Initial state (Sec. "Potential and concentration profiles"): uncharged
+ * capacitor, n_k = rho_bulk on fluid nodes, solvent at rest with unit
+ * density, potential = Laplace solution for the applied voltage. */
+int lbe_init(lbe_handle *h);
+
+/* Advance nsteps LBE time steps.  One step: link fluxes of Eq. LF2 and the
+ * solvent force, BGK collision with forcing (Eq. LBpop) and streaming with
+ * bounce-back, advection, then the Poisson solve of Eq. SOR's fixed point
+ * with the modified Laplacian of Eq. DiscreteLaplacianModif.  Returns
+ * LBE_ERR_NOCONVERGE if a Poisson solve reached poisson_max_iter. */
+int lbe_step(lbe_handle *h, int nsteps);
+
+/* Induced charge of every electrode, Eq. Qelec, from the current potential:
+ * Q_e = -(1/(4 pi l_B)) sum over nodes of electrode e of the modified
+ * Laplacian, taken over links to fluid nodes.  q_out receives n_electrodes
+ * doubles in host (out_on_device = 0) or device memory.  FP64 reduction in a
+ * fixed order (bitwise reproducible). */
+int lbe_induced_charge(lbe_handle *h, double *q_out, int out_on_device);
+
+/* Copy one field (LBE_FIELD_*) of the current state into out as doubles. */
+int lbe_fields(lbe_handle *h, int which, void *out, int out_on_device);
+
+/* Overwrite the solute amounts (nspecies*N doubles) and/or the potential
+ * (N doubles) of an initialised lattice; either pointer may be NULL.  The
+ * potential on solid nodes is reset to the electrode potentials. */
+int lbe_set_state(lbe_handle *h, const double *n, const double *phi, int on_device);
+
+/* Checkpoint: the complete dynamic state as an opaque blob.  With blob NULL,
+ * *size receives the needed size.  lbe_load_state restores a blob written by
+ * a handle with the same parameters and geometry. */
+int lbe_save_state(lbe_handle *h, void *blob, size_t *size);
+int lbe_load_state(lbe_handle *h, const void *blob, size_t size);
+
+/* Statistics of the most recent lbe_init/lbe_step call. */
+typedef struct {
+  long long poisson_iters;      /* CG iterations summed over the call's solves */
+  int poisson_solves;           /* Poisson solves in the call */
+  int poisson_max_iters;        /* largest single solve */
+  double poisson_residual;      /* final max |res|/diag of the last solve */
+} lbe_stats;
+int lbe_get_stats(const lbe_handle *h, lbe_stats *out);
+
+/* Device time per phase of the lbe_step calls made between
+ * lbe_profile_begin and lbe_profile_end, from CUDA events recorded on the
+ * handle's stream around each phase (a measurement aid; results unchanged). */
+typedef struct {
+  double sweep_ms;             /* fused flux + collide-stream kernel */
+  long long sweep_launches;
+  double advect_ms;            /* advection kernel */
+  long long advect_launches;
+  double poisson_ms;           /* whole Poisson solves */
+  long long poisson_solves;
+  long long poisson_iters;
+  long long kernel_launches;   /* every kernel launched by the profiled steps */
+} lbe_profile;
+int lbe_profile_begin(lbe_handle *h);
+int lbe_profile_end(lbe_handle *h, lbe_profile *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBE_H */

@@ -1,0 +1,168 @@
+// Internal declarations of the GB300 LBE library: lattice geometry helpers,
+// the D3Q19 velocity set, the handle and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lbe.h"
+
+namespace lbe {
+
+// D3Q19 velocity set: 0 = rest; 1..9 one half of the moving velocities and
+// 10..18 their opposites (opp(i) = i +- 9).  Weights 1/3, 1/18, 1/36 and
+// c_s^2 = 1/3 (Sec. "Lattice Boltzmann Electrokinetics").
+constexpr int kQ = 19;
+__host__ __device__ constexpr int cx_of(int i) {
+  constexpr int t[kQ] = {0, 1, 0, 0, 1, 1, 1, 1, 0, 0, -1, 0, 0, -1, -1, -1, -1, 0, 0};
+  return t[i];
+}
+__host__ __device__ constexpr int cy_of(int i) {
+  constexpr int t[kQ] = {0, 0, 1, 0, 1, -1, 0, 0, 1, 1, 0, -1, 0, -1, 1, 0, 0, -1, -1};
+  return t[i];
+}
+__host__ __device__ constexpr int cz_of(int i) {
+  constexpr int t[kQ] = {0, 0, 0, 1, 0, 0, 1, -1, 1, -1, 0, 0, -1, 0, 0, -1, 1, -1, 1};
+  return t[i];
+}
+__host__ __device__ constexpr int opp_of(int i) { return i == 0 ? 0 : (i <= 9 ? i + 9 : i - 9); }
+__host__ __device__ constexpr int c2_of(int i) {
+  return cx_of(i) * cx_of(i) + cy_of(i) * cy_of(i) + cz_of(i) * cz_of(i);
+}
+__host__ __device__ constexpr double w_of(int i) {
+  return c2_of(i) == 0 ? 1.0 / 3.0 : (c2_of(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+// (2/c_s^2) w_i: the Laplacian link coefficient of Eq. DiscreteLaplacian
+__host__ __device__ constexpr double lapc_of(int i) { return c2_of(i) == 1 ? 1.0 / 3.0 : 1.0 / 6.0; }
+// 1/|c_i|
+__host__ __device__ constexpr double invlen_of(int i) {
+  return c2_of(i) == 1 ? 1.0 : 0.70710678118654752440;
+}
+
+// Per-node link mask: bit (i-1), i = 1..18, set when the D3Q19 neighbour
+// r + c_i is inside the box and fluid; bits 18..25 the same for the eight
+// cube corners (+-1,+-1,+-1), corner index 18 + (sx>0) + 2(sy>0) + 4(sz>0);
+// bit 31 set when r itself is fluid.
+constexpr uint32_t kFluidBit = 1u << 31;
+__host__ __device__ constexpr int corner_bit(int sx, int sy, int sz) {
+  return 18 + (sx > 0) + 2 * (sy > 0) + 4 * (sz > 0);
+}
+
+struct Geo {
+  int nx, ny, nz;
+  int px, py, pz;  // periodic flags
+  long long N;
+};
+
+__host__ __device__ inline void coords(const Geo &g, long long r, int &x, int &y, int &z) {
+  x = (int)(r % g.nx);
+  long long t = r / g.nx;
+  y = (int)(t % g.ny);
+  z = (int)(t / g.ny);
+}
+
+// Neighbour index at integer offset (dx,dy,dz) in {-1,0,1}^3, -1 when it
+// leaves a non-periodic box.
+__host__ __device__ inline long long nbr(const Geo &g, int x, int y, int z, int dx, int dy, int dz) {
+  int X = x + dx, Y = y + dy, Z = z + dz;
+  if (X < 0 || X >= g.nx) { if (!g.px) return -1; X = X < 0 ? X + g.nx : X - g.nx; }
+  if (Y < 0 || Y >= g.ny) { if (!g.py) return -1; Y = Y < 0 ? Y + g.ny : Y - g.ny; }
+  if (Z < 0 || Z >= g.nz) { if (!g.pz) return -1; Z = Z < 0 ? Z + g.nz : Z - g.nz; }
+  return (long long)X + (long long)g.nx * ((long long)Y + (long long)g.ny * Z);
+}
+
+// Physical constants of one lattice, passed by value to kernels.
+struct Phys {
+  int ns;
+  double z[LBE_MAX_SPECIES];
+  double d[LBE_MAX_SPECIES];      // D_k / A0
+  double inv_d[LBE_MAX_SPECIES];  // A0 / D_k
+  double e_dot_c[kQ];             // E_app . c_i
+  double tau, omega;              // omega = 1/tau
+  double guo;                     // 1 - 1/(2 tau)
+  double four_pi_lb;
+  double eps;                     // 1/(4 pi l_B)
+  double inv_2a0;                 // 1/(2 A0)
+  uint32_t selfmask;              // links that join a node to itself
+};
+
+// Deterministic block reductions (fixed tree order).
+constexpr int kBlock = 256;
+
+struct PoissonWork {
+  double *rhs = nullptr;   // 4 pi l_B rho_el, fluid nodes
+  double *res = nullptr;   // residual
+  double *p = nullptr;
+  double *q = nullptr;
+  double *partial = nullptr;  // [4][nblk]
+  int nblk = 0;
+  struct Ctl {
+    int done;
+    int iters;
+    int status;
+    int pad;
+    double res;
+    double rz;
+  } *ctl = nullptr;           // device
+  Ctl *ctl_host = nullptr;    // pinned
+};
+
+}  // namespace lbe
+
+struct lbe_handle {
+  lbe_params prm{};
+  lbe::Geo geo{};
+  lbe::Phys phys{};
+  cudaStream_t stream = nullptr;
+  bool owns_stream = false;           // stream created by the library
+  int n_elec = 0;
+  bool have_geometry = false;
+  bool initialised = false;
+  double psi[LBE_MAX_ELECTRODES] = {};
+  std::string err;
+  lbe_stats stats{};
+
+  // device state
+  uint8_t *id = nullptr;
+  uint32_t *mask = nullptr;
+  double *f[2] = {nullptr, nullptr};  // post-collision populations, [i][r]
+  int cur = 0;                        // f[cur] holds the latest populations
+  double *n = nullptr;                // [k][r]
+  double *nstar = nullptr;            // [k][r]
+  double *phi = nullptr;
+  double *u = nullptr;                // [a][r], velocity of the last collision
+  double *qpart = nullptr;            // charge partials [nblk][n_elec]
+  double *qout = nullptr;             // [n_elec]
+  double *qhost = nullptr;            // pinned
+  double *psi_dev = nullptr;          // [LBE_MAX_ELECTRODES+1], index = electrode id
+  int qblk = 0;
+  lbe::PoissonWork pw;
+
+  // profiling (lbe_profile_begin/end): events [sweep start, sweep end,
+  // advect end, poisson end] per step
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  long long launches = 0;     // kernels launched since profile_begin
+  long long prof_iters = 0, prof_solves = 0, prof_steps = 0;
+};
+
+namespace lbe {
+// kernels_fp64.cu
+cudaError_t launch_build_mask(const Geo &g, const uint8_t *id, uint32_t *mask, cudaStream_t s);
+cudaError_t launch_init_state(lbe_handle *h);
+cudaError_t launch_set_solid_phi(lbe_handle *h);
+cudaError_t launch_sweep(lbe_handle *h);
+cudaError_t launch_advect(lbe_handle *h);
+cudaError_t launch_moments(lbe_handle *h, double *rho_out, double *u_out);
+cudaError_t launch_gather_f(lbe_handle *h, double *out);
+cudaError_t launch_charge(lbe_handle *h);
+// poisson.cu
+cudaError_t poisson_alloc(lbe_handle *h);
+void poisson_free(lbe_handle *h);
+// returns LBE_OK / LBE_ERR_NOCONVERGE / LBE_ERR_CUDA; iterations in *iters
+int poisson_solve(lbe_handle *h, int *iters, double *res);
+}  // namespace lbe
