@@ -66,9 +66,10 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-# bytes per fluid node moved by each kernel of the FP64 path (algorithmic:
-# every array element read or written once; neighbour re-reads come from cache)
-BYTES_FP64 = {
+# bytes per node moved by each kernel (algorithmic: every array element read
+# or written once; neighbour re-reads come from cache)
+BYTES = {}
+BYTES["fp64"] = {
     # 19 populations read + 19 written, n_k read + n*_k written, phi read,
     # u written (3), link mask read
     "sweep": lambda ns: 8 * (19 + 19 + 2 * ns + 1 + 3) + 4,
@@ -78,6 +79,18 @@ BYTES_FP64 = {
     # phi, res write), direction (res, p read; p write), mask read thrice
     "cg_iter": lambda ns: 8 * (2 + 6 + 3) + 3 * 4,
 }
+BYTES["fp32"] = {
+    # 19 FP32 deviations read + 19 written, int32 q_k read + q*_k written,
+    # FP32 phi read, FP32 u written (3), link mask
+    "sweep": lambda ns: 4 * (19 + 19 + 2 * ns + 1 + 3) + 4,
+    # q*_k read, q_k written, u read (3), mask
+    "advect": lambda ns: 4 * (2 * ns + 3) + 4,
+    # one FP32 CG iteration of the inner correction solve: matvec (p read,
+    # q write), update (e, res, p, q read; e, res write), direction (res, p
+    # read; p write), mask read thrice
+    "cg_iter": lambda ns: 4 * (2 + 6 + 3) + 3 * 4,
+}
+BYTES_FP64 = BYTES["fp64"]
 
 
 class ClockSampler:
@@ -196,8 +209,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="eof")
-    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-12)
+    ap.add_argument("--compare-steps", type=int, default=5,
+                    help="steps of the plain FP64 form timed for comparison (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     args = ap.parse_args()
@@ -223,7 +238,8 @@ def main():
     lbe.load()
 
     stream = torch.cuda.Stream()
-    params = lbe.params_for(w, tol=args.tol)
+    prec = lbe.LBE_FP32 if args.precision == "fp32" else lbe.LBE_FP64
+    params = lbe.params_for(w, tol=args.tol, precision=prec)
     lat = lbe.Lattice(params, stream=stream.cuda_stream)
     lat.set_geometry(w.ids, w.n_elec)
     lat.set_voltage(w.psi)
@@ -275,6 +291,7 @@ def main():
 
     peak, peak_kind = load_peaks()
     ns = len(w.z)
+    BYTES_FP64 = BYTES[args.precision]
     iters = prof.poisson_iters / max(prof.poisson_solves, 1)
     phases = {"sweep": prof.sweep_ms / max(prof.sweep_launches, 1),
               "advect": prof.advect_ms / max(prof.advect_launches, 1),
@@ -297,10 +314,11 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": w.name, "lattice": list(w.shape), "nodes": w.nodes, "fluid_nodes": fluid,
-                   "precision": "fp64", "poisson_tol": args.tol,
-                   "l2": "inputs larger than L2 (FP64 populations %.0f MB)" % (w.nodes * 19 * 8 * 2 / 1e6),
+                   "precision": args.precision, "poisson_tol": args.tol,
+                   "l2": "inputs larger than L2 (populations, two buffers: %.0f MB)"
+                         % (w.nodes * 19 * (4 if args.precision == "fp32" else 8) * 2 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,
         "step_hbm_frac": step_bytes / (ms_step * 1e-3) / 1e9 / peak,
@@ -311,9 +329,28 @@ def main():
         "gpu_launches": int(prof.kernel_launches),
         "clocks": clk,
     }
+    lat.close()
+    if args.precision == "fp32" and args.compare_steps > 0:
+        # the plain FP64 form on the same workload, same tolerance
+        p64 = lbe.params_for(w, tol=args.tol, precision=lbe.LBE_FP64)
+        l64 = lbe.Lattice(p64, stream=stream.cuda_stream)
+        l64.set_geometry(w.ids, w.n_elec)
+        l64.set_voltage(w.psi)
+        l64.init()
+        for _ in range(args.warmup):
+            l64.step(1)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.compare_steps):
+            l64.step(1)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = ev0.elapsed_time(ev1) / args.compare_steps
+        line["fp64_plain"] = {"value": w.nodes / (ms64 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms64,
+                              "steps": args.compare_steps, "speedup_fp32": ms64 / ms_step}
+        l64.close()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.tol)
-    lat.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:

@@ -56,6 +56,12 @@ __global__ void k_init(const Geo g, int ns, const uint8_t *__restrict__ id,
   for (int a = 0; a < 3; ++a) u[a * g.N + r] = 0.0;
 }
 
+__global__ void k_init_phi(const Geo g, const uint8_t *__restrict__ id, const double *psi, double *__restrict__ phi) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= g.N) return;
+  phi[r] = id[r] ? psi[id[r]] : 0.0;
+}
+
 __global__ void k_set_solid_phi(const Geo g, const uint8_t *__restrict__ id, const double *psi,
                                 double *__restrict__ phi) {
   long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -339,6 +345,13 @@ cudaError_t launch_init_state(lbe_handle *h) {
   k_init<<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->prm.nspecies, h->id, h->psi_dev,
                                                         h->f[h->cur], h->n, h->phi, h->u, rb[0], rb[1],
                                                         rb[2], rb[3]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_phi(lbe_handle *h) {
+  cudaError_t err = stage_psi(h);
+  if (err != cudaSuccess) return err;
+  k_init_phi<<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->id, h->psi_dev, h->phi);
   return cudaGetLastError();
 }
 

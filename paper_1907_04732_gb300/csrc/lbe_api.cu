@@ -37,18 +37,12 @@ struct StreamGuard {
   }
 };
 
+bool fp32(const lbe_handle *h) { return h->prm.precision == LBE_FP32; }
+
 void free_all(lbe_handle *h) {
-  cudaFree(h->id);
-  cudaFree(h->mask);
-  cudaFree(h->f[0]);
-  cudaFree(h->f[1]);
-  cudaFree(h->n);
-  cudaFree(h->nstar);
-  cudaFree(h->phi);
-  cudaFree(h->u);
-  cudaFree(h->qpart);
-  cudaFree(h->qout);
-  cudaFree(h->psi_dev);
+  void *ptrs[] = {h->id, h->mask, h->f[0], h->f[1], h->n, h->nstar, h->phi, h->u, h->qpart, h->qout, h->psi_dev,
+                  h->f32[0], h->f32[1], h->q, h->qstar, h->phi32, h->u32, h->flag};
+  for (void *p : ptrs) cudaFree(p);
   if (h->qhost) cudaFreeHost(h->qhost);
   lbe::poisson_free(h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -73,6 +67,55 @@ cudaError_t mark(lbe_handle *h) {
   cudaError_t err = next_event(h, &e);
   if (err != cudaSuccess) return err;
   return cudaEventRecord(e, h->stream);
+}
+
+void set_constants(lbe_handle *h) {
+  const lbe_params *p = &h->prm;
+  Phys &P = h->phys;
+  memset(&P, 0, sizeof(P));
+  const double A0 = 1.0 + 2.0 * sqrt(2.0);
+  P.ns = p->nspecies;
+  for (int k = 0; k < p->nspecies; ++k) {
+    P.z[k] = p->z[k];
+    P.d[k] = p->D[k] / A0;
+    P.inv_d[k] = p->D[k] > 0.0 ? A0 / p->D[k] : 0.0;
+  }
+  for (int i = 0; i < lbe::kQ; ++i)
+    P.e_dot_c[i] = p->e_app[0] * lbe::cx_of(i) + p->e_app[1] * lbe::cy_of(i) + p->e_app[2] * lbe::cz_of(i);
+  P.tau = p->tau;
+  P.omega = 1.0 / p->tau;
+  P.guo = 1.0 - 0.5 / p->tau;
+  P.four_pi_lb = 4.0 * M_PI * p->bjerrum;
+  P.eps = 1.0 / (4.0 * M_PI * p->bjerrum);
+  P.inv_2a0 = 1.0 / (2.0 * A0);
+  P.selfmask = 0;
+  for (int i = 1; i < lbe::kQ; ++i) {
+    const bool self = (lbe::cx_of(i) == 0 || p->nx == 1) && (lbe::cy_of(i) == 0 || p->ny == 1) &&
+                      (lbe::cz_of(i) == 0 || p->nz == 1);
+    if (self) P.selfmask |= 1u << (i - 1);
+  }
+  // FP32 form
+  lbe::P32 &Q = h->p32;
+  memset(&Q, 0, sizeof(Q));
+  Q.ns = p->nspecies;
+  for (int k = 0; k < p->nspecies; ++k) {
+    Q.zi[k] = (int)p->z[k];
+    Q.zf[k] = (float)p->z[k];
+    Q.rbd[k] = p->rho_bulk[k];
+    Q.sd[k] = ldexp(p->rho_bulk[k], -lbe::kFixBits);
+    Q.rb[k] = (float)Q.rbd[k];
+    Q.s[k] = (float)Q.sd[k];
+    Q.kq1[k] = (float)(-P.d[k] / 2.0 / Q.sd[k]);
+    Q.kq2[k] = (float)(-P.d[k] / (2.0 * sqrt(2.0)) / Q.sd[k]);
+  }
+  for (int i = 0; i < lbe::kQ; ++i) {
+    const int io = lbe::opp_of(i);
+    // one rounding, mirrored for the opposite link so that ec[opp] = -ec
+    Q.ec[i] = i <= 9 ? (float)P.e_dot_c[i] : -(float)P.e_dot_c[io];
+  }
+  Q.omega = (float)P.omega;
+  Q.guo = (float)P.guo;
+  Q.inv_2a0 = (float)P.inv_2a0;
 }
 
 }  // namespace
@@ -112,40 +155,20 @@ int lbe_create(const lbe_params *p, void *cuda_stream, lbe_handle **out) {
   for (int k = 0; k < p->nspecies; ++k) {
     if (!(p->D[k] >= 0.0) || !(p->rho_bulk[k] >= 0.0)) return LBE_ERR_ARG;
     if (fabs(p->z[k]) > 4.0 || p->z[k] != floor(p->z[k])) return LBE_ERR_ARG;
+    // the fixed-point unit of the FP32 form is relative to the bulk value
+    if (p->precision == LBE_FP32 && !(p->rho_bulk[k] > 0.0)) return LBE_ERR_ARG;
   }
-  if (p->precision == LBE_FP32) return LBE_ERR_ARG;  // not built in this library version
+  for (int a = 0; a < 3; ++a)
+    if (!isfinite(p->e_app[a])) return LBE_ERR_ARG;
 
   lbe_handle *h = new lbe_handle();
   h->prm = *p;
   h->geo = Geo{p->nx, p->ny, p->nz, p->periodic[0] != 0, p->periodic[1] != 0, p->periodic[2] != 0, N};
-  Phys &P = h->phys;
-  memset(&P, 0, sizeof(P));
-  const double A0 = 1.0 + 2.0 * sqrt(2.0);
-  P.ns = p->nspecies;
-  for (int k = 0; k < p->nspecies; ++k) {
-    P.z[k] = p->z[k];
-    P.d[k] = p->D[k] / A0;
-    P.inv_d[k] = p->D[k] > 0.0 ? A0 / p->D[k] : 0.0;
-  }
-  for (int i = 0; i < lbe::kQ; ++i)
-    P.e_dot_c[i] = p->e_app[0] * lbe::cx_of(i) + p->e_app[1] * lbe::cy_of(i) + p->e_app[2] * lbe::cz_of(i);
-  P.tau = p->tau;
-  P.omega = 1.0 / p->tau;
-  P.guo = 1.0 - 0.5 / p->tau;
-  P.four_pi_lb = 4.0 * M_PI * p->bjerrum;
-  P.eps = 1.0 / (4.0 * M_PI * p->bjerrum);
-  P.inv_2a0 = 1.0 / (2.0 * A0);
-  P.selfmask = 0;
-  for (int i = 1; i < lbe::kQ; ++i) {
-    const bool self = (lbe::cx_of(i) == 0 || p->nx == 1) && (lbe::cy_of(i) == 0 || p->ny == 1) &&
-                      (lbe::cz_of(i) == 0 || p->nz == 1);
-    if (self) P.selfmask |= 1u << (i - 1);
-  }
+  set_constants(h);
 
-  bool own = cuda_stream == nullptr;
+  const bool own = cuda_stream == nullptr;
   if (own) {
-    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
       delete h;
       return LBE_ERR_CUDA;
     }
@@ -154,27 +177,39 @@ int lbe_create(const lbe_params *p, void *cuda_stream, lbe_handle **out) {
   }
   h->owns_stream = own;
 
-  auto alloc = [&](void **ptr, size_t bytes) { return cudaMalloc(ptr, bytes); };
   cudaError_t e = cudaSuccess;
-  const size_t nd = sizeof(double) * (size_t)N;
-  if (e == cudaSuccess) e = alloc((void **)&h->id, (size_t)N);
-  if (e == cudaSuccess) e = alloc((void **)&h->mask, sizeof(uint32_t) * (size_t)N);
-  if (e == cudaSuccess) e = alloc((void **)&h->f[0], nd * lbe::kQ);
-  if (e == cudaSuccess && p->flow) e = alloc((void **)&h->f[1], nd * lbe::kQ);
-  if (e == cudaSuccess) e = alloc((void **)&h->n, nd * p->nspecies);
-  if (e == cudaSuccess) e = alloc((void **)&h->nstar, nd * p->nspecies);
-  if (e == cudaSuccess) e = alloc((void **)&h->phi, nd);
-  if (e == cudaSuccess) e = alloc((void **)&h->u, nd * 3);
-  if (e == cudaSuccess) e = alloc((void **)&h->psi_dev, sizeof(double) * (LBE_MAX_ELECTRODES + 1));
-  if (e == cudaSuccess) e = lbe::poisson_alloc(h);
-  if (e == cudaSuccess) {
-    long long blocks = (N + lbe::kBlock - 1) / lbe::kBlock;
-    h->qblk = (int)(blocks < 608 ? blocks : 608);
-    e = alloc((void **)&h->qpart, sizeof(double) * h->qblk * LBE_MAX_ELECTRODES);
+  auto alloc = [&](void **ptr, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+  };
+  const size_t nd = sizeof(double) * (size_t)N, nf = sizeof(float) * (size_t)N;
+  alloc((void **)&h->id, (size_t)N);
+  alloc((void **)&h->mask, sizeof(uint32_t) * (size_t)N);
+  alloc((void **)&h->phi, nd);
+  alloc((void **)&h->psi_dev, sizeof(double) * (LBE_MAX_ELECTRODES + 1));
+  if (fp32(h)) {
+    alloc((void **)&h->f32[0], nf * lbe::kQ);
+    if (p->flow) alloc((void **)&h->f32[1], nf * lbe::kQ);
+    alloc((void **)&h->q, sizeof(int64_t) * (size_t)N * p->nspecies);
+    alloc((void **)&h->qstar, sizeof(int64_t) * (size_t)N * p->nspecies);
+    alloc((void **)&h->phi32, nf);
+    alloc((void **)&h->u32, nf * 3);
+    alloc((void **)&h->flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->u32, 0, nf * 3, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
+  } else {
+    alloc((void **)&h->f[0], nd * lbe::kQ);
+    if (p->flow) alloc((void **)&h->f[1], nd * lbe::kQ);
+    alloc((void **)&h->n, nd * p->nspecies);
+    alloc((void **)&h->nstar, nd * p->nspecies);
+    alloc((void **)&h->u, nd * 3);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->u, 0, nd * 3, h->stream);
   }
-  if (e == cudaSuccess) e = alloc((void **)&h->qout, sizeof(double) * LBE_MAX_ELECTRODES);
+  if (e == cudaSuccess) e = lbe::poisson_alloc(h);
+  long long blocks = (N + lbe::kBlock - 1) / lbe::kBlock;
+  h->qblk = (int)(blocks < 608 ? blocks : 608);
+  alloc((void **)&h->qpart, sizeof(double) * h->qblk * LBE_MAX_ELECTRODES);
+  alloc((void **)&h->qout, sizeof(double) * LBE_MAX_ELECTRODES);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->qhost, sizeof(double) * LBE_MAX_ELECTRODES);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->u, 0, nd * 3, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     free_all(h);
@@ -230,7 +265,7 @@ int lbe_set_geometry(lbe_handle *h, const uint8_t *node_id, int n_electrodes, in
 static int solve(lbe_handle *h) {
   int it = 0;
   double res = 0.0;
-  int rc = lbe::poisson_solve(h, &it, &res);
+  int rc = fp32(h) ? lbe::poisson_solve_mixed(h, &it, &res) : lbe::poisson_solve(h, &it, &res);
   h->stats.poisson_iters += it;
   h->stats.poisson_solves += 1;
   if (it > h->stats.poisson_max_iters) h->stats.poisson_max_iters = it;
@@ -243,13 +278,13 @@ int lbe_set_voltage(lbe_handle *h, const double *psi) {
   if (!h->have_geometry) return fail(h, LBE_ERR_STATE, "set_voltage: no geometry");
   if (!psi && h->n_elec > 0) return fail(h, LBE_ERR_ARG, "set_voltage: NULL psi");
   StreamGuard sg{h, h->owns_stream};
-  for (int e = 0; e < h->n_elec; ++e) {
+  for (int e = 0; e < h->n_elec; ++e)
     if (!isfinite(psi[e])) return fail(h, LBE_ERR_ARG, "set_voltage: non-finite potential");
-    h->psi[e] = psi[e];
-  }
+  for (int e = 0; e < h->n_elec; ++e) h->psi[e] = psi[e];
   if (!h->initialised) return LBE_OK;
   h->stats = lbe_stats{};
   LBE_CK(h, lbe::launch_set_solid_phi(h));
+  if (fp32(h)) LBE_CK(h, lbe::launch_phi32_sync(h));
   return solve(h);
 }
 
@@ -259,10 +294,26 @@ int lbe_init(lbe_handle *h) {
   StreamGuard sg{h, h->owns_stream};
   h->stats = lbe_stats{};
   h->cur = 0;
-  LBE_CK(h, lbe::launch_init_state(h));
+  if (fp32(h)) {
+    LBE_CK(h, lbe::launch_init32(h));
+    LBE_CK(h, lbe::launch_init_phi(h));
+    LBE_CK(h, lbe::launch_phi32_sync(h));
+  } else {
+    LBE_CK(h, lbe::launch_init_state(h));
+  }
   int rc = solve(h);
   if (rc == LBE_OK) h->initialised = true;
   return rc;
+}
+
+static int check_flags(lbe_handle *h) {
+  if (!fp32(h)) return LBE_OK;
+  int flag = 0;
+  LBE_CK(h, cudaMemcpyAsync(h->qhost, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  LBE_CK(h, cudaStreamSynchronize(h->stream));
+  memcpy(&flag, h->qhost, sizeof(int));
+  if (flag) return fail(h, LBE_ERR_NONFINITE, "fixed-point solute range exceeded (|link flux| or |n| too large)");
+  return LBE_OK;
 }
 
 int lbe_step(lbe_handle *h, int nsteps) {
@@ -271,14 +322,19 @@ int lbe_step(lbe_handle *h, int nsteps) {
   if (nsteps < 0) return fail(h, LBE_ERR_ARG, "step: negative step count");
   StreamGuard sg{h, h->owns_stream};
   h->stats = lbe_stats{};
+  const bool f32 = fp32(h);
   for (int s = 0; s < nsteps; ++s) {
     LBE_CK(h, mark(h));
-    LBE_CK(h, lbe::launch_sweep(h));
+    LBE_CK(h, f32 ? lbe::launch_sweep32(h) : lbe::launch_sweep(h));
     LBE_CK(h, mark(h));
     h->launches += 1;
     if (h->prm.flow) {
-      LBE_CK(h, lbe::launch_advect(h));
+      LBE_CK(h, f32 ? lbe::launch_advect32(h) : lbe::launch_advect(h));
       h->launches += 1;
+    } else if (f32) {
+      int64_t *t = h->q;
+      h->q = h->qstar;
+      h->qstar = t;
     } else {
       double *t = h->n;
       h->n = h->nstar;
@@ -295,7 +351,7 @@ int lbe_step(lbe_handle *h, int nsteps) {
     }
     if (rc != LBE_OK) return rc;
   }
-  return LBE_OK;
+  return check_flags(h);
 }
 
 int lbe_induced_charge(lbe_handle *h, double *q_out, int out_on_device) {
@@ -339,12 +395,22 @@ int lbe_fields(lbe_handle *h, int which, void *out, int out_on_device) {
     dst = tmp;
   }
   cudaError_t e = cudaSuccess;
+  const bool f32 = fp32(h);
   switch (which) {
     case LBE_FIELD_PHI: e = cudaMemcpyAsync(dst, h->phi, bytes, cudaMemcpyDeviceToDevice, h->stream); break;
-    case LBE_FIELD_N: e = cudaMemcpyAsync(dst, h->n, bytes, cudaMemcpyDeviceToDevice, h->stream); break;
-    case LBE_FIELD_RHO: e = lbe::launch_moments(h, dst, nullptr); break;
-    case LBE_FIELD_U: e = lbe::launch_moments(h, nullptr, dst); break;
-    case LBE_FIELD_F: e = lbe::launch_gather_f(h, dst); break;
+    case LBE_FIELD_N:
+      e = f32 ? lbe::launch_n_to_double(h, dst)
+              : cudaMemcpyAsync(dst, h->n, bytes, cudaMemcpyDeviceToDevice, h->stream);
+      break;
+    case LBE_FIELD_RHO:
+      e = f32 ? lbe::launch_moments32(h, dst, nullptr, nullptr) : lbe::launch_moments(h, dst, nullptr);
+      break;
+    case LBE_FIELD_U:
+      e = f32 ? lbe::launch_moments32(h, nullptr, dst, nullptr) : lbe::launch_moments(h, nullptr, dst);
+      break;
+    case LBE_FIELD_F:
+      e = f32 ? lbe::launch_moments32(h, nullptr, nullptr, dst) : lbe::launch_gather_f(h, dst);
+      break;
   }
   if (e == cudaSuccess && !out_on_device) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess && !out_on_device) e = cudaStreamSynchronize(h->stream);
@@ -359,28 +425,53 @@ int lbe_set_state(lbe_handle *h, const double *n, const double *phi, int on_devi
   StreamGuard sg{h, h->owns_stream};
   const long long N = h->geo.N;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if (n) LBE_CK(h, cudaMemcpyAsync(h->n, n, sizeof(double) * N * h->prm.nspecies, kind, h->stream));
+  const size_t nbytes = sizeof(double) * N * h->prm.nspecies;
+  if (n && !fp32(h)) LBE_CK(h, cudaMemcpyAsync(h->n, n, nbytes, kind, h->stream));
+  if (n && fp32(h)) {
+    const double *src = n;
+    double *tmp = nullptr;
+    if (!on_device) {
+      LBE_CK(h, cudaMalloc(&tmp, nbytes));
+      LBE_CK(h, cudaMemcpyAsync(tmp, n, nbytes, cudaMemcpyHostToDevice, h->stream));
+      src = tmp;
+    }
+    cudaError_t e = lbe::launch_n_from_double(h, src);
+    if (e == cudaSuccess && tmp) e = cudaStreamSynchronize(h->stream);
+    if (tmp) cudaFree(tmp);
+    LBE_CK(h, e);
+  }
   if (phi) {
     LBE_CK(h, cudaMemcpyAsync(h->phi, phi, sizeof(double) * N, kind, h->stream));
     LBE_CK(h, lbe::launch_set_solid_phi(h));
+    if (fp32(h)) LBE_CK(h, lbe::launch_phi32_sync(h));
   }
   if (!on_device) LBE_CK(h, cudaStreamSynchronize(h->stream));
-  return LBE_OK;
+  return check_flags(h);
 }
 
-// blob: header | f[cur] (19N) | n (ns N) | phi (N) | u (3N)
+// blob: header | populations (19N) | solute (ns N) | phi (N doubles) |
+// velocity (3N); populations, solute and velocity in the form's own types
 struct BlobHeader {
   uint64_t magic;
   int64_t N;
-  int32_t ns, flow;
+  int32_t ns, flow, precision, pad;
 };
-static const uint64_t kMagic = 0x4c42453634763031ULL;  // "LBE64v01"
+static const uint64_t kMagic = 0x4c42457374763033ULL;
+
+static void blob_sizes(const lbe_handle *h, size_t *fb, size_t *nb, size_t *pb, size_t *ub) {
+  const size_t N = (size_t)h->geo.N;
+  const bool f32 = h->prm.precision == LBE_FP32;
+  *fb = N * lbe::kQ * (f32 ? sizeof(float) : sizeof(double));
+  *nb = N * h->prm.nspecies * (f32 ? sizeof(int64_t) : sizeof(double));
+  *pb = N * sizeof(double);
+  *ub = N * 3 * (f32 ? sizeof(float) : sizeof(double));
+}
 
 int lbe_save_state(lbe_handle *h, void *blob, size_t *size) {
   if (!h || !size) return LBE_ERR_ARG;
-  const long long N = h->geo.N;
-  const int ns = h->prm.nspecies;
-  const size_t need = sizeof(BlobHeader) + sizeof(double) * (size_t)N * (lbe::kQ + ns + 1 + 3);
+  size_t fb, nb, pb, ub;
+  blob_sizes(h, &fb, &nb, &pb, &ub);
+  const size_t need = sizeof(BlobHeader) + fb + nb + pb + ub;
   if (!blob) {
     *size = need;
     return LBE_OK;
@@ -388,18 +479,19 @@ int lbe_save_state(lbe_handle *h, void *blob, size_t *size) {
   if (!h->initialised) return fail(h, LBE_ERR_STATE, "save_state: call lbe_init first");
   if (*size < need) return fail(h, LBE_ERR_ARG, "save_state: blob too small");
   StreamGuard sg{h, h->owns_stream};
-  BlobHeader hd{kMagic, N, ns, h->prm.flow};
+  const bool f32 = fp32(h);
+  BlobHeader hd{kMagic, h->geo.N, h->prm.nspecies, h->prm.flow, h->prm.precision, 0};
   char *p = (char *)blob;
   memcpy(p, &hd, sizeof(hd));
   p += sizeof(hd);
-  const size_t nd = sizeof(double) * (size_t)N;
-  LBE_CK(h, cudaMemcpyAsync(p, h->f[h->cur], nd * lbe::kQ, cudaMemcpyDeviceToHost, h->stream));
-  p += nd * lbe::kQ;
-  LBE_CK(h, cudaMemcpyAsync(p, h->n, nd * ns, cudaMemcpyDeviceToHost, h->stream));
-  p += nd * ns;
-  LBE_CK(h, cudaMemcpyAsync(p, h->phi, nd, cudaMemcpyDeviceToHost, h->stream));
-  p += nd;
-  LBE_CK(h, cudaMemcpyAsync(p, h->u, nd * 3, cudaMemcpyDeviceToHost, h->stream));
+  LBE_CK(h, cudaMemcpyAsync(p, f32 ? (void *)h->f32[h->cur] : (void *)h->f[h->cur], fb, cudaMemcpyDeviceToHost,
+                            h->stream));
+  p += fb;
+  LBE_CK(h, cudaMemcpyAsync(p, f32 ? (void *)h->q : (void *)h->n, nb, cudaMemcpyDeviceToHost, h->stream));
+  p += nb;
+  LBE_CK(h, cudaMemcpyAsync(p, h->phi, pb, cudaMemcpyDeviceToHost, h->stream));
+  p += pb;
+  LBE_CK(h, cudaMemcpyAsync(p, f32 ? (void *)h->u32 : (void *)h->u, ub, cudaMemcpyDeviceToHost, h->stream));
   LBE_CK(h, cudaStreamSynchronize(h->stream));
   *size = need;
   return LBE_OK;
@@ -408,27 +500,35 @@ int lbe_save_state(lbe_handle *h, void *blob, size_t *size) {
 int lbe_load_state(lbe_handle *h, const void *blob, size_t size) {
   if (!h || !blob) return LBE_ERR_ARG;
   if (!h->have_geometry) return fail(h, LBE_ERR_STATE, "load_state: no geometry");
-  const long long N = h->geo.N;
-  const int ns = h->prm.nspecies;
-  const size_t need = sizeof(BlobHeader) + sizeof(double) * (size_t)N * (lbe::kQ + ns + 1 + 3);
+  size_t fb, nb, pb, ub;
+  blob_sizes(h, &fb, &nb, &pb, &ub);
+  const size_t need = sizeof(BlobHeader) + fb + nb + pb + ub;
   BlobHeader hd;
   if (size < need) return fail(h, LBE_ERR_ARG, "load_state: blob too small");
   memcpy(&hd, blob, sizeof(hd));
-  if (hd.magic != kMagic || hd.N != N || hd.ns != ns || hd.flow != h->prm.flow)
+  if (hd.magic != kMagic || hd.N != h->geo.N || hd.ns != h->prm.nspecies || hd.flow != h->prm.flow ||
+      hd.precision != h->prm.precision)
     return fail(h, LBE_ERR_ARG, "load_state: blob does not match this lattice");
   StreamGuard sg{h, h->owns_stream};
+  const bool f32 = fp32(h);
   const char *p = (const char *)blob + sizeof(hd);
-  const size_t nd = sizeof(double) * (size_t)N;
   h->cur = 0;
-  LBE_CK(h, cudaMemcpyAsync(h->f[0], p, nd * lbe::kQ, cudaMemcpyHostToDevice, h->stream));
-  p += nd * lbe::kQ;
-  LBE_CK(h, cudaMemcpyAsync(h->n, p, nd * ns, cudaMemcpyHostToDevice, h->stream));
-  p += nd * ns;
-  LBE_CK(h, cudaMemcpyAsync(h->phi, p, nd, cudaMemcpyHostToDevice, h->stream));
-  p += nd;
-  LBE_CK(h, cudaMemcpyAsync(h->u, p, nd * 3, cudaMemcpyHostToDevice, h->stream));
+  LBE_CK(h, cudaMemcpyAsync(f32 ? (void *)h->f32[0] : (void *)h->f[0], p, fb, cudaMemcpyHostToDevice, h->stream));
+  p += fb;
+  LBE_CK(h, cudaMemcpyAsync(f32 ? (void *)h->q : (void *)h->n, p, nb, cudaMemcpyHostToDevice, h->stream));
+  p += nb;
+  LBE_CK(h, cudaMemcpyAsync(h->phi, p, pb, cudaMemcpyHostToDevice, h->stream));
+  p += pb;
+  LBE_CK(h, cudaMemcpyAsync(f32 ? (void *)h->u32 : (void *)h->u, p, ub, cudaMemcpyHostToDevice, h->stream));
+  if (f32) LBE_CK(h, lbe::launch_phi32_sync(h));
   LBE_CK(h, cudaStreamSynchronize(h->stream));
   h->initialised = true;
+  return LBE_OK;
+}
+
+int lbe_get_stats(const lbe_handle *h, lbe_stats *out) {
+  if (!h || !out) return LBE_ERR_ARG;
+  *out = h->stats;
   return LBE_OK;
 }
 
@@ -463,12 +563,6 @@ int lbe_profile_end(lbe_handle *h, lbe_profile *out) {
   out->kernel_launches = h->launches;
   h->profiling = false;
   h->ev_used = 0;
-  return LBE_OK;
-}
-
-int lbe_get_stats(const lbe_handle *h, lbe_stats *out) {
-  if (!h || !out) return LBE_ERR_ARG;
-  *out = h->stats;
   return LBE_OK;
 }
 

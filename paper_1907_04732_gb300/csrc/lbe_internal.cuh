@@ -89,6 +89,23 @@ struct Phys {
   uint32_t selfmask;              // links that join a node to itself
 };
 
+// Constants of the FP32 form.  Solute amounts are int64 fixed point:
+// n_k = rho_k^bulk + s_k q_k with s_k = rho_k^bulk 2^-kFixBits (solid nodes
+// hold q = -2^kFixBits, i.e. n = 0).  The unit is fine enough that rounding
+// each link flux to it leaves no measurable bias even where the fluxes are
+// smooth in space and time.
+constexpr int kFixBits = 40;
+struct P32 {
+  int ns;
+  int zi[LBE_MAX_SPECIES];
+  float zf[LBE_MAX_SPECIES];
+  float rb[LBE_MAX_SPECIES], s[LBE_MAX_SPECIES];
+  double rbd[LBE_MAX_SPECIES], sd[LBE_MAX_SPECIES];
+  float kq1[LBE_MAX_SPECIES], kq2[LBE_MAX_SPECIES];  // -d_k/(2|c| s_k), |c| = 1, sqrt 2
+  float ec[kQ];                                      // E_app . c_i, ec[opp] = -ec
+  float omega, guo, inv_2a0;
+};
+
 // Deterministic block reductions (fixed tree order).
 constexpr int kBlock = 256;
 
@@ -104,9 +121,9 @@ struct PoissonWork {
     int iters;
     int status;
     int pad;
-    double res;
-    double rz;
-  } *ctl = nullptr;           // device
+    double res;   // latest max |res|/diag
+    double res0;  // max |res|/diag at the start of the solve
+  } *ctl = nullptr;           // device, [0] CG loop, [1] refinement rounds
   Ctl *ctl_host = nullptr;    // pinned
 };
 
@@ -116,6 +133,7 @@ struct lbe_handle {
   lbe_params prm{};
   lbe::Geo geo{};
   lbe::Phys phys{};
+  lbe::P32 p32{};
   cudaStream_t stream = nullptr;
   bool owns_stream = false;           // stream created by the library
   int n_elec = 0;
@@ -141,6 +159,15 @@ struct lbe_handle {
   int qblk = 0;
   lbe::PoissonWork pw;
 
+  // FP32 form state
+  float *f32[2] = {nullptr, nullptr};  // population deviations f_i - w_i
+  int64_t *q = nullptr;                // fixed-point solute amounts [k][r]
+  int64_t *qstar = nullptr;
+  float *phi32 = nullptr;              // FP32 copy of phi
+  float *u32 = nullptr;                // velocity of the last collision
+  int *flag = nullptr;                 // device error flags (fixed-point range)
+  float *pw32 = nullptr;               // FP32 Poisson work: res, p, q, e [4][N]
+
   // profiling (lbe_profile_begin/end): events [sweep start, sweep end,
   // advect end, poisson end] per step
   bool profiling = false;
@@ -154,15 +181,26 @@ namespace lbe {
 // kernels_fp64.cu
 cudaError_t launch_build_mask(const Geo &g, const uint8_t *id, uint32_t *mask, cudaStream_t s);
 cudaError_t launch_init_state(lbe_handle *h);
+cudaError_t launch_init_phi(lbe_handle *h);
 cudaError_t launch_set_solid_phi(lbe_handle *h);
 cudaError_t launch_sweep(lbe_handle *h);
 cudaError_t launch_advect(lbe_handle *h);
 cudaError_t launch_moments(lbe_handle *h, double *rho_out, double *u_out);
 cudaError_t launch_gather_f(lbe_handle *h, double *out);
 cudaError_t launch_charge(lbe_handle *h);
+// kernels_fp32.cu
+cudaError_t launch_init32(lbe_handle *h);
+cudaError_t launch_sweep32(lbe_handle *h);
+cudaError_t launch_advect32(lbe_handle *h);
+cudaError_t launch_n_to_double(lbe_handle *h, double *out);
+cudaError_t launch_n_from_double(lbe_handle *h, const double *n);
+cudaError_t launch_moments32(lbe_handle *h, double *rho_out, double *u_out, double *f_out);
 // poisson.cu
 cudaError_t poisson_alloc(lbe_handle *h);
 void poisson_free(lbe_handle *h);
 // returns LBE_OK / LBE_ERR_NOCONVERGE / LBE_ERR_CUDA; iterations in *iters
 int poisson_solve(lbe_handle *h, int *iters, double *res);
+// FP32 form: FP64 residual + FP32 PCG correction (iterative refinement)
+int poisson_solve_mixed(lbe_handle *h, int *iters, double *res);
+cudaError_t launch_phi32_sync(lbe_handle *h);
 }  // namespace lbe

@@ -1,0 +1,119 @@
+"""FP32 form (FP32 deviations, int32 fixed-point solute, FP64 Poisson
+refinement) against the FP64 oracle.
+
+Tolerances (relative): potential 1e-6 of the voltage, induced charge 1e-5,
+velocity 1e-5 of the largest velocity; total solute amount of each species
+conserved exactly (integer fixed-point sums).
+"""
+import numpy as np
+import pytest
+
+from paper_1907_04732_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL_PHI, TOL_Q, TOL_U = 1e-6, 1e-5, 1e-5
+
+
+def oracle_for(w, tol=1e-14):
+    from oracle import Oracle
+    o = Oracle(w.shape, w.periodic, tau=w.tau, bjerrum=w.bjerrum, z=w.z, D=w.D, rho_bulk=w.rho_bulk,
+               e_app=w.e_app, flow=w.flow, tol=tol)
+    o.set_geometry(w.ids, w.n_elec)
+    o.set_voltage(w.psi)
+    o.init()
+    return o
+
+
+def gpu_for(lbe, w, tol=1e-12):
+    g = lbe.Lattice.from_workload(w, precision=lbe.LBE_FP32, tol=tol)
+    g.init()
+    return g
+
+
+def fixed_point_units(n, w):
+    """Recover the integer solute amounts (units of rho_b 2^-40)."""
+    s = np.array(w.rho_bulk)[:, None, None, None] * 2.0 ** -40
+    rb = np.array(w.rho_bulk)[:, None, None, None]
+    return np.rint((n - rb) / s).astype(np.int64) * (w.ids == 0)
+
+
+def check(o, g, w, scale_phi, tol_n=2e-6):
+    phi_o, phi_g = o.phi(), g.phi()
+    assert np.abs(phi_g - phi_o).max() <= TOL_PHI * scale_phi, np.abs(phi_g - phi_o).max() / scale_phi
+    q_o, q_g = o.charge(), g.charge()
+    assert np.all(np.abs(q_g - q_o) <= TOL_Q * np.abs(q_o).max()), (q_g, q_o)
+    u_o, u_g = o.u(), g.u()
+    umax = np.abs(u_o).max()
+    assert np.abs(u_g - u_o).max() <= TOL_U * umax + 1e-12, (np.abs(u_g - u_o).max(), umax)
+    n_o, n_g = o.n(), g.n()
+    rb = np.array(w.rho_bulk)[:, None, None, None]
+    assert np.abs(n_g - n_o).max() <= tol_n * rb.max(), np.abs(n_g - n_o).max() / rb.max()
+
+
+@pytest.mark.parametrize("flow", [True, False])
+def test_fp32_random_geometry(lbe, flow):
+    ids = wl.random_blobs(21, 19, 17, 2, 0.2, seed=17)
+    w = wl.Workload("blob", ids, 2, (1, 1, 1), (0.0, 0.25), 1.1, 2.5, e_app=(2e-3, -1e-3, 5e-4), flow=flow)
+    o, g = oracle_for(w), gpu_for(lbe, w)
+    q0 = fixed_point_units(g.n(), w).sum(axis=(1, 2, 3))
+    o.step(30)
+    g.step(30)
+    check(o, g, w, 0.25)
+    # exact conservation of the solute in fixed point
+    np.testing.assert_array_equal(fixed_point_units(g.n(), w).sum(axis=(1, 2, 3)), q0)
+
+
+def test_fp32_plate_charging_column(lbe):
+    w = wl.plate_capacitor(1, 1, 64, psi=(0.1, 0.2))
+    o, g = oracle_for(w), gpu_for(lbe, w)
+    for _ in range(4):
+        o.step(500)
+        g.step(500)
+        check(o, g, w, 0.1)
+
+
+def test_fp32_full_coax_vs_oracle_slice(lbe):
+    full = wl.coax_capacitor()
+    red = wl.coax_capacitor(128, 128, 1)
+    o, g = oracle_for(red), gpu_for(lbe, full)
+    o.step(20)
+    g.step(20)
+    phi_g = g.phi()
+    assert np.abs(phi_g - np.tile(o.phi(), (4, 1, 1))).max() <= TOL_PHI * 0.1
+    q_o = o.charge() * 4
+    assert np.all(np.abs(g.charge() - q_o) <= TOL_Q * np.abs(q_o).max())
+
+
+def test_fp32_eof_column_flow(lbe):
+    # charged state from the oracle, then the tangential field drives flow
+    base = wl.plate_capacitor(1, 1, 42, debye=5.0, bjerrum=1.0, psi=(0.0, 0.05), D=(0.15, 0.15), flow=False)
+    ob = oracle_for(base)
+    ob.step(2000)
+    w = base.with_(e_app=(2e-3, 0.0, 0.0), flow=True)
+    o, g = oracle_for(w), gpu_for(lbe, w)
+    o.set_state(n=ob.n(), phi=ob.phi())
+    g.set_state(n=ob.n(), phi=ob.phi())
+    o.step(600)
+    g.step(600)
+    check(o, g, w, 0.05)
+
+
+def test_fp32_determinism_and_checkpoint(lbe):
+    ids = wl.random_blobs(16, 15, 14, 2, 0.2, seed=9)
+    w = wl.Workload("blob", ids, 2, (1, 1, 1), (0.0, 0.2), 1.0, 2.0, e_app=(1e-3, 0.0, 0.0))
+    a = gpu_for(lbe, w)
+    a.step(5)
+    blob = a.save_state()
+    a.step(5)
+    b = gpu_for(lbe, w)
+    b.step(10)
+    np.testing.assert_array_equal(a.phi(), b.phi())
+    np.testing.assert_array_equal(a.n(), b.n())
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    c = lbe.Lattice.from_workload(w, precision=lbe.LBE_FP32, tol=1e-12)
+    c.load_state(blob)
+    c.step(5)
+    np.testing.assert_array_equal(c.populations(), a.populations())
+    np.testing.assert_array_equal(c.n(), a.n())
+    np.testing.assert_array_equal(c.charge(), a.charge())
