@@ -63,7 +63,8 @@ extern "C" {
 typedef struct lbe_handle lbe_handle;
 
 typedef struct {
-  int nx, ny, nz;       /* lattice size (Sec. "Parallel plate capacitor") */
+  int nx, ny, nz;       /* lattice size (Sec. "Parallel plate capacitor");
+                           nx*ny*nz < 2^31 */
   int periodic[3];      /* 1 = periodic along x/y/z; a non-periodic face must
                            be solid (its nodes are electrode nodes) */
   double tau;           /* BGK relaxation time, Eq. LBpop (nu = (tau-1/2)/3) */

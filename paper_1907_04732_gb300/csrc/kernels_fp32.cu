@@ -11,15 +11,15 @@
 // amount of every species is conserved exactly (integer sums), as the link
 // flux method conserves it in exact arithmetic (Sec. "Lattice Boltzmann
 // Electrokinetics").
+//
+// No FP64 instruction runs in these kernels: 64-bit integers are converted
+// through their 32-bit halves (the 64-bit conversion instructions use the FP64
+// pipe, which is narrow on this GPU).
 #include "lbe_internal.cuh"
 
 namespace lbe {
 
 namespace {
-
-__device__ __forceinline__ long long nbr_i(const Geo &g, int x, int y, int z, int i) {
-  return nbr(g, x, y, z, cx_of(i), cy_of(i), cz_of(i));
-}
 
 // P = e^x - 1 and M = e^-x - 1.  For |x| <= 1/4 from the Taylor series of
 // sinh and cosh - 1 (odd and even parts: P = ch + sh, M = ch - sh), so that
@@ -38,11 +38,29 @@ __device__ __forceinline__ void em1_pair(float x, float &P, float &M) {
   }
 }
 
-// t - 2 rho_b for t = n (1 + e^{+-mu}), n = rho_b + s q, E = e^{+-mu} - 1:
-//   rho_b E + s q (2 + E), with a fixed rounding sequence
-__device__ __forceinline__ float tterm(float rb, float s, long long q, float E) {
-  return __fmaf_rn(__fmul_rn(s, (float)q), __fadd_rn(2.f, E), __fmul_rn(rb, E));
+// 64-bit integer <-> float with 32-bit conversions only.  Deterministic, and
+// f2ll_rn(-x) = -f2ll_rn(x).
+__device__ __forceinline__ float ll2f(long long v) {
+  const int lo = (int)v;
+  if ((long long)lo == v) return (float)lo;  // fits 32 bits: one conversion
+  return __fmaf_rn((float)(int)(v >> 32), 4294967296.f, (float)(unsigned)v);
 }
+// nearest integer (ties to even) of x, |x| < 2^62
+__device__ __forceinline__ long long f2ll_rn(float x) {
+  const float r = rintf(x);
+  if (fabsf(r) < 2147483648.f) return (long long)__float2int_rn(r);
+  const float hi = floorf(r * (1.f / 4294967296.f));
+  const float lo = r - hi * 4294967296.f;  // exact: a multiple of ulp(r) below 2^32
+  return ((long long)__float2int_rz(hi) << 32) + (long long)__float2uint_rz(lo);
+}
+
+// t - 2 rho_b for t = n (1 + e^{+-mu}), n = rho_b + s q, E = e^{+-mu} - 1:
+//   rho_b E + s q (2 + E), with a fixed rounding sequence (qf = float(q))
+__device__ __forceinline__ float tterm(float rb, float s, float qf, float E) {
+  return __fmaf_rn(__fmul_rn(s, qf), __fadd_rn(2.f, E), __fmul_rn(rb, E));
+}
+
+__device__ __forceinline__ int nb_of(const Offs &o, int r, int i) { return r + o.at(cx_of(i), cy_of(i), cz_of(i)); }
 
 __global__ void k_init32(const Geo g, const P32 P, const uint8_t *__restrict__ id, float *__restrict__ f,
                          int64_t *__restrict__ q, float *__restrict__ u) {
@@ -55,47 +73,30 @@ __global__ void k_init32(const Geo g, const P32 P, const uint8_t *__restrict__ i
   u[r] = u[g.N + r] = u[2 * g.N + r] = 0.f;
 }
 
-__device__ __forceinline__ void gather32(const Geo &g, long long r, int x, int y, int z, uint32_t m,
-                                         const float *__restrict__ fin, float f[kQ]) {
+// pull streaming with halfway bounce-back (see kernels_fp64.cu)
+__device__ __forceinline__ void gather32(int N, int r, const Offs &o, uint32_t m, const float *__restrict__ fin,
+                                         float f[kQ]) {
   f[0] = fin[r];
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     const int io = opp_of(i);
-    if (m & (1u << (io - 1)))
-      f[i] = fin[i * g.N + nbr_i(g, x, y, z, io)];
-    else
-      f[i] = fin[io * g.N + r];
+    f[i] = (m & (1u << (io - 1))) ? fin[i * N + nb_of(o, r, io)] : fin[io * N + r];
   }
 }
 
-// Fused step kernel: link fluxes (quantised), solute update q* = q - sum Jq,
-// solvent force, and (FLOW) BGK + Guo collision and pull streaming with
-// halfway bounce-back, all in FP32 deviations.
-template <bool FLOW>
-__global__ void __launch_bounds__(kBlock) k_sweep32(const Geo g, const P32 P, const uint32_t *__restrict__ mask,
-                                                    const float *__restrict__ fin, float *__restrict__ fout,
-                                                    const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
-                                                    const float *__restrict__ phi, float *__restrict__ u,
-                                                    int *__restrict__ flag) {
-  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= g.N) return;
-  const uint32_t m = mask[r];
-  if (!(m & kFluidBit)) return;
-  int x, y, z;
-  coords(g, r, x, y, z);
+// Ion part of the step at one fluid node: quantised link fluxes -> dq, and
+// the solvent force from the link excess fluxes.
+template <bool QUANT>
+__device__ __forceinline__ void ion_links(const P32 &P, int N, int r, const Offs &o, uint32_t m,
+                                          const int64_t *__restrict__ q, const float *__restrict__ phi,
+                                          const long long q0[LBE_MAX_SPECIES], const float q0f[LBE_MAX_SPECIES],
+                                          long long dq[LBE_MAX_SPECIES], float F[3], bool &over) {
   const float phi0 = phi[r];
-  long long q0[LBE_MAX_SPECIES], dq[LBE_MAX_SPECIES];
-#pragma unroll
-  for (int k = 0; k < LBE_MAX_SPECIES; ++k) {
-    q0[k] = k < P.ns ? q[k * g.N + r] : 0;
-    dq[k] = 0;
-  }
   float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-  bool over = false;
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     if (!(m & (1u << (i - 1)))) continue;
-    const long long r2 = nbr_i(g, x, y, z, i);
+    const int r2 = nb_of(o, r, i);
     // exactly antisymmetric potential difference along the link
     const float dphi = __fsub_rn(__fsub_rn(phi[r2], phi0), P.ec[i]);
     float P1, M1;
@@ -107,35 +108,68 @@ __global__ void __launch_bounds__(kBlock) k_sweep32(const Geo g, const P32 P, co
       if (k >= P.ns) break;
       float Pk, Mk;
       if (P.zi[k] == 1) {
-        Pk = P1; Mk = M1;
+        Pk = P1;
+        Mk = M1;
       } else if (P.zi[k] == -1) {
-        Pk = M1; Mk = P1;
+        Pk = M1;
+        Mk = P1;
       } else {
         em1_pair(__fmul_rn(P.zf[k], dphi), Pk, Mk);
       }
-      const long long q1 = q[k * g.N + r2];
-      const float X = tterm(P.rb[k], P.s[k], q1, Pk);
-      const float Y = tterm(P.rb[k], P.s[k], q0[k], Mk);
+      const long long q1 = q[k * N + r2];
+      const float X = tterm(P.rb[k], P.s[k], ll2f(q1), Pk);
+      const float Y = tterm(P.rb[k], P.s[k], q0f[k], Mk);
       const float J = __fsub_rn(X, Y);  // t1 - t0, exactly odd under link reversal
-      const float jq = __fmul_rn(J, c2_of(i) == 1 ? P.kq1[k] : P.kq2[k]);
-      over |= fabsf(jq) > 1.0e17f;
-      dq[k] -= __float2ll_rn(jq);
+      if (QUANT) {
+        const float jq = __fmul_rn(J, c2_of(i) == 1 ? P.kq1[k] : P.kq2[k]);
+        over |= fabsf(jq) > 1.0e17f;
+        dq[k] -= f2ll_rn(jq);
+      }
       // link excess flux g = j/d + (n' - n)/|c| = (-(t1 - t0)/2 + s (q1 - q0))/|c|
-      gs += il * __fmaf_rn(-0.5f, J, P.s[k] * (float)(q1 - q0[k]));
+      gs += il * __fmaf_rn(-0.5f, J, P.s[k] * ll2f(q1 - q0[k]));
     }
     Fx += cx_of(i) * gs;
     Fy += cy_of(i) * gs;
     Fz += cz_of(i) * gs;
   }
+  F[0] = Fx * P.inv_2a0;
+  F[1] = Fy * P.inv_2a0;
+  F[2] = Fz * P.inv_2a0;
+}
+
+// Fused step kernel: link fluxes (quantised), solute update q* = q - sum Jq,
+// solvent force, and (FLOW) BGK + Guo collision and pull streaming with
+// halfway bounce-back, all in FP32 deviations.
+template <bool FLOW>
+__global__ void __launch_bounds__(kBlock) k_sweep32(const Geo g, const P32 P, const uint32_t *__restrict__ mask,
+                                                    const float *__restrict__ fin, float *__restrict__ fout,
+                                                    const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
+                                                    const float *__restrict__ phi, float *__restrict__ u,
+                                                    int *__restrict__ flag) {
+  int x, y, z;
+  long long rl;
+  if (!node_of(g, 1, 0, x, y, z, rl)) return;
+  const int r = (int)rl, N = (int)g.N;
+  const uint32_t m = mask[r];
+  if (!(m & kFluidBit)) return;
+  const Offs o = offsets_of(g, x, y, z);
+  long long q0[LBE_MAX_SPECIES], dq[LBE_MAX_SPECIES];
+  float q0f[LBE_MAX_SPECIES];
+#pragma unroll
+  for (int k = 0; k < LBE_MAX_SPECIES; ++k) {
+    q0[k] = k < P.ns ? q[k * N + r] : 0;
+    q0f[k] = ll2f(q0[k]);
+    dq[k] = 0;
+  }
+  float F[3];
+  bool over = false;
+  ion_links<true>(P, N, r, o, m, q, phi, q0, q0f, dq, F, over);
   if (over) atomicOr(flag, 1);
-  for (int k = 0; k < P.ns; ++k) qstar[k * g.N + r] = q0[k] + dq[k];
+  for (int k = 0; k < P.ns; ++k) qstar[k * N + r] = q0[k] + dq[k];
   if (!FLOW) return;
-  Fx *= P.inv_2a0;
-  Fy *= P.inv_2a0;
-  Fz *= P.inv_2a0;
 
   float f[kQ];
-  gather32(g, r, x, y, z, m, fin, f);
+  gather32(N, r, o, m, fin, f);
   float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
@@ -146,20 +180,20 @@ __global__ void __launch_bounds__(kBlock) k_sweep32(const Geo g, const P32 P, co
   }
   const float rho = 1.f + drho;
   const float inv_rho = 1.f / rho;
-  const float ux = (jx + 0.5f * Fx) * inv_rho, uy = (jy + 0.5f * Fy) * inv_rho, uz = (jz + 0.5f * Fz) * inv_rho;
+  const float ux = (jx + 0.5f * F[0]) * inv_rho, uy = (jy + 0.5f * F[1]) * inv_rho, uz = (jz + 0.5f * F[2]) * inv_rho;
   u[r] = ux;
-  u[g.N + r] = uy;
-  u[2 * g.N + r] = uz;
+  u[N + r] = uy;
+  u[2 * N + r] = uz;
   const float uu = ux * ux + uy * uy + uz * uz;
-  const float uF = ux * Fx + uy * Fy + uz * Fz;
+  const float uF = ux * F[0] + uy * F[1] + uz * F[2];
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const float w = (float)w_of(i);
     const float cu = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
-    const float cF = cx_of(i) * Fx + cy_of(i) * Fy + cz_of(i) * Fz;
+    const float cF = cx_of(i) * F[0] + cy_of(i) * F[1] + cz_of(i) * F[2];
     const float eq = w * (drho + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * uu));
     const float src = P.guo * w * (3.f * (cF - uF) + 9.f * cu * cF);
-    fout[i * g.N + r] = f[i] - P.omega * (f[i] - eq) + src;
+    fout[i * N + r] = f[i] - P.omega * (f[i] - eq) + src;
   }
 }
 
@@ -176,54 +210,62 @@ __device__ __forceinline__ int dir_bit(int dx, int dy, int dz) {
   return -1;
 }
 
-// integer share of a node's solute (in fixed-point units, total amount
-// 2^40 + q) that its displaced cell hands to the neighbour at offset s
-__device__ __forceinline__ long long share(long long total, float ux, float uy, float uz, int sx, int sy, int sz) {
+// integer share (fixed-point units) of a node's total solute 2^40 + q that its
+// displaced cell hands to the neighbour at offset s
+__device__ __forceinline__ long long share(float totf, float ux, float uy, float uz, int sx, int sy, int sz) {
   const float w = ov(sx, ux) * ov(sy, uy) * ov(sz, uz);
-  return (long long)__float2ll_rn(__fmul_rn(w, (float)total));
+  return w == 0.f ? 0LL : f2ll_rn(__fmul_rn(w, totf));
 }
 
 // Cell-overlap advection in fixed point: the share a source hands to a fluid
 // neighbour is computed identically by the source (which gives it away) and
-// by the target (which collects it), so solute is moved in exact integers.
+// by the target (which collects it), so solute moves in exact integers.  A
+// displaced cell only reaches the octant its velocity points to, so a node
+// gives to at most 7 neighbours and collects only from neighbours whose
+// velocity points at it.
 __global__ void __launch_bounds__(kBlock) k_advect32(const Geo g, int ns, const uint32_t *__restrict__ mask,
                                                      const int64_t *__restrict__ qin, const float *__restrict__ u,
                                                      int64_t *__restrict__ qout) {
-  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= g.N) return;
+  int x, y, z;
+  long long rl;
+  if (!node_of(g, 1, 0, x, y, z, rl)) return;
+  const int r = (int)rl, N = (int)g.N;
   const uint32_t m = mask[r];
   if (!(m & kFluidBit)) {
-    for (int k = 0; k < ns; ++k) qout[k * g.N + r] = qin[k * g.N + r];
+    for (int k = 0; k < ns; ++k) qout[k * N + r] = qin[k * N + r];
     return;
   }
-  int x, y, z;
-  coords(g, r, x, y, z);
-  const float ux = u[r], uy = u[g.N + r], uz = u[2 * g.N + r];
+  const Offs o = offsets_of(g, x, y, z);
+  const float ux = u[r], uy = u[N + r], uz = u[2 * N + r];
   const long long base = 1LL << kFixBits;
-  long long acc[LBE_MAX_SPECIES], own[LBE_MAX_SPECIES];
+  long long acc[LBE_MAX_SPECIES];
+  float totf[LBE_MAX_SPECIES];
   for (int k = 0; k < ns; ++k) {
-    own[k] = base + qin[k * g.N + r];
-    acc[k] = own[k];
+    acc[k] = base + qin[k * N + r];
+    totf[k] = ll2f(acc[k]);
   }
+  // outgoing: the octant of u
+  const int sx = ux > 0.f ? 1 : -1, sy = uy > 0.f ? 1 : -1, sz = uz > 0.f ? 1 : -1;
+  for (int c = 1; c < 8; ++c) {
+    const int dx = (c & 1) ? sx : 0, dy = (c & 2) ? sy : 0, dz = (c & 4) ? sz : 0;
+    if (!(m & (1u << dir_bit(dx, dy, dz)))) continue;  // shares bound for solid stay
+    for (int k = 0; k < ns; ++k) acc[k] -= share(totf[k], ux, uy, uz, dx, dy, dz);
+  }
+  // incoming from every fluid neighbour whose cell reaches r
   for (int dz = -1; dz <= 1; ++dz)
     for (int dy = -1; dy <= 1; ++dy)
       for (int dx = -1; dx <= 1; ++dx) {
         if (dx == 0 && dy == 0 && dz == 0) continue;
-        // outgoing share to the neighbour at +s, if it is fluid
-        if (m & (1u << dir_bit(dx, dy, dz))) {
-          for (int k = 0; k < ns; ++k) acc[k] -= share(own[k], ux, uy, uz, dx, dy, dz);
-        }
-        // incoming share from the neighbour at -s, if it is fluid
-        if (m & (1u << dir_bit(-dx, -dy, -dz))) {
-          const long long s = nbr(g, x, y, z, -dx, -dy, -dz);
-          const float sx = u[s], sy = u[g.N + s], sz = u[2 * g.N + s];
-          for (int k = 0; k < ns; ++k) acc[k] += share(base + qin[k * g.N + s], sx, sy, sz, dx, dy, dz);
-        }
+        // the source at r - s gives along +s
+        if (!(m & (1u << dir_bit(-dx, -dy, -dz)))) continue;
+        const int s = r + o.at(-dx, -dy, -dz);
+        const float vx = u[s], vy = u[N + s], vz = u[2 * N + s];
+        const float w = ov(dx, vx) * ov(dy, vy) * ov(dz, vz);
+        if (w == 0.f) continue;
+        for (int k = 0; k < ns; ++k) acc[k] += share(ll2f(base + qin[k * N + s]), vx, vy, vz, dx, dy, dz);
       }
-  for (int k = 0; k < ns; ++k) qout[k * g.N + r] = acc[k] - base;
+  for (int k = 0; k < ns; ++k) qout[k * N + r] = acc[k] - base;
 }
-
-// output conversions
 __global__ void k_n_to_double(const Geo g, const P32 P, const int64_t *__restrict__ q, const uint32_t *__restrict__ mask,
                               double *__restrict__ out) {
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -253,54 +295,40 @@ __global__ void k_n_from_double(const Geo g, const P32 P, const double *__restri
   }
 }
 
+// density, velocity (current state) or populations, as FP64
 __global__ void k_moments32(const Geo g, const P32 P, int flow, const uint32_t *__restrict__ mask,
                             const float *__restrict__ fin, const int64_t *__restrict__ q,
                             const float *__restrict__ phi, double *__restrict__ rho_out,
                             double *__restrict__ u_out, double *__restrict__ f_out) {
-  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= g.N) return;
+  int x, y, z;
+  long long rl;
+  if (!node_of(g, 1, 0, x, y, z, rl)) return;
+  const int r = (int)rl, N = (int)g.N;
   const uint32_t m = mask[r];
   if (!(m & kFluidBit)) {
     if (rho_out) rho_out[r] = 0.0;
-    if (u_out) u_out[r] = u_out[g.N + r] = u_out[2 * g.N + r] = 0.0;
+    if (u_out) u_out[r] = u_out[N + r] = u_out[2 * N + r] = 0.0;
     if (f_out)
-      for (int i = 0; i < kQ; ++i) f_out[i * g.N + r] = 0.0;
+      for (int i = 0; i < kQ; ++i) f_out[i * N + r] = 0.0;
     return;
   }
-  int x, y, z;
-  coords(g, r, x, y, z);
+  const Offs o = offsets_of(g, x, y, z);
   float f[kQ];
-  gather32(g, r, x, y, z, m, fin, f);
+  gather32(N, r, o, m, fin, f);
   if (f_out) {
-    for (int i = 0; i < kQ; ++i) f_out[i * g.N + r] = w_of(i) + (double)f[i];
+    for (int i = 0; i < kQ; ++i) f_out[i * N + r] = w_of(i) + (double)f[i];
     return;
   }
-  // solvent force of the current state (same expressions as k_sweep32)
-  const float phi0 = phi[r];
-  float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-  for (int i = 1; i < kQ; ++i) {
-    if (!(m & (1u << (i - 1)))) continue;
-    const long long r2 = nbr_i(g, x, y, z, i);
-    const float dphi = __fsub_rn(__fsub_rn(phi[r2], phi0), P.ec[i]);
-    float P1, M1;
-    em1_pair(dphi, P1, M1);
-    float gs = 0.f;
-    for (int k = 0; k < P.ns; ++k) {
-      float Pk, Mk;
-      if (P.zi[k] == 1) { Pk = P1; Mk = M1; }
-      else if (P.zi[k] == -1) { Pk = M1; Mk = P1; }
-      else em1_pair(__fmul_rn(P.zf[k], dphi), Pk, Mk);
-      const long long q1 = q[k * g.N + r2], q0 = q[k * g.N + r];
-      const float J = __fsub_rn(tterm(P.rb[k], P.s[k], q1, Pk), tterm(P.rb[k], P.s[k], q0, Mk));
-      gs += (float)invlen_of(i) * __fmaf_rn(-0.5f, J, P.s[k] * (float)(q1 - q0));
-    }
-    Fx += cx_of(i) * gs;
-    Fy += cy_of(i) * gs;
-    Fz += cz_of(i) * gs;
+  long long q0[LBE_MAX_SPECIES], dq[LBE_MAX_SPECIES];
+  float q0f[LBE_MAX_SPECIES];
+  for (int k = 0; k < LBE_MAX_SPECIES; ++k) {
+    q0[k] = k < P.ns ? q[k * N + r] : 0;
+    q0f[k] = ll2f(q0[k]);
+    dq[k] = 0;
   }
-  Fx *= P.inv_2a0;
-  Fy *= P.inv_2a0;
-  Fz *= P.inv_2a0;
+  float F[3];
+  bool over = false;
+  ion_links<false>(P, N, r, o, m, q, phi, q0, q0f, dq, F, over);
   double drho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
   for (int i = 0; i < kQ; ++i) {
     drho += f[i];
@@ -311,13 +339,14 @@ __global__ void k_moments32(const Geo g, const P32 P, int flow, const uint32_t *
   const double rho = 1.0 + drho;
   if (rho_out) rho_out[r] = rho;
   if (u_out) {
-    u_out[r] = flow ? (jx + 0.5 * Fx) / rho : 0.0;
-    u_out[g.N + r] = flow ? (jy + 0.5 * Fy) / rho : 0.0;
-    u_out[2 * g.N + r] = flow ? (jz + 0.5 * Fz) / rho : 0.0;
+    u_out[r] = flow ? (jx + 0.5 * F[0]) / rho : 0.0;
+    u_out[N + r] = flow ? (jy + 0.5 * F[1]) / rho : 0.0;
+    u_out[2 * N + r] = flow ? (jz + 0.5 * F[2]) / rho : 0.0;
   }
 }
 
 inline unsigned grid_for(long long N) { return (unsigned)((N + kBlock - 1) / kBlock); }
+#define LAUNCH3(h) make_launch((h)->geo).grid, make_launch((h)->geo).block
 
 }  // namespace
 
@@ -329,11 +358,11 @@ cudaError_t launch_init32(lbe_handle *h) {
 cudaError_t launch_sweep32(lbe_handle *h) {
   const int nxt = h->cur ^ 1;
   if (h->prm.flow)
-    k_sweep32<true><<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->p32, h->mask, h->f32[h->cur],
+    k_sweep32<true><<<LAUNCH3(h), 0, h->stream>>>(h->geo, h->p32, h->mask, h->f32[h->cur],
                                                                    h->f32[nxt], h->q, h->qstar, h->phi32,
                                                                    h->u32, h->flag);
   else
-    k_sweep32<false><<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->p32, h->mask, h->f32[h->cur],
+    k_sweep32<false><<<LAUNCH3(h), 0, h->stream>>>(h->geo, h->p32, h->mask, h->f32[h->cur],
                                                                     h->f32[nxt], h->q, h->qstar, h->phi32,
                                                                     h->u32, h->flag);
   if (h->prm.flow) h->cur = nxt;
@@ -341,7 +370,7 @@ cudaError_t launch_sweep32(lbe_handle *h) {
 }
 
 cudaError_t launch_advect32(lbe_handle *h) {
-  k_advect32<<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->prm.nspecies, h->mask, h->qstar, h->u32, h->q);
+  k_advect32<<<LAUNCH3(h), 0, h->stream>>>(h->geo, h->prm.nspecies, h->mask, h->qstar, h->u32, h->q);
   return cudaGetLastError();
 }
 
@@ -356,7 +385,7 @@ cudaError_t launch_n_from_double(lbe_handle *h, const double *n) {
 }
 
 cudaError_t launch_moments32(lbe_handle *h, double *rho_out, double *u_out, double *f_out) {
-  k_moments32<<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->p32, h->prm.flow, h->mask, h->f32[h->cur],
+  k_moments32<<<LAUNCH3(h), 0, h->stream>>>(h->geo, h->p32, h->prm.flow, h->mask, h->f32[h->cur],
                                                              h->q, h->phi32, rho_out, u_out, f_out);
   return cudaGetLastError();
 }

@@ -128,12 +128,11 @@ __global__ void __launch_bounds__(kBlock) k_sweep(const Geo g, const Phys P, con
                                                   const double *__restrict__ fin, double *__restrict__ fout,
                                                   const double *__restrict__ n, double *__restrict__ nstar,
                                                   const double *__restrict__ phi, double *__restrict__ u) {
-  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= g.N) return;
+  int x, y, z;
+  long long r;
+  if (!node_of(g, 1, 0, x, y, z, r)) return;
   const uint32_t m = mask[r];
   if (!(m & kFluidBit)) return;
-  int x, y, z;
-  coords(g, r, x, y, z);
   double ns_r[LBE_MAX_SPECIES];
   double F[3];
   ion_fluxes(g, P, r, x, y, z, m, n, phi, ns_r, F);
@@ -186,15 +185,14 @@ __device__ __forceinline__ int dir_bit(int dx, int dy, int dz) {
 __global__ void __launch_bounds__(kBlock) k_advect(const Geo g, int ns, const uint32_t *__restrict__ mask,
                                                    const double *__restrict__ nin, const double *__restrict__ u,
                                                    double *__restrict__ nout) {
-  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= g.N) return;
+  int x, y, z;
+  long long r;
+  if (!node_of(g, 1, 0, x, y, z, r)) return;
   const uint32_t m = mask[r];
   if (!(m & kFluidBit)) {
     for (int k = 0; k < ns; ++k) nout[k * g.N + r] = 0.0;
     return;
   }
-  int x, y, z;
-  coords(g, r, x, y, z);
   double acc[LBE_MAX_SPECIES] = {0.0, 0.0, 0.0, 0.0};
   const double ux = u[r], uy = u[g.N + r], uz = u[2 * g.N + r];
   double keep = 0.0;  // own shares bound for solid neighbours
@@ -224,16 +222,15 @@ __global__ void k_moments(const Geo g, const Phys P, int flow, const uint32_t *_
                           const double *__restrict__ fin, const double *__restrict__ n,
                           const double *__restrict__ phi, double *__restrict__ rho_out,
                           double *__restrict__ u_out) {
-  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= g.N) return;
+  int x, y, z;
+  long long r;
+  if (!node_of(g, 1, 0, x, y, z, r)) return;
   const uint32_t m = mask[r];
   if (!(m & kFluidBit)) {
     if (rho_out) rho_out[r] = 0.0;
     if (u_out) u_out[r] = u_out[g.N + r] = u_out[2 * g.N + r] = 0.0;
     return;
   }
-  int x, y, z;
-  coords(g, r, x, y, z);
   double ns_r[LBE_MAX_SPECIES], F[3];
   ion_fluxes(g, P, r, x, y, z, m, n, phi, ns_r, F);
   double f[kQ];
@@ -255,15 +252,14 @@ __global__ void k_moments(const Geo g, const Phys P, int flow, const uint32_t *_
 
 __global__ void k_gather_f(const Geo g, const uint32_t *__restrict__ mask, const double *__restrict__ fin,
                            double *__restrict__ out) {
-  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= g.N) return;
+  int x, y, z;
+  long long r;
+  if (!node_of(g, 1, 0, x, y, z, r)) return;
   const uint32_t m = mask[r];
   if (!(m & kFluidBit)) {
     for (int i = 0; i < kQ; ++i) out[i * g.N + r] = 0.0;
     return;
   }
-  int x, y, z;
-  coords(g, r, x, y, z);
   double f[kQ];
   gather(g, r, x, y, z, m, fin, f);
   for (int i = 0; i < kQ; ++i) out[i * g.N + r] = f[i];
@@ -320,6 +316,7 @@ __global__ void k_charge_final(int nblk, int n_elec, const double *__restrict__ 
 }
 
 inline unsigned grid_for(long long N) { return (unsigned)((N + kBlock - 1) / kBlock); }
+#define LAUNCH3(h) make_launch((h)->geo).grid, make_launch((h)->geo).block
 
 }  // namespace
 
@@ -365,28 +362,28 @@ cudaError_t launch_set_solid_phi(lbe_handle *h) {
 cudaError_t launch_sweep(lbe_handle *h) {
   const int nxt = h->cur ^ 1;
   if (h->prm.flow)
-    k_sweep<true><<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->phys, h->mask, h->f[h->cur],
+    k_sweep<true><<<LAUNCH3(h), 0, h->stream>>>(h->geo, h->phys, h->mask, h->f[h->cur],
                                                                  h->f[nxt], h->n, h->nstar, h->phi, h->u);
   else
-    k_sweep<false><<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->phys, h->mask, h->f[h->cur],
+    k_sweep<false><<<LAUNCH3(h), 0, h->stream>>>(h->geo, h->phys, h->mask, h->f[h->cur],
                                                                   h->f[nxt], h->n, h->nstar, h->phi, h->u);
   if (h->prm.flow) h->cur = nxt;
   return cudaGetLastError();
 }
 
 cudaError_t launch_advect(lbe_handle *h) {
-  k_advect<<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->prm.nspecies, h->mask, h->nstar, h->u, h->n);
+  k_advect<<<LAUNCH3(h), 0, h->stream>>>(h->geo, h->prm.nspecies, h->mask, h->nstar, h->u, h->n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_moments(lbe_handle *h, double *rho_out, double *u_out) {
-  k_moments<<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->phys, h->prm.flow, h->mask,
+  k_moments<<<LAUNCH3(h), 0, h->stream>>>(h->geo, h->phys, h->prm.flow, h->mask,
                                                            h->f[h->cur], h->n, h->phi, rho_out, u_out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather_f(lbe_handle *h, double *out) {
-  k_gather_f<<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->mask, h->f[h->cur], out);
+  k_gather_f<<<LAUNCH3(h), 0, h->stream>>>(h->geo, h->mask, h->f[h->cur], out);
   return cudaGetLastError();
 }
 

@@ -151,7 +151,7 @@ int lbe_create(const lbe_params *p, void *cuda_stream, lbe_handle **out) {
   if (p->precision != LBE_FP64 && p->precision != LBE_FP32) return LBE_ERR_ARG;
   if (!(p->poisson_tol > 0.0) || p->poisson_max_iter < 1) return LBE_ERR_ARG;
   const long long N = (long long)p->nx * p->ny * p->nz;
-  if (N > (1LL << 40)) return LBE_ERR_ARG;
+  if (N >= (1LL << 31)) return LBE_ERR_ARG;  // 32-bit node indices in the kernels
   for (int k = 0; k < p->nspecies; ++k) {
     if (!(p->D[k] >= 0.0) || !(p->rho_bulk[k] >= 0.0)) return LBE_ERR_ARG;
     if (fabs(p->z[k]) > 4.0 || p->z[k] != floor(p->z[k])) return LBE_ERR_ARG;
@@ -262,15 +262,12 @@ int lbe_set_geometry(lbe_handle *h, const uint8_t *node_id, int n_electrodes, in
   return LBE_OK;
 }
 
-static int solve(lbe_handle *h) {
-  int it = 0;
-  double res = 0.0;
-  int rc = fp32(h) ? lbe::poisson_solve_mixed(h, &it, &res) : lbe::poisson_solve(h, &it, &res);
-  h->stats.poisson_iters += it;
-  h->stats.poisson_solves += 1;
-  if (it > h->stats.poisson_max_iters) h->stats.poisson_max_iters = it;
-  h->stats.poisson_residual = res;
-  return rc;
+// enqueue one Poisson solve and wait for its status (init, set_voltage)
+static int solve_now(lbe_handle *h) {
+  LBE_CK(h, lbe::poisson_reset_stats(h));
+  int rc = lbe::poisson_enqueue(h, false);
+  if (rc != LBE_OK) return rc;
+  return lbe::poisson_status(h, &h->stats, nullptr);
 }
 
 int lbe_set_voltage(lbe_handle *h, const double *psi) {
@@ -285,7 +282,7 @@ int lbe_set_voltage(lbe_handle *h, const double *psi) {
   h->stats = lbe_stats{};
   LBE_CK(h, lbe::launch_set_solid_phi(h));
   if (fp32(h)) LBE_CK(h, lbe::launch_phi32_sync(h));
-  return solve(h);
+  return solve_now(h);
 }
 
 int lbe_init(lbe_handle *h) {
@@ -301,7 +298,7 @@ int lbe_init(lbe_handle *h) {
   } else {
     LBE_CK(h, lbe::launch_init_state(h));
   }
-  int rc = solve(h);
+  int rc = solve_now(h);
   if (rc == LBE_OK) h->initialised = true;
   return rc;
 }
@@ -323,6 +320,7 @@ int lbe_step(lbe_handle *h, int nsteps) {
   StreamGuard sg{h, h->owns_stream};
   h->stats = lbe_stats{};
   const bool f32 = fp32(h);
+  LBE_CK(h, lbe::poisson_reset_stats(h));
   for (int s = 0; s < nsteps; ++s) {
     LBE_CK(h, mark(h));
     LBE_CK(h, f32 ? lbe::launch_sweep32(h) : lbe::launch_sweep(h));
@@ -341,16 +339,21 @@ int lbe_step(lbe_handle *h, int nsteps) {
       h->nstar = t;
     }
     LBE_CK(h, mark(h));
-    const long long it0 = h->stats.poisson_iters;
-    int rc = solve(h);
+    int rc = lbe::poisson_enqueue(h, true);
     LBE_CK(h, mark(h));
-    if (h->profiling) {
-      h->prof_iters += h->stats.poisson_iters - it0;
-      h->prof_solves += 1;
-      h->prof_steps += 1;
-    }
     if (rc != LBE_OK) return rc;
   }
+  // the solves ran without host synchronisation; their status and counts
+  // are read once here (a failed solve is reported at the end of the call)
+  long long graph_kernels = 0;
+  int rc = lbe::poisson_status(h, &h->stats, &graph_kernels);
+  h->launches += graph_kernels;
+  if (h->profiling) {
+    h->prof_iters += h->stats.poisson_iters;
+    h->prof_solves += h->stats.poisson_solves;
+    h->prof_steps += nsteps;
+  }
+  if (rc != LBE_OK) return rc;
   return check_flags(h);
 }
 
@@ -440,6 +443,7 @@ int lbe_set_state(lbe_handle *h, const double *n, const double *phi, int on_devi
     if (tmp) cudaFree(tmp);
     LBE_CK(h, e);
   }
+  h->pw.have_history = false;  // no warm-start extrapolation across a state change
   if (phi) {
     LBE_CK(h, cudaMemcpyAsync(h->phi, phi, sizeof(double) * N, kind, h->stream));
     LBE_CK(h, lbe::launch_set_solid_phi(h));
@@ -450,13 +454,14 @@ int lbe_set_state(lbe_handle *h, const double *n, const double *phi, int on_devi
 }
 
 // blob: header | populations (19N) | solute (ns N) | phi (N doubles) |
-// velocity (3N); populations, solute and velocity in the form's own types
+// velocity (3N) | previous-step phi (N doubles, warm start of the next
+// solve); populations, solute and velocity in the form's own types
 struct BlobHeader {
   uint64_t magic;
   int64_t N;
-  int32_t ns, flow, precision, pad;
+  int32_t ns, flow, precision, history;
 };
-static const uint64_t kMagic = 0x4c42457374763033ULL;
+static const uint64_t kMagic = 0x4c42457374763034ULL;
 
 static void blob_sizes(const lbe_handle *h, size_t *fb, size_t *nb, size_t *pb, size_t *ub) {
   const size_t N = (size_t)h->geo.N;
@@ -464,7 +469,7 @@ static void blob_sizes(const lbe_handle *h, size_t *fb, size_t *nb, size_t *pb, 
   *fb = N * lbe::kQ * (f32 ? sizeof(float) : sizeof(double));
   *nb = N * h->prm.nspecies * (f32 ? sizeof(int64_t) : sizeof(double));
   *pb = N * sizeof(double);
-  *ub = N * 3 * (f32 ? sizeof(float) : sizeof(double));
+  *ub = N * 3 * (f32 ? sizeof(float) : sizeof(double)) + N * sizeof(double);
 }
 
 int lbe_save_state(lbe_handle *h, void *blob, size_t *size) {
@@ -480,7 +485,7 @@ int lbe_save_state(lbe_handle *h, void *blob, size_t *size) {
   if (*size < need) return fail(h, LBE_ERR_ARG, "save_state: blob too small");
   StreamGuard sg{h, h->owns_stream};
   const bool f32 = fp32(h);
-  BlobHeader hd{kMagic, h->geo.N, h->prm.nspecies, h->prm.flow, h->prm.precision, 0};
+  BlobHeader hd{kMagic, h->geo.N, h->prm.nspecies, h->prm.flow, h->prm.precision, h->pw.have_history ? 1 : 0};
   char *p = (char *)blob;
   memcpy(p, &hd, sizeof(hd));
   p += sizeof(hd);
@@ -491,7 +496,11 @@ int lbe_save_state(lbe_handle *h, void *blob, size_t *size) {
   p += nb;
   LBE_CK(h, cudaMemcpyAsync(p, h->phi, pb, cudaMemcpyDeviceToHost, h->stream));
   p += pb;
-  LBE_CK(h, cudaMemcpyAsync(p, f32 ? (void *)h->u32 : (void *)h->u, ub, cudaMemcpyDeviceToHost, h->stream));
+  const size_t vb = ub - (size_t)h->geo.N * sizeof(double);
+  LBE_CK(h, cudaMemcpyAsync(p, f32 ? (void *)h->u32 : (void *)h->u, vb, cudaMemcpyDeviceToHost, h->stream));
+  p += vb;
+  LBE_CK(h, cudaMemcpyAsync(p, h->pw.phi_prev, (size_t)h->geo.N * sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
   LBE_CK(h, cudaStreamSynchronize(h->stream));
   *size = need;
   return LBE_OK;
@@ -513,13 +522,19 @@ int lbe_load_state(lbe_handle *h, const void *blob, size_t size) {
   const bool f32 = fp32(h);
   const char *p = (const char *)blob + sizeof(hd);
   h->cur = 0;
+  h->pw.have_history = false;
   LBE_CK(h, cudaMemcpyAsync(f32 ? (void *)h->f32[0] : (void *)h->f[0], p, fb, cudaMemcpyHostToDevice, h->stream));
   p += fb;
   LBE_CK(h, cudaMemcpyAsync(f32 ? (void *)h->q : (void *)h->n, p, nb, cudaMemcpyHostToDevice, h->stream));
   p += nb;
   LBE_CK(h, cudaMemcpyAsync(h->phi, p, pb, cudaMemcpyHostToDevice, h->stream));
   p += pb;
-  LBE_CK(h, cudaMemcpyAsync(f32 ? (void *)h->u32 : (void *)h->u, p, ub, cudaMemcpyHostToDevice, h->stream));
+  const size_t vb = ub - (size_t)h->geo.N * sizeof(double);
+  LBE_CK(h, cudaMemcpyAsync(f32 ? (void *)h->u32 : (void *)h->u, p, vb, cudaMemcpyHostToDevice, h->stream));
+  p += vb;
+  LBE_CK(h, cudaMemcpyAsync(h->pw.phi_prev, p, (size_t)h->geo.N * sizeof(double), cudaMemcpyHostToDevice,
+                            h->stream));
+  h->pw.have_history = hd.history != 0;
   if (f32) LBE_CK(h, lbe::launch_phi32_sync(h));
   LBE_CK(h, cudaStreamSynchronize(h->stream));
   h->initialised = true;

@@ -74,6 +74,79 @@ __host__ __device__ inline long long nbr(const Geo &g, int x, int y, int z, int 
   return (long long)X + (long long)g.nx * ((long long)Y + (long long)g.ny * Z);
 }
 
+// 3-D launch geometry: 256-thread blocks tiled over (x, y, z), x fastest, so
+// that node coordinates come from the thread indices (no divisions).  Each
+// thread visits zpt z-planes (zpt > 1 bounds the block count of kernels that
+// write one reduction partial per block).
+struct Launch {
+  dim3 grid, block;
+  int zpt;
+  long long nblk() const { return (long long)grid.x * grid.y * grid.z; }
+};
+
+inline int pow2_at_least(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+inline Launch make_launch(const Geo &g, long long max_blocks = 0) {
+  const int bx = pow2_at_least(g.nx) < 256 ? pow2_at_least(g.nx) : 256;
+  int by = pow2_at_least(g.ny) < 256 / bx ? pow2_at_least(g.ny) : 256 / bx;
+  int bz = 256 / (bx * by);
+  if (bz > 64) {  // blockDim.z <= 64: widen the block along y instead
+    bz = 64;
+    by = 256 / (bx * bz);
+  }
+  Launch L;
+  L.block = dim3(bx, by, bz);
+  const long long gx = (g.nx + bx - 1) / bx, gy = (g.ny + by - 1) / by, gz0 = (g.nz + bz - 1) / bz;
+  L.zpt = 1;
+  if (max_blocks > 0 && gx * gy * gz0 > max_blocks)
+    L.zpt = (int)((gx * gy * gz0 + max_blocks - 1) / max_blocks);
+  L.grid = dim3((unsigned)gx, (unsigned)gy, (unsigned)((gz0 + L.zpt - 1) / L.zpt));
+  return L;
+}
+
+// coordinates of this thread's node on z-pass kz; false when outside the box
+__device__ __forceinline__ bool node_of(const Geo &g, int zpt, int kz, int &x, int &y, int &z, long long &r) {
+  x = blockIdx.x * blockDim.x + threadIdx.x;
+  y = blockIdx.y * blockDim.y + threadIdx.y;
+  z = (blockIdx.z * zpt + kz) * blockDim.z + threadIdx.z;
+  if (x >= g.nx || y >= g.ny || z >= g.nz) return false;
+  r = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+  return true;
+}
+
+// Neighbour offsets of a node, periodic wrap included: the index of the
+// neighbour at (dx,dy,dz) in {-1,0,1}^3 is r + off(dx,dy,dz).  32-bit: the
+// library limits a lattice to fewer than 2^31 nodes.  On a non-periodic face
+// the wrapped offset is never used by fluid nodes (those faces are solid).
+struct Offs {
+  int xm, xp, ym, yp, zm, zp;
+  __device__ __forceinline__ int at(int dx, int dy, int dz) const {
+    return (dx < 0 ? xm : (dx > 0 ? xp : 0)) + (dy < 0 ? ym : (dy > 0 ? yp : 0)) + (dz < 0 ? zm : (dz > 0 ? zp : 0));
+  }
+};
+__device__ __forceinline__ Offs offsets_of(const Geo &g, int x, int y, int z) {
+  const int sy = g.nx, sz = g.nx * g.ny;
+  Offs o;
+  o.xm = x == 0 ? g.nx - 1 : -1;
+  o.xp = x == g.nx - 1 ? 1 - g.nx : 1;
+  o.ym = y == 0 ? (g.ny - 1) * sy : -sy;
+  o.yp = y == g.ny - 1 ? (1 - g.ny) * sy : sy;
+  o.zm = z == 0 ? (g.nz - 1) * sz : -sz;
+  o.zp = z == g.nz - 1 ? (1 - g.nz) * sz : sz;
+  return o;
+}
+
+__device__ __forceinline__ int flat_tid() {
+  return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+}
+__device__ __forceinline__ long long flat_bid() {
+  return blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+}
+
 // Physical constants of one lattice, passed by value to kernels.
 struct Phys {
   int ns;
@@ -109,23 +182,26 @@ struct P32 {
 // Deterministic block reductions (fixed tree order).
 constexpr int kBlock = 256;
 
-struct PoissonWork {
-  double *rhs = nullptr;   // 4 pi l_B rho_el, fluid nodes
-  double *res = nullptr;   // residual
-  double *p = nullptr;
-  double *q = nullptr;
-  double *partial = nullptr;  // [4][nblk]
-  int nblk = 0;
-  struct Ctl {
-    int done;
-    int iters;
-    int status;
-    int pad;
-    double res;   // latest max |res|/diag
-    double res0;  // max |res|/diag at the start of the solve
-  } *ctl = nullptr;           // device, [0] CG loop, [1] refinement rounds
-  Ctl *ctl_host = nullptr;    // pinned
+// Control block of the Poisson solves (device memory; see poisson.cu).
+struct PoissonCtl {
+  int outer_done, inner_done, rounds, status, sticky_status, arrive;
+  long long solve_iters, total_iters, total_rounds, solves, max_solve_iters;
+  double res, res0, alpha, beta, gamma;
 };
+
+struct PoissonWork {
+  void *vec = nullptr;        // CG vectors r, u, w, x, p, s ([6][N], FP32 or FP64)
+  double *partial = nullptr;  // block partials [3][nblk]
+  PoissonCtl *ctl = nullptr;  // device
+  PoissonCtl *ctl_host = nullptr;  // pinned
+  Launch L{};                 // launch of the CG kernels (<= kMaxPartials blocks)
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  const void *exec_key[2] = {nullptr, nullptr};
+  bool graph_ok = false;
+  double *phi_prev = nullptr;  // phi of the previous step (warm start)
+  bool have_history = false;
+};
+constexpr int kMaxPartials = 2048;
 
 }  // namespace lbe
 
@@ -198,9 +274,12 @@ cudaError_t launch_moments32(lbe_handle *h, double *rho_out, double *u_out, doub
 // poisson.cu
 cudaError_t poisson_alloc(lbe_handle *h);
 void poisson_free(lbe_handle *h);
-// returns LBE_OK / LBE_ERR_NOCONVERGE / LBE_ERR_CUDA; iterations in *iters
-int poisson_solve(lbe_handle *h, int *iters, double *res);
-// FP32 form: FP64 residual + FP32 PCG correction (iterative refinement)
-int poisson_solve_mixed(lbe_handle *h, int *iters, double *res);
+// enqueue one Poisson solve on the handle's stream (no host synchronisation
+// on the graph path)
+int poisson_enqueue(lbe_handle *h, bool extrapolate);
+// synchronise and read the solves' status/statistics since the last reset;
+// *kernels (optional) receives the kernels the graph path launched
+int poisson_status(lbe_handle *h, lbe_stats *st, long long *kernels);
+cudaError_t poisson_reset_stats(lbe_handle *h);
 cudaError_t launch_phi32_sync(lbe_handle *h);
 }  // namespace lbe

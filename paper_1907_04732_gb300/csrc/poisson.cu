@@ -3,37 +3,40 @@
 //     lap_mod(phi)(r) + 4 pi l_B rho_el(r) = 0,
 // where lap_mod is Eq. DiscreteLaplacianModif (every fluid-solid link
 // doubled) and solid nodes hold their electrode potential.  The paper relaxes
-// with Eq. SOR and keeps the converged potential; this file reaches the same
-// fixed point with Jacobi-preconditioned conjugate gradients on the symmetric
-// positive definite fluid-node system, warm-started from the previous
-// potential.  Stopping rule: max_r |res(r)|/diag(r) <= poisson_tol.
+// with Eq. SOR and keeps the converged potential; here the same fixed point is
+// reached by iterative refinement:
 //
-//  * FP64 form: CG in FP64 on phi itself.
-//  * FP32 form: iterative refinement -- the residual is formed in FP64 from
-//    the FP64 potential, the correction e (A e = res) is solved by CG in FP32
-//    to a relative reduction, and phi += e in FP64; repeated until the FP64
-//    residual meets the tolerance.
+//   round:  res = 4 pi l_B rho_el + lap_mod(phi)      (FP64, from FP64 phi)
+//           stop when max_r |res(r)|/diag(r) <= poisson_tol
+//           solve A e = res approximately by Jacobi-preconditioned conjugate
+//           gradients (T = double in the FP64 form, float in the FP32 form)
+//           phi += e                                  (FP64)
+//
+// The CG is the Chronopoulos-Gear variant: both inner products of an
+// iteration come from one reduction phase, so an iteration is three kernels
+// (vector update, stencil + dot products, scalar recurrence).  The whole solve
+// is one CUDA graph: a device-side `while` over refinement rounds containing a
+// `while` over CG iterations; kernels set the loop conditions, bounded by the
+// round limit and poisson_max_iter.  Where conditional graph nodes are not
+// available the same kernels run from a host loop that polls the device.
 //
 // Reductions are deterministic: each block reduces in a fixed tree order and
-// writes one partial; every consumer sums the partials in block order.
+// writes one partial; a single block sums the partials in block order.
+#include <stdlib.h>
+#include <string.h>
+
 #include "lbe_internal.cuh"
 
 namespace lbe {
 
 namespace {
 
-constexpr int kChunk = 16;          // CG iterations launched between host polls
-constexpr int kRefresh = 50;        // true-residual refresh period (FP64 form)
-constexpr double kInnerEta = 2e-4;  // FP32 inner solve: relative reduction
-constexpr int kMaxOuter = 40;       // FP32 form: refinement rounds per solve
+constexpr int kMaxOuter = 24;  // refinement rounds per solve
+constexpr int kChunk = 16;     // fallback: iterations between host polls
 
-enum { P_PQ = 0, P_RZ0 = 1, P_RZ1 = 2, P_MAX = 3 };
+enum { S_RU = 0, S_WU = 1, S_MAX = 2 };
+enum { C_INIT = 0, C_ITER = 1 };
 
-__device__ __forceinline__ long long nb(const Geo &g, int x, int y, int z, int i) {
-  return nbr(g, x, y, z, cx_of(i), cy_of(i), cz_of(i));
-}
-
-// Link masks of the nearest (|c| = 1) and next-nearest neighbours.
 __host__ __device__ constexpr uint32_t nn_bits() {
   uint32_t b = 0;
   for (int i = 1; i < kQ; ++i)
@@ -46,15 +49,6 @@ constexpr uint32_t kNNN = ((1u << 18) - 1) & ~kNN;
 // diagonal of -lap_mod at a fluid node: 1/3 per nearest and 1/6 per
 // next-nearest link, doubled towards solid; links joining a node to itself
 // (boxes one node wide) cancel and are left out.
-__device__ __forceinline__ double diag_of(uint32_t m, uint32_t selfmask) {
-  const uint32_t nself = ~selfmask;
-  const int nn = __popc(kNN & nself), nns = __popc(kNN & nself & ~m);
-  const int mm = __popc(kNNN & nself), mms = __popc(kNNN & nself & ~m);
-  return (double)(2 * (nn + nns) + (mm + mms)) * (1.0 / 6.0);
-}
-
-// the same diagonal in the vector type of a CG kernel (no FP64 work in the
-// FP32 kernels)
 template <typename T>
 __device__ __forceinline__ T diag_t(uint32_t m, uint32_t selfmask) {
   const uint32_t nself = ~selfmask;
@@ -63,323 +57,507 @@ __device__ __forceinline__ T diag_t(uint32_t m, uint32_t selfmask) {
   return (T)(2 * (nn + nns) + (mm + mms)) * (T)(1.0 / 6.0);
 }
 
-// lap_mod(v)(r) at a fluid node, FP64
-__device__ __forceinline__ double lap_at(const Geo &g, long long r, int x, int y, int z, uint32_t m,
+// lap_mod(v)(r) at a fluid node, FP64.  With the link weights scaled by 6
+// (2 nearest, 1 next-nearest, doubled towards solid) the sum needs one FP64
+// add per link: 6 lap = sum_i w_i v_i - (sum_i w_i) v0, w_i in {1, 2, 4}.
+__device__ __forceinline__ double lap_at(const Geo &g, int r, int x, int y, int z, uint32_t m,
                                          const double *__restrict__ v) {
-  const double v0 = v[r];
-  double s = 0.0;
+  const Offs o = offsets_of(g, x, y, z);
+  double s1 = 0.0, s2 = 0.0, s4 = 0.0;
+  int wsum = 0;
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
-    const double vi = v[nb(g, x, y, z, i)];
-    s += ((m & (1u << (i - 1))) ? lapc_of(i) : 2.0 * lapc_of(i)) * (vi - v0);
+    const double vi = v[r + o.at(cx_of(i), cy_of(i), cz_of(i))];
+    const int w = (c2_of(i) == 1 ? 2 : 1) * ((m & (1u << (i - 1))) ? 1 : 2);
+    if (w == 1) s1 += vi;
+    else if (w == 2) s2 += vi;
+    else s4 += vi;
+    wsum += w;
   }
-  return s;
+  return (s1 + 2.0 * s2 + 4.0 * s4 - (double)wsum * v[r]) * (1.0 / 6.0);
 }
 
-template <bool MAX>
-__device__ __forceinline__ double block_reduce(double v) {
-  __shared__ double sh[kBlock / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+// block-wide sum or max in a fixed order; result valid in thread 0.  The
+// FP32 kernels reduce in FP32 within the block (FP64 is slow on this GPU);
+// block partials are stored and combined in FP64.
+template <bool MAX, typename V = double>
+__device__ __forceinline__ V block_reduce(V v) {
+  __shared__ V sh[kBlock / 32];
+  const int t = flat_tid(), lane = t & 31, wid = t >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double t = __shfl_down_sync(0xffffffffu, v, o);
-    v = MAX ? fmax(v, t) : v + t;
+    const V u = __shfl_down_sync(0xffffffffu, v, o);
+    v = MAX ? fmax(v, u) : v + u;
   }
   __syncthreads();
   if (lane == 0) sh[wid] = v;
   __syncthreads();
-  double out = 0.0;
-  if (threadIdx.x == 0) {
+  V out = 0;
+  if (t == 0) {
     out = sh[0];
     for (int w = 1; w < kBlock / 32; ++w) out = MAX ? fmax(out, sh[w]) : out + sh[w];
   }
-  return out;  // valid in thread 0
+  return out;
 }
 
-// sum of the nblk partials of slot s, in block order; every thread gets it
-__device__ __forceinline__ double sum_partials(const double *__restrict__ part, int nblk, int s) {
-  __shared__ double sh_tot;
-  if (threadIdx.x < 32) {
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += 32) v += part[(long long)s * nblk + b];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) sh_tot = v;
+__device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int use, unsigned v) {
+  if (use) cudaGraphSetConditional(h, v);
+}
+
+// Last-block-done: after a block has written its partials it takes a ticket;
+// the block that takes the last ticket sees every partial (each block fenced
+// its writes before its ticket) and finishes the reduction.  No block waits.
+__device__ __forceinline__ bool last_block(PoissonCtl *c, int nblk) {
+  __shared__ int last;
+  __syncthreads();
+  if (flat_tid() == 0) {
+    __threadfence();
+    last = atomicAdd(&c->arrive, 1) == nblk - 1;
   }
   __syncthreads();
-  const double t = sh_tot;
-  __syncthreads();
-  return t;
+  return last;
 }
 
-__device__ __forceinline__ void reset_ctl(PoissonWork::Ctl *ctl) {
-  if (ctl && blockIdx.x == 0 && threadIdx.x == 0) {
-    ctl->done = 0;
-    ctl->iters = 0;
-    ctl->status = 0;
+// sums/max of the partials in block order (every thread of the block calls)
+__device__ __forceinline__ void reduce_partials(const double *part, int nblk, double *ru, double *wu, double *mx) {
+  double a = 0.0, b = 0.0, m = 0.0;
+  for (int i = flat_tid(); i < nblk; i += kBlock) {
+    a += __ldcg(part + S_RU * nblk + i);
+    b += __ldcg(part + S_WU * nblk + i);
+    m = fmax(m, __ldcg(part + S_MAX * nblk + i));
   }
+  *ru = block_reduce<false>(a);
+  *wu = block_reduce<false>(b);
+  *mx = block_reduce<true>(m);
 }
 
-// FP64 form: res = 4 pi l_B rho_el + lap_mod(phi); p = res/diag
-__global__ void __launch_bounds__(kBlock) k_cg_init64(const Geo g, const Phys P, const uint32_t *__restrict__ mask,
-                                                      const double *__restrict__ n, const double *__restrict__ phi,
-                                                      double *__restrict__ rhs, double *__restrict__ res,
-                                                      double *__restrict__ p, double *__restrict__ part, int nblk,
-                                                      PoissonWork::Ctl *ctl) {
-  reset_ctl(ctl);
-  double rz = 0.0, mx = 0.0;
-  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < g.N;
-       r += (long long)gridDim.x * blockDim.x) {
-    const uint32_t m = mask[r];
+// outer test of a refinement round (thread 0 of the last block of k_res):
+// converged, out of rounds or out of iterations?
+__device__ void outer_check(PoissonCtl *c, double m, double tol, int maxit, cudaGraphConditionalHandle hout,
+                            cudaGraphConditionalHandle hin, int use_cond) {
+  c->res = m;
+  int done = 0;
+  if (m <= tol) {
+    done = 1;
+  } else if (!(m == m) || m > 1e300) {
+    done = 1;
+    c->status = LBE_ERR_NONFINITE;
+  } else if (c->rounds >= kMaxOuter || c->solve_iters >= maxit) {
+    done = 1;
+    c->status = LBE_ERR_NOCONVERGE;
+  }
+  c->outer_done = done;
+  c->inner_done = done;  // nothing more of the round runs once converged
+  c->rounds += 1;
+  c->total_rounds += 1;
+  set_cond(hout, use_cond, done ? 0u : 1u);
+  if (done) set_cond(hin, use_cond, 0u);
+}
+
+// scalar recurrence of the Chronopoulos-Gear CG and the inner stopping test
+// (relative reduction eta of the round's starting residual); thread 0 of the
+// last block of k_cg_b
+__device__ void cg_scalars(PoissonCtl *c, double gam, double del, double mx, double eta, double tol_abs, int maxit,
+                           int mode, cudaGraphConditionalHandle hin, int use_cond) {
+  int done = 0;
+  if (mode == C_INIT) {
+    c->res0 = c->res;
+    c->beta = 0.0;
+    c->alpha = gam / del;
+    c->gamma = gam;
+    if (!(del > 0.0) || !(gam > 0.0)) done = 1;  // zero residual: nothing to solve
+  } else {
+    c->solve_iters += 1;
+    c->total_iters += 1;
+    if (mx <= fmax(eta * c->res0, tol_abs)) {
+      done = 1;
+    } else if (!(mx == mx) || !(del == del)) {
+      done = 1;
+      c->status = LBE_ERR_NONFINITE;
+      c->outer_done = 1;
+    } else if (c->solve_iters >= maxit) {
+      done = 1;
+    } else {
+      const double beta = gam / c->gamma;
+      const double den = del - beta * gam / c->alpha;
+      if (!(den > 0.0) || !(gam > 0.0)) {
+        done = 1;  // breakdown: the correction is converged to rounding
+      } else {
+        c->beta = beta;
+        c->alpha = gam / den;
+        c->gamma = gam;
+      }
+    }
+  }
+  c->inner_done = done;
+  set_cond(hin, use_cond, done ? 0u : 1u);
+}
+
+// ---------------------------------------------------------------------------
+// start of a solve: fold the previous solve into the sticky fields, reset
+__global__ void k_solve_reset(PoissonCtl *c) {
+  if (c->status && !c->sticky_status) c->sticky_status = c->status;
+  if (c->solve_iters > c->max_solve_iters) c->max_solve_iters = c->solve_iters;
+  c->outer_done = 0;
+  c->inner_done = 0;
+  c->rounds = 0;
+  c->status = 0;
+  c->solve_iters = 0;
+  c->solves += 1;
+}
+
+// FP64 residual of the current potential; seeds the inner solve:
+// r = (T)res, u = r/diag, x = p = s = 0.  Partial max |res|/diag.
+template <typename T, bool FIXED>
+__global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys P, const P32 P3,
+                                                const uint32_t *__restrict__ mask, const double *__restrict__ n64,
+                                                const int64_t *__restrict__ nq, const double *__restrict__ phi,
+                                                T *__restrict__ r, T *__restrict__ u, T *__restrict__ x,
+                                                T *__restrict__ p, T *__restrict__ s, double *__restrict__ part,
+                                                int nblk, PoissonCtl *c, double tol, int maxit,
+                                                cudaGraphConditionalHandle hout, cudaGraphConditionalHandle hin,
+                                                int use_cond) {
+  double mx = 0.0;
+  for (int kz = 0; kz < zpt; ++kz) {
+    int X, Y, Z;
+    long long i;
+    if (!node_of(g, zpt, kz, X, Y, Z, i)) continue;
+    const uint32_t m = mask[i];
     if (!(m & kFluidBit)) {
-      rhs[r] = 0.0;
-      res[r] = 0.0;
-      p[r] = 0.0;
+      r[i] = u[i] = x[i] = p[i] = s[i] = (T)0;
       continue;
     }
-    int x, y, z;
-    coords(g, r, x, y, z);
     double q = 0.0;
-    for (int k = 0; k < P.ns; ++k) q += P.z[k] * n[k * g.N + r];
-    const double b = P.four_pi_lb * q;
-    const double rr = b + lap_at(g, r, x, y, z, m, phi);
-    const double d = diag_of(m, P.selfmask);
-    rhs[r] = b;
-    res[r] = rr;
-    p[r] = rr / d;
-    rz += rr * rr / d;
+    for (int k = 0; k < P.ns; ++k)
+      q += P.z[k] * (FIXED ? P3.rbd[k] + P3.sd[k] * (double)nq[k * g.N + i] : n64[k * g.N + i]);
+    const double rr = P.four_pi_lb * q + lap_at(g, (int)i, X, Y, Z, m, phi);
+    const double d = diag_t<double>(m, P.selfmask);
+    const T rt = (T)rr;
+    r[i] = rt;
+    u[i] = rt / diag_t<T>(m, P.selfmask);
+    x[i] = p[i] = s[i] = (T)0;
     mx = fmax(mx, fabs(rr) / d);
   }
-  rz = block_reduce<false>(rz);
-  if (threadIdx.x == 0) part[P_RZ0 * nblk + blockIdx.x] = rz;
   mx = block_reduce<true>(mx);
-  if (threadIdx.x == 0) part[P_MAX * nblk + blockIdx.x] = mx;
-}
-
-// FP32 form, start of a refinement round: res64 = 4 pi l_B rho_el +
-// lap_mod(phi64) in FP64 from the fixed-point solute amounts; its FP32 copy
-// seeds the inner solve (e = 0, p = res/diag).  Partial max |res64|/diag.
-__global__ void __launch_bounds__(kBlock) k_res64(const Geo g, const Phys P, const P32 P3,
-                                                  const uint32_t *__restrict__ mask, const int64_t *__restrict__ qn,
-                                                  const double *__restrict__ phi, float *__restrict__ res,
-                                                  float *__restrict__ p, float *__restrict__ e,
-                                                  double *__restrict__ part, int nblk, PoissonWork::Ctl *outer,
-                                                  PoissonWork::Ctl *inner) {
-  reset_ctl(outer);
-  reset_ctl(inner);
-  double rz = 0.0, mx = 0.0;
-  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < g.N;
-       r += (long long)gridDim.x * blockDim.x) {
-    const uint32_t m = mask[r];
-    if (!(m & kFluidBit)) {
-      res[r] = 0.f;
-      p[r] = 0.f;
-      e[r] = 0.f;
-      continue;
-    }
-    int x, y, z;
-    coords(g, r, x, y, z);
-    double q = 0.0;
-    for (int k = 0; k < P.ns; ++k) q += P.z[k] * (P3.rbd[k] + P3.sd[k] * (double)qn[k * g.N + r]);
-    const double rr = P.four_pi_lb * q + lap_at(g, r, x, y, z, m, phi);
-    const double d = diag_of(m, P.selfmask);
-    const float rf = (float)rr, df = (float)d;
-    res[r] = rf;
-    p[r] = rf / df;
-    e[r] = 0.f;
-    rz += (double)(rf * (rf / df));
-    mx = fmax(mx, fabs(rr) / d);
-  }
-  rz = block_reduce<false>(rz);
-  if (threadIdx.x == 0) part[P_RZ0 * nblk + blockIdx.x] = rz;
-  mx = block_reduce<true>(mx);
-  if (threadIdx.x == 0) part[P_MAX * nblk + blockIdx.x] = mx;
-}
-
-// convergence test after an init or an update: reduce the max partials.
-// tol_eff = max(tol, eta * first max), so eta > 0 asks for a relative
-// reduction (FP32 inner solves).
-__global__ void k_cg_check(const double *__restrict__ part, int nblk, PoissonWork::Ctl *ctl, double tol, double eta,
-                           int maxit, int count_iteration) {
-  if (ctl->done) return;
-  double v = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += 32) v = fmax(v, part[P_MAX * nblk + b]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-  if (threadIdx.x == 0) {
-    if (count_iteration) ctl->iters += 1;
-    else ctl->res0 = v;
-    ctl->res = v;
-    const double tol_eff = fmax(tol, eta * ctl->res0);
-    if (v <= tol_eff) {
-      ctl->done = 1;
-    } else if (!(v == v) || v > 1e300) {
-      ctl->done = 1;
-      ctl->status = LBE_ERR_NONFINITE;
-    } else if (ctl->iters >= maxit) {
-      ctl->done = 1;
-      ctl->status = LBE_ERR_NOCONVERGE;
-    }
+  if (flat_tid() == 0) part[S_MAX * nblk + flat_bid()] = mx;
+  if (!last_block(c, nblk)) return;
+  double m = 0.0;
+  for (int i = flat_tid(); i < nblk; i += kBlock) m = fmax(m, __ldcg(part + S_MAX * nblk + i));
+  m = block_reduce<true>(m);
+  if (flat_tid() == 0) {
+    c->arrive = 0;
+    outer_check(c, m, tol, maxit, hout, hin, use_cond);
   }
 }
 
-// q = A p = -lap_mod(p) with p = 0 on solid nodes; partial p.q
+// stencil + dot products: w = A u; partials (r,u), (w,u); the last block
+// runs the scalar recurrence
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_cg_matvec(const Geo g, uint32_t selfmask, const uint32_t *__restrict__ mask,
-                                                      const T *__restrict__ p, T *__restrict__ q,
-                                                      double *__restrict__ part, int nblk,
-                                                      const PoissonWork::Ctl *ctl) {
-  if (ctl->done) return;
-  T pqt = 0;
-  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < g.N;
-       r += (long long)gridDim.x * blockDim.x) {
-    const uint32_t m = mask[r];
+__global__ void __launch_bounds__(kBlock) k_cg_b(const Geo g, int zpt, uint32_t selfmask,
+                                                 const uint32_t *__restrict__ mask, const T *__restrict__ u,
+                                                 const T *__restrict__ r, T *__restrict__ w,
+                                                 double *__restrict__ part, int nblk, PoissonCtl *c, double eta,
+                                                 double tol_abs, int maxit, int mode,
+                                                 cudaGraphConditionalHandle hin, int use_cond) {
+  if (c->inner_done) return;
+  T ru = 0, wu = 0;
+  for (int kz = 0; kz < zpt; ++kz) {
+    int X, Y, Z;
+    long long i;
+    if (!node_of(g, zpt, kz, X, Y, Z, i)) continue;
+    const uint32_t m = mask[i];
     if (!(m & kFluidBit)) continue;
-    int x, y, z;
-    coords(g, r, x, y, z);
-    const T p0 = p[r];
-    T s = 0;
+    const T u0 = u[i];
+    const Offs o = offsets_of(g, X, Y, Z);
+    const int ii = (int)i;
+    T sum = 0;
 #pragma unroll
-    for (int i = 1; i < kQ; ++i) {
-      const uint32_t b = 1u << (i - 1);
+    for (int l = 1; l < kQ; ++l) {
+      const uint32_t b = 1u << (l - 1);
       if ((selfmask & b) || !(m & b)) continue;
-      s += (T)lapc_of(i) * p[nb(g, x, y, z, i)];
+      sum += (T)lapc_of(l) * u[ii + o.at(cx_of(l), cy_of(l), cz_of(l))];
     }
-    const T qq = diag_t<T>(m, selfmask) * p0 - s;
-    q[r] = qq;
-    pqt += p0 * qq;
+    const T wv = diag_t<T>(m, selfmask) * u0 - sum;
+    w[i] = wv;
+    ru += r[i] * u0;
+    wu += wv * u0;
   }
-  double pq = block_reduce<false>((double)pqt);
-  if (threadIdx.x == 0) part[P_PQ * nblk + blockIdx.x] = pq;
+  const T a = block_reduce<false, T>(ru);
+  const T b = block_reduce<false, T>(wu);
+  if (flat_tid() == 0) {
+    part[S_RU * nblk + flat_bid()] = (double)a;
+    part[S_WU * nblk + flat_bid()] = (double)b;
+  }
+  if (!last_block(c, nblk)) return;
+  double gam, del, mx;
+  reduce_partials(part, nblk, &gam, &del, &mx);
+  if (flat_tid() == 0) {
+    c->arrive = 0;
+    cg_scalars(c, gam, del, mx, eta, tol_abs, maxit, mode, hin, use_cond);
+  }
 }
 
-// x += alpha p, res -= alpha q; partial rz_new, max
+// vector update: p = u + beta p, s = w + beta s, x += alpha p,
+// r -= alpha s, u = r/diag; partial max |r|/diag
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_cg_update(const Geo g, uint32_t selfmask, const uint32_t *__restrict__ mask,
-                                                      T *__restrict__ xv, T *__restrict__ res,
-                                                      const T *__restrict__ p, const T *__restrict__ q,
-                                                      double *__restrict__ part, int nblk,
-                                                      const PoissonWork::Ctl *ctl) {
-  if (ctl->done) return;
-  const int par = ctl->iters & 1;
-  const double pq = sum_partials(part, nblk, P_PQ);
-  const double rz = sum_partials(part, nblk, P_RZ0 + par);
-  const T alpha = (T)(rz / pq);
-  T rzt = 0, mxt = 0;
-  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < g.N;
-       r += (long long)gridDim.x * blockDim.x) {
-    const uint32_t m = mask[r];
+__global__ void __launch_bounds__(kBlock) k_cg_a(const Geo g, int zpt, uint32_t selfmask,
+                                                 const uint32_t *__restrict__ mask, T *__restrict__ x,
+                                                 T *__restrict__ r, T *__restrict__ u, const T *__restrict__ w,
+                                                 T *__restrict__ p, T *__restrict__ s, double *__restrict__ part,
+                                                 int nblk, const PoissonCtl *c) {
+  if (c->inner_done) return;
+  const T alpha = (T)c->alpha, beta = (T)c->beta;
+  T mx = 0;
+  for (int kz = 0; kz < zpt; ++kz) {
+    int X, Y, Z;
+    long long i;
+    if (!node_of(g, zpt, kz, X, Y, Z, i)) continue;
+    const uint32_t m = mask[i];
     if (!(m & kFluidBit)) continue;
-    xv[r] += alpha * p[r];
-    const T rr = res[r] - alpha * q[r];
-    res[r] = rr;
+    const T pv = u[i] + beta * p[i];
+    const T sv = w[i] + beta * s[i];
+    p[i] = pv;
+    s[i] = sv;
+    x[i] += alpha * pv;
+    const T rv = r[i] - alpha * sv;
+    r[i] = rv;
     const T dinv = (T)1 / diag_t<T>(m, selfmask);
-    rzt += rr * rr * dinv;
-    mxt = fmax(mxt, fabs(rr) * dinv);
+    u[i] = rv * dinv;
+    mx = fmax(mx, fabs(rv) * dinv);
   }
-  double rzn = block_reduce<false>((double)rzt);
-  double mx = (double)mxt;
-  if (threadIdx.x == 0) part[(P_RZ0 + (par ^ 1)) * nblk + blockIdx.x] = rzn;
-  mx = block_reduce<true>(mx);
-  if (threadIdx.x == 0) part[P_MAX * nblk + blockIdx.x] = mx;
+  const T v = block_reduce<true, T>(mx);
+  if (flat_tid() == 0) part[S_MAX * nblk + flat_bid()] = (double)v;
 }
 
-// p = res/diag + beta p (ctl->iters already counts the finished iteration);
-// FP64 form: every kRefresh iterations the recursive residual is replaced by
-// the true one
-template <typename T, bool REFRESH>
-__global__ void __launch_bounds__(kBlock) k_cg_direction(const Geo g, uint32_t selfmask,
-                                                         const uint32_t *__restrict__ mask,
-                                                         const double *__restrict__ rhs, const double *__restrict__ phi,
-                                                         T *__restrict__ res, T *__restrict__ p,
-                                                         const double *__restrict__ part, int nblk,
-                                                         const PoissonWork::Ctl *ctl) {
-  if (ctl->done) return;
-  const int it = ctl->iters;
-  const int par = it & 1;
-  const double rzn = sum_partials(part, nblk, P_RZ0 + par);
-  const double rzo = sum_partials(part, nblk, P_RZ0 + (par ^ 1));
-  const T beta = (T)(rzn / rzo);
-  const bool refresh = REFRESH && (it % kRefresh) == 0;
-  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < g.N;
-       r += (long long)gridDim.x * blockDim.x) {
-    const uint32_t m = mask[r];
-    if (!(m & kFluidBit)) continue;
-    const T d = diag_t<T>(m, selfmask);
-    p[r] = res[r] / d + beta * p[r];
-    if (refresh) {
-      int x, y, z;
-      coords(g, r, x, y, z);
-      res[r] = (T)(rhs[r] + lap_at(g, r, x, y, z, m, phi));
-    }
-  }
+// warm start of a step's solve: phi <- 2 phi(t) - phi(t-1) on fluid nodes
+// (linear extrapolation in time; the converged potential does not depend on
+// the starting guess), and remember phi(t)
+__global__ void k_extrapolate(const Geo g, const uint32_t *__restrict__ mask, double *__restrict__ phi,
+                              double *__restrict__ prev, int have_history) {
+  int X, Y, Z;
+  long long i;
+  if (!node_of(g, 1, 0, X, Y, Z, i)) return;
+  if (!(mask[i] & kFluidBit)) return;
+  const double v = phi[i];
+  if (have_history) phi[i] = 2.0 * v - prev[i];
+  prev[i] = v;
 }
 
-// FP32 form: phi64 += e on fluid nodes; refresh the FP32 copy everywhere
-__global__ void k_correct(const Geo g, const uint32_t *__restrict__ mask, const float *__restrict__ e,
+// phi64 += e on fluid nodes; the FP32 form refreshes its FP32 copy
+template <typename T>
+__global__ void k_correct(const Geo g, const uint32_t *__restrict__ mask, const T *__restrict__ e,
                           double *__restrict__ phi, float *__restrict__ phi32) {
-  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= g.N) return;
-  double v = phi[r];
-  if (e && (mask[r] & kFluidBit)) {
-    v += (double)e[r];
-    phi[r] = v;
+  int X, Y, Z;
+  long long i;
+  if (!node_of(g, 1, 0, X, Y, Z, i)) return;
+  double v = phi[i];
+  if (e && (mask[i] & kFluidBit)) {
+    v += (double)e[i];
+    phi[i] = v;
   }
-  phi32[r] = (float)v;
+  if (phi32) phi32[i] = (float)v;
 }
 
-inline unsigned grid_for(long long N) { return (unsigned)((N + kBlock - 1) / kBlock); }
+// ---------------------------------------------------------------------------
+// kernel argument storage for graph nodes (values are copied at node creation)
+struct Args {
+  Geo g;
+  int zpt, nblk, maxit, use_cond = 1, mode_init = C_INIT, mode_iter = C_ITER;
+  Phys P;
+  P32 P3;
+  uint32_t selfmask;
+  double tol, eta, tol_inner;
+  const uint32_t *mask;
+  const double *n64;
+  const int64_t *nq;
+  double *phi;
+  float *phi32;
+  void *r, *u, *w, *x, *p, *s;
+  double *part;
+  PoissonCtl *c;
+  cudaGraphConditionalHandle hout = 0, hin = 0;
+};
 
-// poll the control block of a solve (one D2H copy + stream sync)
-int poll(lbe_handle *h, PoissonWork::Ctl *dev, PoissonWork::Ctl *host) {
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(host, dev, sizeof(PoissonWork::Ctl), cudaMemcpyDeviceToHost, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (e != cudaSuccess) {
-    h->err = std::string("poisson: ") + cudaGetErrorString(e);
-    return LBE_ERR_CUDA;
-  }
-  return LBE_OK;
+cudaError_t add_kernel(cudaGraph_t gr, cudaGraphNode_t *last, void *func, dim3 grid, dim3 block, void **args) {
+  cudaKernelNodeParams kp;
+  memset(&kp, 0, sizeof(kp));
+  kp.func = func;
+  kp.gridDim = grid;
+  kp.blockDim = block;
+  kp.kernelParams = args;
+  cudaGraphNode_t n;
+  cudaError_t e = cudaGraphAddKernelNode(&n, gr, *last ? last : nullptr, *last ? 1 : 0, &kp);
+  if (e == cudaSuccess) *last = n;
+  return e;
 }
 
-int status_of(lbe_handle *h, const PoissonWork::Ctl &c) {
-  if (c.status == LBE_ERR_NOCONVERGE) {
-    h->err = "poisson: no convergence within poisson_max_iter";
-    return LBE_ERR_NOCONVERGE;
+cudaError_t add_while(cudaGraph_t gr, cudaGraphNode_t *last, cudaGraphConditionalHandle h, cudaGraph_t *body) {
+  // cudaGraphNodeParams has no default constructor: zeroed raw storage
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  memset(raw, 0, sizeof(raw));
+  cudaGraphNodeParams *np = reinterpret_cast<cudaGraphNodeParams *>(raw);
+  np->type = cudaGraphNodeTypeConditional;
+  np->conditional.handle = h;
+  np->conditional.type = cudaGraphCondTypeWhile;
+  np->conditional.size = 1;
+  cudaGraphNode_t n;
+  cudaError_t e = cudaGraphAddNode(&n, gr, *last ? last : nullptr, nullptr, *last ? 1 : 0, np);
+  if (e == cudaSuccess) {
+    *last = n;
+    *body = np->conditional.phGraph_out[0];
   }
-  if (c.status == LBE_ERR_NONFINITE) {
-    h->err = "poisson: non-finite residual";
-    return LBE_ERR_NONFINITE;
-  }
-  return LBE_OK;
+  return e;
 }
 
-// CG chunks until the control block says done (bounded by maxit on the
-// device and by a round count on the host)
-template <typename T, bool REFRESH>
-int cg_loop(lbe_handle *h, T *x, T *res, T *p, T *q, const double *rhs, const double *phi, PoissonWork::Ctl *ctl,
-            PoissonWork::Ctl *ctl_host, double tol, double eta, int maxit) {
+template <typename T>
+void fill_args(lbe_handle *h, Args &A) {
   PoissonWork &w = h->pw;
-  const Geo &g = h->geo;
-  const uint32_t sm = h->phys.selfmask;
-  cudaStream_t s = h->stream;
-  const long long max_rounds = (long long)maxit / kChunk + 3;
-  for (long long round = 0;; ++round) {
-    if (round >= max_rounds) {
-      h->err = "poisson: device never reported completion";
-      return LBE_ERR_NOCONVERGE;
+  const long long N = h->geo.N;
+  T *base = (T *)w.vec;
+  A.g = h->geo;
+  A.zpt = w.L.zpt;
+  A.nblk = (int)w.L.nblk();
+  A.maxit = h->prm.poisson_max_iter;
+  A.P = h->phys;
+  A.P3 = h->p32;
+  A.selfmask = h->phys.selfmask;
+  A.tol = h->prm.poisson_tol;
+  A.eta = sizeof(T) == 4 ? 1e-4 : 1e-9;
+  // an inner solve need not go below a fraction of the outer tolerance
+  A.tol_inner = 0.25 * A.tol;
+  A.mask = h->mask;
+  A.n64 = h->n;
+  A.nq = h->q;
+  A.phi = h->phi;
+  A.phi32 = h->phi32;
+  A.r = base;
+  A.u = base + N;
+  A.w = base + 2 * N;
+  A.x = base + 3 * N;
+  A.p = base + 4 * N;
+  A.s = base + 5 * N;
+  A.part = w.partial;
+  A.c = w.ctl;
+}
+
+template <typename T>
+cudaError_t build_graph(lbe_handle *h, Args &A, cudaGraphExec_t *exec) {
+  const Launch &L = h->pw.L;
+  const Launch L1 = make_launch(h->geo);
+  const dim3 one(1);
+  const bool fixed = h->prm.precision == LBE_FP32;
+  void *f_res = fixed ? (void *)k_res<T, true> : (void *)k_res<T, false>;
+  cudaGraph_t G = nullptr;
+  cudaError_t e = cudaGraphCreate(&G, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphNode_t last = nullptr, lo = nullptr, li = nullptr;
+  cudaGraph_t body_out = nullptr, body_in = nullptr;
+  void *a_reset[] = {&A.c};
+  void *a_res[] = {&A.g, &A.zpt, &A.P, &A.P3, &A.mask, &A.n64, &A.nq, &A.phi, &A.r, &A.u, &A.x, &A.p, &A.s,
+                   &A.part, &A.nblk, &A.c, &A.tol, &A.maxit, &A.hout, &A.hin, &A.use_cond};
+  void *a_bi[] = {&A.g, &A.zpt, &A.selfmask, &A.mask, &A.u, &A.r, &A.w, &A.part, &A.nblk, &A.c,
+                  &A.eta, &A.tol_inner, &A.maxit, &A.mode_init, &A.hin, &A.use_cond};
+  void *a_bt[] = {&A.g, &A.zpt, &A.selfmask, &A.mask, &A.u, &A.r, &A.w, &A.part, &A.nblk, &A.c,
+                  &A.eta, &A.tol_inner, &A.maxit, &A.mode_iter, &A.hin, &A.use_cond};
+  void *a_a[] = {&A.g, &A.zpt, &A.selfmask, &A.mask, &A.x, &A.r, &A.u, &A.w, &A.p, &A.s, &A.part, &A.nblk, &A.c};
+  void *a_cor[] = {&A.g, &A.mask, &A.x, &A.phi, &A.phi32};
+  e = cudaGraphConditionalHandleCreate(&A.hout, G, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) e = add_kernel(G, &last, (void *)k_solve_reset, one, one, a_reset);
+  if (e == cudaSuccess) e = add_while(G, &last, A.hout, &body_out);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&A.hin, body_out, 0, 0);
+  if (e == cudaSuccess) e = add_kernel(body_out, &lo, f_res, L.grid, L.block, a_res);
+  if (e == cudaSuccess) e = add_kernel(body_out, &lo, (void *)k_cg_b<T>, L.grid, L.block, a_bi);
+  if (e == cudaSuccess) e = add_while(body_out, &lo, A.hin, &body_in);
+  if (e == cudaSuccess) e = add_kernel(body_in, &li, (void *)k_cg_a<T>, L.grid, L.block, a_a);
+  if (e == cudaSuccess) e = add_kernel(body_in, &li, (void *)k_cg_b<T>, L.grid, L.block, a_bt);
+  if (e == cudaSuccess) e = add_kernel(body_out, &lo, (void *)k_correct<T>, L1.grid, L1.block, a_cor);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(exec, G, 0);
+  cudaGraphDestroy(G);
+  return e;
+}
+
+// host-driven fallback: the same kernels, polling the control block
+template <typename T>
+int solve_polled(lbe_handle *h, Args &A) {
+  PoissonWork &w = h->pw;
+  const Launch &L = w.L;
+  const Launch L1 = make_launch(h->geo);
+  cudaStream_t st = h->stream;
+  const bool fixed = h->prm.precision == LBE_FP32;
+  A.use_cond = 0;
+  k_solve_reset<<<1, 1, 0, st>>>(A.c);
+  h->launches += 1;
+  for (int round = 0; round <= kMaxOuter; ++round) {
+    if (fixed)
+      k_res<T, true><<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.P, A.P3, A.mask, A.n64, A.nq, A.phi, (T *)A.r,
+                                                  (T *)A.u, (T *)A.x, (T *)A.p, (T *)A.s, A.part, A.nblk, A.c,
+                                                  A.tol, A.maxit, 0, 0, 0);
+    else
+      k_res<T, false><<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.P, A.P3, A.mask, A.n64, A.nq, A.phi, (T *)A.r,
+                                                   (T *)A.u, (T *)A.x, (T *)A.p, (T *)A.s, A.part, A.nblk, A.c,
+                                                   A.tol, A.maxit, 0, 0, 0);
+    k_cg_b<T><<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.selfmask, A.mask, (T *)A.u, (T *)A.r, (T *)A.w, A.part,
+                                           A.nblk, A.c, A.eta, A.tol_inner, A.maxit, C_INIT, 0, 0);
+    h->launches += 2;
+    const long long max_chunks = (long long)A.maxit / kChunk + 2;
+    for (long long ch = 0;; ++ch) {
+      cudaError_t e = cudaMemcpyAsync(w.ctl_host, w.ctl, sizeof(PoissonCtl), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) {
+        h->err = std::string("poisson: ") + cudaGetErrorString(e);
+        return LBE_ERR_CUDA;
+      }
+      if (w.ctl_host->inner_done || ch >= max_chunks) break;
+      for (int k = 0; k < kChunk; ++k) {
+        k_cg_a<T><<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.selfmask, A.mask, (T *)A.x, (T *)A.r, (T *)A.u,
+                                               (T *)A.w, (T *)A.p, (T *)A.s, A.part, A.nblk, A.c);
+        k_cg_b<T><<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.selfmask, A.mask, (T *)A.u, (T *)A.r, (T *)A.w,
+                                               A.part, A.nblk, A.c, A.eta, A.tol_inner, A.maxit, C_ITER, 0, 0);
+      }
+      h->launches += 2 * kChunk;
     }
-    for (int c = 0; c < kChunk; ++c) {
-      k_cg_matvec<T><<<w.nblk, kBlock, 0, s>>>(g, sm, h->mask, p, q, w.partial, w.nblk, ctl);
-      k_cg_update<T><<<w.nblk, kBlock, 0, s>>>(g, sm, h->mask, x, res, p, q, w.partial, w.nblk, ctl);
-      k_cg_check<<<1, 32, 0, s>>>(w.partial, w.nblk, ctl, tol, eta, maxit, 1);
-      k_cg_direction<T, REFRESH><<<w.nblk, kBlock, 0, s>>>(g, sm, h->mask, rhs, phi, res, p, w.partial, w.nblk, ctl);
-    }
-    h->launches += 4 * kChunk;
-    int rc = poll(h, ctl, ctl_host);
-    if (rc != LBE_OK) return rc;
-    if (ctl_host->done) return LBE_OK;
+    k_correct<T><<<L1.grid, L1.block, 0, st>>>(A.g, A.mask, (const T *)A.x, A.phi, A.phi32);
+    h->launches += 1;
+    if (w.ctl_host->outer_done) break;
   }
+  return cudaGetLastError() == cudaSuccess ? LBE_OK : LBE_ERR_CUDA;
+}
+
+template <typename T>
+int solve_t(lbe_handle *h) {
+  PoissonWork &w = h->pw;
+  // one graph per solute buffer (flow-off steps swap the two buffers)
+  const void *key = h->prm.precision == LBE_FP32 ? (const void *)h->q : (const void *)h->n;
+  int slot = -1;
+  for (int k = 0; k < 2; ++k)
+    if (w.exec[k] && w.exec_key[k] == key) slot = k;
+  if (slot < 0 && w.graph_ok) {
+    slot = !w.exec[0] ? 0 : (!w.exec[1] ? 1 : 0);
+    if (w.exec[slot]) cudaGraphExecDestroy(w.exec[slot]);
+    w.exec[slot] = nullptr;
+    Args A;
+    fill_args<T>(h, A);
+    cudaError_t e = build_graph<T>(h, A, &w.exec[slot]);
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // clear the error; use the polled loop from now on
+      w.graph_ok = false;
+      w.exec[slot] = nullptr;
+      slot = -1;
+    } else {
+      w.exec_key[slot] = key;
+    }
+  }
+  if (slot >= 0) {
+    cudaError_t e = cudaGraphLaunch(w.exec[slot], h->stream);
+    if (e != cudaSuccess) {
+      h->err = std::string("poisson graph launch: ") + cudaGetErrorString(e);
+      return LBE_ERR_CUDA;
+    }
+    return LBE_OK;
+  }
+  Args A;
+  fill_args<T>(h, A);
+  return solve_polled<T>(h, A);
 }
 
 }  // namespace
@@ -387,103 +565,81 @@ int cg_loop(lbe_handle *h, T *x, T *res, T *p, T *q, const double *rhs, const do
 cudaError_t poisson_alloc(lbe_handle *h) {
   PoissonWork &w = h->pw;
   const long long N = h->geo.N;
-  long long blocks = (N + kBlock - 1) / kBlock;
-  w.nblk = (int)(blocks < 608 ? blocks : 608);
+  w.L = make_launch(h->geo, kMaxPartials);
+  const size_t tsz = h->prm.precision == LBE_FP32 ? sizeof(float) : sizeof(double);
   cudaError_t e;
-  if (h->prm.precision == LBE_FP64) {
-    if ((e = cudaMalloc(&w.rhs, sizeof(double) * N)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&w.res, sizeof(double) * N)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&w.p, sizeof(double) * N)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&w.q, sizeof(double) * N)) != cudaSuccess) return e;
-  } else {
-    if ((e = cudaMalloc(&h->pw32, sizeof(float) * 4 * N)) != cudaSuccess) return e;
-  }
-  if ((e = cudaMalloc(&w.partial, sizeof(double) * 4 * w.nblk)) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&w.ctl, 2 * sizeof(PoissonWork::Ctl))) != cudaSuccess) return e;
-  if ((e = cudaMallocHost(&w.ctl_host, 2 * sizeof(PoissonWork::Ctl))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.vec, tsz * 6 * N)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.partial, sizeof(double) * 3 * w.L.nblk())) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.phi_prev, sizeof(double) * N)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.ctl, sizeof(PoissonCtl))) != cudaSuccess) return e;
+  if ((e = cudaMemset(w.ctl, 0, sizeof(PoissonCtl))) != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&w.ctl_host, sizeof(PoissonCtl))) != cudaSuccess) return e;
+  // LBE_POISSON_GRAPH=0 runs the solves from the host loop (same kernels),
+  // e.g. for profilers that do not follow conditional graph nodes
+  const char *env = getenv("LBE_POISSON_GRAPH");
+  w.graph_ok = !(env && env[0] == '0');
   return cudaSuccess;
 }
 
 void poisson_free(lbe_handle *h) {
   PoissonWork &w = h->pw;
-  cudaFree(w.rhs);
-  cudaFree(w.res);
-  cudaFree(w.p);
-  cudaFree(w.q);
+  for (int k = 0; k < 2; ++k)
+    if (w.exec[k]) cudaGraphExecDestroy(w.exec[k]);
+  cudaFree(w.vec);
   cudaFree(w.partial);
+  cudaFree(w.phi_prev);
   cudaFree(w.ctl);
-  cudaFree(h->pw32);
-  h->pw32 = nullptr;
   if (w.ctl_host) cudaFreeHost(w.ctl_host);
   w = PoissonWork{};
 }
 
-int poisson_solve(lbe_handle *h, int *iters, double *res) {
+int poisson_enqueue(lbe_handle *h, bool extrapolate) {
   PoissonWork &w = h->pw;
-  const double tol = h->prm.poisson_tol;
-  const int maxit = h->prm.poisson_max_iter;
-  k_cg_init64<<<w.nblk, kBlock, 0, h->stream>>>(h->geo, h->phys, h->mask, h->n, h->phi, w.rhs, w.res, w.p,
-                                                 w.partial, w.nblk, w.ctl);
-  k_cg_check<<<1, 32, 0, h->stream>>>(w.partial, w.nblk, w.ctl, tol, 0.0, maxit, 0);
-  h->launches += 2;
-  int rc = cg_loop<double, true>(h, h->phi, w.res, w.p, w.q, w.rhs, h->phi, w.ctl, w.ctl_host, tol, 0.0, maxit);
-  *iters = w.ctl_host->iters;
-  *res = w.ctl_host->res;
-  if (rc != LBE_OK) return rc;
-  return status_of(h, *w.ctl_host);
+  if (extrapolate) {
+    const Launch L1 = make_launch(h->geo);
+    k_extrapolate<<<L1.grid, L1.block, 0, h->stream>>>(h->geo, h->mask, h->phi, w.phi_prev, w.have_history ? 1 : 0);
+    h->launches += 1;
+    w.have_history = true;
+  } else {
+    w.have_history = false;
+  }
+  return h->prm.precision == LBE_FP32 ? solve_t<float>(h) : solve_t<double>(h);
 }
 
-int poisson_solve_mixed(lbe_handle *h, int *iters, double *res) {
+int poisson_status(lbe_handle *h, lbe_stats *st, long long *kernels) {
   PoissonWork &w = h->pw;
-  const Geo &g = h->geo;
-  const long long N = g.N;
-  float *r32 = h->pw32, *p32 = h->pw32 + N, *q32 = h->pw32 + 2 * N, *e32 = h->pw32 + 3 * N;
-  PoissonWork::Ctl *outer = w.ctl + 1, *outer_h = w.ctl_host + 1;
-  const double tol = h->prm.poisson_tol;
-  const int maxit = h->prm.poisson_max_iter;
-  int total = 0;
-  *res = 0.0;
-  for (int round = 0; round < kMaxOuter; ++round) {
-    // FP64 residual of the current potential; seeds the inner FP32 solve and
-    // resets both control blocks
-    k_res64<<<w.nblk, kBlock, 0, h->stream>>>(g, h->phys, h->p32, h->mask, h->q, h->phi, r32, p32, e32, w.partial,
-                                               w.nblk, outer, w.ctl);
-    k_cg_check<<<1, 32, 0, h->stream>>>(w.partial, w.nblk, outer, tol, 0.0, 1 << 30, 0);
-    // inner solve's starting residual (same partials), relative stop
-    k_cg_check<<<1, 32, 0, h->stream>>>(w.partial, w.nblk, w.ctl, 0.0, kInnerEta, maxit, 0);
-    h->launches += 3;
-    int rc = poll(h, outer, outer_h);
-    if (rc != LBE_OK) return rc;
-    *res = outer_h->res;
-    if (!(outer_h->res == outer_h->res) || outer_h->res > 1e300) {
-      h->err = "poisson: non-finite residual";
-      return LBE_ERR_NONFINITE;
-    }
-    if (outer_h->done) {
-      *iters = total;
-      return LBE_OK;
-    }
-    rc = cg_loop<float, false>(h, e32, r32, p32, q32, nullptr, nullptr, w.ctl, w.ctl_host, 0.0, kInnerEta,
-                               maxit - total);
-    total += w.ctl_host->iters;
-    if (rc != LBE_OK) return rc;
-    if (w.ctl_host->status == LBE_ERR_NONFINITE) return status_of(h, *w.ctl_host);
-    k_correct<<<grid_for(N), kBlock, 0, h->stream>>>(g, h->mask, e32, h->phi, h->phi32);
-    h->launches += 1;
-    if (total >= maxit) {
-      *iters = total;
-      h->err = "poisson: no convergence within poisson_max_iter";
-      return LBE_ERR_NOCONVERGE;
-    }
+  cudaError_t e = cudaMemcpyAsync(w.ctl_host, w.ctl, sizeof(PoissonCtl), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    h->err = std::string("poisson: ") + cudaGetErrorString(e);
+    return LBE_ERR_CUDA;
   }
-  *iters = total;
-  h->err = "poisson: refinement did not reach the tolerance";
-  return LBE_ERR_NOCONVERGE;
+  const PoissonCtl &c = *w.ctl_host;
+  if (st) {
+    st->poisson_iters = c.total_iters;
+    st->poisson_solves = (int)c.solves;
+    st->poisson_max_iters = (int)(c.solve_iters > c.max_solve_iters ? c.solve_iters : c.max_solve_iters);
+    st->poisson_residual = c.res;
+  }
+  // kernels of the graph path: reset + per round (residual, stencil,
+  // correct) + per iteration (update, stencil)
+  if (kernels && w.graph_ok) *kernels = c.solves + 3 * c.total_rounds + 2 * c.total_iters;
+  if (c.sticky_status == LBE_ERR_NOCONVERGE || c.status == LBE_ERR_NOCONVERGE) {
+    h->err = "poisson: no convergence within poisson_max_iter";
+    return LBE_ERR_NOCONVERGE;
+  }
+  if (c.sticky_status == LBE_ERR_NONFINITE || c.status == LBE_ERR_NONFINITE) {
+    h->err = "poisson: non-finite residual";
+    return LBE_ERR_NONFINITE;
+  }
+  return LBE_OK;
 }
+
+cudaError_t poisson_reset_stats(lbe_handle *h) { return cudaMemsetAsync(h->pw.ctl, 0, sizeof(PoissonCtl), h->stream); }
 
 cudaError_t launch_phi32_sync(lbe_handle *h) {
-  // phi32 = (float) phi64 everywhere (after init / set_state / set_voltage)
-  k_correct<<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->mask, nullptr, h->phi, h->phi32);
+  const Launch L = make_launch(h->geo);
+  k_correct<float><<<L.grid, L.block, 0, h->stream>>>(h->geo, h->mask, nullptr, h->phi, h->phi32);
   return cudaGetLastError();
 }
 
