@@ -86,7 +86,7 @@ __device__ __forceinline__ void gather32(int N, int r, const Offs &o, uint32_t m
 
 // Ion part of the step at one fluid node: quantised link fluxes -> dq, and
 // the solvent force from the link excess fluxes.
-template <bool QUANT>
+template <bool QUANT, bool SALT11>
 __device__ __forceinline__ void ion_links(const P32 &P, int N, int r, const Offs &o, uint32_t m,
                                           const int64_t *__restrict__ q, const float *__restrict__ phi,
                                           const long long q0[LBE_MAX_SPECIES], const float q0f[LBE_MAX_SPECIES],
@@ -104,10 +104,13 @@ __device__ __forceinline__ void ion_links(const P32 &P, int N, int r, const Offs
     const float il = (float)invlen_of(i);
     float gs = 0.f;
 #pragma unroll
-    for (int k = 0; k < LBE_MAX_SPECIES; ++k) {
-      if (k >= P.ns) break;
+    for (int k = 0; k < (SALT11 ? 2 : LBE_MAX_SPECIES); ++k) {
+      if (!SALT11 && k >= P.ns) break;
       float Pk, Mk;
-      if (P.zi[k] == 1) {
+      if (SALT11) {  // z = +1, -1
+        Pk = k == 0 ? P1 : M1;
+        Mk = k == 0 ? M1 : P1;
+      } else if (P.zi[k] == 1) {
         Pk = P1;
         Mk = M1;
       } else if (P.zi[k] == -1) {
@@ -140,7 +143,7 @@ __device__ __forceinline__ void ion_links(const P32 &P, int N, int r, const Offs
 // Fused step kernel: link fluxes (quantised), solute update q* = q - sum Jq,
 // solvent force, and (FLOW) BGK + Guo collision and pull streaming with
 // halfway bounce-back, all in FP32 deviations.
-template <bool FLOW>
+template <bool FLOW, bool SALT11>
 __global__ void __launch_bounds__(kBlock) k_sweep32(const Geo g, const P32 P, const uint32_t *__restrict__ mask,
                                                     const float *__restrict__ fin, float *__restrict__ fout,
                                                     const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
@@ -163,9 +166,9 @@ __global__ void __launch_bounds__(kBlock) k_sweep32(const Geo g, const P32 P, co
   }
   float F[3];
   bool over = false;
-  ion_links<true>(P, N, r, o, m, q, phi, q0, q0f, dq, F, over);
+  ion_links<true, SALT11>(P, N, r, o, m, q, phi, q0, q0f, dq, F, over);
   if (over) atomicOr(flag, 1);
-  for (int k = 0; k < P.ns; ++k) qstar[k * N + r] = q0[k] + dq[k];
+  for (int k = 0; k < (SALT11 ? 2 : P.ns); ++k) qstar[k * N + r] = q0[k] + dq[k];
   if (!FLOW) return;
 
   float f[kQ];
@@ -186,14 +189,26 @@ __global__ void __launch_bounds__(kBlock) k_sweep32(const Geo g, const P32 P, co
   u[2 * N + r] = uz;
   const float uu = ux * ux + uy * uy + uz * uz;
   const float uF = ux * F[0] + uy * F[1] + uz * F[2];
+  // BGK + Guo forcing; c_{i+9} = -c_i, so each opposite pair shares the even
+  // part of the equilibrium and of the source and flips the odd part
+  {
+    const float w = (float)w_of(0);
+    const float eq = w * (drho - rho * 1.5f * uu);
+    const float src = -P.guo * w * 3.f * uF;
+    fout[r] = f[0] - P.omega * (f[0] - eq) + src;
+  }
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) {
+  for (int i = 1; i <= 9; ++i) {
     const float w = (float)w_of(i);
     const float cu = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
     const float cF = cx_of(i) * F[0] + cy_of(i) * F[1] + cz_of(i) * F[2];
-    const float eq = w * (drho + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * uu));
-    const float src = P.guo * w * (3.f * (cF - uF) + 9.f * cu * cF);
-    fout[i * N + r] = f[i] - P.omega * (f[i] - eq) + src;
+    const float eq_even = w * (drho + rho * (4.5f * cu * cu - 1.5f * uu));
+    const float eq_odd = w * rho * 3.f * cu;
+    const float src_even = P.guo * w * (9.f * cu * cF - 3.f * uF);
+    const float src_odd = P.guo * w * 3.f * cF;
+    const int io = i + 9;
+    fout[i * N + r] = f[i] - P.omega * (f[i] - (eq_even + eq_odd)) + (src_even + src_odd);
+    fout[io * N + r] = f[io] - P.omega * (f[io] - (eq_even - eq_odd)) + (src_even - src_odd);
   }
 }
 
@@ -202,9 +217,8 @@ __device__ __forceinline__ float ov(int s, float u) {
   return s == 0 ? 1.f - fabsf(u) : (s > 0 ? fmaxf(u, 0.f) : fmaxf(-u, 0.f));
 }
 
-__device__ __forceinline__ int dir_bit(int dx, int dy, int dz) {
+__host__ __device__ constexpr int dir_bit(int dx, int dy, int dz) {
   if (dx != 0 && dy != 0 && dz != 0) return corner_bit(dx, dy, dz);
-#pragma unroll
   for (int i = 1; i < kQ; ++i)
     if (cx_of(i) == dx && cy_of(i) == dy && cz_of(i) == dz) return i - 1;
   return -1;
@@ -244,26 +258,27 @@ __global__ void __launch_bounds__(kBlock) k_advect32(const Geo g, int ns, const 
     acc[k] = base + qin[k * N + r];
     totf[k] = ll2f(acc[k]);
   }
-  // outgoing: the octant of u
-  const int sx = ux > 0.f ? 1 : -1, sy = uy > 0.f ? 1 : -1, sz = uz > 0.f ? 1 : -1;
-  for (int c = 1; c < 8; ++c) {
-    const int dx = (c & 1) ? sx : 0, dy = (c & 2) ? sy : 0, dz = (c & 4) ? sz : 0;
-    if (!(m & (1u << dir_bit(dx, dy, dz)))) continue;  // shares bound for solid stay
+  // outgoing (the share is zero outside the octant of u); shares bound for
+  // solid neighbours stay
+#pragma unroll
+  for (int d = 0; d < 27; ++d) {
+    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+    if (d == 13 || !(m & (1u << dir_bit(dx, dy, dz)))) continue;
+    if ((dx && dx * ux <= 0.f) || (dy && dy * uy <= 0.f) || (dz && dz * uz <= 0.f)) continue;
     for (int k = 0; k < ns; ++k) acc[k] -= share(totf[k], ux, uy, uz, dx, dy, dz);
   }
-  // incoming from every fluid neighbour whose cell reaches r
-  for (int dz = -1; dz <= 1; ++dz)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        if (dx == 0 && dy == 0 && dz == 0) continue;
-        // the source at r - s gives along +s
-        if (!(m & (1u << dir_bit(-dx, -dy, -dz)))) continue;
-        const int s = r + o.at(-dx, -dy, -dz);
-        const float vx = u[s], vy = u[N + s], vz = u[2 * N + s];
-        const float w = ov(dx, vx) * ov(dy, vy) * ov(dz, vz);
-        if (w == 0.f) continue;
-        for (int k = 0; k < ns; ++k) acc[k] += share(ll2f(base + qin[k * N + s]), vx, vy, vz, dx, dy, dz);
-      }
+  // incoming from every fluid neighbour whose cell reaches r: the source at
+  // r - s gives along +s
+#pragma unroll
+  for (int d = 0; d < 27; ++d) {
+    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+    if (d == 13 || !(m & (1u << dir_bit(-dx, -dy, -dz)))) continue;
+    const int s = r + o.at(-dx, -dy, -dz);
+    const float vx = u[s], vy = u[N + s], vz = u[2 * N + s];
+    const float w = ov(dx, vx) * ov(dy, vy) * ov(dz, vz);
+    if (w == 0.f) continue;
+    for (int k = 0; k < ns; ++k) acc[k] += share(ll2f(base + qin[k * N + s]), vx, vy, vz, dx, dy, dz);
+  }
   for (int k = 0; k < ns; ++k) qout[k * N + r] = acc[k] - base;
 }
 __global__ void k_n_to_double(const Geo g, const P32 P, const int64_t *__restrict__ q, const uint32_t *__restrict__ mask,
@@ -328,7 +343,7 @@ __global__ void k_moments32(const Geo g, const P32 P, int flow, const uint32_t *
   }
   float F[3];
   bool over = false;
-  ion_links<false>(P, N, r, o, m, q, phi, q0, q0f, dq, F, over);
+  ion_links<false, false>(P, N, r, o, m, q, phi, q0, q0f, dq, F, over);
   double drho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
   for (int i = 0; i < kQ; ++i) {
     drho += f[i];
@@ -357,14 +372,14 @@ cudaError_t launch_init32(lbe_handle *h) {
 
 cudaError_t launch_sweep32(lbe_handle *h) {
   const int nxt = h->cur ^ 1;
-  if (h->prm.flow)
-    k_sweep32<true><<<LAUNCH3(h), 0, h->stream>>>(h->geo, h->p32, h->mask, h->f32[h->cur],
-                                                                   h->f32[nxt], h->q, h->qstar, h->phi32,
-                                                                   h->u32, h->flag);
-  else
-    k_sweep32<false><<<LAUNCH3(h), 0, h->stream>>>(h->geo, h->p32, h->mask, h->f32[h->cur],
-                                                                    h->f32[nxt], h->q, h->qstar, h->phi32,
-                                                                    h->u32, h->flag);
+  const P32 &P = h->p32;
+  const bool salt11 = P.ns == 2 && P.zi[0] == 1 && P.zi[1] == -1;
+  using Kern = void (*)(const Geo, const P32, const uint32_t *, const float *, float *, const int64_t *, int64_t *,
+                        const float *, float *, int *);
+  Kern kern = h->prm.flow ? (salt11 ? k_sweep32<true, true> : k_sweep32<true, false>)
+                          : (salt11 ? k_sweep32<false, true> : k_sweep32<false, false>);
+  kern<<<LAUNCH3(h), 0, h->stream>>>(h->geo, P, h->mask, h->f32[h->cur], h->f32[nxt], h->q, h->qstar, h->phi32,
+                                     h->u32, h->flag);
   if (h->prm.flow) h->cur = nxt;
   return cudaGetLastError();
 }

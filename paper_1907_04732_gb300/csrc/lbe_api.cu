@@ -45,6 +45,7 @@ void free_all(lbe_handle *h) {
   for (void *p : ptrs) cudaFree(p);
   if (h->qhost) cudaFreeHost(h->qhost);
   lbe::poisson_free(h);
+  lbe::mg_free(h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   h->ev_pool.clear();
 }
@@ -113,6 +114,7 @@ void set_constants(lbe_handle *h) {
     // one rounding, mirrored for the opposite link so that ec[opp] = -ec
     Q.ec[i] = i <= 9 ? (float)P.e_dot_c[i] : -(float)P.e_dot_c[io];
   }
+  Q.salt11 = p->nspecies == 2 && p->z[0] == 1.0 && p->z[1] == -1.0 && p->rho_bulk[0] == p->rho_bulk[1];
   Q.omega = (float)P.omega;
   Q.guo = (float)P.guo;
   Q.inv_2a0 = (float)P.inv_2a0;
@@ -255,6 +257,8 @@ int lbe_set_geometry(lbe_handle *h, const uint8_t *node_id, int n_electrodes, in
   }
   LBE_CK(h, cudaMemcpyAsync(h->id, ids.data(), (size_t)g.N, cudaMemcpyHostToDevice, h->stream));
   LBE_CK(h, lbe::launch_build_mask(g, h->id, h->mask, h->stream));
+  if (fp32(h)) LBE_CK(h, lbe::mg_setup(h));  // multigrid preconditioner of the FP32 Poisson solve
+  lbe::poisson_drop_graphs(h);               // graphs capture the hierarchy
   LBE_CK(h, cudaStreamSynchronize(h->stream));  // ids is a host vector
   h->n_elec = n_electrodes;
   h->have_geometry = true;

@@ -177,6 +177,7 @@ struct P32 {
   float kq1[LBE_MAX_SPECIES], kq2[LBE_MAX_SPECIES];  // -d_k/(2|c| s_k), |c| = 1, sqrt 2
   float ec[kQ];                                      // E_app . c_i, ec[opp] = -ec
   float omega, guo, inv_2a0;
+  int salt11;  // two species, z = +1 and -1, equal bulk concentrations
 };
 
 // Deterministic block reductions (fixed tree order).
@@ -202,6 +203,22 @@ struct PoissonWork {
   bool have_history = false;
 };
 constexpr int kMaxPartials = 2048;
+
+// Multigrid hierarchy of the FP32 Poisson preconditioner (mg.cu); level 0 is
+// the lattice itself.
+constexpr int kMaxLevels = 10;
+struct MGLevel {
+  int nx = 0, ny = 0, nz = 0, sx = 0, sy = 0, sz = 0;
+  long long N = 0;
+  float *A = nullptr;  // 27-point Galerkin operator [27][N]
+  float *r = nullptr, *e = nullptr, *t = nullptr;
+};
+struct MGWork {
+  MGLevel lv[kMaxLevels];
+  int nlev = 0;        // 0: no hierarchy (Jacobi preconditioning)
+  float *t0 = nullptr;  // fine-level scratch
+  float *inv0 = nullptr;  // inverse diagonal of the fine operator
+};
 
 }  // namespace lbe
 
@@ -234,6 +251,7 @@ struct lbe_handle {
   double *psi_dev = nullptr;          // [LBE_MAX_ELECTRODES+1], index = electrode id
   int qblk = 0;
   lbe::PoissonWork pw;
+  lbe::MGWork mg;
 
   // FP32 form state
   float *f32[2] = {nullptr, nullptr};  // population deviations f_i - w_i
@@ -281,5 +299,12 @@ int poisson_enqueue(lbe_handle *h, bool extrapolate);
 // *kernels (optional) receives the kernels the graph path launched
 int poisson_status(lbe_handle *h, lbe_stats *st, long long *kernels);
 cudaError_t poisson_reset_stats(lbe_handle *h);
+void poisson_drop_graphs(lbe_handle *h);
+// mg.cu
+cudaError_t mg_setup(lbe_handle *h);
+void mg_free(lbe_handle *h);
+cudaError_t mg_vcycle(lbe_handle *h, const float *r0, float *u0, const PoissonCtl *c, cudaGraph_t gr,
+                      cudaGraphNode_t *last, cudaStream_t st);
+int mg_kernels_per_cycle(const lbe_handle *h);
 cudaError_t launch_phi32_sync(lbe_handle *h);
 }  // namespace lbe

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys
                                                 int nblk, PoissonCtl *c, double tol, int maxit,
                                                 cudaGraphConditionalHandle hout, cudaGraphConditionalHandle hin,
                                                 int use_cond) {
-  double mx = 0.0;
+  float mx = 0.f;
   for (int kz = 0; kz < zpt; ++kz) {
     int X, Y, Z;
     long long i;
@@ -227,19 +227,25 @@ __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys
       r[i] = u[i] = x[i] = p[i] = s[i] = (T)0;
       continue;
     }
-    double q = 0.0;
-    for (int k = 0; k < P.ns; ++k)
-      q += P.z[k] * (FIXED ? P3.rbd[k] + P3.sd[k] * (double)nq[k * g.N + i] : n64[k * g.N + i]);
+    double q;
+    if (FIXED && P3.salt11) {
+      // 1:1 salt with one bulk value: rho_el = s (q+ - q-), exact integer difference
+      q = P3.sd[0] * (double)(nq[i] - nq[g.N + i]);
+    } else {
+      q = 0.0;
+      for (int k = 0; k < P.ns; ++k)
+        q += P.z[k] * (FIXED ? P3.rbd[k] + P3.sd[k] * (double)nq[k * g.N + i] : n64[k * g.N + i]);
+    }
     const double rr = P.four_pi_lb * q + lap_at(g, (int)i, X, Y, Z, m, phi);
-    const double d = diag_t<double>(m, P.selfmask);
     const T rt = (T)rr;
+    const T dinv = (T)1 / diag_t<T>(m, P.selfmask);
     r[i] = rt;
-    u[i] = rt / diag_t<T>(m, P.selfmask);
+    u[i] = rt * dinv;
     x[i] = p[i] = s[i] = (T)0;
-    mx = fmax(mx, fabs(rr) / d);
+    mx = fmaxf(mx, fabsf((float)rr) * (float)dinv);  // the stopping test needs no FP64
   }
-  mx = block_reduce<true>(mx);
-  if (flat_tid() == 0) part[S_MAX * nblk + flat_bid()] = mx;
+  mx = block_reduce<true, float>(mx);
+  if (flat_tid() == 0) part[S_MAX * nblk + flat_bid()] = (double)mx;
   if (!last_block(c, nblk)) return;
   double m = 0.0;
   for (int i = flat_tid(); i < nblk; i += kBlock) m = fmax(m, __ldcg(part + S_MAX * nblk + i));
@@ -465,10 +471,13 @@ cudaError_t build_graph(lbe_handle *h, Args &A, cudaGraphExec_t *exec) {
   if (e == cudaSuccess) e = add_kernel(G, &last, (void *)k_solve_reset, one, one, a_reset);
   if (e == cudaSuccess) e = add_while(G, &last, A.hout, &body_out);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&A.hin, body_out, 0, 0);
+  const bool mg = sizeof(T) == 4 && h->mg.nlev >= 2;
   if (e == cudaSuccess) e = add_kernel(body_out, &lo, f_res, L.grid, L.block, a_res);
+  if (e == cudaSuccess && mg) e = mg_vcycle(h, (const float *)A.r, (float *)A.u, A.c, body_out, &lo, nullptr);
   if (e == cudaSuccess) e = add_kernel(body_out, &lo, (void *)k_cg_b<T>, L.grid, L.block, a_bi);
   if (e == cudaSuccess) e = add_while(body_out, &lo, A.hin, &body_in);
   if (e == cudaSuccess) e = add_kernel(body_in, &li, (void *)k_cg_a<T>, L.grid, L.block, a_a);
+  if (e == cudaSuccess && mg) e = mg_vcycle(h, (const float *)A.r, (float *)A.u, A.c, body_in, &li, nullptr);
   if (e == cudaSuccess) e = add_kernel(body_in, &li, (void *)k_cg_b<T>, L.grid, L.block, a_bt);
   if (e == cudaSuccess) e = add_kernel(body_out, &lo, (void *)k_correct<T>, L1.grid, L1.block, a_cor);
   if (e == cudaSuccess) e = cudaGraphInstantiate(exec, G, 0);
@@ -496,6 +505,9 @@ int solve_polled(lbe_handle *h, Args &A) {
       k_res<T, false><<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.P, A.P3, A.mask, A.n64, A.nq, A.phi, (T *)A.r,
                                                    (T *)A.u, (T *)A.x, (T *)A.p, (T *)A.s, A.part, A.nblk, A.c,
                                                    A.tol, A.maxit, 0, 0, 0);
+    const bool mg = sizeof(T) == 4 && h->mg.nlev >= 2;
+    if (mg && mg_vcycle(h, (const float *)A.r, (float *)A.u, A.c, nullptr, nullptr, st) != cudaSuccess)
+      return LBE_ERR_CUDA;
     k_cg_b<T><<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.selfmask, A.mask, (T *)A.u, (T *)A.r, (T *)A.w, A.part,
                                            A.nblk, A.c, A.eta, A.tol_inner, A.maxit, C_INIT, 0, 0);
     h->launches += 2;
@@ -511,6 +523,8 @@ int solve_polled(lbe_handle *h, Args &A) {
       for (int k = 0; k < kChunk; ++k) {
         k_cg_a<T><<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.selfmask, A.mask, (T *)A.x, (T *)A.r, (T *)A.u,
                                                (T *)A.w, (T *)A.p, (T *)A.s, A.part, A.nblk, A.c);
+        if (mg && mg_vcycle(h, (const float *)A.r, (float *)A.u, A.c, nullptr, nullptr, st) != cudaSuccess)
+          return LBE_ERR_CUDA;
         k_cg_b<T><<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.selfmask, A.mask, (T *)A.u, (T *)A.r, (T *)A.w,
                                                A.part, A.nblk, A.c, A.eta, A.tol_inner, A.maxit, C_ITER, 0, 0);
       }
@@ -593,6 +607,15 @@ void poisson_free(lbe_handle *h) {
   w = PoissonWork{};
 }
 
+void poisson_drop_graphs(lbe_handle *h) {
+  PoissonWork &w = h->pw;
+  for (int k = 0; k < 2; ++k) {
+    if (w.exec[k]) cudaGraphExecDestroy(w.exec[k]);
+    w.exec[k] = nullptr;
+    w.exec_key[k] = nullptr;
+  }
+}
+
 int poisson_enqueue(lbe_handle *h, bool extrapolate) {
   PoissonWork &w = h->pw;
   if (extrapolate) {
@@ -623,7 +646,11 @@ int poisson_status(lbe_handle *h, lbe_stats *st, long long *kernels) {
   }
   // kernels of the graph path: reset + per round (residual, stencil,
   // correct) + per iteration (update, stencil)
-  if (kernels && w.graph_ok) *kernels = c.solves + 3 * c.total_rounds + 2 * c.total_iters;
+  if (kernels && w.graph_ok) {
+    // a V-cycle after every residual and every iteration when multigrid is on
+    const long long vc = h->prm.precision == LBE_FP32 ? mg_kernels_per_cycle(h) : 0;
+    *kernels = c.solves + (3 + vc) * c.total_rounds + (2 + vc) * c.total_iters;
+  }
   if (c.sticky_status == LBE_ERR_NOCONVERGE || c.status == LBE_ERR_NOCONVERGE) {
     h->err = "poisson: no convergence within poisson_max_iter";
     return LBE_ERR_NOCONVERGE;
