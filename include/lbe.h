@@ -151,6 +151,33 @@ typedef struct {
 } lbe_stats;
 int lbe_get_stats(const lbe_handle *h, lbe_stats *out);
 
+/* Induced charge of every electrode (the same quantity as
+ * lbe_induced_charge) from buffers the caller owns, without allocating any
+ * device memory.  (The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate -- code whose device memory all comes from its
+ * own pool or budget, or that must not allocate while it is recording work,
+ * for instance during CUDA stream capture.)
+ *   phi      device, N doubles: potential of every node (solid nodes hold
+ *            their electrode potential), layout as lbe_fields(LBE_FIELD_PHI)
+ *   node_id  device, N bytes: 0 fluid, e = 1..n_electrodes electrode e
+ *   nx,ny,nz lattice size (nx*ny*nz < 2^31); periodic[3] host flags
+ *   bjerrum  l_B > 0; q_out device, n_electrodes doubles (written)
+ *   cuda_stream  stream the work is ordered on (NULL = legacy stream)
+ * Scratch: the per-block partial sums use a fixed device array of 128 KiB
+ * (1024 blocks x LBE_MAX_ELECTRODES doubles) that every GPU which loads this
+ * library keeps until the process exits; any lattice size fits it, while
+ * n_electrodes above LBE_MAX_ELECTRODES is rejected with LBE_ERR_ARG.  The
+ * first call on a device looks up that array's device address (and caches
+ * it), so make that first call outside any stream capture.  Every call
+ * rewrites the partials it reads, but all calls share the one array: calls
+ * that can overlap on the GPU (different streams, or threads without
+ * ordering) race and must be serialised by the caller.  Returns LBE_OK,
+ * LBE_ERR_ARG or LBE_ERR_CUDA; the message is lbe_last_error(NULL) on the
+ * calling thread.  Asynchronous: q_out is ready when the stream has run. */
+int lbe_induced_charge_static(const double *phi, const uint8_t *node_id, int nx, int ny, int nz,
+                              const int *periodic, double bjerrum, int n_electrodes, double *q_out,
+                              void *cuda_stream);
+
 /* Device time per phase of the lbe_step calls made between
  * lbe_profile_begin and lbe_profile_end, from CUDA events recorded on the
  * handle's stream around each phase (a measurement aid; results unchanged). */

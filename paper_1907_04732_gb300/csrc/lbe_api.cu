@@ -13,6 +13,7 @@ using lbe::Phys;
 namespace {
 
 const char *g_static_err = "invalid handle";
+thread_local std::string g_thread_err;
 
 int fail(lbe_handle *h, int code, const std::string &msg) {
   if (h) h->err = msg;
@@ -122,6 +123,10 @@ void set_constants(lbe_handle *h) {
 
 }  // namespace
 
+namespace lbe {
+void set_static_error(const char *msg) { g_thread_err = msg; }
+}  // namespace lbe
+
 extern "C" {
 
 void lbe_default_params(lbe_params *p) {
@@ -142,7 +147,10 @@ void lbe_default_params(lbe_params *p) {
   p->poisson_max_iter = 100000;
 }
 
-const char *lbe_last_error(const lbe_handle *h) { return h ? h->err.c_str() : g_static_err; }
+const char *lbe_last_error(const lbe_handle *h) {
+  if (h) return h->err.c_str();
+  return g_thread_err.empty() ? g_static_err : g_thread_err.c_str();
+}
 
 int lbe_create(const lbe_params *p, void *cuda_stream, lbe_handle **out) {
   if (!p || !out) return LBE_ERR_ARG;

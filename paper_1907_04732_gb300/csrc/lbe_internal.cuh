@@ -300,6 +300,8 @@ int poisson_enqueue(lbe_handle *h, bool extrapolate);
 int poisson_status(lbe_handle *h, lbe_stats *st, long long *kernels);
 cudaError_t poisson_reset_stats(lbe_handle *h);
 void poisson_drop_graphs(lbe_handle *h);
+// lbe_api.cu: message returned by lbe_last_error(NULL) (thread-local)
+void set_static_error(const char *msg);
 // mg.cu
 cudaError_t mg_setup(lbe_handle *h);
 void mg_free(lbe_handle *h);

@@ -36,7 +36,7 @@ VELOCITIES = [(0, 0, 0)] + _HALF + [(-a, -b, -c) for (a, b, c) in _HALF]
 EXPORTED = ["lbe_default_params", "lbe_create", "lbe_destroy", "lbe_last_error", "lbe_set_geometry",
             "lbe_set_voltage", "lbe_init", "lbe_step", "lbe_induced_charge", "lbe_fields",
             "lbe_set_state", "lbe_save_state", "lbe_load_state", "lbe_get_stats",
-            "lbe_profile_begin", "lbe_profile_end"]
+            "lbe_profile_begin", "lbe_profile_end", "lbe_induced_charge_static"]
 
 
 class lbe_params(ctypes.Structure):
@@ -96,6 +96,8 @@ def load(path: str = LIB_PATH):
     lib.lbe_get_stats.argtypes = [vp, ctypes.POINTER(lbe_stats)]
     lib.lbe_profile_begin.argtypes = [vp]
     lib.lbe_profile_end.argtypes = [vp, ctypes.POINTER(lbe_profile)]
+    lib.lbe_induced_charge_static.argtypes = [vp, vp, ip, ip, ip, ctypes.POINTER(ctypes.c_int), ctypes.c_double,
+                                              ip, vp, vp]
     for name in EXPORTED:
         if name not in ("lbe_default_params", "lbe_last_error"):
             getattr(lib, name).restype = ctypes.c_int
@@ -180,6 +182,16 @@ def lbe_profile_end(h) -> lbe_profile:
     out = lbe_profile()
     _check(h, load().lbe_profile_end(h, ctypes.byref(out)))
     return out
+
+
+def lbe_induced_charge_static(phi_ptr: int, node_id_ptr: int, shape, periodic, bjerrum: float,
+                              n_electrodes: int, q_out_ptr: int, stream: int = 0):
+    """Induced charges from caller-owned device buffers; allocates nothing."""
+    per = (ctypes.c_int * 3)(*[int(bool(p)) for p in periodic])
+    rc = load().lbe_induced_charge_static(phi_ptr, node_id_ptr, int(shape[0]), int(shape[1]), int(shape[2]),
+                                          per, float(bjerrum), int(n_electrodes), q_out_ptr,
+                                          ctypes.c_void_p(stream or None))
+    return _check(None, rc)
 
 
 # --- convenience wrapper ---------------------------------------------------
