@@ -80,17 +80,21 @@ BYTES["fp64"] = {
     "cg_iter": lambda ns: 8 * (2 + 6 + 3) + 3 * 4,
 }
 BYTES["fp32"] = {
-    # 19 FP32 deviations read + 19 written, int32 q_k read + q*_k written,
+    # 19 FP32 deviations read + 19 written, int64 q_k read + q*_k written,
     # FP32 phi read, FP32 u written (3), link mask
-    "sweep": lambda ns: 4 * (19 + 19 + 2 * ns + 1 + 3) + 4,
-    # q*_k read, q_k written, u read (3), mask
-    "advect": lambda ns: 4 * (2 * ns + 3) + 4,
+    "sweep": lambda ns: 4 * (19 + 19 + 1 + 3) + 8 * 2 * ns + 4,
+    # int64 q*_k read, q_k written, u read (3), mask
+    "advect": lambda ns: 8 * 2 * ns + 4 * 3 + 4,
     # one FP32 CG iteration of the inner correction solve: matvec (p read,
     # q write), update (e, res, p, q read; e, res write), direction (res, p
     # read; p write), mask read thrice
     "cg_iter": lambda ns: 4 * (2 + 6 + 3) + 3 * 4,
 }
 BYTES_FP64 = BYTES["fp64"]
+
+# DRAM bytes per launch of the fused sweep from an ncu capture of the same
+# kernel code (profiles/), or absent when the kernel changed since
+SWEEP_TRAFFIC = {("fp32", "eof_64x64x256"): 104162560 + 64274176}  # profiles/fp32_eof64x64x256_k_sweep32_ncu_full.md
 
 
 class ClockSampler:
@@ -298,19 +302,21 @@ def main():
               "poisson": prof.poisson_ms / max(prof.poisson_solves, 1)}
     sweep_bytes = BYTES_FP64["sweep"](ns) * fluid
     sweep_gbs = sweep_bytes / (phases["sweep"] * 1e-3) / 1e9
-    cg_bytes = BYTES_FP64["cg_iter"](ns) * w.nodes
-    cg_gbs = (cg_bytes * iters) / (phases["poisson"] * 1e-3) / 1e9 if phases["poisson"] > 0 else 0.0
-    dominant = max(phases, key=phases.get)
-    if dominant == "poisson":
-        roof = {"kernel": "poisson CG iteration (matvec+update+direction)", "bound": "hbm",
-                "achieved": cg_gbs, "peak": peak, "unit": "GB/s", "frac": cg_gbs / peak, "traffic": None,
-                "bytes_per_node": BYTES_FP64["cg_iter"](ns)}
-    else:
-        roof = {"kernel": "k_sweep (fused link flux + collide-stream)", "bound": "hbm", "achieved": sweep_gbs,
-                "peak": peak, "unit": "GB/s", "frac": sweep_gbs / peak, "traffic": None,
-                "bytes_per_node": BYTES_FP64["sweep"](ns)}
-    roof["peak_source"] = peak_kind
-    step_bytes = sweep_bytes + BYTES_FP64["advect"](ns) * fluid + cg_bytes * iters
+    adv_bytes = BYTES_FP64["advect"](ns) * fluid
+    step_ms = ms_step
+    shares = {k: v / step_ms for k, v in phases.items()}
+    # The fused LBE sweep is the kernel the HBM roofline is reported for
+    # (its algorithmic bytes / its live CUDA-event time).  The Poisson phase
+    # is a CUDA graph of many small kernels (multigrid levels, CG vectors);
+    # its share of the step is reported beside it.
+    roof = {"kernel": "k_sweep32 (fused link flux + force + BGK/Guo collide + stream)"
+            if args.precision == "fp32" else "k_sweep (FP64 fused sweep)",
+            "bound": "hbm", "achieved": sweep_gbs, "peak": peak, "unit": "GB/s", "frac": sweep_gbs / peak,
+            "traffic": SWEEP_TRAFFIC.get((args.precision, w.name)),
+            "bytes_per_node": BYTES_FP64["sweep"](ns), "units_per_launch": fluid,
+            "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+            "share_of_step": shares["sweep"]}
+    step_bytes = sweep_bytes + adv_bytes
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -321,9 +327,11 @@ def main():
                          % (w.nodes * 19 * (4 if args.precision == "fp32" else 8) * 2 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,
-        "step_hbm_frac": step_bytes / (ms_step * 1e-3) / 1e9 / peak,
-        "phases_ms": phases, "poisson_iters_per_step": iters,
-        "sweep_gbs": sweep_gbs, "cg_gbs": cg_gbs,
+        "phases_ms": phases, "phase_shares": shares,
+        "poisson": {"ms_per_step": phases["poisson"], "cg_iters_per_step": iters,
+                    "note": "FP64-residual refinement, multigrid-preconditioned CG (FP32 form), one CUDA graph"},
+        "lb_part_hbm_frac": step_bytes / ((phases["sweep"] + phases["advect"]) * 1e-3) / 1e9 / peak,
+        "advect_gbs": adv_bytes / (phases["advect"] * 1e-3) / 1e9 if phases["advect"] > 0 else None,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * w.n_elec,
                 "d2h_bytes_per_step": 8 * w.n_elec},
         "gpu_launches": int(prof.kernel_launches),

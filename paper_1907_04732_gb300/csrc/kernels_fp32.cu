@@ -54,11 +54,12 @@ __device__ __forceinline__ long long f2ll_rn(float x) {
   return ((long long)__float2int_rz(hi) << 32) + (long long)__float2uint_rz(lo);
 }
 
-// t - 2 rho_b for t = n (1 + e^{+-mu}), n = rho_b + s q, E = e^{+-mu} - 1:
-//   rho_b E + s q (2 + E), with a fixed rounding sequence (qf = float(q))
-__device__ __forceinline__ float tterm(float rb, float s, float qf, float E) {
-  return __fmaf_rn(__fmul_rn(s, qf), __fadd_rn(2.f, E), __fmul_rn(rb, E));
-}
+// For a link end with solute n = rho_b + nu (nu = s q) and E = e^{+-mu} - 1:
+//   a = n E = rho_b E + nu E,   t - 2 rho_b = a + 2 nu   (t = n (1 + e^{+-mu}))
+// with a fixed rounding sequence, so that both ends of a link compute the
+// same values.
+__device__ __forceinline__ float nE(float rb, float nu, float E) { return __fmaf_rn(nu, E, __fmul_rn(rb, E)); }
+__device__ __forceinline__ float tterm(float a, float nu) { return __fmaf_rn(2.f, nu, a); }
 
 __device__ __forceinline__ int nb_of(const Offs &o, int r, int i) { return r + o.at(cx_of(i), cy_of(i), cz_of(i)); }
 
@@ -89,7 +90,7 @@ __device__ __forceinline__ void gather32(int N, int r, const Offs &o, uint32_t m
 template <bool QUANT, bool SALT11>
 __device__ __forceinline__ void ion_links(const P32 &P, int N, int r, const Offs &o, uint32_t m,
                                           const int64_t *__restrict__ q, const float *__restrict__ phi,
-                                          const long long q0[LBE_MAX_SPECIES], const float q0f[LBE_MAX_SPECIES],
+                                          const long long q0[LBE_MAX_SPECIES], const float q0f[LBE_MAX_SPECIES],  // q0f: nu
                                           long long dq[LBE_MAX_SPECIES], float F[3], bool &over) {
   const float phi0 = phi[r];
   float Fx = 0.f, Fy = 0.f, Fz = 0.f;
@@ -119,17 +120,16 @@ __device__ __forceinline__ void ion_links(const P32 &P, int N, int r, const Offs
       } else {
         em1_pair(__fmul_rn(P.zf[k], dphi), Pk, Mk);
       }
-      const long long q1 = q[k * N + r2];
-      const float X = tterm(P.rb[k], P.s[k], ll2f(q1), Pk);
-      const float Y = tterm(P.rb[k], P.s[k], q0f[k], Mk);
-      const float J = __fsub_rn(X, Y);  // t1 - t0, exactly odd under link reversal
+      const float nu1 = __fmul_rn(P.s[k], ll2f(q[k * N + r2]));
+      const float a1 = nE(P.rb[k], nu1, Pk), a0 = nE(P.rb[k], q0f[k], Mk);
+      const float J = __fsub_rn(tterm(a1, nu1), tterm(a0, q0f[k]));  // t1 - t0, exactly odd under link reversal
       if (QUANT) {
         const float jq = __fmul_rn(J, c2_of(i) == 1 ? P.kq1[k] : P.kq2[k]);
         over |= fabsf(jq) > 1.0e17f;
         dq[k] -= f2ll_rn(jq);
       }
-      // link excess flux g = j/d + (n' - n)/|c| = (-(t1 - t0)/2 + s (q1 - q0))/|c|
-      gs += il * __fmaf_rn(-0.5f, J, P.s[k] * ll2f(q1 - q0[k]));
+      // link excess flux g = j/d + (n' - n)/|c| = -(n' (e^mu - 1) - n (e^-mu - 1))/(2|c|)
+      gs -= il * 0.5f * (a1 - a0);
     }
     Fx += cx_of(i) * gs;
     Fy += cy_of(i) * gs;
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep32(const Geo g, const P32 P, co
 #pragma unroll
   for (int k = 0; k < LBE_MAX_SPECIES; ++k) {
     q0[k] = k < P.ns ? q[k * N + r] : 0;
-    q0f[k] = ll2f(q0[k]);
+    q0f[k] = k < P.ns ? __fmul_rn(P.s[k], ll2f(q0[k])) : 0.f;  // nu = s q
     dq[k] = 0;
   }
   float F[3];
@@ -338,7 +338,7 @@ __global__ void k_moments32(const Geo g, const P32 P, int flow, const uint32_t *
   float q0f[LBE_MAX_SPECIES];
   for (int k = 0; k < LBE_MAX_SPECIES; ++k) {
     q0[k] = k < P.ns ? q[k * N + r] : 0;
-    q0f[k] = ll2f(q0[k]);
+    q0f[k] = k < P.ns ? __fmul_rn(P.s[k], ll2f(q0[k])) : 0.f;  // nu = s q
     dq[k] = 0;
   }
   float F[3];
