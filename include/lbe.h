@@ -194,6 +194,62 @@ typedef struct {
 int lbe_profile_begin(lbe_handle *h);
 int lbe_profile_end(lbe_handle *h, lbe_profile *out);
 
+/* ------------------------------------------------------------------------
+ * Batched FP32 form: many independent lattices ("instances", each with its
+ * own size, geometry, voltages, Debye length and diffusivities) advanced
+ * together.  The instances' state is concatenated in device memory; every
+ * kernel of a step is one persistent launch over all instances (tiles of 256
+ * consecutive nodes of one instance), and a whole step -- fused flux and
+ * collide-stream sweep, advection, Poisson solve with per-instance
+ * convergence -- runs as one CUDA graph launch.  The arithmetic per node is
+ * that of LBE_FP32 on a single lattice; results match a single-lattice
+ * LBE_FP32 run of each instance up to the Poisson stopping point.
+ *
+ * Restrictions: precision LBE_FP32; a 1:1 monovalent salt (nspecies 2,
+ * z = +1, -1, equal rho_bulk); flow, poisson_tol and poisson_max_iter equal
+ * for all instances; at most LBE_BATCH_MAX_ELECTRODES electrodes per
+ * instance; total node count < 2^31.  Other violations return LBE_ERR_ARG.
+ * ------------------------------------------------------------------------ */
+#define LBE_BATCH_MAX_ELECTRODES 4
+typedef struct lbe_batch lbe_batch;
+
+/* Create a batch of n instances from params[0..n-1] (host).  cuda_stream as
+ * for lbe_create (NULL: the batch creates and owns a stream). */
+int lbe_batch_create(const lbe_params *params, int n, void *cuda_stream, lbe_batch **out);
+int lbe_batch_destroy(lbe_batch *b);
+/* Message of the last error on b (or for b == NULL). */
+const char *lbe_batch_last_error(const lbe_batch *b);
+/* Geometry of instance i: node_id host, N_i bytes, as lbe_set_geometry. */
+int lbe_batch_set_geometry(lbe_batch *b, int i, const uint8_t *node_id, int n_electrodes);
+/* Potentials of instance i's electrodes: psi host, n_electrodes doubles.
+ * Before lbe_batch_init (LBE_ERR_STATE after). */
+int lbe_batch_set_voltage(lbe_batch *b, int i, const double *psi);
+/* Equilibrium start of every instance (as lbe_init), the persistent grid
+ * picked by timing candidate grids (autotuner), and the first Poisson
+ * solves.  Every instance needs a geometry first. */
+int lbe_batch_init(lbe_batch *b);
+/* nsteps time steps of every instance; synchronises once at the end to read
+ * the Poisson status (LBE_ERR_NOCONVERGE / LBE_ERR_NONFINITE if any
+ * instance failed). */
+int lbe_batch_step(lbe_batch *b, int nsteps);
+/* Induced charge of every electrode of every instance (Eq. of the induced
+ * charge, FP64 reductions in a fixed order): q_out receives
+ * n * LBE_BATCH_MAX_ELECTRODES doubles, [i][e], zero past an instance's
+ * electrode count; host or device memory by out_on_device. */
+int lbe_batch_charge(lbe_batch *b, double *q_out, int out_on_device);
+/* Field of instance i: LBE_FIELD_PHI (N_i doubles) or LBE_FIELD_N
+ * (2*N_i doubles), layout as lbe_fields. */
+int lbe_batch_fields(lbe_batch *b, int i, int which, double *out, int out_on_device);
+/* lbe_stats of the last init/step call; poisson_iters sums CG iterations
+ * over instances, poisson_max_iters is the most iterations of one solve of
+ * one instance. */
+int lbe_batch_get_stats(const lbe_batch *b, lbe_stats *out);
+/* Autotuner outcome: the persistent grid (blocks) in use, and the measured
+ * sweep time (ms) of each of the LBE_BATCH_TUNE_CANDIDATES candidate grids
+ * of k * SM-count blocks, k = 1, 2, 3, 4, 6, 8 (ms_out may be NULL). */
+#define LBE_BATCH_TUNE_CANDIDATES 6
+int lbe_batch_tuning(const lbe_batch *b, int *grid_blocks, double *ms_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,239 @@
+// Per-node device code of the FP32 form, shared by the single-lattice
+// kernels (kernels_fp32.cu) and the batched kernels (batch.cu).  Arrays are
+// SoA with component stride N; r is a node's index and o its neighbour
+// offsets.
+#pragma once
+
+#include "lbe_internal.cuh"
+
+namespace lbe {
+namespace fp32 {
+
+// P = e^x - 1 and M = e^-x - 1.  For |x| <= 1/4 from the Taylor series of
+// sinh and cosh - 1 (odd and even parts: P = ch + sh, M = ch - sh), so that
+// the pair for -x is exactly (M, P); beyond that from expm1f on x and -x,
+// which has the same property.  Truncation error < 1e-10 relative.
+__device__ __forceinline__ void em1_pair(float x, float &P, float &M) {
+  if (fabsf(x) <= 0.25f) {
+    const float x2 = x * x;
+    const float sh = x * (1.f + x2 * (1.f / 6.f) * (1.f + x2 * (1.f / 20.f) * (1.f + x2 * (1.f / 42.f))));
+    const float ch = x2 * 0.5f * (1.f + x2 * (1.f / 12.f) * (1.f + x2 * (1.f / 30.f) * (1.f + x2 * (1.f / 56.f))));
+    P = __fadd_rn(ch, sh);
+    M = __fsub_rn(ch, sh);
+  } else {
+    P = expm1f(x);
+    M = expm1f(-x);
+  }
+}
+
+// 64-bit integer <-> float with 32-bit conversions only.  Deterministic, and
+// f2ll_rn(-x) = -f2ll_rn(x).
+__device__ __forceinline__ float ll2f(long long v) {
+  const int lo = (int)v;
+  if ((long long)lo == v) return (float)lo;  // fits 32 bits: one conversion
+  return __fmaf_rn((float)(int)(v >> 32), 4294967296.f, (float)(unsigned)v);
+}
+// nearest integer (ties to even) of x, |x| < 2^62
+__device__ __forceinline__ long long f2ll_rn(float x) {
+  const float r = rintf(x);
+  if (fabsf(r) < 2147483648.f) return (long long)__float2int_rn(r);
+  const float hi = floorf(r * (1.f / 4294967296.f));
+  const float lo = r - hi * 4294967296.f;  // exact: a multiple of ulp(r) below 2^32
+  return ((long long)__float2int_rz(hi) << 32) + (long long)__float2uint_rz(lo);
+}
+
+// For a link end with solute n = rho_b + nu (nu = s q) and E = e^{+-mu} - 1:
+//   a = n E = rho_b E + nu E,   t - 2 rho_b = a + 2 nu   (t = n (1 + e^{+-mu}))
+// with a fixed rounding sequence, so that both ends of a link compute the
+// same values.
+__device__ __forceinline__ float nE(float rb, float nu, float E) { return __fmaf_rn(nu, E, __fmul_rn(rb, E)); }
+__device__ __forceinline__ float tterm(float a, float nu) { return __fmaf_rn(2.f, nu, a); }
+
+__device__ __forceinline__ int nb_of(const Offs &o, int r, int i) { return r + o.at(cx_of(i), cy_of(i), cz_of(i)); }
+
+// pull streaming with halfway bounce-back (see kernels_fp64.cu)
+__device__ __forceinline__ void gather32(int N, int r, const Offs &o, uint32_t m, const float *__restrict__ fin,
+                                         float f[kQ]) {
+  f[0] = fin[r];
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    const int io = opp_of(i);
+    // component offsets in 64 bits: 19 components of a large lattice pass 2^31
+    f[i] = (m & (1u << (io - 1))) ? fin[(long long)i * N + nb_of(o, r, io)] : fin[(long long)io * N + r];
+  }
+}
+
+// Ion part of the step at one fluid node: quantised link fluxes -> dq, and
+// the solvent force from the link excess fluxes.
+template <bool QUANT, bool SALT11>
+__device__ __forceinline__ void ion_links(const P32 &P, int N, int r, const Offs &o, uint32_t m,
+                                          const int64_t *__restrict__ q, const float *__restrict__ phi,
+                                          const long long q0[LBE_MAX_SPECIES], const float q0f[LBE_MAX_SPECIES],  // q0f: nu
+                                          long long dq[LBE_MAX_SPECIES], float F[3], bool &over) {
+  const float phi0 = phi[r];
+  float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    if (!(m & (1u << (i - 1)))) continue;
+    const int r2 = nb_of(o, r, i);
+    // exactly antisymmetric potential difference along the link
+    const float dphi = __fsub_rn(__fsub_rn(phi[r2], phi0), P.ec[i]);
+    float P1, M1;
+    em1_pair(dphi, P1, M1);
+    const float il = (float)invlen_of(i);
+    float gs = 0.f;
+#pragma unroll
+    for (int k = 0; k < (SALT11 ? 2 : LBE_MAX_SPECIES); ++k) {
+      if (!SALT11 && k >= P.ns) break;
+      float Pk, Mk;
+      if (SALT11) {  // z = +1, -1
+        Pk = k == 0 ? P1 : M1;
+        Mk = k == 0 ? M1 : P1;
+      } else if (P.zi[k] == 1) {
+        Pk = P1;
+        Mk = M1;
+      } else if (P.zi[k] == -1) {
+        Pk = M1;
+        Mk = P1;
+      } else {
+        em1_pair(__fmul_rn(P.zf[k], dphi), Pk, Mk);
+      }
+      const float nu1 = __fmul_rn(P.s[k], ll2f(q[k * N + r2]));
+      const float a1 = nE(P.rb[k], nu1, Pk), a0 = nE(P.rb[k], q0f[k], Mk);
+      const float J = __fsub_rn(tterm(a1, nu1), tterm(a0, q0f[k]));  // t1 - t0, exactly odd under link reversal
+      if (QUANT) {
+        const float jq = __fmul_rn(J, c2_of(i) == 1 ? P.kq1[k] : P.kq2[k]);
+        over |= fabsf(jq) > 1.0e17f;
+        dq[k] -= f2ll_rn(jq);
+      }
+      // link excess flux g = j/d + (n' - n)/|c| = -(n' (e^mu - 1) - n (e^-mu - 1))/(2|c|)
+      gs -= il * 0.5f * (a1 - a0);
+    }
+    Fx += cx_of(i) * gs;
+    Fy += cy_of(i) * gs;
+    Fz += cz_of(i) * gs;
+  }
+  F[0] = Fx * P.inv_2a0;
+  F[1] = Fy * P.inv_2a0;
+  F[2] = Fz * P.inv_2a0;
+}
+
+// fraction of a unit cell displaced by u that overlaps the cell at offset s
+__device__ __forceinline__ float ov(int s, float u) {
+  return s == 0 ? 1.f - fabsf(u) : (s > 0 ? fmaxf(u, 0.f) : fmaxf(-u, 0.f));
+}
+
+__host__ __device__ constexpr int dir_bit(int dx, int dy, int dz) {
+  if (dx != 0 && dy != 0 && dz != 0) return corner_bit(dx, dy, dz);
+  for (int i = 1; i < kQ; ++i)
+    if (cx_of(i) == dx && cy_of(i) == dy && cz_of(i) == dz) return i - 1;
+  return -1;
+}
+
+// integer share (fixed-point units) of a node's total solute 2^40 + q that its
+// displaced cell hands to the neighbour at offset s
+__device__ __forceinline__ long long share(float totf, float ux, float uy, float uz, int sx, int sy, int sz) {
+  const float w = ov(sx, ux) * ov(sy, uy) * ov(sz, uz);
+  return w == 0.f ? 0LL : f2ll_rn(__fmul_rn(w, totf));
+}
+
+
+// Fused step at one fluid node: quantised link fluxes and q* = q - sum Jq,
+// solvent force, and (FLOW) BGK + Guo collision with pull streaming.
+template <bool FLOW, bool SALT11>
+__device__ __forceinline__ void sweep_node(const P32 &P, int N, int r, const Offs &o, uint32_t m,
+                                           const float *__restrict__ fin, float *__restrict__ fout,
+                                           const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
+                                           const float *__restrict__ phi, float *__restrict__ u, bool &over) {
+  long long q0[LBE_MAX_SPECIES], dq[LBE_MAX_SPECIES];
+  float q0f[LBE_MAX_SPECIES];
+#pragma unroll
+  for (int k = 0; k < LBE_MAX_SPECIES; ++k) {
+    q0[k] = k < P.ns ? q[k * N + r] : 0;
+    q0f[k] = k < P.ns ? __fmul_rn(P.s[k], ll2f(q0[k])) : 0.f;  // nu = s q
+    dq[k] = 0;
+  }
+  float F[3];
+  ion_links<true, SALT11>(P, N, r, o, m, q, phi, q0, q0f, dq, F, over);
+  for (int k = 0; k < (SALT11 ? 2 : P.ns); ++k) qstar[k * N + r] = q0[k] + dq[k];
+  if (!FLOW) return;
+
+  float f[kQ];
+  gather32(N, r, o, m, fin, f);
+  float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    drho += f[i];
+    jx += cx_of(i) * f[i];
+    jy += cy_of(i) * f[i];
+    jz += cz_of(i) * f[i];
+  }
+  const float rho = 1.f + drho;
+  const float inv_rho = 1.f / rho;
+  const float ux = (jx + 0.5f * F[0]) * inv_rho, uy = (jy + 0.5f * F[1]) * inv_rho, uz = (jz + 0.5f * F[2]) * inv_rho;
+  u[r] = ux;
+  u[N + r] = uy;
+  u[2 * N + r] = uz;
+  const float uu = ux * ux + uy * uy + uz * uz;
+  const float uF = ux * F[0] + uy * F[1] + uz * F[2];
+  // BGK + Guo forcing; c_{i+9} = -c_i, so each opposite pair shares the even
+  // part of the equilibrium and of the source and flips the odd part
+  {
+    const float w = (float)w_of(0);
+    const float eq = w * (drho - rho * 1.5f * uu);
+    const float src = -P.guo * w * 3.f * uF;
+    fout[r] = f[0] - P.omega * (f[0] - eq) + src;
+  }
+#pragma unroll
+  for (int i = 1; i <= 9; ++i) {
+    const float w = (float)w_of(i);
+    const float cu = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
+    const float cF = cx_of(i) * F[0] + cy_of(i) * F[1] + cz_of(i) * F[2];
+    const float eq_even = w * (drho + rho * (4.5f * cu * cu - 1.5f * uu));
+    const float eq_odd = w * rho * 3.f * cu;
+    const float src_even = P.guo * w * (9.f * cu * cF - 3.f * uF);
+    const float src_odd = P.guo * w * 3.f * cF;
+    const int io = i + 9;
+    fout[(long long)i * N + r] = f[i] - P.omega * (f[i] - (eq_even + eq_odd)) + (src_even + src_odd);
+    fout[(long long)io * N + r] = f[io] - P.omega * (f[io] - (eq_even - eq_odd)) + (src_even - src_odd);
+  }
+}
+
+// Cell-overlap advection at one fluid node (see k_advect32).
+__device__ __forceinline__ void advect_node(int ns, int N, int r, const Offs &o, uint32_t m,
+                                            const int64_t *__restrict__ qin, const float *__restrict__ u,
+                                            int64_t *__restrict__ qout) {
+  const float ux = u[r], uy = u[N + r], uz = u[2 * N + r];
+  const long long base = 1LL << kFixBits;
+  long long acc[LBE_MAX_SPECIES];
+  float totf[LBE_MAX_SPECIES];
+  for (int k = 0; k < ns; ++k) {
+    acc[k] = base + qin[k * N + r];
+    totf[k] = ll2f(acc[k]);
+  }
+  // outgoing (the share is zero outside the octant of u); shares bound for
+  // solid neighbours stay
+#pragma unroll
+  for (int d = 0; d < 27; ++d) {
+    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+    if (d == 13 || !(m & (1u << dir_bit(dx, dy, dz)))) continue;
+    if ((dx && dx * ux <= 0.f) || (dy && dy * uy <= 0.f) || (dz && dz * uz <= 0.f)) continue;
+    for (int k = 0; k < ns; ++k) acc[k] -= share(totf[k], ux, uy, uz, dx, dy, dz);
+  }
+  // incoming from every fluid neighbour whose cell reaches r: the source at
+  // r - s gives along +s
+#pragma unroll
+  for (int d = 0; d < 27; ++d) {
+    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+    if (d == 13 || !(m & (1u << dir_bit(-dx, -dy, -dz)))) continue;
+    const int s = r + o.at(-dx, -dy, -dz);
+    const float vx = u[s], vy = u[N + s], vz = u[2 * N + s];
+    const float w = ov(dx, vx) * ov(dy, vy) * ov(dz, vz);
+    if (w == 0.f) continue;
+    for (int k = 0; k < ns; ++k) acc[k] += share(ll2f(base + qin[k * N + s]), vx, vy, vz, dx, dy, dz);
+  }
+  for (int k = 0; k < ns; ++k) qout[k * N + r] = acc[k] - base;
+}
+
+}  // namespace fp32
+}  // namespace lbe

@@ -71,7 +71,12 @@ cudaError_t mark(lbe_handle *h) {
   return cudaEventRecord(e, h->stream);
 }
 
-void set_constants(lbe_handle *h) {
+}  // namespace
+
+namespace lbe {
+void set_static_error(const char *msg) { g_thread_err = msg; }
+
+void fill_constants(lbe_handle *h) {
   const lbe_params *p = &h->prm;
   Phys &P = h->phys;
   memset(&P, 0, sizeof(P));
@@ -120,11 +125,6 @@ void set_constants(lbe_handle *h) {
   Q.guo = (float)P.guo;
   Q.inv_2a0 = (float)P.inv_2a0;
 }
-
-}  // namespace
-
-namespace lbe {
-void set_static_error(const char *msg) { g_thread_err = msg; }
 }  // namespace lbe
 
 extern "C" {
@@ -162,6 +162,8 @@ int lbe_create(const lbe_params *p, void *cuda_stream, lbe_handle **out) {
   if (!(p->poisson_tol > 0.0) || p->poisson_max_iter < 1) return LBE_ERR_ARG;
   const long long N = (long long)p->nx * p->ny * p->nz;
   if (N >= (1LL << 31)) return LBE_ERR_ARG;  // 32-bit node indices in the kernels
+  // FP32 kernels offset solute and velocity components in 32 bits
+  if (p->precision == LBE_FP32 && N * (p->nspecies > 3 ? p->nspecies : 3) >= (1LL << 31)) return LBE_ERR_ARG;
   for (int k = 0; k < p->nspecies; ++k) {
     if (!(p->D[k] >= 0.0) || !(p->rho_bulk[k] >= 0.0)) return LBE_ERR_ARG;
     if (fabs(p->z[k]) > 4.0 || p->z[k] != floor(p->z[k])) return LBE_ERR_ARG;
@@ -174,7 +176,7 @@ int lbe_create(const lbe_params *p, void *cuda_stream, lbe_handle **out) {
   lbe_handle *h = new lbe_handle();
   h->prm = *p;
   h->geo = Geo{p->nx, p->ny, p->nz, p->periodic[0] != 0, p->periodic[1] != 0, p->periodic[2] != 0, N};
-  set_constants(h);
+  lbe::fill_constants(h);
 
   const bool own = cuda_stream == nullptr;
   if (own) {

@@ -302,6 +302,8 @@ cudaError_t poisson_reset_stats(lbe_handle *h);
 void poisson_drop_graphs(lbe_handle *h);
 // lbe_api.cu: message returned by lbe_last_error(NULL) (thread-local)
 void set_static_error(const char *msg);
+// lbe_api.cu: derived constants (Phys, P32) of h->prm
+void fill_constants(lbe_handle *h);
 // mg.cu
 cudaError_t mg_setup(lbe_handle *h);
 void mg_free(lbe_handle *h);

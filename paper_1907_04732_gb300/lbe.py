@@ -36,7 +36,12 @@ VELOCITIES = [(0, 0, 0)] + _HALF + [(-a, -b, -c) for (a, b, c) in _HALF]
 EXPORTED = ["lbe_default_params", "lbe_create", "lbe_destroy", "lbe_last_error", "lbe_set_geometry",
             "lbe_set_voltage", "lbe_init", "lbe_step", "lbe_induced_charge", "lbe_fields",
             "lbe_set_state", "lbe_save_state", "lbe_load_state", "lbe_get_stats",
-            "lbe_profile_begin", "lbe_profile_end", "lbe_induced_charge_static"]
+            "lbe_profile_begin", "lbe_profile_end", "lbe_induced_charge_static",
+            "lbe_batch_create", "lbe_batch_destroy", "lbe_batch_last_error", "lbe_batch_set_geometry",
+            "lbe_batch_set_voltage", "lbe_batch_init", "lbe_batch_step", "lbe_batch_charge",
+            "lbe_batch_fields", "lbe_batch_get_stats", "lbe_batch_tuning"]
+LBE_BATCH_MAX_ELECTRODES = 4
+LBE_BATCH_TUNE_CANDIDATES = 6
 
 
 class lbe_params(ctypes.Structure):
@@ -98,8 +103,20 @@ def load(path: str = LIB_PATH):
     lib.lbe_profile_end.argtypes = [vp, ctypes.POINTER(lbe_profile)]
     lib.lbe_induced_charge_static.argtypes = [vp, vp, ip, ip, ip, ctypes.POINTER(ctypes.c_int), ctypes.c_double,
                                               ip, vp, vp]
+    lib.lbe_batch_create.argtypes = [ctypes.POINTER(lbe_params), ip, vp, ctypes.POINTER(vp)]
+    lib.lbe_batch_destroy.argtypes = [vp]
+    lib.lbe_batch_last_error.argtypes = [vp]
+    lib.lbe_batch_last_error.restype = ctypes.c_char_p
+    lib.lbe_batch_set_geometry.argtypes = [vp, ip, vp, ip]
+    lib.lbe_batch_set_voltage.argtypes = [vp, ip, dp]
+    lib.lbe_batch_init.argtypes = [vp]
+    lib.lbe_batch_step.argtypes = [vp, ip]
+    lib.lbe_batch_charge.argtypes = [vp, vp, ip]
+    lib.lbe_batch_fields.argtypes = [vp, ip, ip, vp, ip]
+    lib.lbe_batch_get_stats.argtypes = [vp, ctypes.POINTER(lbe_stats)]
+    lib.lbe_batch_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp]
     for name in EXPORTED:
-        if name not in ("lbe_default_params", "lbe_last_error"):
+        if name not in ("lbe_default_params", "lbe_last_error", "lbe_batch_last_error"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -192,6 +209,64 @@ def lbe_induced_charge_static(phi_ptr: int, node_id_ptr: int, shape, periodic, b
                                           per, float(bjerrum), int(n_electrodes), q_out_ptr,
                                           ctypes.c_void_p(stream or None))
     return _check(None, rc)
+
+
+def _bcheck(b, rc):
+    if rc != LBE_OK:
+        msg = load().lbe_batch_last_error(b)
+        raise LBEError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def lbe_batch_create(params_list, stream: int = 0) -> int:
+    arr = (lbe_params * len(params_list))(*params_list)
+    b = ctypes.c_void_p()
+    rc = load().lbe_batch_create(arr, len(params_list), ctypes.c_void_p(stream or None), ctypes.byref(b))
+    if rc != LBE_OK:
+        raise LBEError(rc, "lbe_batch_create failed (invalid parameters or CUDA error)")
+    return b.value
+
+
+def lbe_batch_destroy(b):
+    load().lbe_batch_destroy(b)
+
+
+def lbe_batch_set_geometry(b, i: int, node_id_ptr: int, n_electrodes: int):
+    return _bcheck(b, load().lbe_batch_set_geometry(b, i, node_id_ptr, n_electrodes))
+
+
+def lbe_batch_set_voltage(b, i: int, psi):
+    arr = (ctypes.c_double * max(len(psi), 1))(*psi)
+    return _bcheck(b, load().lbe_batch_set_voltage(b, i, arr))
+
+
+def lbe_batch_init(b):
+    return _bcheck(b, load().lbe_batch_init(b))
+
+
+def lbe_batch_step(b, nsteps: int):
+    return _bcheck(b, load().lbe_batch_step(b, int(nsteps)))
+
+
+def lbe_batch_charge(b, out_ptr: int, on_device: bool):
+    return _bcheck(b, load().lbe_batch_charge(b, out_ptr, int(on_device)))
+
+
+def lbe_batch_fields(b, i: int, which: int, out_ptr: int, on_device: bool):
+    return _bcheck(b, load().lbe_batch_fields(b, i, which, out_ptr, int(on_device)))
+
+
+def lbe_batch_get_stats(b) -> lbe_stats:
+    s = lbe_stats()
+    _bcheck(b, load().lbe_batch_get_stats(b, ctypes.byref(s)))
+    return s
+
+
+def lbe_batch_tuning(b):
+    grid = ctypes.c_int(0)
+    ms = (ctypes.c_double * LBE_BATCH_TUNE_CANDIDATES)()
+    _bcheck(b, load().lbe_batch_tuning(b, ctypes.byref(grid), ms))
+    return grid.value, list(ms)
 
 
 # --- convenience wrapper ---------------------------------------------------
@@ -328,3 +403,70 @@ class Lattice:
 
     def profile_end(self) -> lbe_profile:
         return lbe_profile_end(self.h)
+
+
+class Batch:
+    """Many independent FP32 lattices advanced together (owns an lbe_batch)."""
+
+    def __init__(self, workloads, *, tol=1e-12, maxit=100000, stream: int | None = None):
+        import torch
+        self.w = list(workloads)
+        self.params = [params_for(w, precision=LBE_FP32, tol=tol, maxit=maxit) for w in self.w]
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        self.b = lbe_batch_create(self.params, stream)
+        for i, w in enumerate(self.w):
+            a = np.ascontiguousarray(np.asarray(w.ids).reshape(-1), dtype=np.uint8)
+            lbe_batch_set_geometry(self.b, i, a.ctypes.data, w.n_elec)
+            lbe_batch_set_voltage(self.b, i, [float(v) for v in w.psi])
+
+    @property
+    def n(self):
+        return len(self.w)
+
+    @property
+    def nodes(self):
+        return sum(w.nodes for w in self.w)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lbe_batch_destroy(self.b)
+            self.b = None
+
+    __del__ = close
+
+    def init(self):
+        lbe_batch_init(self.b)
+
+    def step(self, nsteps: int = 1):
+        lbe_batch_step(self.b, nsteps)
+
+    def charge(self) -> np.ndarray:
+        """[n, LBE_BATCH_MAX_ELECTRODES] induced charges (zero past n_elec)."""
+        out = np.zeros((self.n, LBE_BATCH_MAX_ELECTRODES))
+        lbe_batch_charge(self.b, out.ctypes.data, False)
+        return out
+
+    def charge_device(self, out):
+        lbe_batch_charge(self.b, out.data_ptr(), True)
+        return out
+
+    def field(self, i: int, which: int) -> np.ndarray:
+        nx, ny, nz = self.w[i].shape
+        shape = (nz, ny, nx) if which == FIELD_PHI else (2, nz, ny, nx)
+        out = np.zeros(shape)
+        lbe_batch_fields(self.b, i, which, out.ctypes.data, False)
+        return out
+
+    def phi(self, i):
+        return self.field(i, FIELD_PHI)
+
+    def n_field(self, i):
+        return self.field(i, FIELD_N)
+
+    def stats(self) -> lbe_stats:
+        return lbe_batch_get_stats(self.b)
+
+    def tuning(self):
+        return lbe_batch_tuning(self.b)

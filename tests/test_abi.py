@@ -55,3 +55,34 @@ def test_default_params_and_argument_checks(lib):
     assert lib.lbe_step(None, 1) == lbe.LBE_ERR_ARG
     assert lib.lbe_last_error(None) == b"invalid handle"
     assert lib.lbe_destroy(None) == lbe.LBE_OK
+
+
+def test_batch_argument_checks(lib):
+    """lbe_batch_create rejects what the batched form does not cover before
+    any CUDA call."""
+    b = ctypes.c_void_p()
+
+    def create(plist):
+        arr = (lbe.lbe_params * len(plist))(*plist)
+        return lib.lbe_batch_create(arr, len(plist), None, ctypes.byref(b))
+
+    def fp32(**kw):
+        q = lbe.lbe_default_params()
+        q.precision = lbe.LBE_FP32
+        q.nx, q.ny, q.nz = 4, 4, 8
+        for k, v in kw.items():
+            setattr(q, k, v)
+        return q
+
+    assert lib.lbe_batch_create(None, 1, None, ctypes.byref(b)) == lbe.LBE_ERR_ARG
+    assert create([fp32(precision=lbe.LBE_FP64)]) == lbe.LBE_ERR_ARG
+    assert create([fp32(nspecies=3)]) == lbe.LBE_ERR_ARG
+    q = fp32()
+    q.rho_bulk[1] = 2 * q.rho_bulk[0]  # not a symmetric 1:1 salt
+    assert create([q]) == lbe.LBE_ERR_ARG
+    assert create([fp32(), fp32(flow=0)]) == lbe.LBE_ERR_ARG
+    assert create([fp32(), fp32(poisson_tol=1e-9)]) == lbe.LBE_ERR_ARG
+    assert create([fp32(nz=0)]) == lbe.LBE_ERR_ARG
+    assert lib.lbe_batch_step(None, 1) == lbe.LBE_ERR_ARG
+    assert lib.lbe_batch_last_error(None) == b"invalid batch"
+    assert lib.lbe_batch_destroy(None) == lbe.LBE_OK
