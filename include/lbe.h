@@ -244,6 +244,13 @@ int lbe_batch_fields(lbe_batch *b, int i, int which, double *out, int out_on_dev
  * over instances, poisson_max_iters is the most iterations of one solve of
  * one instance. */
 int lbe_batch_get_stats(const lbe_batch *b, lbe_stats *out);
+/* Device time per phase of the lbe_batch_step calls made between
+ * lbe_batch_profile_begin and lbe_batch_profile_end (events recorded around
+ * the sweep, the advection and the Poisson solve of every step; each step is
+ * then waited for).  poisson_iters sums CG iterations over instances;
+ * kernel_launches is counted with LBE_POISSON_GRAPH=0 only (else -1). */
+int lbe_batch_profile_begin(lbe_batch *b);
+int lbe_batch_profile_end(lbe_batch *b, lbe_profile *out);
 /* Autotuner outcome: the persistent grid (blocks) in use, and the measured
  * sweep time (ms) of each of the LBE_BATCH_TUNE_CANDIDATES candidate grids
  * of k * SM-count blocks, k = 1, 2, 3, 4, 6, 8 (ms_out may be NULL). */

@@ -2,34 +2,111 @@
 // advanced together (declarations and contracts in include/lbe.h).
 //
 // The instances' arrays are concatenated (component stride = total node
-// count).  Work is cut into tiles of kBlock consecutive nodes of one instance;
-// every kernel is a persistent launch whose blocks stride over the tile list,
-// so one launch covers all instances whatever their sizes.  The per-node
-// physics is the single-lattice FP32 code (fp32_device.cuh).  The Poisson
-// solve is the same iterative refinement with a Chronopoulos-Gear CG, batched:
-// every instance has its own scalars and its own convergence test, and the
-// nested device-side while loops of the solve run while any instance is
-// still working.  Reductions are per instance and in a fixed order.
+// count).  Work is cut into tiles of kTile consecutive nodes of one instance;
+// every kernel is a persistent launch whose blocks stride over a tile list,
+// so one launch covers all instances whatever their sizes, and a whole step
+// is one CUDA graph launch.  The per-node physics is the single-lattice FP32
+// code (fp32_device.cuh).
+//
+// The Poisson solve is the single-lattice iterative refinement with a
+// Chronopoulos-Gear CG preconditioned by a multigrid V-cycle (mg_device.cuh),
+// batched: every instance has its own scalars, hierarchy and convergence
+// test, and the nested device-side while loops run while any instance is
+// still working.  Instances converge after different iteration counts, so
+// the CG and V-cycle kernels walk only the tiles of instances still
+// iterating: after every convergence test the test kernel's last block
+// rebuilds, per tile list, the prefix sums of the active instances' tile
+// counts, and a block finds the instance of its k-th active tile by binary
+// search.  Reductions are per instance and in a fixed order, so results do
+// not depend on the launch shape.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
 #include "fp32_device.cuh"
+#include "mg_device.cuh"
 
 constexpr int kBE = LBE_BATCH_MAX_ELECTRODES;  // electrodes per instance
 
 namespace lbe {
 
+// Division of unsigned 32-bit integers by a run-time invariant divisor d >= 1
+// by a multiplication and shifts (Granlund and Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994, Sec. 4): with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// q = (t + ((n - t) >> min(l,1))) >> max(l-1,0), t = high word of m n.
+struct FastDiv {
+  uint32_t d, m;
+  int sh1, sh2;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  FastDiv f;
+  f.d = d;
+  f.m = (uint32_t)(((((uint64_t)1 << l) - d) << 32) / d + 1);
+  f.sh1 = l < 1 ? l : 1;
+  f.sh2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+
+__host__ __device__ __forceinline__ uint32_t fdiv(const FastDiv &f, uint32_t n) {
+#ifdef __CUDA_ARCH__
+  const uint32_t t = __umulhi(f.m, n);
+#else
+  const uint32_t t = (uint32_t)(((uint64_t)f.m * n) >> 32);
+#endif
+  return (t + ((n - t) >> f.sh1)) >> f.sh2;
+}
+
+// host check of a divisor on the values around every multiple boundary that
+// matters for indices below nmax, and a spread of others
+inline bool fastdiv_ok(const FastDiv &f, uint32_t nmax) {
+  const uint32_t d = f.d;
+  for (uint64_t k = 0; k * d <= (uint64_t)nmax + d && k < 70000; ++k)
+    for (int64_t o = -1; o <= 1; ++o) {
+      const int64_t n = (int64_t)(k * d) + o;
+      if (n < 0 || n > (int64_t)nmax) continue;
+      if (fdiv(f, (uint32_t)n) != (uint32_t)n / d) return false;
+    }
+  for (uint64_t n = 0; n <= nmax; n += 1 + nmax / 4096)
+    if (fdiv(f, (uint32_t)n) != (uint32_t)n / d) return false;
+  return true;
+}
+
+constexpr int kTile = 1024;           // nodes per tile
+constexpr int kSub = kTile / kBlock;  // nodes per thread per tile
+
 struct InstDev {
-  Geo g;             // this instance's lattice
-  int off;           // first node in the batch arrays
-  int tile0, ntiles; // its tiles in the tile list
+  Geo g;              // this instance's lattice
+  int off;            // first node in the batch arrays
+  int tile0, ntiles;  // its tiles in the level-0 tile list
   int n_elec;
   uint32_t selfmask;
+  int mg_levels;      // multigrid levels incl. the lattice (0: Jacobi)
+  FastDiv fx, fxy;    // division by nx and by nx*ny
   double four_pi_lb, eps;
   P32 P;
+};
+
+// one multigrid level of one instance: its shape (component stride = the
+// level's total node count), first node in the level arrays, first tile in
+// the level's tile list, tile count
+struct LvSeg {
+  mgd::MgLevel L;
+  int off, tile0, ntiles;
+  FastDiv fx, fxy;  // division by nx and by nx*ny of the level
+};
+
+// device arrays of the coarse levels (index = level; 0 unused)
+struct LvPtrs {
+  float *A[kMaxLevels], *r[kMaxLevels], *e[kMaxLevels];
+  float *z[kMaxLevels];  // pre-smoothed iterate omega r/diag
 };
 
 struct InstCtl {
@@ -42,6 +119,12 @@ struct BatchCtl {
   int arrive;
   int sticky_status;
   long long total_iters, solves, max_iters;
+  int any_outer, any_inner;  // loop conditions, for the host-polled solve
+};
+
+// CG vectors (each Ntot floats)
+struct CgVec {
+  float *r, *u, *w, *x, *p, *s;
 };
 
 }  // namespace lbe
@@ -51,17 +134,17 @@ struct lbe_batch {
   std::vector<lbe_params> prm;
   std::vector<lbe::InstDev> inst;
   std::vector<std::vector<uint8_t>> ids;
-  std::vector<double> psi;  // [n][LBE_BATCH_MAX_ELECTRODES + 1]
+  std::vector<double> psi;  // [n][kBE + 1]
   std::vector<int> have_geometry;
   bool initialised = false;
   bool flow = true;
   long long Ntot = 0;
-  int T = 0;  // tiles
+  int T = 0;  // level-0 tiles
   cudaStream_t stream = nullptr;
   bool owns_stream = false;
   std::string err;
   lbe_stats stats{};
-  int grid = 0;       // persistent grid (blocks), picked by the autotuner
+  int grid = 0;  // persistent grid (blocks), picked by the autotuner
   double tuned_ms[LBE_BATCH_TUNE_CANDIDATES] = {};
   int cur = 0;
   // device
@@ -73,17 +156,42 @@ struct lbe_batch {
   int64_t *q = nullptr, *qstar = nullptr;
   double *phi = nullptr, *phi_prev = nullptr;
   float *phi32 = nullptr, *u = nullptr;
-  float *vec = nullptr;        // CG r, u, w, x, p, s [6][Ntot]
-  double *part = nullptr;      // per-tile partials [3][T]
-  double *psi_d = nullptr;     // [n][3]
+  float *vec = nullptr;     // CG vectors [6][Ntot]
+  double *part = nullptr;   // per-tile partials [3][T]
+  double *psi_d = nullptr;  // [n][kBE + 1]
   lbe::InstCtl *ictl = nullptr;
   lbe::BatchCtl *bctl = nullptr, *bctl_h = nullptr;
   double *qpart = nullptr, *qout = nullptr, *qhost = nullptr;
   int *flag = nullptr;
   int *hist = nullptr;  // device: phi_prev holds the previous solution
-  // step graphs keyed by (populations read, solute read); [4] = solve only
-  cudaGraphExec_t exec[5] = {};
-  const void *key_f[4] = {}, *key_q[4] = {};
+  // tile lists of active instances: family f counts, prefix sums
+  int nfam = 0;
+  int *fam_cnt = nullptr;   // [nfam][n]
+  int *fam_pref = nullptr;  // [nfam][n + 1]
+  // batched multigrid preconditioner
+  int mg_nlev = 0;                       // most levels of any instance
+  long long mg_M[lbe::kMaxLevels] = {};  // nodes per coarse level (all instances)
+  int mg_T[lbe::kMaxLevels] = {};        // tiles per level
+  int mg_tbase[lbe::kMaxLevels] = {};    // level's first entry in mg_tiles
+  int *mg_tiles = nullptr;               // tile -> instance, levels 1.. concatenated
+  lbe::LvSeg *mg_seg = nullptr;          // [kMaxLevels][n]
+  lbe::LvPtrs mg_p{};
+  float *mg_t0 = nullptr;
+  // step graphs keyed by (populations read, solute read); [4] = solve only;
+  // [5..8] step graphs with profiling events
+  cudaGraphExec_t exec[9] = {};
+  const void *key_f[9] = {}, *key_q[9] = {};
+  bool polled = false;  // LBE_POISSON_GRAPH=0: solve loops driven by the host
+  // profiling (lbe_batch_profile_begin/end): events around the phases
+  bool profiling = false;
+  cudaEvent_t ev[4] = {};
+  double prof_ms[3] = {};
+  long long prof_steps = 0, prof_iters = 0, prof_solves = 0, prof_launches = 0;
+
+  lbe::CgVec cg() const {
+    const long long N = Ntot;
+    return lbe::CgVec{vec, vec + N, vec + 2 * N, vec + 3 * N, vec + 4 * N, vec + 5 * N};
+  }
 };
 
 namespace lbe {
@@ -92,19 +200,39 @@ namespace {
 using namespace fp32;
 constexpr int kMaxOuterB = 24;
 
-// node of tile t handled by this thread
-__device__ __forceinline__ bool tile_node(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst, int t,
-                                          int &ii, int &x, int &y, int &z, int &lo) {
-  ii = tile_inst[t];
-  const InstDev &I = inst[ii];
-  lo = (t - I.tile0) * kBlock + threadIdx.x;
+// Families of active-tile lists (index f):
+//   f = l           level-l tiles of instances that have level l (l = 0: all)
+//   f = nlev + l    level-l tiles of instances that have level l+1
+__host__ __device__ constexpr int famA(int l) { return l; }
+__host__ __device__ constexpr int famB(int nlev, int l) { return nlev + l; }
+
+// instance-local coordinates of node lo (false past the instance's end)
+__device__ __forceinline__ bool node_xyz(const InstDev &I, int lo, int &x, int &y, int &z) {
   if (lo >= I.g.N) return false;
-  const int nx = I.g.nx, ny = I.g.ny;
-  x = lo % nx;
-  const int t2 = lo / nx;
-  y = t2 % ny;
-  z = t2 / ny;
+  z = (int)fdiv(I.fxy, (uint32_t)lo);
+  const int rem = lo - z * (int)I.fxy.d;
+  y = (int)fdiv(I.fx, (uint32_t)rem);
+  x = rem - y * I.g.nx;
   return true;
+}
+
+// coordinates of node I of a coarse level
+__device__ __forceinline__ void lv_xyz(const LvSeg &S, int I, int &X, int &Y, int &Z) {
+  Z = (int)fdiv(S.fxy, (uint32_t)I);
+  const int rem = I - Z * (int)S.fxy.d;
+  Y = (int)fdiv(S.fx, (uint32_t)rem);
+  X = rem - Y * S.L.nx;
+}
+
+// instance of the tp-th active tile: pref[i] <= tp < pref[i+1]
+__device__ __forceinline__ int find_inst(const int *__restrict__ pref, int n, int tp) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pref[mid] <= tp) lo = mid;
+    else hi = mid;
+  }
+  return lo;
 }
 
 __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int use, unsigned v) {
@@ -160,18 +288,39 @@ __device__ __forceinline__ bool last_block(int *arrive, int nblk) {
   return last;
 }
 
-__device__ __forceinline__ float diag_f(uint32_t m, uint32_t selfmask) {
-  float dg = 0.f;
-#pragma unroll
-  for (int l = 1; l < kQ; ++l) {
-    const uint32_t b = 1u << (l - 1);
-    if (selfmask & b) continue;
-    dg += (m & b) ? (float)lapc_of(l) : 2.f * (float)lapc_of(l);
+// Prefix sums of the active instances' tile counts for every family; all
+// threads of one block (the last block of a convergence-test kernel, after
+// every instance's inner_done is final)
+__device__ void build_active(const InstCtl *__restrict__ c, int n, int nfam, const int *__restrict__ cnt,
+                             int *__restrict__ pref) {
+  __shared__ int sc[kBlock];
+  const int t = threadIdx.x;
+  const int per = (n + kBlock - 1) / kBlock;
+  const int i0 = t * per, i1 = min(i0 + per, n);
+  for (int f = 0; f < nfam; ++f) {
+    const int *cf = cnt + (long long)f * n;
+    int *pf = pref + (long long)f * (n + 1);
+    int s = 0;
+    for (int i = i0; i < i1; ++i) s += __ldcg(&c[i].inner_done) ? 0 : cf[i];
+    sc[t] = s;
+    __syncthreads();
+    for (int o = 1; o < kBlock; o <<= 1) {  // inclusive scan
+      const int v = t >= o ? sc[t - o] : 0;
+      __syncthreads();
+      sc[t] += v;
+      __syncthreads();
+    }
+    int run = t ? sc[t - 1] : 0;
+    for (int i = i0; i < i1; ++i) {
+      pf[i] = run;
+      run += __ldcg(&c[i].inner_done) ? 0 : cf[i];
+    }
+    if (t == kBlock - 1) pf[n] = sc[t];
+    __syncthreads();
   }
-  return dg;
 }
 
-// --- set-up and step kernels -------------------------------------------------
+// --- set-up and step kernels (all level-0 tiles) ------------------------------
 __global__ void __launch_bounds__(kBlock) kb_init(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
                                                   int T, long long Ntot, const uint8_t *__restrict__ id,
                                                   const double *__restrict__ psi, float *__restrict__ f,
@@ -179,17 +328,21 @@ __global__ void __launch_bounds__(kBlock) kb_init(const InstDev *__restrict__ in
                                                   float *__restrict__ phi32, double *__restrict__ phi_prev,
                                                   float *__restrict__ u) {
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
-    int ii, x, y, z, lo;
-    if (!tile_node(inst, tile_inst, t, ii, x, y, z, lo)) continue;
-    const long long r = inst[ii].off + lo;
-    const int e = id[r];
-    for (int i = 0; i < kQ; ++i) f[i * Ntot + r] = 0.f;
-    for (int k = 0; k < 2; ++k) q[k * Ntot + r] = e ? -(1LL << kFixBits) : 0;
-    const double p = e ? psi[ii * (kBE + 1) + e] : 0.0;
-    phi[r] = p;
-    phi32[r] = (float)p;
-    phi_prev[r] = p;
-    u[r] = u[Ntot + r] = u[2 * Ntot + r] = 0.f;
+    const int ii = tile_inst[t];
+    const InstDev &I = inst[ii];
+    for (int k = 0; k < kSub; ++k) {
+      const int lo = (t - I.tile0) * kTile + k * kBlock + threadIdx.x;
+      if (lo >= I.g.N) break;
+      const long long r = I.off + lo;
+      const int e = id[r];
+      for (int i = 0; i < kQ; ++i) f[i * Ntot + r] = 0.f;
+      for (int s = 0; s < 2; ++s) q[s * Ntot + r] = e ? -(1LL << kFixBits) : 0;
+      const double p = e ? psi[ii * (kBE + 1) + e] : 0.0;
+      phi[r] = p;
+      phi32[r] = (float)p;
+      phi_prev[r] = p;
+      u[r] = u[Ntot + r] = u[2 * Ntot + r] = 0.f;
+    }
   }
 }
 
@@ -202,13 +355,16 @@ __global__ void __launch_bounds__(kBlock) kb_sweep(const InstDev *__restrict__ i
                                                    int *__restrict__ flag) {
   bool over = false;
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
-    int ii, x, y, z, lo;
-    if (!tile_node(inst, tile_inst, t, ii, x, y, z, lo)) continue;
-    const InstDev &I = inst[ii];
-    const int r = I.off + lo;
-    const uint32_t m = mask[r];
-    if (!(m & kFluidBit)) continue;
-    sweep_node<FLOW, true>(I.P, Ntot, r, offsets_of(I.g, x, y, z), m, fin, fout, q, qstar, phi, u, over);
+    const InstDev &I = inst[tile_inst[t]];
+    for (int k = 0; k < kSub; ++k) {
+      int x, y, z;
+      const int lo = (t - I.tile0) * kTile + k * kBlock + threadIdx.x;
+      if (!node_xyz(I, lo, x, y, z)) break;
+      const int r = I.off + lo;
+      const uint32_t m = mask[r];
+      if (!(m & kFluidBit)) continue;
+      sweep_node<FLOW, true>(I.P, Ntot, r, offsets_of(I.g, x, y, z), m, fin, fout, q, qstar, phi, u, over);
+    }
   }
   if (over) atomicOr(flag, 1);
 }
@@ -218,17 +374,44 @@ __global__ void __launch_bounds__(kBlock) kb_advect(const InstDev *__restrict__ 
                                                     const int64_t *__restrict__ qin, const float *__restrict__ u,
                                                     int64_t *__restrict__ qout) {
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
-    int ii, x, y, z, lo;
-    if (!tile_node(inst, tile_inst, t, ii, x, y, z, lo)) continue;
-    const InstDev &I = inst[ii];
-    const int r = I.off + lo;
-    const uint32_t m = mask[r];
-    if (!(m & kFluidBit)) {
-      qout[r] = qin[r];
-      qout[Ntot + r] = qin[Ntot + r];
-      continue;
+    const InstDev &I = inst[tile_inst[t]];
+    for (int k = 0; k < kSub; ++k) {
+      int x, y, z;
+      const int lo = (t - I.tile0) * kTile + k * kBlock + threadIdx.x;
+      if (!node_xyz(I, lo, x, y, z)) break;
+      const int r = I.off + lo;
+      const uint32_t m = mask[r];
+      if (!(m & kFluidBit)) {
+        qout[r] = qin[r];
+        qout[Ntot + r] = qin[Ntot + r];
+        continue;
+      }
+      advect_node(2, Ntot, r, offsets_of(I.g, x, y, z), m, qin, u, qout);
     }
-    advect_node(2, Ntot, r, offsets_of(I.g, x, y, z), m, qin, u, qout);
+  }
+}
+
+// warm start phi <- 2 phi(t) - phi(t-1) on fluid nodes (all instances), once
+// the previous solution is there (*hist); the FP32 copy follows
+__global__ void kb_extrapolate(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst, int T,
+                               const uint32_t *__restrict__ mask, double *__restrict__ phi,
+                               double *__restrict__ prev, float *__restrict__ phi32, const int *__restrict__ hist) {
+  const int have = *hist;
+  for (int t = blockIdx.x; t < T; t += gridDim.x) {
+    const InstDev &I = inst[tile_inst[t]];
+    for (int k = 0; k < kSub; ++k) {
+      const int lo = (t - I.tile0) * kTile + k * kBlock + threadIdx.x;
+      if (lo >= I.g.N) break;
+      const int r = I.off + lo;
+      if (!(mask[r] & kFluidBit)) continue;
+      const double v = phi[r];
+      if (have) {
+        const double e = 2.0 * v - prev[r];
+        phi[r] = e;
+        phi32[r] = (float)e;
+      }
+      prev[r] = v;
+    }
   }
 }
 
@@ -249,70 +432,49 @@ __global__ void kb_solve_reset(int n, InstCtl *c, BatchCtl *b, int *hist, int se
   if (i == 0) b->solves += 1;
 }
 
-// warm start phi <- 2 phi(t) - phi(t-1) on fluid nodes (all instances), once
-// the previous solution is there (*hist); the FP32 copy follows
-__global__ void kb_extrapolate(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst, int T,
-                               const uint32_t *__restrict__ mask, double *__restrict__ phi,
-                               double *__restrict__ prev, float *__restrict__ phi32, const int *__restrict__ hist) {
-  const int have = *hist;
-  for (int t = blockIdx.x; t < T; t += gridDim.x) {
-    int ii, x, y, z, lo;
-    if (!tile_node(inst, tile_inst, t, ii, x, y, z, lo)) continue;
-    const int r = inst[ii].off + lo;
-    if (!(mask[r] & kFluidBit)) continue;
-    const double v = phi[r];
-    if (have) {
-      const double e = 2.0 * v - prev[r];
-      phi[r] = e;
-      phi32[r] = (float)e;
-    }
-    prev[r] = v;
-  }
-}
-
-// FP64 residual of instances still solving; seeds their CG (r, u = r/diag,
-// x = p = s = 0); partial max per tile
+// FP64 residual of the instances still solving; seeds their CG (r, u =
+// r/diag, x = p = s = 0); per-tile max |r|/diag
 __global__ void __launch_bounds__(kBlock) kb_res(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
                                                  int T, int Ntot, const uint32_t *__restrict__ mask,
                                                  const int64_t *__restrict__ qn, const double *__restrict__ phi,
-                                                 float *__restrict__ vec, double *__restrict__ part,
+                                                 const CgVec v, double *__restrict__ part,
                                                  const InstCtl *__restrict__ c) {
-  float *r_ = vec, *u_ = vec + Ntot, *x_ = vec + 3LL * Ntot, *p_ = vec + 4LL * Ntot, *s_ = vec + 5LL * Ntot;
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
-    int ii = tile_inst[t];
+    const int ii = tile_inst[t];
     if (c[ii].outer_done) continue;  // block-uniform
-    int x, y, z, lo;
-    const bool in = tile_node(inst, tile_inst, t, ii, x, y, z, lo);
+    const InstDev &I = inst[ii];
     float mx = 0.f;
-    if (in) {
-      const InstDev &I = inst[ii];
+#pragma unroll
+    for (int k = 0; k < kSub; ++k) {
+      int x, y, z;
+      const int lo = (t - I.tile0) * kTile + k * kBlock + threadIdx.x;
+      if (!node_xyz(I, lo, x, y, z)) continue;
       const int r = I.off + lo;
       const uint32_t m = mask[r];
       if (!(m & kFluidBit)) {
-        r_[r] = u_[r] = x_[r] = p_[r] = s_[r] = 0.f;
-      } else {
-        const Offs o = offsets_of(I.g, x, y, z);
-        double s1 = 0.0, s2 = 0.0, s4 = 0.0;
-        int wsum = 0;
-#pragma unroll
-        for (int l = 1; l < kQ; ++l) {
-          const double vi = phi[r + o.at(cx_of(l), cy_of(l), cz_of(l))];
-          const int w = (c2_of(l) == 1 ? 2 : 1) * ((m & (1u << (l - 1))) ? 1 : 2);
-          if (w == 1) s1 += vi;
-          else if (w == 2) s2 += vi;
-          else s4 += vi;
-          wsum += w;
-        }
-        const double lap = (s1 + 2.0 * s2 + 4.0 * s4 - (double)wsum * phi[r]) * (1.0 / 6.0);
-        const double rho = I.P.sd[0] * (double)(qn[r] - qn[Ntot + r]);
-        const double rr = I.four_pi_lb * rho + lap;
-        const float dinv = 1.f / diag_f(m, I.selfmask);
-        const float rf = (float)rr;
-        r_[r] = rf;
-        u_[r] = rf * dinv;
-        x_[r] = p_[r] = s_[r] = 0.f;
-        mx = fabsf(rf) * dinv;
+        v.r[r] = v.u[r] = v.x[r] = v.p[r] = v.s[r] = 0.f;
+        continue;
       }
+      const Offs o = offsets_of(I.g, x, y, z);
+      double s1 = 0.0, s2 = 0.0, s4 = 0.0;
+      int wsum = 0;
+#pragma unroll
+      for (int l = 1; l < kQ; ++l) {
+        const double vi = phi[r + o.at(cx_of(l), cy_of(l), cz_of(l))];
+        const int w = (c2_of(l) == 1 ? 2 : 1) * ((m & (1u << (l - 1))) ? 1 : 2);
+        if (w == 1) s1 += vi;
+        else if (w == 2) s2 += vi;
+        else s4 += vi;
+        wsum += w;
+      }
+      const double lap = (s1 + 2.0 * s2 + 4.0 * s4 - (double)wsum * phi[r]) * (1.0 / 6.0);
+      const double rho = I.P.sd[0] * (double)(qn[r] - qn[Ntot + r]);  // 1:1 salt, one bulk value
+      const float rf = (float)(I.four_pi_lb * rho + lap);
+      const float dinv = __fdividef(6.f, (float)mgd::diag6(m, I.selfmask));
+      v.r[r] = rf;
+      v.u[r] = rf * dinv;
+      v.x[r] = v.p[r] = v.s[r] = 0.f;
+      mx = fmaxf(mx, fabsf(rf) * dinv);
     }
     mx = breducef<true>(mx);
     if (threadIdx.x == 0) part[2LL * T + t] = (double)mx;
@@ -320,10 +482,12 @@ __global__ void __launch_bounds__(kBlock) kb_res(const InstDev *__restrict__ ins
 }
 
 // per-instance outer test (one block per instance); the last block sets the
-// refinement loop's condition: any instance still solving
+// refinement loop's condition (any instance still solving) and rebuilds the
+// active-tile lists
 __global__ void __launch_bounds__(kBlock) kb_outer(const InstDev *__restrict__ inst, int n, int T,
                                                    const double *__restrict__ part, InstCtl *c, BatchCtl *b,
-                                                   double tol, int maxit, cudaGraphConditionalHandle hout,
+                                                   double tol, int maxit, int nfam, const int *__restrict__ fam_cnt,
+                                                   int *__restrict__ fam_pref, cudaGraphConditionalHandle hout,
                                                    cudaGraphConditionalHandle hin, int use_cond) {
   const int ii = blockIdx.x;
   if (!c[ii].outer_done) {
@@ -354,51 +518,42 @@ __global__ void __launch_bounds__(kBlock) kb_outer(const InstDev *__restrict__ i
     for (int i = 0; i < n; ++i) any |= !__ldcg(&c[i].outer_done);
     set_cond(hout, use_cond, any ? 1u : 0u);
     if (!any) set_cond(hin, use_cond, 0u);
+    b->any_outer = any;
+    if (!any) b->any_inner = 0;
   }
+  build_active(c, n, nfam, fam_cnt, fam_pref);
 }
 
-// w = A u (fluid operator), per-tile partials (r,u), (w,u)
-__global__ void __launch_bounds__(kBlock) kb_cg_b(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
-                                                  int T, int Ntot, const uint32_t *__restrict__ mask,
-                                                  float *__restrict__ vec, double *__restrict__ part,
-                                                  const InstCtl *__restrict__ c) {
-  const float *r_ = vec, *u_ = vec + Ntot;
-  float *w_ = vec + 2LL * Ntot;
-  for (int t = blockIdx.x; t < T; t += gridDim.x) {
-    int ii = tile_inst[t];
-    if (c[ii].inner_done) continue;
-    int x, y, z, lo;
-    const bool in = tile_node(inst, tile_inst, t, ii, x, y, z, lo);
+// w = A u (fluid operator) on the active tiles; per-tile partials (r,u), (w,u)
+__global__ void __launch_bounds__(kBlock) kb_cg_b(const InstDev *__restrict__ inst, int n, const int *__restrict__ pref,
+                                                  int T, const uint32_t *__restrict__ mask,
+                                                  const float *__restrict__ r_, const float *__restrict__ u_,
+                                                  float *__restrict__ w_, double *__restrict__ part) {
+  const int Tact = pref[n];
+  for (int tp = blockIdx.x; tp < Tact; tp += gridDim.x) {
+    const int ii = find_inst(pref, n, tp);
+    const InstDev &I = inst[ii];
+    const int j = tp - pref[ii];
     float ru = 0.f, wu = 0.f;
-    if (in) {
-      const InstDev &I = inst[ii];
+#pragma unroll
+    for (int k = 0; k < kSub; ++k) {
+      int x, y, z;
+      const int lo = j * kTile + k * kBlock + threadIdx.x;
+      if (!node_xyz(I, lo, x, y, z)) continue;
       const int r = I.off + lo;
       const uint32_t m = mask[r];
-      if (m & kFluidBit) {
-        const Offs o = offsets_of(I.g, x, y, z);
-        const float u0 = u_[r];
-        float s = 0.f, dg = 0.f;
-#pragma unroll
-        for (int l = 1; l < kQ; ++l) {
-          const uint32_t bit = 1u << (l - 1);
-          if (I.selfmask & bit) continue;
-          const float wl = (float)lapc_of(l);
-          if (m & bit) {
-            dg += wl;
-            s += wl * u_[r + o.at(cx_of(l), cy_of(l), cz_of(l))];
-          } else {
-            dg += 2.f * wl;
-          }
-        }
-        const float wv = dg * u0 - s;
-        w_[r] = wv;
-        ru = r_[r] * u0;
-        wu = wv * u0;
-      }
+      if (!(m & kFluidBit)) continue;
+      const float u0 = u_[r];
+      const float s6 = mgd::nbsum6(m, I.selfmask, offsets_of(I.g, x, y, z), r, u_);
+      const float wv = ((float)mgd::diag6(m, I.selfmask) * u0 - s6) * (1.f / 6.f);
+      w_[r] = wv;
+      ru += r_[r] * u0;
+      wu += wv * u0;
     }
     ru = breducef<false>(ru);
     wu = breducef<false>(wu);
     if (threadIdx.x == 0) {
+      const int t = I.tile0 + j;
       part[t] = (double)ru;
       part[(long long)T + t] = (double)wu;
     }
@@ -406,10 +561,12 @@ __global__ void __launch_bounds__(kBlock) kb_cg_b(const InstDev *__restrict__ in
 }
 
 // per-instance scalar recurrence (one block per instance); the last block
-// sets the CG loop's condition: any instance still iterating
+// sets the CG loop's condition (any instance still iterating) and rebuilds
+// the active-tile lists
 __global__ void __launch_bounds__(kBlock) kb_scal(const InstDev *__restrict__ inst, int n, int T,
                                                   const double *__restrict__ part, InstCtl *c, BatchCtl *b,
-                                                  double eta, double tol_abs, int maxit, int init,
+                                                  double eta, double tol_abs, int maxit, int init, int nfam,
+                                                  const int *__restrict__ fam_cnt, int *__restrict__ fam_pref,
                                                   cudaGraphConditionalHandle hin, int use_cond) {
   const int ii = blockIdx.x;
   if (!c[ii].inner_done) {
@@ -431,7 +588,7 @@ __global__ void __launch_bounds__(kBlock) kb_scal(const InstDev *__restrict__ in
         C.beta = 0.0;
         C.alpha = g / d;
         C.gamma = g;
-        if (!(d > 0.0) || !(g > 0.0)) done = 1;
+        if (!(d > 0.0) || !(g > 0.0)) done = 1;  // zero residual: nothing to solve
       } else {
         C.iters += 1;
         atomicAdd((unsigned long long *)&b->total_iters, 1ULL);
@@ -441,7 +598,7 @@ __global__ void __launch_bounds__(kBlock) kb_scal(const InstDev *__restrict__ in
         else {
           const double beta = g / C.gamma;
           const double den = d - beta * g / C.alpha;
-          if (!(den > 0.0) || !(g > 0.0)) done = 1;
+          if (!(den > 0.0) || !(g > 0.0)) done = 1;  // breakdown: converged to rounding
           else { C.beta = beta; C.alpha = g / den; C.gamma = g; }
         }
       }
@@ -454,62 +611,71 @@ __global__ void __launch_bounds__(kBlock) kb_scal(const InstDev *__restrict__ in
     int any = 0;
     for (int i = 0; i < n; ++i) any |= !__ldcg(&c[i].inner_done);
     set_cond(hin, use_cond, any ? 1u : 0u);
+    b->any_inner = any;
   }
+  build_active(c, n, nfam, fam_cnt, fam_pref);
 }
 
-// p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = r/diag
-__global__ void __launch_bounds__(kBlock) kb_cg_a(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
-                                                  int T, int Ntot, const uint32_t *__restrict__ mask,
-                                                  float *__restrict__ vec, double *__restrict__ part,
-                                                  const InstCtl *__restrict__ c) {
-  float *r_ = vec, *u_ = vec + Ntot, *w_ = vec + 2LL * Ntot, *x_ = vec + 3LL * Ntot, *p_ = vec + 4LL * Ntot,
-        *s_ = vec + 5LL * Ntot;
-  for (int t = blockIdx.x; t < T; t += gridDim.x) {
-    int ii = tile_inst[t];
-    if (c[ii].inner_done) continue;
+// p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = r/diag on
+// the active tiles; per-tile max |r|/diag
+__global__ void __launch_bounds__(kBlock) kb_cg_a(const InstDev *__restrict__ inst, int n, const int *__restrict__ pref,
+                                                  int T, const uint32_t *__restrict__ mask, const CgVec v,
+                                                  double *__restrict__ part, const InstCtl *__restrict__ c) {
+  float *__restrict__ r_ = v.r;
+  float *__restrict__ u_ = v.u;
+  const float *__restrict__ w_ = v.w;
+  float *__restrict__ x_ = v.x;
+  float *__restrict__ p_ = v.p;
+  float *__restrict__ s_ = v.s;
+  const int Tact = pref[n];
+  for (int tp = blockIdx.x; tp < Tact; tp += gridDim.x) {
+    const int ii = find_inst(pref, n, tp);
+    const InstDev &I = inst[ii];
+    const int j = tp - pref[ii];
     const float alpha = (float)c[ii].alpha, beta = (float)c[ii].beta;
-    int x, y, z, lo;
-    const bool in = tile_node(inst, tile_inst, t, ii, x, y, z, lo);
     float mx = 0.f;
-    if (in) {
-      const InstDev &I = inst[ii];
+#pragma unroll
+    for (int k = 0; k < kSub; ++k) {
+      const int lo = j * kTile + k * kBlock + threadIdx.x;
+      if (lo >= I.g.N) continue;
       const int r = I.off + lo;
       const uint32_t m = mask[r];
-      if (m & kFluidBit) {
-        const float pv = u_[r] + beta * p_[r];
-        const float sv = w_[r] + beta * s_[r];
-        p_[r] = pv;
-        s_[r] = sv;
-        x_[r] += alpha * pv;
-        const float rv = r_[r] - alpha * sv;
-        r_[r] = rv;
-        const float dinv = 1.f / diag_f(m, I.selfmask);
-        u_[r] = rv * dinv;
-        mx = fabsf(rv) * dinv;
-      }
+      if (!(m & kFluidBit)) continue;
+      const float pv = u_[r] + beta * p_[r];
+      const float sv = w_[r] + beta * s_[r];
+      p_[r] = pv;
+      s_[r] = sv;
+      x_[r] += alpha * pv;
+      const float rv = r_[r] - alpha * sv;
+      r_[r] = rv;
+      const float dinv = __fdividef(6.f, (float)mgd::diag6(m, I.selfmask));
+      u_[r] = rv * dinv;
+      mx = fmaxf(mx, fabsf(rv) * dinv);
     }
     mx = breducef<true>(mx);
-    if (threadIdx.x == 0) part[2LL * T + t] = (double)mx;
+    if (threadIdx.x == 0) part[2LL * T + I.tile0 + j] = (double)mx;
   }
 }
 
 // phi64 += x for instances that solved this round; FP32 copy refreshed
-__global__ void kb_correct(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst, int T, int Ntot,
-                           const uint32_t *__restrict__ mask, const float *__restrict__ vec, double *__restrict__ phi,
-                           float *__restrict__ phi32, const InstCtl *__restrict__ c) {
-  const float *x_ = vec + 3LL * Ntot;
+__global__ void kb_correct(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst, int T,
+                           const uint32_t *__restrict__ mask, const float *__restrict__ x_,
+                           double *__restrict__ phi, float *__restrict__ phi32, const InstCtl *__restrict__ c) {
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
-    int ii = tile_inst[t];
+    const int ii = tile_inst[t];
     if (!c[ii].solving) continue;
-    int x, y, z, lo;
-    if (!tile_node(inst, tile_inst, t, ii, x, y, z, lo)) continue;
-    const int r = inst[ii].off + lo;
-    double v = phi[r];
-    if (mask[r] & kFluidBit) {
-      v += (double)x_[r];
-      phi[r] = v;
+    const InstDev &I = inst[ii];
+    for (int k = 0; k < kSub; ++k) {
+      const int lo = (t - I.tile0) * kTile + k * kBlock + threadIdx.x;
+      if (lo >= I.g.N) break;
+      const int r = I.off + lo;
+      double v = phi[r];
+      if (mask[r] & kFluidBit) {
+        v += (double)x_[r];
+        phi[r] = v;
+      }
+      phi32[r] = (float)v;
     }
-    phi32[r] = (float)v;
   }
 }
 
@@ -519,26 +685,27 @@ __global__ void __launch_bounds__(kBlock) kb_charge(const InstDev *__restrict__ 
                                                     const uint32_t *__restrict__ mask, const double *__restrict__ phi,
                                                     double *__restrict__ part) {
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
-    int ii, x, y, z, lo;
-    const bool in = tile_node(inst, tile_inst, t, ii, x, y, z, lo);
-    double a[kBE] = {0.0, 0.0};
-    if (in) {
-      const InstDev &I = inst[ii];
+    const InstDev &I = inst[tile_inst[t]];
+    double a[kBE];
+    for (int e = 0; e < kBE; ++e) a[e] = 0.0;
+    for (int k = 0; k < kSub; ++k) {
+      int x, y, z;
+      const int lo = (t - I.tile0) * kTile + k * kBlock + threadIdx.x;
+      if (!node_xyz(I, lo, x, y, z)) break;
       const int r = I.off + lo;
       const int e = id[r];
       const uint32_t m = mask[r];
-      if (e && (m & ((1u << 18) - 1))) {
-        const Offs o = offsets_of(I.g, x, y, z);
-        double s = 0.0;
-        for (int l = 1; l < kQ; ++l)
-          if (m & (1u << (l - 1))) s += lapc_of(l) * 2.0 * (phi[r + o.at(cx_of(l), cy_of(l), cz_of(l))] - phi[r]);
-        for (int k = 0; k < kBE; ++k)
-          if (k == e - 1) a[k] = -I.eps * s;
-      }
+      if (!e || !(m & ((1u << 18) - 1))) continue;
+      const Offs o = offsets_of(I.g, x, y, z);
+      double s = 0.0;
+      for (int l = 1; l < kQ; ++l)
+        if (m & (1u << (l - 1))) s += lapc_of(l) * 2.0 * (phi[r + o.at(cx_of(l), cy_of(l), cz_of(l))] - phi[r]);
+      for (int q = 0; q < kBE; ++q)
+        if (q == e - 1) a[q] += -I.eps * s;
     }
-    for (int k = 0; k < kBE; ++k) {
-      const double v = breduce<false>(a[k]);
-      if (threadIdx.x == 0) part[(long long)k * T + t] = v;
+    for (int q = 0; q < kBE; ++q) {
+      const double v = breduce<false>(a[q]);
+      if (threadIdx.x == 0) part[(long long)q * T + t] = v;
     }
   }
 }
@@ -565,31 +732,248 @@ __global__ void kb_n_to_double(const InstDev *__restrict__ inst, int ii, long lo
   for (int k = 0; k < 2; ++k) out[k * I.g.N + lo] = fl ? I.P.rbd[k] + I.P.sd[k] * (double)q[k * Ntot + r] : 0.0;
 }
 
+// --- batched multigrid V-cycle (per-node arithmetic in mg_device.cuh) --------
+using mgd::MgLevel;
+
+__global__ void kbm_galerkin0(const InstDev *__restrict__ inst, const int *__restrict__ tiles, int T,
+                              const LvSeg *__restrict__ seg1, const uint32_t *__restrict__ mask, float *__restrict__ A1) {
+  for (int t = blockIdx.x; t < T; t += gridDim.x) {
+    const int ii = tiles[t];
+    const LvSeg C = seg1[ii];
+    const InstDev &In = inst[ii];
+    for (int k = 0; k < kSub; ++k) {
+      const int I = (t - C.tile0) * kTile + k * kBlock + threadIdx.x;
+      if (I >= C.L.N) break;
+      int X, Y, Z;
+      lv_xyz(C, I, X, Y, Z);
+      float a[27];
+      mgd::galerkin0_row(In.g, In.selfmask, mask + In.off, C.L, X, Y, Z, a);
+      for (int d = 0; d < 27; ++d) A1[d * C.L.S + C.off + I] = a[d];
+    }
+  }
+}
+
+__global__ void kbm_galerkin(const int *__restrict__ tiles, int T, const LvSeg *__restrict__ segF,
+                             const LvSeg *__restrict__ segC, const float *__restrict__ AF, float *__restrict__ AC) {
+  for (int t = blockIdx.x; t < T; t += gridDim.x) {
+    const int ii = tiles[t];
+    const LvSeg C = segC[ii], F = segF[ii];
+    for (int k = 0; k < kSub; ++k) {
+      const int I = (t - C.tile0) * kTile + k * kBlock + threadIdx.x;
+      if (I >= C.L.N) break;
+      int X, Y, Z;
+      lv_xyz(C, I, X, Y, Z);
+      float a[27];
+      mgd::galerkin_row(F.L, AF + F.off, C.L, X, Y, Z, a);
+      for (int d = 0; d < 27; ++d) AC[d * C.L.S + C.off + I] = a[d];
+    }
+  }
+}
+
+// coarse residual rc and pre-smoothed iterate zc = omega rc/diag of a coarse
+// node (lane ch = 0 of its 8)
+__device__ __forceinline__ void store_coarse(const LvSeg &C, int I, float v, const float *__restrict__ AC,
+                                             float *__restrict__ rc, float *__restrict__ zc) {
+  const float d = AC[13 * C.L.S + C.off + I];
+  rc[C.off + I] = v;
+  zc[C.off + I] = d != 0.f ? mgd::kOmega * v / d : 0.f;
+}
+
+// Restriction into level 1 over the active level-1 tiles.  Work item: 32
+// coarse nodes, 8 threads each (one per child, fixed-order shuffle sum).  A
+// fluid child's pre-smoothed residual is r - omega A u: u = r/diag is the
+// Jacobi vector the CG just formed.
+__global__ void __launch_bounds__(kBlock) kbm_restrict0(const InstDev *__restrict__ inst, int n,
+                                                        const int *__restrict__ pref, const LvSeg *__restrict__ seg1,
+                                                        const uint32_t *__restrict__ mask, const float *__restrict__ r,
+                                                        const float *__restrict__ u, const float *__restrict__ A1,
+                                                        float *__restrict__ rc, float *__restrict__ zc) {
+  const int items = pref[n] * (kTile / 32);
+  const int ch = threadIdx.x & 7;
+  for (int ip = blockIdx.x; ip < items; ip += gridDim.x) {
+    const int tp = ip / (kTile / 32);
+    const int ii = find_inst(pref, n, tp);
+    const LvSeg C = seg1[ii];
+    const InstDev &In = inst[ii];
+    const int I = (tp - pref[ii]) * kTile + (ip % (kTile / 32)) * 32 + (threadIdx.x >> 3);
+    float v = 0.f;
+    int X, Y, Z, x, y, z;
+    if (I < C.L.N) {
+      lv_xyz(C, I, X, Y, Z);
+      if (mgd::child_of(C.L, X, Y, Z, ch, In.g.nx, In.g.ny, In.g.nz, x, y, z)) {
+        const int i = In.off + x + In.g.nx * (y + In.g.ny * z);
+        const uint32_t m = mask[i];
+        if (m & kFluidBit) {
+          const float s6 = mgd::nbsum6(m, In.selfmask, offsets_of(In.g, x, y, z), i, u);
+          v = r[i] - mgd::kOmega * ((float)mgd::diag6(m, In.selfmask) * u[i] - s6) * (1.f / 6.f);
+        }
+      }
+    }
+    v = mgd::sum8(v);
+    if (ch == 0 && I < C.L.N) store_coarse(C, I, v, A1, rc, zc);
+  }
+}
+
+// restriction from level l into level l+1 over the active level-(l+1) tiles
+__global__ void __launch_bounds__(kBlock) kbm_restrict(int n, const int *__restrict__ pref,
+                                                       const LvSeg *__restrict__ segF, const LvSeg *__restrict__ segC,
+                                                       const float *__restrict__ AF, const float *__restrict__ rF,
+                                                       const float *__restrict__ zF, const float *__restrict__ AC,
+                                                       float *__restrict__ rC, float *__restrict__ zC) {
+  const int items = pref[n] * (kTile / 32);
+  const int ch = threadIdx.x & 7;
+  for (int ip = blockIdx.x; ip < items; ip += gridDim.x) {
+    const int tp = ip / (kTile / 32);
+    const int ii = find_inst(pref, n, tp);
+    const LvSeg C = segC[ii], F = segF[ii];
+    const int I = (tp - pref[ii]) * kTile + (ip % (kTile / 32)) * 32 + (threadIdx.x >> 3);
+    float v = 0.f;
+    int X, Y, Z, x, y, z;
+    if (I < C.L.N) {
+      lv_xyz(C, I, X, Y, Z);
+      if (mgd::child_of(C.L, X, Y, Z, ch, F.L.nx, F.L.ny, F.L.nz, x, y, z))
+        v = mgd::presmoothed_res_z(F.L, AF + F.off, rF + F.off, zF + F.off, x, y, z);
+    }
+    v = mgd::sum8(v);
+    if (ch == 0 && I < C.L.N) store_coarse(C, I, v, AC, rC, zC);
+  }
+}
+
+// every instance's coarsest level, one block each
+__global__ void __launch_bounds__(mgd::kCoarseMax) kbm_coarsest(const InstDev *__restrict__ inst, int n,
+                                                                const LvSeg *__restrict__ seg, const LvPtrs P,
+                                                                const InstCtl *__restrict__ c) {
+  const int ii = blockIdx.x;
+  const int nl = inst[ii].mg_levels;
+  if (nl < 2 || c[ii].inner_done) return;
+  __shared__ float buf[2][mgd::kCoarseMax];
+  const LvSeg S = seg[(nl - 1) * n + ii];
+  mgd::coarsest_solve(S.L, P.A[nl - 1] + S.off, P.r[nl - 1] + S.off, P.e[nl - 1] + S.off, buf);
+}
+
+// fused prolongation + post-smoothing on coarse level l over the active
+// level-l tiles of instances that have level l+1; work item: 256 nodes
+__global__ void __launch_bounds__(kBlock) kbm_post(int n, const int *__restrict__ pref, const LvSeg *__restrict__ segL,
+                                                   const LvSeg *__restrict__ segC, const float *__restrict__ A,
+                                                   const float *__restrict__ r, const float *__restrict__ z,
+                                                   const float *__restrict__ ec, float *__restrict__ e) {
+  const int items = pref[n] * kSub;
+  for (int ip = blockIdx.x; ip < items; ip += gridDim.x) {
+    const int tp = ip / kSub;
+    const int ii = find_inst(pref, n, tp);
+    const LvSeg L = segL[ii], C = segC[ii];
+    const int I = (tp - pref[ii]) * kTile + (ip % kSub) * kBlock + threadIdx.x;
+    if (I >= L.L.N) continue;
+    int X, Y, Z;
+    lv_xyz(L, I, X, Y, Z);
+    e[L.off + I] = mgd::post_value_z(L.L, A + L.off, r + L.off, z + L.off, C.L, ec + C.off, X, Y, Z);
+  }
+}
+
+// level 0 over the active tiles of instances with a hierarchy:
+// t = omega u + alpha P e_1 (u = r/diag, the Jacobi vector)
+__global__ void __launch_bounds__(kBlock) kbm_prolong0(const InstDev *__restrict__ inst, int n,
+                                                       const int *__restrict__ pref, const LvSeg *__restrict__ seg1,
+                                                       const uint32_t *__restrict__ mask, const float *__restrict__ u,
+                                                       const float *__restrict__ e1, float *__restrict__ t0) {
+  const int Tact = pref[n];
+  for (int tp = blockIdx.x; tp < Tact; tp += gridDim.x) {
+    const int ii = find_inst(pref, n, tp);
+    const InstDev &I = inst[ii];
+    const LvSeg C = seg1[ii];
+    const int j = tp - pref[ii];
+#pragma unroll
+    for (int k = 0; k < kSub; ++k) {
+      int x, y, z;
+      const int lo = j * kTile + k * kBlock + threadIdx.x;
+      if (!node_xyz(I, lo, x, y, z)) continue;
+      const int rr = I.off + lo;
+      t0[rr] = (mask[rr] & kFluidBit) ? fmaf(mgd::kAlpha, e1[C.off + mgd::agg_index(C.L, x, y, z)], mgd::kOmega * u[rr])
+                                      : 0.f;
+    }
+  }
+}
+
+// then u = t + omega (r - A t)/diag
+__global__ void __launch_bounds__(kBlock) kbm_post0(const InstDev *__restrict__ inst, int n,
+                                                    const int *__restrict__ pref, const uint32_t *__restrict__ mask,
+                                                    const float *__restrict__ r, const float *__restrict__ t0,
+                                                    float *__restrict__ u) {
+  const int Tact = pref[n];
+  for (int tp = blockIdx.x; tp < Tact; tp += gridDim.x) {
+    const int ii = find_inst(pref, n, tp);
+    const InstDev &I = inst[ii];
+    const int j = tp - pref[ii];
+#pragma unroll
+    for (int k = 0; k < kSub; ++k) {
+      int x, y, z;
+      const int lo = j * kTile + k * kBlock + threadIdx.x;
+      if (!node_xyz(I, lo, x, y, z)) continue;
+      const int i = I.off + lo;
+      const uint32_t m = mask[i];
+      if (!(m & kFluidBit)) {
+        u[i] = 0.f;
+        continue;
+      }
+      const float d6 = (float)mgd::diag6(m, I.selfmask);
+      const float s6 = mgd::nbsum6(m, I.selfmask, offsets_of(I.g, x, y, z), i, t0);
+      const float ti = t0[i];
+      u[i] = ti + mgd::kOmega * __fdividef(6.f * r[i] - (d6 * ti - s6), d6);
+    }
+  }
+}
+
 }  // namespace
 }  // namespace lbe
 
 // =============================================================================
 namespace {
 
+using lbe::kTile;
+
 int bfail(lbe_batch *b, int code, const std::string &m) {
   if (b) b->err = m;
   return code;
 }
-#define BCK(b, expr)                                                                                 \
-  do {                                                                                               \
-    cudaError_t e_ = (expr);                                                                         \
+#define BCK(b, expr)                                                                                  \
+  do {                                                                                                \
+    cudaError_t e_ = (expr);                                                                          \
     if (e_ != cudaSuccess) return bfail((b), LBE_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
   } while (0)
+
+void mg_release(lbe_batch *b) {
+  cudaFree(b->mg_tiles);
+  cudaFree(b->mg_seg);
+  cudaFree(b->mg_t0);
+  cudaFree(b->fam_cnt);
+  cudaFree(b->fam_pref);
+  for (int l = 0; l < lbe::kMaxLevels; ++l) {
+    cudaFree(b->mg_p.A[l]);
+    cudaFree(b->mg_p.r[l]);
+    cudaFree(b->mg_p.e[l]);
+    cudaFree(b->mg_p.z[l]);
+  }
+  b->mg_tiles = nullptr;
+  b->mg_seg = nullptr;
+  b->mg_t0 = nullptr;
+  b->fam_cnt = b->fam_pref = nullptr;
+  b->mg_p = lbe::LvPtrs{};
+  b->mg_nlev = 0;
+  b->nfam = 0;
+}
 
 void bfree(lbe_batch *b) {
   void *ptrs[] = {b->inst_d, b->tile_inst, b->id,   b->mask, b->f[0],  b->f[1], b->q,    b->qstar, b->phi,
                   b->phi_prev, b->phi32,  b->u, b->vec,  b->part, b->psi_d, b->ictl, b->bctl, b->qpart, b->qout,
                   b->flag,     b->hist};
   for (void *p : ptrs) cudaFree(p);
+  mg_release(b);
   if (b->bctl_h) cudaFreeHost(b->bctl_h);
   if (b->qhost) cudaFreeHost(b->qhost);
-  for (int k = 0; k < 5; ++k)
+  for (int k = 0; k < 9; ++k)
     if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+  for (int k = 0; k < 4; ++k)
+    if (b->ev[k]) cudaEventDestroy(b->ev[k]);
 }
 
 cudaError_t add_node(cudaGraph_t gr, cudaGraphNode_t *last, void *func, dim3 grid, dim3 block, void **args) {
@@ -622,35 +1006,206 @@ cudaError_t add_while(cudaGraph_t gr, cudaGraphNode_t *last, cudaGraphConditiona
   return e;
 }
 
-// One graph per step: [sweep -> advect ->] extrapolate -> Poisson solve
-// (nested while loops: refinement rounds around the CG iterations).  With
-// step = false only the solve (set-up).  fin/qin are the populations and
-// solute the step reads.
-cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *qin, int64_t *qmid,
-                        cudaGraphExec_t *exec) {
+cudaError_t add_event(cudaGraph_t gr, cudaGraphNode_t *last, cudaEvent_t ev) {
+  cudaGraphNode_t n;
+  cudaError_t e = cudaGraphAddEventRecordNode(&n, gr, *last ? last : nullptr, *last ? 1 : 0, ev);
+  if (e == cudaSuccess) *last = n;
+  return e;
+}
+
+// family prefix array f
+const int *fam(const lbe_batch *b, int f) { return b->fam_pref + (size_t)f * (b->n + 1); }
+int fam_levels(const lbe_batch *b) { return b->mg_nlev >= 2 ? b->mg_nlev : 1; }
+
+// Multigrid hierarchy of every instance (after the link masks): level shapes
+// per instance, the levels' concatenated arrays and tile lists, the active-
+// tile families, then the inverse fine diagonal and the Galerkin operators on
+// the GPU.  Uploads the instance table (it carries each instance's level
+// count).
+int mg_setup(lbe_batch *b) {
   using namespace lbe;
-  struct Args {
-    const InstDev *inst;
-    const int *tile_inst;
-    int T, Ntot, n, maxit, use = 1, init1 = 1, init0 = 0, set_hist;
-    const uint32_t *mask;
-    const float *fin;
-    float *fout;
-    int64_t *qin, *qmid, *qsolve;
-    double *phi, *phi_prev;
-    float *phi32, *u, *vec;
-    double *part;
-    InstCtl *c;
-    BatchCtl *bc;
-    int *flag, *hist;
-    double tol, eta, tol_abs;
-    cudaGraphConditionalHandle hout = 0, hin = 0;
-  } A;
+  mg_release(b);
+  const int n = b->n;
+  std::vector<mgd::MgLevel> shp((size_t)n * kMaxLevels);
+  int L = 0;
+  for (int i = 0; i < n; ++i) {
+    const Geo &g = b->inst[i].g;
+    b->inst[i].mg_levels = mgd::level_shapes(g.nx, g.ny, g.nz, &shp[(size_t)i * kMaxLevels]);
+    L = std::max(L, b->inst[i].mg_levels);
+  }
+  b->mg_nlev = L;
+  BCK(b, cudaMemcpyAsync(b->inst_d, b->inst.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice, b->stream));
+  std::vector<LvSeg> seg((size_t)kMaxLevels * n);
+  memset(seg.data(), 0, sizeof(LvSeg) * seg.size());
+  std::vector<int> tiles;
+  for (int l = 1; l < L; ++l) {
+    b->mg_tbase[l] = (int)tiles.size();
+    long long M = 0;
+    int T = 0;
+    for (int i = 0; i < n; ++i) {
+      if (b->inst[i].mg_levels <= l) continue;
+      LvSeg &S = seg[(size_t)l * n + i];
+      S.L = shp[(size_t)i * kMaxLevels + l];
+      S.off = (int)M;
+      S.tile0 = T;
+      S.ntiles = (S.L.N + kTile - 1) / kTile;
+      S.fx = make_fastdiv((uint32_t)S.L.nx);
+      S.fxy = make_fastdiv((uint32_t)(S.L.nx * S.L.ny));
+      if (!fastdiv_ok(S.fx, (uint32_t)S.L.N) || !fastdiv_ok(S.fxy, (uint32_t)S.L.N))
+        return bfail(b, LBE_ERR_STATE, "batch: index division check failed");
+      for (int k = 0; k < S.ntiles; ++k) tiles.push_back(i);
+      M += S.L.N;
+      T += S.ntiles;
+    }
+    for (int i = 0; i < n; ++i) seg[(size_t)l * n + i].L.S = M;  // component stride
+    b->mg_M[l] = M;
+    b->mg_T[l] = T;
+  }
+  // active-tile families
+  const int FL = fam_levels(b);
+  b->nfam = 2 * FL - 1;
+  std::vector<int> cnt((size_t)b->nfam * n, 0);
+  for (int i = 0; i < n; ++i) {
+    const int ml = b->inst[i].mg_levels;
+    auto tiles_at = [&](int l) { return l == 0 ? b->inst[i].ntiles : seg[(size_t)l * n + i].ntiles; };
+    for (int l = 0; l < FL; ++l) cnt[(size_t)famA(l) * n + i] = (l == 0 || ml > l) ? tiles_at(l) : 0;
+    for (int l = 0; l + 1 < FL; ++l) cnt[(size_t)famB(FL, l) * n + i] = ml > l + 1 ? tiles_at(l) : 0;
+  }
+  cudaError_t e = cudaMalloc(&b->fam_cnt, sizeof(int) * cnt.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->fam_pref, sizeof(int) * (size_t)b->nfam * (n + 1));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->fam_cnt, cnt.data(), sizeof(int) * cnt.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->fam_pref, 0, sizeof(int) * (size_t)b->nfam * (n + 1), b->stream);
+  BCK(b, e);
+  if (L < 2) return LBE_OK;
+  e = cudaMalloc(&b->mg_tiles, sizeof(int) * std::max<size_t>(tiles.size(), 1));
+  if (e == cudaSuccess) e = cudaMalloc(&b->mg_seg, sizeof(LvSeg) * seg.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->mg_t0, sizeof(float) * b->Ntot);
+  for (int l = 1; l < L && e == cudaSuccess; ++l) {
+    e = cudaMalloc(&b->mg_p.A[l], sizeof(float) * 27 * b->mg_M[l]);
+    if (e == cudaSuccess) e = cudaMalloc(&b->mg_p.r[l], sizeof(float) * b->mg_M[l]);
+    if (e == cudaSuccess) e = cudaMalloc(&b->mg_p.e[l], sizeof(float) * b->mg_M[l]);
+    if (e == cudaSuccess) e = cudaMalloc(&b->mg_p.z[l], sizeof(float) * b->mg_M[l]);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->mg_tiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->mg_seg, seg.data(), sizeof(LvSeg) * seg.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->mg_t0, 0, sizeof(float) * b->Ntot, b->stream);
+  BCK(b, e);
+  const int G = b->grid;
+  kbm_galerkin0<<<std::min(G, b->mg_T[1]), kBlock, 0, b->stream>>>(b->inst_d, b->mg_tiles + b->mg_tbase[1],
+                                                                   b->mg_T[1], b->mg_seg + n, b->mask,
+                                                                   b->mg_p.A[1]);
+  for (int l = 1; l + 1 < L; ++l)
+    kbm_galerkin<<<std::min(G, b->mg_T[l + 1]), kBlock, 0, b->stream>>>(
+        b->mg_tiles + b->mg_tbase[l + 1], b->mg_T[l + 1], b->mg_seg + (size_t)l * n, b->mg_seg + (size_t)(l + 1) * n,
+        b->mg_p.A[l], b->mg_p.A[l + 1]);
+  BCK(b, cudaGetLastError());
+  return LBE_OK;
+}
+
+// u = M r (one V-cycle over every active instance with a hierarchy) as graph
+// nodes after *last; r and u are the CG vectors
+cudaError_t add_vcycle(lbe_batch *b, cudaGraph_t gr, cudaGraphNode_t *last) {
+  using namespace lbe;
+  const int L = b->mg_nlev;
+  if (L < 2) return cudaSuccess;
+  int n = b->n;
+  const InstDev *inst = b->inst_d;
+  const InstCtl *c = b->ictl;
+  const uint32_t *mask = b->mask;
+  const CgVec v = b->cg();
+  const float *r0 = v.r, *uj = v.u;
+  float *u0 = v.u, *t0 = b->mg_t0;
+  const LvSeg *seg_all = b->mg_seg;
+  LvPtrs P = b->mg_p;
+  const dim3 G(b->grid), B(kBlock);
+  cudaError_t e;
+  {
+    const int *pref = fam(b, famA(1));
+    const LvSeg *seg1 = seg_all + n;
+    const float *A1 = P.A[1];
+    float *rc = P.r[1], *zc = P.z[1];
+    void *a[] = {&inst, &n, &pref, &seg1, &mask, &r0, &uj, &A1, &rc, &zc};
+    e = add_node(gr, last, (void *)kbm_restrict0, G, B, a);
+    if (e != cudaSuccess) return e;
+  }
+  for (int l = 1; l + 1 < L; ++l) {
+    const int *pref = fam(b, famA(l + 1));
+    const LvSeg *sf = seg_all + (size_t)l * n, *sc = seg_all + (size_t)(l + 1) * n;
+    const float *AF = P.A[l], *rF = P.r[l], *zF = P.z[l], *AC = P.A[l + 1];
+    float *rC = P.r[l + 1], *zC = P.z[l + 1];
+    void *a[] = {&n, &pref, &sf, &sc, &AF, &rF, &zF, &AC, &rC, &zC};
+    e = add_node(gr, last, (void *)kbm_restrict, G, B, a);
+    if (e != cudaSuccess) return e;
+  }
+  {
+    void *a[] = {&inst, &n, &seg_all, &P, &c};
+    e = add_node(gr, last, (void *)kbm_coarsest, dim3(n), dim3(mgd::kCoarseMax), a);
+    if (e != cudaSuccess) return e;
+  }
+  for (int l = L - 2; l >= 1; --l) {
+    const int *pref = fam(b, famB(L, l));
+    const LvSeg *sl = seg_all + (size_t)l * n, *sc = seg_all + (size_t)(l + 1) * n;
+    const float *A = P.A[l], *r = P.r[l], *z = P.z[l], *ec = P.e[l + 1];
+    float *el = P.e[l];
+    void *a[] = {&n, &pref, &sl, &sc, &A, &r, &z, &ec, &el};
+    e = add_node(gr, last, (void *)kbm_post, G, B, a);
+    if (e != cudaSuccess) return e;
+  }
+  const int *prefB0 = fam(b, famB(L, 0));
+  {
+    const LvSeg *seg1 = seg_all + n;
+    const float *e1 = P.e[1];
+    void *a[] = {&inst, &n, &prefB0, &seg1, &mask, &uj, &e1, &t0};
+    e = add_node(gr, last, (void *)kbm_prolong0, G, B, a);
+    if (e != cudaSuccess) return e;
+  }
+  {
+    const float *tc = t0;
+    void *a[] = {&inst, &n, &prefB0, &mask, &r0, &tc, &u0};
+    e = add_node(gr, last, (void *)kbm_post0, G, B, a);
+  }
+  return e;
+}
+
+// kernels of one V-cycle
+int vcycle_kernels(const lbe_batch *b) { return b->mg_nlev >= 2 ? 2 * (b->mg_nlev - 1) + 2 : 0; }
+
+// Arguments of the solve kernels (kept alive while nodes are created or
+// kernels launched)
+struct SolveArgs {
+  const lbe::InstDev *inst;
+  const int *tile_inst, *pref0, *fam_cnt;
+  int T, Ntot, n, maxit, nfam, use = 1, init1 = 1, init0 = 0, set_hist;
+  const uint32_t *mask;
+  const float *fin;
+  float *fout;
+  int64_t *qin, *qmid, *qsolve;
+  double *phi, *phi_prev;
+  float *phi32, *u;
+  lbe::CgVec v;
+  const float *vr, *vu, *vx;
+  float *vw;
+  double *part;
+  lbe::InstCtl *c;
+  lbe::BatchCtl *bc;
+  int *flag, *hist, *fam_pref;
+  double tol, eta, tol_abs;
+  cudaGraphConditionalHandle hout = 0, hin = 0;
+};
+
+void solve_args(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *qin, int64_t *qmid, SolveArgs &A) {
   A.inst = b->inst_d;
   A.tile_inst = b->tile_inst;
+  A.pref0 = fam(b, lbe::famA(0));
+  A.fam_cnt = b->fam_cnt;
+  A.fam_pref = b->fam_pref;
   A.T = b->T;
   A.Ntot = (int)b->Ntot;
   A.n = b->n;
+  A.nfam = b->nfam;
   A.maxit = b->prm[0].poisson_max_iter;
   A.set_hist = step ? 1 : 0;
   A.mask = b->mask;
@@ -665,7 +1220,11 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   A.phi_prev = b->phi_prev;
   A.phi32 = b->phi32;
   A.u = b->u;
-  A.vec = b->vec;
+  A.v = b->cg();
+  A.vr = A.v.r;
+  A.vu = A.v.u;
+  A.vx = A.v.x;
+  A.vw = A.v.w;
   A.part = b->part;
   A.c = b->ictl;
   A.bc = b->bctl;
@@ -674,6 +1233,16 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   A.tol = b->prm[0].poisson_tol;
   A.eta = 1e-4;
   A.tol_abs = 0.25 * A.tol;
+}
+
+// One graph per step: [sweep -> advect ->] extrapolate -> Poisson solve
+// (nested while loops: refinement rounds around the CG iterations).  With
+// step = false only the solve (set-up).
+cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *qin, int64_t *qmid,
+                        cudaGraphExec_t *exec, bool prof = false) {
+  using namespace lbe;
+  SolveArgs A;
+  solve_args(b, step, fin, fout, qin, qmid, A);
   const dim3 G(b->grid), B(kBlock), NB(b->n), rb((b->n + 255) / 256);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaGraphCreate(&g, 0);
@@ -685,17 +1254,23 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   void *a_adv[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.qmid, &A.u, &A.qin};
   void *a_ext[] = {&A.inst, &A.tile_inst, &A.T, &A.mask, &A.phi, &A.phi_prev, &A.phi32, &A.hist};
   void *a_reset[] = {&A.n, &A.c, &A.bc, &A.hist, &A.set_hist};
-  void *a_res[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.qsolve, &A.phi, &A.vec, &A.part, &A.c};
-  void *a_out[] = {&A.inst, &A.n, &A.T, &A.part, &A.c, &A.bc, &A.tol, &A.maxit, &A.hout, &A.hin, &A.use};
-  void *a_b[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.vec, &A.part, &A.c};
-  void *a_si[] = {&A.inst, &A.n, &A.T, &A.part, &A.c, &A.bc, &A.eta, &A.tol_abs, &A.maxit, &A.init1, &A.hin, &A.use};
-  void *a_st[] = {&A.inst, &A.n, &A.T, &A.part, &A.c, &A.bc, &A.eta, &A.tol_abs, &A.maxit, &A.init0, &A.hin, &A.use};
-  void *a_a[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.vec, &A.part, &A.c};
-  void *a_cor[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.vec, &A.phi, &A.phi32, &A.c};
+  void *a_res[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.qsolve, &A.phi, &A.v, &A.part, &A.c};
+  void *a_out[] = {&A.inst, &A.n,       &A.T,        &A.part, &A.c,   &A.bc,  &A.tol,
+                   &A.maxit, &A.nfam,   &A.fam_cnt,  &A.fam_pref, &A.hout, &A.hin, &A.use};
+  void *a_b[] = {&A.inst, &A.n, &A.pref0, &A.T, &A.mask, &A.vr, &A.vu, &A.vw, &A.part};
+  void *a_si[] = {&A.inst, &A.n,     &A.T,    &A.part,    &A.c,        &A.bc,  &A.eta, &A.tol_abs,
+                  &A.maxit, &A.init1, &A.nfam, &A.fam_cnt, &A.fam_pref, &A.hin, &A.use};
+  void *a_st[] = {&A.inst, &A.n,     &A.T,    &A.part,    &A.c,        &A.bc,  &A.eta, &A.tol_abs,
+                  &A.maxit, &A.init0, &A.nfam, &A.fam_cnt, &A.fam_pref, &A.hin, &A.use};
+  void *a_a[] = {&A.inst, &A.n, &A.pref0, &A.T, &A.mask, &A.v, &A.part, &A.c};
+  void *a_cor[] = {&A.inst, &A.tile_inst, &A.T, &A.mask, &A.vx, &A.phi, &A.phi32, &A.c};
   if (step) {
     void *sweep = b->flow ? (void *)kb_sweep<true> : (void *)kb_sweep<false>;
-    e = add_node(g, &last, sweep, G, B, a_sw);
+    if (prof) e = add_event(g, &last, b->ev[0]);
+    if (e == cudaSuccess) e = add_node(g, &last, sweep, G, B, a_sw);
+    if (e == cudaSuccess && prof) e = add_event(g, &last, b->ev[1]);
     if (e == cudaSuccess && b->flow) e = add_node(g, &last, (void *)kb_advect, G, B, a_adv);
+    if (e == cudaSuccess && prof) e = add_event(g, &last, b->ev[2]);
     if (e == cudaSuccess) e = add_node(g, &last, (void *)kb_extrapolate, G, B, a_ext);
   }
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&A.hout, g, 1, cudaGraphCondAssignDefault);
@@ -704,46 +1279,150 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&A.hin, bo, 0, 0);
   if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_res, G, B, a_res);
   if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_outer, NB, B, a_out);
+  if (e == cudaSuccess) e = add_vcycle(b, bo, &lo);
   if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_cg_b, G, B, a_b);
   if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_scal, NB, B, a_si);
   if (e == cudaSuccess) e = add_while(bo, &lo, A.hin, &bi);
   if (e == cudaSuccess) e = add_node(bi, &li, (void *)kb_cg_a, G, B, a_a);
+  if (e == cudaSuccess) e = add_vcycle(b, bi, &li);
   if (e == cudaSuccess) e = add_node(bi, &li, (void *)kb_cg_b, G, B, a_b);
   if (e == cudaSuccess) e = add_node(bi, &li, (void *)kb_scal, NB, B, a_st);
   if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_correct, G, B, a_cor);
+  if (e == cudaSuccess && prof) e = add_event(g, &last, b->ev[3]);
   if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
   cudaGraphDestroy(g);
   return e;
 }
 
 void drop_graphs(lbe_batch *b) {
-  for (int k = 0; k < 5; ++k)
+  for (int k = 0; k < 9; ++k) {
     if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]), b->exec[k] = nullptr;
-  for (int k = 0; k < 4; ++k) b->key_f[k] = b->key_q[k] = nullptr;
+    b->key_f[k] = b->key_q[k] = nullptr;
+  }
 }
 
-// launch one step (or, step = false, one solve) as a graph
-int launch_graph(lbe_batch *b, bool step) {
-  if (!step) {
+// The same step with every kernel launched from the host and the solve's
+// loop conditions read back after each test (LBE_POISSON_GRAPH=0: lets a
+// kernel profiler see the individual launches).
+int run_polled(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *qin, int64_t *qmid) {
+  using namespace lbe;
+  SolveArgs A;
+  solve_args(b, step, fin, fout, qin, qmid, A);
+  cudaStream_t st = b->stream;
+  const int G = b->grid, n = b->n;
+  auto rec = [&](int k) { return b->profiling && step ? cudaEventRecord(b->ev[k], st) : cudaSuccess; };
+  long long &nl = b->prof_launches;
+  if (step) {
+    BCK(b, rec(0));
+    if (b->flow)
+      kb_sweep<true><<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, fin, fout, qin, qmid, A.phi32,
+                                           A.u, A.flag);
+    else
+      kb_sweep<false><<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, fin, fout, qin, qmid, A.phi32,
+                                            A.u, A.flag);
+    BCK(b, rec(1));
+    if (b->flow) kb_advect<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, qmid, A.u, qin);
+    BCK(b, rec(2));
+    kb_extrapolate<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.mask, A.phi, A.phi_prev, A.phi32, A.hist);
+    nl += b->flow ? 3 : 2;
+  }
+  kb_solve_reset<<<(n + 255) / 256, 256, 0, st>>>(n, A.c, A.bc, A.hist, A.set_hist);
+  nl += 1;
+  // the V-cycle through a small graph keeps it identical to the graph path
+  cudaGraphExec_t vc = nullptr;
+  if (b->mg_nlev >= 2) {
+    cudaGraph_t g;
+    BCK(b, cudaGraphCreate(&g, 0));
+    cudaGraphNode_t last = nullptr;
+    cudaError_t e = add_vcycle(b, g, &last);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&vc, g, 0);
+    cudaGraphDestroy(g);
+    BCK(b, e);
+  }
+  const int vck = vcycle_kernels(b);
+  cudaError_t err = cudaSuccess;
+  auto flags = [&](int *outer, int *inner) {
+    if (err == cudaSuccess) err = cudaMemcpyAsync(b->bctl_h, b->bctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (outer) *outer = b->bctl_h->any_outer;
+    if (inner) *inner = b->bctl_h->any_inner;
+  };
+  const cudaGraphConditionalHandle h0 = 0;
+  int any_outer = 1;
+  while (any_outer && err == cudaSuccess) {
+    kb_res<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, A.qsolve, A.phi, A.v, A.part, A.c);
+    kb_outer<<<n, kBlock, 0, st>>>(A.inst, n, A.T, A.part, A.c, A.bc, A.tol, A.maxit, A.nfam, A.fam_cnt, A.fam_pref,
+                                   h0, h0, 0);
+    nl += 2;
+    flags(&any_outer, nullptr);
+    if (!any_outer) break;
+    if (vc && err == cudaSuccess) err = cudaGraphLaunch(vc, st), nl += vck;
+    kb_cg_b<<<G, kBlock, 0, st>>>(A.inst, n, A.pref0, A.T, A.mask, A.vr, A.vu, A.vw, A.part);
+    kb_scal<<<n, kBlock, 0, st>>>(A.inst, n, A.T, A.part, A.c, A.bc, A.eta, A.tol_abs, A.maxit, 1, A.nfam, A.fam_cnt,
+                                  A.fam_pref, h0, 0);
+    nl += 2;
+    int any_inner = 0;
+    flags(nullptr, &any_inner);
+    while (any_inner && err == cudaSuccess) {
+      kb_cg_a<<<G, kBlock, 0, st>>>(A.inst, n, A.pref0, A.T, A.mask, A.v, A.part, A.c);
+      if (vc) err = cudaGraphLaunch(vc, st), nl += vck;
+      kb_cg_b<<<G, kBlock, 0, st>>>(A.inst, n, A.pref0, A.T, A.mask, A.vr, A.vu, A.vw, A.part);
+      kb_scal<<<n, kBlock, 0, st>>>(A.inst, n, A.T, A.part, A.c, A.bc, A.eta, A.tol_abs, A.maxit, 0, A.nfam,
+                                    A.fam_cnt, A.fam_pref, h0, 0);
+      nl += 3;
+      flags(nullptr, &any_inner);
+    }
+    kb_correct<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.mask, A.vx, A.phi, A.phi32, A.c);
+    nl += 1;
+  }
+  if (vc) cudaGraphExecDestroy(vc);
+  BCK(b, err);
+  BCK(b, cudaGetLastError());
+  BCK(b, rec(3));
+  return LBE_OK;
+}
+
+// after a profiled step: accumulate the phase times
+int profile_collect(lbe_batch *b) {
+  BCK(b, cudaEventSynchronize(b->ev[3]));
+  float t[3];
+  for (int k = 0; k < 3; ++k) {
+    BCK(b, cudaEventElapsedTime(&t[k], b->ev[k], b->ev[k + 1]));
+    b->prof_ms[k] += t[k];
+  }
+  b->prof_steps += 1;
+  return LBE_OK;
+}
+
+// launch one step (or, step = false, one solve): one graph launch, or the
+// host-polled sequence
+int launch_step(lbe_batch *b, bool step) {
+  const float *fin = b->f[b->cur];
+  float *fout = b->flow ? b->f[b->cur ^ 1] : b->f[b->cur];
+  if (b->polled) {
+    const int rc = run_polled(b, step, fin, fout, b->q, b->qstar);
+    if (rc != LBE_OK) return rc;
+  } else if (!step) {
     if (!b->exec[4]) BCK(b, build_graph(b, false, nullptr, nullptr, b->q, b->qstar, &b->exec[4]));
     BCK(b, cudaGraphLaunch(b->exec[4], b->stream));
     return LBE_OK;
+  } else {
+    const int base = b->profiling ? 5 : 0;
+    int slot = -1, empty = -1;
+    for (int k = base; k < base + 4; ++k) {
+      if (b->exec[k] && b->key_f[k] == fin && b->key_q[k] == b->q) slot = k;
+      if (!b->exec[k] && empty < 0) empty = k;
+    }
+    if (slot < 0) {
+      if (empty < 0) return bfail(b, LBE_ERR_STATE, "batch: graph cache full");
+      BCK(b, build_graph(b, true, fin, fout, b->q, b->qstar, &b->exec[empty], b->profiling));
+      b->key_f[empty] = fin;
+      b->key_q[empty] = b->q;
+      slot = empty;
+    }
+    BCK(b, cudaGraphLaunch(b->exec[slot], b->stream));
   }
-  const float *fin = b->f[b->cur];
-  float *fout = b->flow ? b->f[b->cur ^ 1] : b->f[b->cur];
-  int slot = -1, empty = -1;
-  for (int k = 0; k < 4; ++k) {
-    if (b->exec[k] && b->key_f[k] == fin && b->key_q[k] == b->q) slot = k;
-    if (!b->exec[k] && empty < 0) empty = k;
-  }
-  if (slot < 0) {
-    if (empty < 0) return bfail(b, LBE_ERR_STATE, "batch: graph cache full");
-    BCK(b, build_graph(b, true, fin, fout, b->q, b->qstar, &b->exec[empty]));
-    b->key_f[empty] = fin;
-    b->key_q[empty] = b->q;
-    slot = empty;
-  }
-  BCK(b, cudaGraphLaunch(b->exec[slot], b->stream));
+  if (!step) return LBE_OK;
   if (b->flow) {
     b->cur ^= 1;
   } else {
@@ -751,6 +1430,7 @@ int launch_graph(lbe_batch *b, bool step) {
     b->q = b->qstar;
     b->qstar = t;
   }
+  if (b->profiling) return profile_collect(b);
   return LBE_OK;
 }
 
@@ -856,7 +1536,7 @@ int lbe_batch_create(const lbe_params *params, int n, void *cuda_stream, lbe_bat
       return LBE_ERR_ARG;
     const long long N = (long long)p.nx * p.ny * p.nz;
     Ntot += N;
-    T += (N + lbe::kBlock - 1) / lbe::kBlock;
+    T += (N + lbe::kTile - 1) / lbe::kTile;
   }
   // 32-bit node indices; component offsets of the 3 velocity components stay
   // below 2^31 (the population components are offset in 64 bits)
@@ -884,7 +1564,13 @@ int lbe_batch_create(const lbe_params *params, int n, void *cuda_stream, lbe_bat
     I.g = lbe::Geo{p.nx, p.ny, p.nz, p.periodic[0] != 0, p.periodic[1] != 0, p.periodic[2] != 0, N};
     I.off = (int)off;
     I.tile0 = (int)t0;
-    I.ntiles = (int)((N + lbe::kBlock - 1) / lbe::kBlock);
+    I.ntiles = (int)((N + lbe::kTile - 1) / lbe::kTile);
+    I.fx = lbe::make_fastdiv((uint32_t)p.nx);
+    I.fxy = lbe::make_fastdiv((uint32_t)(p.nx * p.ny));
+    if (!lbe::fastdiv_ok(I.fx, (uint32_t)N) || !lbe::fastdiv_ok(I.fxy, (uint32_t)N)) {
+      delete b;
+      return LBE_ERR_ARG;
+    }
     I.n_elec = 0;
     I.selfmask = tmp.phys.selfmask;
     I.four_pi_lb = tmp.phys.four_pi_lb;
@@ -948,6 +1634,8 @@ int lbe_batch_create(const lbe_params *params, int n, void *cuda_stream, lbe_bat
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   b->grid = 4 * (sms > 0 ? sms : 152);
+  const char *env = getenv("LBE_POISSON_GRAPH");
+  b->polled = env && env[0] == '0';
   *out = b;
   return LBE_OK;
 }
@@ -1006,7 +1694,8 @@ int lbe_batch_init(lbe_batch *b) {
     BCK(b, cudaMemcpyAsync(b->id + I.off, b->ids[i].data(), I.g.N, cudaMemcpyHostToDevice, b->stream));
     BCK(b, launch_build_mask(I.g, b->id + I.off, b->mask + I.off, b->stream));
   }
-  BCK(b, cudaMemcpyAsync(b->inst_d, b->inst.data(), sizeof(InstDev) * b->n, cudaMemcpyHostToDevice, b->stream));
+  int rc = mg_setup(b);  // also uploads the instance table
+  if (rc != LBE_OK) return rc;
   BCK(b, cudaMemcpyAsync(b->psi_d, b->psi.data(), sizeof(double) * b->psi.size(), cudaMemcpyHostToDevice, b->stream));
   b->cur = 0;
   kb_init<<<b->grid, kBlock, 0, b->stream>>>(b->inst_d, b->tile_inst, b->T, b->Ntot, b->id, b->psi_d, b->f[0], b->q,
@@ -1015,11 +1704,11 @@ int lbe_batch_init(lbe_batch *b) {
   BCK(b, cudaMemsetAsync(b->hist, 0, sizeof(int), b->stream));
   BCK(b, cudaStreamSynchronize(b->stream));
   drop_graphs(b);
-  int rc = autotune(b);
+  rc = autotune(b);
   if (rc != LBE_OK) return rc;
   BCK(b, cudaMemsetAsync(b->flag, 0, sizeof(int), b->stream));
   BCK(b, cudaMemsetAsync(b->bctl, 0, sizeof(BatchCtl), b->stream));
-  rc = launch_graph(b, false);
+  rc = launch_step(b, false);
   if (rc != LBE_OK) return rc;
   rc = read_status(b);
   if (rc == LBE_OK) b->initialised = true;
@@ -1033,10 +1722,14 @@ int lbe_batch_step(lbe_batch *b, int nsteps) {
   if (nsteps < 0) return bfail(b, LBE_ERR_ARG, "batch step: negative step count");
   BCK(b, cudaMemsetAsync(b->bctl, 0, sizeof(BatchCtl), b->stream));
   for (int s = 0; s < nsteps; ++s) {
-    const int rc = launch_graph(b, true);
+    const int rc = launch_step(b, true);
     if (rc != LBE_OK) return rc;
   }
   int rc = read_status(b);
+  if (b->profiling) {
+    b->prof_iters += b->stats.poisson_iters;
+    b->prof_solves += b->stats.poisson_solves;
+  }
   if (rc != LBE_OK) return rc;
   return flags(b);
 }
@@ -1090,6 +1783,32 @@ int lbe_batch_fields(lbe_batch *b, int i, int which, double *out, int out_on_dev
 int lbe_batch_get_stats(const lbe_batch *b, lbe_stats *out) {
   if (!b || !out) return LBE_ERR_ARG;
   *out = b->stats;
+  return LBE_OK;
+}
+
+int lbe_batch_profile_begin(lbe_batch *b) {
+  if (!b) return LBE_ERR_ARG;
+  for (int k = 0; k < 4; ++k)
+    if (!b->ev[k]) BCK(b, cudaEventCreate(&b->ev[k]));
+  b->profiling = true;
+  b->prof_ms[0] = b->prof_ms[1] = b->prof_ms[2] = 0.0;
+  b->prof_steps = b->prof_iters = b->prof_solves = b->prof_launches = 0;
+  return LBE_OK;
+}
+
+int lbe_batch_profile_end(lbe_batch *b, lbe_profile *out) {
+  if (!b || !out) return LBE_ERR_ARG;
+  BCK(b, cudaStreamSynchronize(b->stream));
+  memset(out, 0, sizeof(*out));
+  out->sweep_ms = b->prof_ms[0];
+  out->advect_ms = b->prof_ms[1];
+  out->poisson_ms = b->prof_ms[2];
+  out->sweep_launches = b->prof_steps;
+  out->advect_launches = b->flow ? b->prof_steps : 0;
+  out->poisson_solves = b->prof_solves;
+  out->poisson_iters = b->prof_iters;
+  out->kernel_launches = b->polled ? b->prof_launches : -1;
+  b->profiling = false;
   return LBE_OK;
 }
 

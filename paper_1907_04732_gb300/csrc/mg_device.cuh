@@ -1,0 +1,382 @@
+// Per-node arithmetic of the geometric multigrid preconditioner of the FP32
+// Poisson correction solve, shared by the single-lattice V-cycle (mg.cu) and
+// the batched one (batch.cu).
+//
+//   hierarchy   level 0 is the lattice with the modified-Laplacian operator
+//               of Eq. DiscreteLaplacianModif on fluid nodes; level l+1
+//               aggregates 2x2x2 nodes of level l (an axis of one node is
+//               kept) and carries the Galerkin operator A_{l+1} = P^T A_l P
+//               of the piecewise-constant prolongation P: 27 points, exact
+//               for any electrode shape, solid nodes being Dirichlet zeros
+//               of the correction
+//   smoother    weighted Jacobi, one sweep before and one after the coarse
+//               correction (the same on both sides, so the preconditioner
+//               is symmetric)
+//   correction  e += alpha P e_c, alpha > 1 compensating the stiffness of
+//               piecewise-constant coarse spaces
+//   coarsest    a fixed number of Jacobi sweeps in one thread block
+//
+// A coarse level is an MgLevel; its operator is stored component-major with
+// component stride S (S = N for one lattice, the level's total node count
+// when several lattices are concatenated), and every pointer handed to these
+// functions is already offset to the lattice's first node of that level.
+#pragma once
+
+#include "lbe_internal.cuh"
+
+namespace lbe {
+namespace mgd {
+
+constexpr float kOmega = 0.7f;     // Jacobi weight
+constexpr float kAlpha = 1.6f;     // coarse-correction scaling
+constexpr int kCoarseSweeps = 32;  // Jacobi sweeps on the coarsest level
+constexpr int kCoarseTarget = 256; // coarsening stops at or below this size
+constexpr int kCoarseMax = 1024;   // the coarsest solve owns one node per thread
+
+struct MgLevel {
+  int nx, ny, nz;
+  int sx, sy, sz;  // 1 when this level halves the axis of the finer level
+  int N;
+  long long S;     // component stride of the operator array
+};
+
+// Shapes of the coarse levels of an nx x ny x nz lattice: every axis longer
+// than one node is halved (rounding up; the last aggregate of an odd axis
+// holds one node, on a periodic axis it neighbours the first one) until the
+// level has at most kCoarseTarget nodes.  Returns the level count (including
+// level 0), or 0 when the coarsest level would not fit the one-block solve.
+inline int level_shapes(int nx, int ny, int nz, MgLevel out[kMaxLevels]) {
+  int nlev = 1;
+  for (int l = 1; l < kMaxLevels; ++l) {
+    const bool cx = nx > 1, cy = ny > 1, cz = nz > 1;
+    if (!cx && !cy && !cz) break;
+    if ((long long)nx * ny * nz <= kCoarseTarget && l > 1) break;
+    nx = cx ? (nx + 1) / 2 : nx;
+    ny = cy ? (ny + 1) / 2 : ny;
+    nz = cz ? (nz + 1) / 2 : nz;
+    out[l] = MgLevel{nx, ny, nz, cx, cy, cz, nx * ny * nz, (long long)nx * ny * nz};
+    nlev = l + 1;
+  }
+  if (nlev < 2 || out[nlev - 1].N > kCoarseMax) return 0;
+  return nlev;
+}
+
+__host__ __device__ constexpr int d27(int dx, int dy, int dz) { return (dx + 1) + 3 * ((dy + 1) + 3 * (dz + 1)); }
+
+// wrapped coordinate (periodic axes; coordinates stay in range otherwise)
+__device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// offset of the (coarse) node J relative to I along one axis, in {-1,0,1}
+__device__ __forceinline__ int rel(int J, int I, int n) {
+  int d = J - I;
+  if (d > 1) d -= n;
+  if (d < -1) d += n;
+  if (n == 2 && d == -1) d = 1;  // on a 2-node periodic axis +1 and -1 coincide
+  return d;
+}
+
+__device__ __forceinline__ int agg_index(const MgLevel &C, int x, int y, int z) {
+  return (x >> C.sx) + C.nx * ((y >> C.sy) + C.ny * (z >> C.sz));
+}
+
+__device__ __forceinline__ void level_coords(const MgLevel &L, int I, int &X, int &Y, int &Z) {
+  X = I % L.nx;
+  Y = (I / L.nx) % L.ny;
+  Z = I / (L.nx * L.ny);
+}
+
+// child ch (0..7) of coarse node (X,Y,Z) in the finer level of size n*;
+// false when the child does not exist
+__device__ __forceinline__ bool child_of(const MgLevel &C, int X, int Y, int Z, int ch, int fnx, int fny, int fnz,
+                                         int &x, int &y, int &z) {
+  const int ax = ch & 1, ay = (ch >> 1) & 1, az = ch >> 2;
+  if ((ax && !C.sx) || (ay && !C.sy) || (az && !C.sz)) return false;
+  x = (X << C.sx) + ax;
+  y = (Y << C.sy) + ay;
+  z = (Z << C.sz) + az;
+  return x < fnx && y < fny && z < fnz;
+}
+
+// --- set-up ------------------------------------------------------------------
+__device__ __forceinline__ float inv_diag0(uint32_t m, uint32_t selfmask) {
+  if (!(m & kFluidBit)) return 0.f;
+  float dg = 0.f;
+#pragma unroll
+  for (int l = 1; l < kQ; ++l) {
+    const uint32_t b = 1u << (l - 1);
+    if (selfmask & b) continue;
+    dg += (m & b) ? (float)lapc_of(l) : 2.f * (float)lapc_of(l);
+  }
+  return 1.f / dg;
+}
+
+// Galerkin row of coarse node (X,Y,Z) of level 1 from the fine lattice
+// (mask-defined operator); mask points at the lattice's node 0
+__device__ __forceinline__ void galerkin0_row(const Geo &g, uint32_t selfmask, const uint32_t *__restrict__ mask,
+                                              const MgLevel &C, int X, int Y, int Z, float a[27]) {
+#pragma unroll
+  for (int d = 0; d < 27; ++d) a[d] = 0.f;
+  for (int c = 0; c < 8; ++c) {
+    int x, y, z;
+    if (!child_of(C, X, Y, Z, c, g.nx, g.ny, g.nz, x, y, z)) continue;
+    const int i = x + g.nx * (y + g.ny * z);
+    const uint32_t m = mask[i];
+    if (!(m & kFluidBit)) continue;
+    float diag = 0.f;
+    for (int l = 1; l < kQ; ++l) {
+      const uint32_t b = 1u << (l - 1);
+      if (selfmask & b) continue;
+      const float w = (float)lapc_of(l);
+      if (!(m & b)) {  // link to solid: doubled, Dirichlet
+        diag += 2.f * w;
+        continue;
+      }
+      diag += w;
+      const int jx = wrap(x + cx_of(l), g.nx), jy = wrap(y + cy_of(l), g.ny), jz = wrap(z + cz_of(l), g.nz);
+      const int dx = rel(jx >> C.sx, X, C.nx), dy = rel(jy >> C.sy, Y, C.ny), dz = rel(jz >> C.sz, Z, C.nz);
+      a[d27(dx, dy, dz)] -= w;
+    }
+    a[13] += diag;
+  }
+}
+
+// Galerkin row of coarse node (X,Y,Z) of level l+1 from level l (27-point)
+__device__ __forceinline__ void galerkin_row(const MgLevel &F, const float *__restrict__ AF, const MgLevel &C, int X,
+                                             int Y, int Z, float a[27]) {
+#pragma unroll
+  for (int d = 0; d < 27; ++d) a[d] = 0.f;
+  for (int c = 0; c < 8; ++c) {
+    int x, y, z;
+    if (!child_of(C, X, Y, Z, c, F.nx, F.ny, F.nz, x, y, z)) continue;
+    const int i = x + F.nx * (y + F.ny * z);
+    if (AF[13 * F.S + i] == 0.f) continue;  // inactive node
+    for (int d = 0; d < 27; ++d) {
+      const float v = AF[d * F.S + i];
+      if (v == 0.f) continue;
+      const int jx = wrap(x + d % 3 - 1, F.nx), jy = wrap(y + (d / 3) % 3 - 1, F.ny), jz = wrap(z + d / 9 - 1, F.nz);
+      const int dx = rel(jx >> C.sx, X, C.nx), dy = rel(jy >> C.sy, Y, C.ny), dz = rel(jz >> C.sz, Z, C.nz);
+      a[d27(dx, dy, dz)] += v;
+    }
+  }
+}
+
+// --- V-cycle -----------------------------------------------------------------
+__device__ __forceinline__ float sum8(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  return v;
+}
+
+// Residual after pre-smoothing from zero (e = omega r/diag) at fine node
+// (x,y,z) of the lattice: r - A e.  Pointers at the lattice's node 0.
+__device__ __forceinline__ float presmoothed_res0(const Geo &g, uint32_t selfmask, const uint32_t *__restrict__ mask,
+                                                  const float *__restrict__ r, const float *__restrict__ inv, int x,
+                                                  int y, int z) {
+  const int i = x + g.nx * (y + g.ny * z);
+  const uint32_t m = mask[i];
+  if (!(m & kFluidBit)) return 0.f;
+  const Offs o = offsets_of(g, x, y, z);
+  float s = 0.f, dg = 0.f;
+#pragma unroll
+  for (int l = 1; l < kQ; ++l) {
+    const uint32_t b = 1u << (l - 1);
+    if (selfmask & b) continue;
+    const float w = (float)lapc_of(l);
+    if (m & b) {
+      dg += w;
+      const int j = i + o.at(cx_of(l), cy_of(l), cz_of(l));
+      s += w * (kOmega * r[j] * inv[j]);
+    } else {
+      dg += 2.f * w;
+    }
+  }
+  const float ri = r[i];
+  return ri - (dg * (kOmega * ri * inv[i]) - s);
+}
+
+// the same on a 27-point level
+__device__ __forceinline__ float presmoothed_res(const MgLevel &L, const float *__restrict__ A,
+                                                 const float *__restrict__ r, int X, int Y, int Z) {
+  const int I = X + L.nx * (Y + L.ny * Z);
+  if (A[13 * L.S + I] == 0.f) return 0.f;
+  float s = 0.f;
+#pragma unroll
+  for (int d = 0; d < 27; ++d) {
+    const float a = A[d * L.S + I];
+    if (a == 0.f) continue;
+    const int jx = wrap(X + d % 3 - 1, L.nx), jy = wrap(Y + (d / 3) % 3 - 1, L.ny), jz = wrap(Z + d / 9 - 1, L.nz);
+    const int j = jx + L.nx * (jy + L.ny * jz);
+    s += a * (kOmega * r[j] / A[13 * L.S + j]);
+  }
+  return r[I] - s;
+}
+
+// corrected iterate of a 27-point level at node j: e = omega r/diag + alpha e_c
+__device__ __forceinline__ float corrected(const MgLevel &L, const float *__restrict__ A, const float *__restrict__ r,
+                                           const MgLevel &C, const float *__restrict__ ec, int x, int y, int z,
+                                           int j) {
+  const float d = A[13 * L.S + j];
+  return d != 0.f ? kOmega * r[j] / d + kAlpha * ec[agg_index(C, x, y, z)] : 0.f;
+}
+
+// fused prolongation + post-smoothing on a 27-point level:
+// e + omega (r - A e)/diag with e as in corrected()
+__device__ __forceinline__ float post_value(const MgLevel &L, const float *__restrict__ A, const float *__restrict__ r,
+                                           const MgLevel &C, const float *__restrict__ ec, int X, int Y, int Z) {
+  const int I = X + L.nx * (Y + L.ny * Z);
+  const float d = A[13 * L.S + I];
+  if (d == 0.f) return 0.f;
+  float s = 0.f;
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    const float a = A[q * L.S + I];
+    if (a == 0.f) continue;
+    const int jx = wrap(X + q % 3 - 1, L.nx), jy = wrap(Y + (q / 3) % 3 - 1, L.ny), jz = wrap(Z + q / 9 - 1, L.nz);
+    s += a * corrected(L, A, r, C, ec, jx, jy, jz, jx + L.nx * (jy + L.ny * jz));
+  }
+  const float e = corrected(L, A, r, C, ec, X, Y, Z, I);
+  return e + kOmega * (r[I] - s) / d;
+}
+
+// level 0 after the prolongation t: t + omega (r - A t)/diag
+__device__ __forceinline__ float post_value0(const Geo &g, uint32_t selfmask, uint32_t m, int x, int y, int z, int i,
+                                            const float *__restrict__ r, const float *__restrict__ inv,
+                                            const float *__restrict__ t) {
+  if (!(m & kFluidBit)) return 0.f;
+  const Offs o = offsets_of(g, x, y, z);
+  float s = 0.f, dg = 0.f;
+#pragma unroll
+  for (int l = 1; l < kQ; ++l) {
+    const uint32_t b = 1u << (l - 1);
+    if (selfmask & b) continue;
+    const float w = (float)lapc_of(l);
+    if (m & b) {
+      dg += w;
+      s += w * t[i + o.at(cx_of(l), cy_of(l), cz_of(l))];
+    } else {
+      dg += 2.f * w;
+    }
+  }
+  const float ti = t[i];
+  return ti + kOmega * (r[i] - (dg * ti - s)) * inv[i];
+}
+
+// coarsest level: kCoarseSweeps weighted Jacobi sweeps from zero by one
+// block of kCoarseMax threads, one node per thread, iterates in buf
+__device__ __forceinline__ void coarsest_solve(const MgLevel &L, const float *__restrict__ A,
+                                               const float *__restrict__ r, float *__restrict__ e,
+                                               float (*buf)[kCoarseMax]) {
+  const int I = threadIdx.x;
+  const bool own = I < L.N;
+  float d = 0.f, ri = 0.f, a[27];
+  int nb[27];
+  if (own) {
+    int X, Y, Z;
+    level_coords(L, I, X, Y, Z);
+    d = A[13 * L.S + I];
+    ri = r[I];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      a[q] = A[q * L.S + I];
+      const int jx = wrap(X + q % 3 - 1, L.nx), jy = wrap(Y + (q / 3) % 3 - 1, L.ny), jz = wrap(Z + q / 9 - 1, L.nz);
+      nb[q] = jx + L.nx * (jy + L.ny * jz);
+    }
+    buf[0][I] = d != 0.f ? kOmega * ri / d : 0.f;
+  }
+  __syncthreads();
+  int cur = 0;
+  for (int s = 1; s < kCoarseSweeps; ++s) {
+    if (own) {
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < 27; ++q) acc += a[q] * buf[cur][nb[q]];
+      buf[cur ^ 1][I] = d != 0.f ? buf[cur][I] + kOmega * (ri - acc) / d : 0.f;
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  if (own) e[I] = buf[cur][I];
+}
+
+
+// --- forms with integer link weights and a stored pre-smoothed iterate -------
+// The modified Laplacian's link weights 1/3 (axis) and 1/6 (diagonal) are
+// 2/6 and 1/6: sums of weights are integers over 6, and a node's diagonal
+// 6 * diag = sum over non-self links of (2 - fluid) * (2 axis, 1 diagonal)
+// follows from two population counts of its link mask.
+__host__ __device__ constexpr uint32_t axis_links() {
+  uint32_t m = 0;
+  for (int l = 1; l < kQ; ++l)
+    if (c2_of(l) == 1) m |= 1u << (l - 1);
+  return m;
+}
+__host__ __device__ constexpr uint32_t diag_links() {
+  uint32_t m = 0;
+  for (int l = 1; l < kQ; ++l)
+    if (c2_of(l) == 2) m |= 1u << (l - 1);
+  return m;
+}
+
+// 6 * diagonal of a fluid node's row
+__device__ __forceinline__ int diag6(uint32_t m, uint32_t selfmask) {
+  const uint32_t ax = axis_links() & ~selfmask, dg = diag_links() & ~selfmask;
+  return 2 * (2 * __popc(ax) + __popc(dg)) - (2 * __popc(m & ax) + __popc(m & dg));
+}
+
+// 6 * sum over fluid links of weight * v[neighbour]
+__device__ __forceinline__ float nbsum6(uint32_t m, uint32_t selfmask, const Offs &o, int i,
+                                        const float *__restrict__ v) {
+  float s = 0.f;
+#pragma unroll
+  for (int l = 1; l < kQ; ++l) {
+    const uint32_t b = 1u << (l - 1);
+    if ((m & b) && !(selfmask & b)) {
+      const float vj = v[i + o.at(cx_of(l), cy_of(l), cz_of(l))];
+      s = c2_of(l) == 1 ? fmaf(2.f, vj, s) : s + vj;
+    }
+  }
+  return s;
+}
+
+// residual of a 27-point level after pre-smoothing, the pre-smoothed iterate
+// z = omega r/diag being stored: r - A z at (X,Y,Z)
+__device__ __forceinline__ float presmoothed_res_z(const MgLevel &L, const float *__restrict__ A,
+                                                   const float *__restrict__ r, const float *__restrict__ z, int X,
+                                                   int Y, int Z) {
+  const int I = X + L.nx * (Y + L.ny * Z);
+  if (A[13 * L.S + I] == 0.f) return 0.f;
+  float s = 0.f;
+#pragma unroll
+  for (int d = 0; d < 27; ++d) {
+    const float a = A[d * L.S + I];
+    if (a == 0.f) continue;
+    const int jx = wrap(X + d % 3 - 1, L.nx), jy = wrap(Y + (d / 3) % 3 - 1, L.ny), jz = wrap(Z + d / 9 - 1, L.nz);
+    s = fmaf(a, z[jx + L.nx * (jy + L.ny * jz)], s);
+  }
+  return r[I] - s;
+}
+
+// fused prolongation + post-smoothing with the stored iterate:
+// e = z + alpha P e_c, out = e + omega (r - A e)/diag
+__device__ __forceinline__ float post_value_z(const MgLevel &L, const float *__restrict__ A,
+                                             const float *__restrict__ r, const float *__restrict__ z,
+                                             const MgLevel &C, const float *__restrict__ ec, int X, int Y, int Z) {
+  const int I = X + L.nx * (Y + L.ny * Z);
+  const float d = A[13 * L.S + I];
+  if (d == 0.f) return 0.f;
+  float s = 0.f;
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    const float a = A[q * L.S + I];
+    if (a == 0.f) continue;
+    const int jx = wrap(X + q % 3 - 1, L.nx), jy = wrap(Y + (q / 3) % 3 - 1, L.ny), jz = wrap(Z + q / 9 - 1, L.nz);
+    const float ej = fmaf(kAlpha, ec[agg_index(C, jx, jy, jz)], z[jx + L.nx * (jy + L.ny * jz)]);
+    s = fmaf(a, ej, s);
+  }
+  const float e = fmaf(kAlpha, ec[agg_index(C, X, Y, Z)], z[I]);
+  return e + kOmega * (r[I] - s) / d;
+}
+
+}  // namespace mgd
+}  // namespace lbe

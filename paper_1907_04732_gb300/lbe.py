@@ -39,7 +39,8 @@ EXPORTED = ["lbe_default_params", "lbe_create", "lbe_destroy", "lbe_last_error",
             "lbe_profile_begin", "lbe_profile_end", "lbe_induced_charge_static",
             "lbe_batch_create", "lbe_batch_destroy", "lbe_batch_last_error", "lbe_batch_set_geometry",
             "lbe_batch_set_voltage", "lbe_batch_init", "lbe_batch_step", "lbe_batch_charge",
-            "lbe_batch_fields", "lbe_batch_get_stats", "lbe_batch_tuning"]
+            "lbe_batch_fields", "lbe_batch_get_stats", "lbe_batch_tuning",
+            "lbe_batch_profile_begin", "lbe_batch_profile_end"]
 LBE_BATCH_MAX_ELECTRODES = 4
 LBE_BATCH_TUNE_CANDIDATES = 6
 
@@ -115,6 +116,8 @@ def load(path: str = LIB_PATH):
     lib.lbe_batch_fields.argtypes = [vp, ip, ip, vp, ip]
     lib.lbe_batch_get_stats.argtypes = [vp, ctypes.POINTER(lbe_stats)]
     lib.lbe_batch_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp]
+    lib.lbe_batch_profile_begin.argtypes = [vp]
+    lib.lbe_batch_profile_end.argtypes = [vp, ctypes.POINTER(lbe_profile)]
     for name in EXPORTED:
         if name not in ("lbe_default_params", "lbe_last_error", "lbe_batch_last_error"):
             getattr(lib, name).restype = ctypes.c_int
@@ -260,6 +263,16 @@ def lbe_batch_get_stats(b) -> lbe_stats:
     s = lbe_stats()
     _bcheck(b, load().lbe_batch_get_stats(b, ctypes.byref(s)))
     return s
+
+
+def lbe_batch_profile_begin(b):
+    return _bcheck(b, load().lbe_batch_profile_begin(b))
+
+
+def lbe_batch_profile_end(b) -> lbe_profile:
+    out = lbe_profile()
+    _bcheck(b, load().lbe_batch_profile_end(b, ctypes.byref(out)))
+    return out
 
 
 def lbe_batch_tuning(b):
@@ -470,3 +483,9 @@ class Batch:
 
     def tuning(self):
         return lbe_batch_tuning(self.b)
+
+    def profile_begin(self):
+        lbe_batch_profile_begin(self.b)
+
+    def profile_end(self) -> lbe_profile:
+        return lbe_batch_profile_end(self.b)

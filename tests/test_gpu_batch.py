@@ -159,3 +159,29 @@ def test_batch_full_size_sampled_vs_oracle(lbe):
         scale = max(abs(v) for v in w.psi)
         assert np.abs(phi_b - ref).max() <= TOL_PHI * scale, (w.name, np.abs(phi_b - ref).max() / scale)
         np.testing.assert_array_equal(units(b.n_field(i), w).sum(axis=(1, 2, 3)), units0[i])
+
+
+def test_batch_polled_matches_graph_and_profile(lbe, monkeypatch):
+    """The host-polled solve (LBE_POISSON_GRAPH=0, used to list kernels in a
+    profiler) launches the same kernels in the same order as the graph: the
+    results are bitwise equal.  The phase profiler reports every step."""
+    ws = small_mix(True)
+    out = []
+    for polled in (False, True):
+        if polled:
+            monkeypatch.setenv("LBE_POISSON_GRAPH", "0")
+        b = lbe.Batch(ws, tol=1e-12)
+        monkeypatch.delenv("LBE_POISSON_GRAPH", raising=False)
+        b.init()
+        b.profile_begin()
+        b.step(7)
+        p = b.profile_end()
+        assert p.sweep_launches == 7 and p.poisson_ms > 0 and p.sweep_ms > 0 and p.advect_ms > 0
+        assert p.poisson_iters > 0
+        assert (p.kernel_launches > 0) if polled else (p.kernel_launches == -1)
+        b.step(3)  # unprofiled steps after profiling use the plain graphs
+        out.append((b.charge(), [b.phi(i) for i in range(len(ws))]))
+        b.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    for a, c in zip(out[0][1], out[1][1]):
+        np.testing.assert_array_equal(a, c)
