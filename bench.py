@@ -9,6 +9,13 @@ uncharged capacitor with the voltage applied.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--workload eof|coax|plates|porous] [--precision fp64]
+                    [--batch-steps K2]
+
+Beside the main workload the line carries a "batched" object: the batched
+FP32 form on the 256-instance sweep of parallel-plate and coaxial capacitors
+(seeded sizes, Debye lengths and voltages), timed as one graph launch per
+step, with the plain FP64 single-lattice form timed on a sample of the same
+instances for comparison.
 
 Under torchrun (N > 1) every rank advances its own replica of the lattice
 (the workload does not shard across GPUs in this build); ``value`` sums the
@@ -206,6 +213,76 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def batch_leg(args, lbe, torch, stream, peak):
+    """The batched FP32 form on the 256-instance capacitor sweep: MLUPS of
+    one graph launch per step over all instances, the fused sweep's HBM
+    fraction, and the plain FP64 form timed instance by instance on a
+    sample (largest, smallest and four seeded others)."""
+    import numpy as np
+    ws = wl.batch_instances(256)
+    b = lbe.Batch(ws, tol=args.tol, stream=stream.cuda_stream)
+    b.init()
+    grid, tuned = b.tuning()
+    for _ in range(args.batch_warmup):
+        b.step(1)
+    torch.cuda.synchronize()
+    nodes = sum(w.nodes for w in ws)
+    fluid = sum(int((w.ids == 0).sum()) for w in ws)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    b.step(args.batch_steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.batch_steps
+    st = b.stats()
+    b.profile_begin()
+    b.step(2)
+    prof = b.profile_end()
+    q = b.charge()
+    b.close()
+    sweep_ms = prof.sweep_ms / max(prof.sweep_launches, 1)
+    sweep_gbs = BYTES["fp32"]["sweep"](2) * fluid / (sweep_ms * 1e-3) / 1e9
+    # plain FP64 single-lattice form on a sample of the instances
+    rng = np.random.Generator(np.random.PCG64(wl.SEED))
+    sizes = [w.nodes for w in ws]
+    sample = sorted({int(np.argmax(sizes)), int(np.argmin(sizes))} |
+                    set(int(i) for i in rng.choice(len(ws), 4, replace=False)))
+    t64, n64 = 0.0, 0
+    for i in sample:
+        w = ws[i]
+        lat = lbe.Lattice(lbe.params_for(w, tol=args.tol, precision=lbe.LBE_FP64), stream=stream.cuda_stream)
+        lat.set_geometry(w.ids, w.n_elec)
+        lat.set_voltage(w.psi)
+        lat.init()
+        lat.step(2)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        lat.step(3)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t64 += ev0.elapsed_time(ev1) / 3
+        n64 += w.nodes
+        lat.close()
+    fp64_mlups = n64 / (t64 * 1e-3) / 1e6
+    value = nodes / (ms * 1e-3) / 1e6
+    return {"workload": "256 plate/coax capacitors (seeded gaps 32-512, sides 8-64, Debye 2-32, "
+                        "voltages -0.5..0.5)",
+            "instances": len(ws), "nodes": nodes, "fluid_nodes": fluid,
+            "value": value, "unit": UNIT, "ms_per_step": ms, "steps": args.batch_steps,
+            "launch": "one CUDA graph launch per step (persistent kernels over all instances)",
+            "autotuned_grid_blocks": grid, "tuned_sweep_ms": tuned,
+            "phases_ms": {"sweep": sweep_ms,
+                          "advect": prof.advect_ms / max(prof.advect_launches, 1),
+                          "poisson": prof.poisson_ms / max(prof.sweep_launches, 1)},
+            "sweep_roofline": {"kernel": "kb_sweep (batched fused sweep)", "bound": "hbm",
+                               "achieved": sweep_gbs, "peak": peak, "unit": "GB/s", "frac": sweep_gbs / peak},
+            "cg_iters_per_step_summed_over_instances": st.poisson_iters / max(st.poisson_solves, 1),
+            "cg_iters_per_step_max_instance": st.poisson_max_iters,
+            "fp64_plain": {"value": fp64_mlups, "unit": UNIT, "speedup_batched_fp32": value / fp64_mlups,
+                           "sample": f"instances {sample}, one lattice at a time, 3 timed steps each"},
+            "charge_finite": bool(np.all(np.isfinite(q)))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -219,6 +296,9 @@ def main():
                     help="steps of the plain FP64 form timed for comparison (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--batch-steps", type=int, default=5,
+                    help="timed steps of the 256-instance batched form (0 = skip)")
+    ap.add_argument("--batch-warmup", type=int, default=3)
     args = ap.parse_args()
     w = make_workload(args.workload)
     if args.impl == "reference":
@@ -357,6 +437,8 @@ def main():
         line["fp64_plain"] = {"value": w.nodes / (ms64 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms64,
                               "steps": args.compare_steps, "speedup_fp32": ms64 / ms_step}
         l64.close()
+    if args.batch_steps > 0:
+        line["batched"] = batch_leg(args, lbe, torch, stream, peak)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.tol)
     if world > 1:
