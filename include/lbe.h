@@ -257,6 +257,48 @@ int lbe_batch_profile_end(lbe_batch *b, lbe_profile *out);
 #define LBE_BATCH_TUNE_CANDIDATES 6
 int lbe_batch_tuning(const lbe_batch *b, int *grid_blocks, double *ms_out);
 
+/* ------------------------------------------------------------------------
+ * Reverse-mode derivative (adjoint) of the induced charge after T steps of
+ * the FP32 form with the solvent at rest (flow = 0; a 1:1 salt with one
+ * bulk concentration).  The objective is S = sum_e dq[e] Q_e(T) (Eq. Qelec);
+ * its gradient is returned with respect to the electrode potentials, the
+ * bulk concentration rho_b (the Debye length enters only through it:
+ * rho_b = 1 / (8 pi l_B lambda_D^2)), the ion diffusivities and a soft
+ * electrode occupancy chi per node.  The occupancy derivative is that of a
+ * continuous reading of the method which equals it at chi in {0, 1}: the
+ * Poisson row of node r is (1 - chi_r)(lap phi + 4 pi l_B rho_el) +
+ * chi_r (psi - phi_r) with link factor 1 + (chi_r - chi_j)^2 (the doubling
+ * of fluid-solid links of Eq. DiscreteLaplacianModif), an ion link carries
+ * the flux of Eq. LF2 times (1 - chi_r)(1 - chi_j), the initial ions are
+ * rho_b (1 - chi), and Q_e sums chi_r (1 - chi_j) over the modified-Laplacian
+ * links of electrode-e nodes.  It is evaluated at the handle's (binary)
+ * geometry; a fluid node's chi turns it into part of soft_electrode.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  double dpsi[LBE_MAX_ELECTRODES]; /* dS/dpsi_e */
+  double drho_bulk;                /* dS/drho_b */
+  double dD[LBE_MAX_SPECIES];      /* dS/dD_k (species order of lbe_params) */
+  long long poisson_iters;         /* CG iterations of the adjoint Poisson solves */
+  long long recomputed_steps;      /* forward steps recomputed from checkpoints */
+} lbe_adjoint_grad;
+
+/* Forward pass for a later lbe_adjoint_backward: lbe_init, then nsteps
+ * steps, keeping the state every checkpoint_every steps in device memory
+ * (32 bytes per node per checkpoint, plus 20 bytes per node per step of one
+ * segment during the backward pass).  q_out (host, n_electrodes doubles,
+ * may be NULL) receives Q(T).  LBE_ERR_STATE when the handle is not an FP32,
+ * flow-off, 1:1-salt lattice with a geometry. */
+int lbe_adjoint_forward(lbe_handle *h, int nsteps, int checkpoint_every, double *q_out);
+
+/* Backward pass of the last lbe_adjoint_forward (LBE_ERR_STATE if the state
+ * changed since): dq (host, n_electrodes weights), soft_electrode in
+ * 1..n_electrodes, out receives the parameter gradients, dchi (N doubles,
+ * host or device by dchi_on_device, may be NULL) the occupancy gradient.
+ * Recomputes the forward states segment by segment and leaves the handle in
+ * the forward pass's final state. */
+int lbe_adjoint_backward(lbe_handle *h, const double *dq, int soft_electrode, lbe_adjoint_grad *out, double *dchi,
+                         int dchi_on_device);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "liblbe.so")
 OBJ = os.path.join(HERE, "_build")
-SOURCES = ["lbe_api.cu", "kernels_fp64.cu", "kernels_fp32.cu", "poisson.cu", "mg.cu", "charge_static.cu", "batch.cu"]
+SOURCES = ["lbe_api.cu", "kernels_fp64.cu", "kernels_fp32.cu", "poisson.cu", "mg.cu", "charge_static.cu", "batch.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -1,0 +1,543 @@
+// Reverse-mode derivative (adjoint) of the induced charge after T steps of
+// the FP32 form with the solvent at rest (declarations in include/lbe.h).
+//
+// Forward (Sec. "Lattice Boltzmann Electrokinetics", flow off):
+//   n^0 = rho_b (1 - chi),  phi^t = Poisson(n^t),
+//   n^{t+1} = n^t - sum_i J_i(n^t, phi^t)     (Eq. LF2 link fluxes)
+//   S = sum_e c_e Q_e(phi^T)                   (Eq. Qelec)
+// The derivatives are those of the soft-occupancy reading of the method
+// (row-scaled Poisson with a chi (psi - phi) term, link factor
+// 1 + (chi - chi')^2, ion-link openness (1 - chi)(1 - chi'), chi-weighted
+// charge), evaluated at the binary geometry of the handle, where that
+// reading is the method itself.
+//
+// Backward, t = T .. 0:
+//   phibar^T = dS/dphi^T                      (seed; direct chi terms of Q)
+//   mu^t: A mu = -phibar on fluid nodes       (adjoint Poisson, the FP32
+//         refinement solver with multigrid; A is symmetric), and on solid
+//         nodes mu_s = sum 2 w mu_fluid - phibar_s
+//   nbar^t += -4 pi l_B z_k mu;  psibar_e -= sum_{s in e} mu_s;  chibar += ...
+//   t > 0: the flux step's transpose gives nbar^{t-1}, phibar^{t-1}, Dbar,
+//          chibar (openness)
+//   t = 0: rho_bbar += sum nbar^0, chibar -= rho_b sum_k nbar^0
+// The forward states of a step are recomputed from checkpoints taken every
+// K steps (two-level checkpointing: the states of one segment are kept while
+// it is differentiated).  Parameter sums are FP64, in a fixed order.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "lbe_internal.cuh"
+
+namespace lbe {
+
+constexpr int kAdjSlots = LBE_MAX_ELECTRODES + LBE_MAX_SPECIES + 1;  // psibar, Dbar, rho_bbar
+constexpr int kSlotD = LBE_MAX_ELECTRODES, kSlotRho = LBE_MAX_ELECTRODES + LBE_MAX_SPECIES;
+
+struct AdjWork {
+  long long N = 0;
+  int T = 0, every = 0, nseg = 0, nblk = 0;
+  long long gen = -1;  // handle generation after the forward pass
+  bool ready = false;
+  int64_t *ck_q = nullptr;  // checkpoints [nseg + 1][2N] (the last: time T)
+  double *ck_phi = nullptr, *ck_prev = nullptr;  // [nseg + 1][N]
+  std::vector<char> ck_hist;
+  int64_t *st_q = nullptr;  // states of one segment [every][2N]
+  float *st_phi = nullptr;  // [every][N]
+  float *lam = nullptr, *lam2 = nullptr;  // nbar [2][N]
+  float *phibar = nullptr;
+  double *mu = nullptr, *rhs = nullptr, *chibar = nullptr;
+  double *part = nullptr, *acc = nullptr;  // [kAdjSlots][nblk], [kAdjSlots]
+  double q[LBE_MAX_ELECTRODES] = {};
+};
+
+namespace {
+
+struct Weights {
+  double c[LBE_MAX_ELECTRODES + 1];  // index = electrode id (0 unused)
+};
+
+// node index r -> coordinates and the in-box neighbour along link l (-1
+// outside a non-periodic face)
+__device__ __forceinline__ long long link_nbr(const Geo &g, int x, int y, int z, int l) {
+  return nbr(g, x, y, z, cx_of(l), cy_of(l), cz_of(l));
+}
+
+__device__ __forceinline__ float phi_at(long long j, const uint8_t *__restrict__ id, const float *__restrict__ phi,
+                                        const Weights &psi) {
+  const int e = id[j];
+  return e ? (float)psi.c[e] : phi[j];
+}
+
+// block partial sums of kAdjSlots values in a fixed order (thread 0 writes)
+__device__ __forceinline__ void block_partials(double *v, double *__restrict__ part, int nblk) {
+  __shared__ double sh[kBlock / 32][kAdjSlots];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  for (int k = 0; k < kAdjSlots; ++k) {
+    double a = v[k];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) sh[wid][k] = a;
+  }
+  __syncthreads();
+  if (t < kAdjSlots) {
+    double a = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) a += sh[w][t];
+    part[(long long)t * nblk + blockIdx.x] = a;
+  }
+}
+
+// seed of the backward pass: phibar = dS/dphi^T and the direct chi terms of
+// S = sum_e c_e Q_e (links from electrode nodes to fluid, weight 2 w)
+__global__ void __launch_bounds__(kBlock) k_adj_seed(const Geo g, const Phys P, const uint32_t *__restrict__ mask,
+                                                     const uint8_t *__restrict__ id, const float *__restrict__ phi,
+                                                     const Weights cq, const Weights psi, int soft,
+                                                     float *__restrict__ phibar, double *__restrict__ chibar) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < g.N; r += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    coords(g, r, x, y, z);
+    const uint32_t m = mask[r];
+    const int e = id[r];
+    const double pr = phi_at(r, id, phi, psi);
+    double pb = 0.0, cb = 0.0;
+    for (int l = 1; l < kQ; ++l) {
+      const uint32_t b = 1u << (l - 1);
+      if (P.selfmask & b) continue;
+      const double w = lapc_of(l);
+      const long long j = link_nbr(g, x, y, z, l);
+      if (j < 0 || j == r) continue;
+      const int ej = id[j];
+      const double pj = phi_at(j, id, phi, psi);
+      if (!e) {
+        if (m & b) {
+          cb += cq.c[soft] * (-P.eps) * w * (pj - pr);
+        } else {
+          pb += cq.c[ej] * (-P.eps) * 2.0 * w;
+          cb += cq.c[ej] * 4.0 * P.eps * w * (pr - pj);
+        }
+      } else {
+        if (m & b) {
+          pb += cq.c[e] * P.eps * 2.0 * w;
+          cb += cq.c[e] * (-4.0) * P.eps * w * (pj - pr);
+        } else if (ej && ej != e) {
+          cb += cq.c[ej] * P.eps * w * (pr - pj);
+        }
+      }
+    }
+    phibar[r] = (float)pb;
+    chibar[r] += cb;
+  }
+}
+
+// right-hand side of the adjoint Poisson solve: -phibar on fluid nodes
+__global__ void k_adj_rhs(long long N, const uint32_t *__restrict__ mask, const float *__restrict__ phibar,
+                          double *__restrict__ rhs) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x)
+    rhs[r] = (mask[r] & kFluidBit) ? -(double)phibar[r] : 0.0;
+}
+
+// after the adjoint solve: nbar += -4 pi l_B z mu (fluid), mu on solid nodes,
+// psibar, and the chi terms of the Poisson equation
+__global__ void __launch_bounds__(kBlock) k_adj_post(const Geo g, const Phys P, const uint32_t *__restrict__ mask,
+                                                     const uint8_t *__restrict__ id, const float *__restrict__ phi,
+                                                     const float *__restrict__ phibar, const double *__restrict__ mu,
+                                                     const Weights psi, int soft, float *__restrict__ lam,
+                                                     double *__restrict__ chibar, double *__restrict__ part,
+                                                     int nblk) {
+  double acc[kAdjSlots];
+  for (int k = 0; k < kAdjSlots; ++k) acc[k] = 0.0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < g.N; r += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    coords(g, r, x, y, z);
+    const uint32_t m = mask[r];
+    const int e = id[r];
+    if (!e) {
+      const double mr = mu[r], pr = phi[r];
+      lam[r] += (float)(-P.four_pi_lb * P.z[0] * mr);
+      lam[g.N + r] += (float)(-P.four_pi_lb * P.z[1] * mr);
+      double dR = psi.c[soft] - pr;  // d R_r / d chi_r
+      for (int l = 1; l < kQ; ++l) {
+        const uint32_t b = 1u << (l - 1);
+        if ((P.selfmask & b) || (m & b)) continue;
+        const long long j = link_nbr(g, x, y, z, l);
+        dR -= 2.0 * lapc_of(l) * (psi.c[id[j]] - pr);
+      }
+      chibar[r] += -mr * dR;
+    } else {
+      const double ps = psi.c[e];
+      double mus = -(double)phibar[r], lphi = 0.0, nb = 0.0;
+      for (int l = 1; l < kQ; ++l) {
+        const uint32_t b = 1u << (l - 1);
+        if (P.selfmask & b) continue;
+        const long long j = link_nbr(g, x, y, z, l);
+        if (j < 0 || j == r) continue;
+        const double w = lapc_of(l);
+        if (m & b) {
+          mus += 2.0 * w * mu[j];
+          lphi += 2.0 * w * ((double)phi[j] - ps);
+          nb += mu[j] * 2.0 * w * (ps - (double)phi[j]);
+        } else {
+          lphi += w * (psi.c[id[j]] - ps);
+        }
+      }
+      acc[e - 1] += -mus;
+      chibar[r] += mus * lphi - nb;
+    }
+  }
+  block_partials(acc, part, nblk);
+}
+
+// transpose of one flux step: lam_in = nbar^{t+1}, state (q, phi) of time t
+// -> nbar^t, phibar^t, Dbar, chibar (openness)
+__global__ void __launch_bounds__(kBlock) k_adj_flux(const Geo g, const Phys P, const P32 P3,
+                                                     const uint32_t *__restrict__ mask, const uint8_t *__restrict__ id,
+                                                     const int64_t *__restrict__ q, const float *__restrict__ phi,
+                                                     const Weights psi, const float *__restrict__ lam_in,
+                                                     float *__restrict__ lam_out, float *__restrict__ phibar,
+                                                     double *__restrict__ chibar, double *__restrict__ part,
+                                                     int nblk) {
+  const float a0inv = 1.f / (1.f + 2.f * sqrtf(2.f));  // d = D / A0
+  double acc[kAdjSlots];
+  for (int k = 0; k < kAdjSlots; ++k) acc[k] = 0.0;
+  const float unit = ldexpf(1.f, -kFixBits);
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < g.N; r += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    coords(g, r, x, y, z);
+    const uint32_t m = mask[r];
+    const int e = id[r];
+    if (!e) {
+      const float pr = phi[r];
+      float nbar[2], pb = 0.f;
+      double cb = 0.0, dD[2] = {0.0, 0.0};
+      for (int k = 0; k < 2; ++k) nbar[k] = lam_in[k * g.N + r];
+      for (int l = 1; l < kQ; ++l) {
+        const uint32_t b = 1u << (l - 1);
+        if ((P.selfmask & b) || !(m & b)) continue;
+        const long long j = link_nbr(g, x, y, z, l);
+        const float dl_len = (float)invlen_of(l);
+        for (int k = 0; k < 2; ++k) {
+          const float zk = (float)P.z[k], dk = (float)P.d[k];
+          const float dlam = lam_in[k * g.N + j] - lam_in[k * g.N + r];
+          const float dmu = zk * (phi[j] - pr - (float)P.e_dot_c[l]);
+          const float ep = expf(dmu), em = expf(-dmu), epm1 = expm1f(dmu);
+          const float avg = 0.5f * (1.f + em);
+          // n = rho_b (1 + nu), nu = 2^-40 q: n' e^dmu - n = rho_b ((nu' - nu) + (1 + nu') (e^dmu - 1))
+          const float nur = unit * (float)q[k * g.N + r], nuj = unit * (float)q[k * g.N + j];
+          const float dnu = unit * (float)(q[k * g.N + j] - q[k * g.N + r]);
+          const float rb = (float)P3.rbd[k];
+          const float bracket = rb * (dnu + (1.f + nuj) * epm1);
+          const float nr = rb * (1.f + nur), nj = rb * (1.f + nuj);
+          const float J = -dk * dl_len * avg * bracket;
+          nbar[k] += dlam * dk * dl_len * avg;                               // dJ/dn_r
+          pb += dlam * (-dk * dl_len * 0.5f * (nr * em + nj * ep)) * (-zk);  // dJ/ddmu ddmu/dphi_r
+          dD[k] += 0.5 * (double)(dlam * (-a0inv * dl_len * avg * bracket));  // dJ/dD_k (each link seen twice)
+          cb += (double)(dlam * -J);                                          // d openness / d chi_r
+        }
+      }
+      for (int k = 0; k < 2; ++k) {
+        lam_out[k * g.N + r] = nbar[k];
+        acc[kSlotD + k] += dD[k];
+      }
+      phibar[r] = pb;
+      chibar[r] += cb;
+    } else {
+      lam_out[r] = lam_out[g.N + r] = 0.f;
+      phibar[r] = 0.f;
+      if (!(m & ((1u << 18) - 1))) continue;
+      const float ps = (float)psi.c[e];
+      double cb = 0.0;
+      for (int l = 1; l < kQ; ++l) {
+        const uint32_t b = 1u << (l - 1);
+        if ((P.selfmask & b) || !(m & b)) continue;
+        const long long j = link_nbr(g, x, y, z, l);
+        const float dl_len = (float)invlen_of(l);
+        for (int k = 0; k < 2; ++k) {
+          const float zk = (float)P.z[k], dk = (float)P.d[k];
+          const float dmu = zk * (phi[j] - ps - (float)P.e_dot_c[l]);
+          const float nj = (float)P3.rbd[k] * (1.f + unit * (float)q[k * g.N + j]);
+          // flux a link from this node (no ions) to fluid j would carry
+          const float Jt = -dk * dl_len * 0.5f * (1.f + expf(-dmu)) * nj * expf(dmu);
+          cb += (double)(lam_in[k * g.N + j] * -Jt);
+        }
+      }
+      chibar[r] += cb;
+    }
+  }
+  block_partials(acc, part, nblk);
+}
+
+// t = 0: n^0 = rho_b (1 - chi)
+__global__ void __launch_bounds__(kBlock) k_adj_init(long long N, const uint32_t *__restrict__ mask, double rho_b,
+                                                     const float *__restrict__ lam, double *__restrict__ chibar,
+                                                     double *__restrict__ part, int nblk) {
+  double acc[kAdjSlots];
+  for (int k = 0; k < kAdjSlots; ++k) acc[k] = 0.0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x) {
+    if (!(mask[r] & kFluidBit)) continue;
+    const double s = (double)lam[r] + (double)lam[N + r];
+    acc[kSlotRho] += s;
+    chibar[r] += -rho_b * s;
+  }
+  block_partials(acc, part, nblk);
+}
+
+// acc[k] += sum of the block partials, in block order
+__global__ void k_adj_accumulate(const double *__restrict__ part, int nblk, double *__restrict__ acc) {
+  const int k = blockIdx.x;
+  double a = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += 32) a += part[(long long)k * nblk + b];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+  if (threadIdx.x == 0) acc[k] += a;
+}
+
+int afail(lbe_handle *h, int code, const std::string &m) {
+  h->err = m;
+  return code;
+}
+
+#define ACK(h, expr)                                                                                   \
+  do {                                                                                                 \
+    cudaError_t e_ = (expr);                                                                           \
+    if (e_ != cudaSuccess) return afail((h), LBE_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+int adj_alloc(lbe_handle *h, int T, int every) {
+  AdjWork *a = h->adj;
+  const long long N = h->geo.N;
+  const int nseg = T > 0 ? (T + every - 1) / every : 0;
+  const bool same = a && a->N == N && a->nseg == nseg && a->every == every;
+  if (!same) {
+    adjoint_free(h);
+    a = h->adj = new AdjWork();
+    a->N = N;
+    a->nseg = nseg;
+    a->every = every;
+    a->nblk = (int)std::min<long long>((N + kBlock - 1) / kBlock, 1184);
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **p, size_t bytes) {
+      if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    const size_t ns1 = (size_t)nseg + 1;
+    alloc((void **)&a->ck_q, sizeof(int64_t) * 2 * N * ns1);
+    alloc((void **)&a->ck_phi, sizeof(double) * N * ns1);
+    alloc((void **)&a->ck_prev, sizeof(double) * N * ns1);
+    alloc((void **)&a->st_q, sizeof(int64_t) * 2 * N * std::max(every, 1));
+    alloc((void **)&a->st_phi, sizeof(float) * N * std::max(every, 1));
+    alloc((void **)&a->lam, sizeof(float) * 2 * N);
+    alloc((void **)&a->lam2, sizeof(float) * 2 * N);
+    alloc((void **)&a->phibar, sizeof(float) * N);
+    alloc((void **)&a->mu, sizeof(double) * N);
+    alloc((void **)&a->rhs, sizeof(double) * N);
+    alloc((void **)&a->chibar, sizeof(double) * N);
+    alloc((void **)&a->part, sizeof(double) * kAdjSlots * a->nblk);
+    alloc((void **)&a->acc, sizeof(double) * kAdjSlots);
+    a->ck_hist.assign(ns1, 0);
+    if (e != cudaSuccess) {
+      adjoint_free(h);
+      return afail(h, LBE_ERR_CUDA, std::string("adjoint: device memory: ") + cudaGetErrorString(e));
+    }
+  }
+  a->T = T;
+  return LBE_OK;
+}
+
+// checkpoint k <-> the handle's state (solute, potential, warm-start history)
+int save_ck(lbe_handle *h, int k) {
+  AdjWork *a = h->adj;
+  const long long N = h->geo.N;
+  ACK(h, cudaMemcpyAsync(a->ck_q + (size_t)k * 2 * N, h->q, sizeof(int64_t) * 2 * N, cudaMemcpyDeviceToDevice,
+                         h->stream));
+  ACK(h, cudaMemcpyAsync(a->ck_phi + (size_t)k * N, h->phi, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+  ACK(h, cudaMemcpyAsync(a->ck_prev + (size_t)k * N, h->pw.phi_prev, sizeof(double) * N, cudaMemcpyDeviceToDevice,
+                         h->stream));
+  a->ck_hist[k] = h->pw.have_history ? 1 : 0;
+  return LBE_OK;
+}
+
+int load_ck(lbe_handle *h, int k) {
+  AdjWork *a = h->adj;
+  const long long N = h->geo.N;
+  ACK(h, cudaMemcpyAsync(h->q, a->ck_q + (size_t)k * 2 * N, sizeof(int64_t) * 2 * N, cudaMemcpyDeviceToDevice,
+                         h->stream));
+  ACK(h, cudaMemcpyAsync(h->phi, a->ck_phi + (size_t)k * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+  ACK(h, cudaMemcpyAsync(h->pw.phi_prev, a->ck_prev + (size_t)k * N, sizeof(double) * N, cudaMemcpyDeviceToDevice,
+                         h->stream));
+  h->pw.have_history = a->ck_hist[k] != 0;
+  ACK(h, launch_phi32_sync(h));
+  return LBE_OK;
+}
+
+// adjoint Poisson solve at one time: mu, then nbar, psibar, chibar
+int adj_poisson(lbe_handle *h, const float *phi_t, const Weights &psi, int soft) {
+  AdjWork *a = h->adj;
+  const Geo g = h->geo;
+  const int nb = a->nblk;
+  k_adj_rhs<<<nb, kBlock, 0, h->stream>>>(g.N, h->mask, a->phibar, a->rhs);
+  ACK(h, cudaGetLastError());
+  const int rc = poisson_solve_linear(h, a->rhs, a->mu, 1e-30, 1e-9);
+  if (rc != LBE_OK) return rc;
+  k_adj_post<<<nb, kBlock, 0, h->stream>>>(g, h->phys, h->mask, h->id, phi_t, a->phibar, a->mu, psi, soft, a->lam,
+                                           a->chibar, a->part, nb);
+  k_adj_accumulate<<<kAdjSlots, 32, 0, h->stream>>>(a->part, nb, a->acc);
+  ACK(h, cudaGetLastError());
+  return LBE_OK;
+}
+
+bool adjoint_supported(const lbe_handle *h, std::string *why) {
+  const lbe_params &p = h->prm;
+  if (p.precision != LBE_FP32) return *why = "adjoint: FP32 form only", false;
+  if (p.flow) return *why = "adjoint: solvent at rest only (flow = 0)", false;
+  if (!h->p32.salt11 || p.rho_bulk[0] != p.rho_bulk[1])
+    return *why = "adjoint: 1:1 salt (z = +1, -1) with one bulk concentration only", false;
+  if (!h->have_geometry) return *why = "adjoint: no geometry", false;
+  return true;
+}
+
+}  // namespace
+
+void adjoint_free(lbe_handle *h) {
+  AdjWork *a = h->adj;
+  if (!a) return;
+  void *ptrs[] = {a->ck_q, a->ck_phi, a->ck_prev, a->st_q, a->st_phi, a->lam, a->lam2, a->phibar,
+                  a->mu,   a->rhs,    a->chibar,  a->part, a->acc};
+  for (void *p : ptrs) cudaFree(p);
+  delete a;
+  h->adj = nullptr;
+}
+
+}  // namespace lbe
+
+extern "C" {
+
+int lbe_adjoint_forward(lbe_handle *h, int nsteps, int checkpoint_every, double *q_out) {
+  using namespace lbe;
+  if (!h) return LBE_ERR_ARG;
+  std::string why;
+  if (!adjoint_supported(h, &why)) return afail(h, LBE_ERR_STATE, why);
+  if (nsteps < 0 || checkpoint_every < 1) return afail(h, LBE_ERR_ARG, "adjoint_forward: bad step counts");
+  int rc = adj_alloc(h, nsteps, checkpoint_every);
+  if (rc != LBE_OK) return rc;
+  AdjWork *a = h->adj;
+  a->ready = false;
+  rc = lbe_init(h);
+  if (rc != LBE_OK) return rc;
+  for (int s = 0; s < a->nseg; ++s) {
+    rc = save_ck(h, s);
+    if (rc != LBE_OK) return rc;
+    rc = lbe_step(h, std::min(checkpoint_every, nsteps - s * checkpoint_every));
+    if (rc != LBE_OK) return rc;
+  }
+  rc = save_ck(h, a->nseg);  // time T, restored after a backward pass
+  if (rc != LBE_OK) return rc;
+  double q[LBE_MAX_ELECTRODES] = {};
+  if (h->n_elec) {
+    rc = lbe_induced_charge(h, q, 0);
+    if (rc != LBE_OK) return rc;
+  }
+  for (int e = 0; e < h->n_elec; ++e) {
+    a->q[e] = q[e];
+    if (q_out) q_out[e] = q[e];
+  }
+  ACK(h, cudaStreamSynchronize(h->stream));
+  a->gen = h->gen;
+  a->ready = true;
+  return LBE_OK;
+}
+
+int lbe_adjoint_backward(lbe_handle *h, const double *dq, int soft_electrode, lbe_adjoint_grad *out, double *dchi,
+                         int dchi_on_device) {
+  using namespace lbe;
+  if (!h) return LBE_ERR_ARG;
+  AdjWork *a = h->adj;
+  if (!a || !a->ready || a->gen != h->gen)
+    return afail(h, LBE_ERR_STATE, "adjoint_backward: no forward pass (or the state changed since)");
+  if (!dq || !out || soft_electrode < 1 || soft_electrode > h->n_elec)
+    return afail(h, LBE_ERR_ARG, "adjoint_backward: bad arguments");
+  const Geo g = h->geo;
+  const long long N = g.N;
+  const int nb = a->nblk;
+  Weights cq{}, psi{};
+  for (int e = 0; e < h->n_elec; ++e) {
+    cq.c[e + 1] = dq[e];
+    psi.c[e + 1] = h->psi[e];
+  }
+  cudaStream_t st = h->stream;
+  ACK(h, cudaMemsetAsync(a->lam, 0, sizeof(float) * 2 * N, st));
+  ACK(h, cudaMemsetAsync(a->mu, 0, sizeof(double) * N, st));
+  ACK(h, cudaMemsetAsync(a->chibar, 0, sizeof(double) * N, st));
+  ACK(h, cudaMemsetAsync(a->acc, 0, sizeof(double) * kAdjSlots, st));
+  // CG iterations of the adjoint solves: the recomputing steps reset the
+  // solver's counters, so they are read after each block of adjoint solves
+  long long adj_iters = 0;
+  auto count = [&]() -> int {
+    ACK(h, cudaMemcpyAsync(h->pw.ctl_host, h->pw.ctl, sizeof(PoissonCtl), cudaMemcpyDeviceToHost, st));
+    ACK(h, cudaStreamSynchronize(st));
+    adj_iters += h->pw.ctl_host->total_iters;
+    const int status = h->pw.ctl_host->status ? h->pw.ctl_host->status : h->pw.ctl_host->sticky_status;
+    if (status) return afail(h, status, "adjoint: Poisson solve failed");
+    return LBE_OK;
+  };
+  ACK(h, poisson_reset_stats(h));
+  // time T (the handle holds the forward pass's final state)
+  k_adj_seed<<<nb, kBlock, 0, st>>>(g, h->phys, h->mask, h->id, h->phi32, cq, psi, soft_electrode, a->phibar,
+                                    a->chibar);
+  ACK(h, cudaGetLastError());
+  int rc = adj_poisson(h, h->phi32, psi, soft_electrode);
+  if (rc != LBE_OK) return rc;
+  if ((rc = count()) != LBE_OK) return rc;
+  long long recomputed = 0;
+  for (int s = a->nseg - 1; s >= 0; --s) {
+    const int t0 = s * a->every, t1 = std::min(a->T, t0 + a->every);
+    rc = load_ck(h, s);
+    if (rc != LBE_OK) return rc;
+    for (int t = t0; t < t1; ++t) {
+      ACK(h, cudaMemcpyAsync(a->st_q + (size_t)(t - t0) * 2 * N, h->q, sizeof(int64_t) * 2 * N,
+                             cudaMemcpyDeviceToDevice, st));
+      ACK(h, cudaMemcpyAsync(a->st_phi + (size_t)(t - t0) * N, h->phi32, sizeof(float) * N, cudaMemcpyDeviceToDevice,
+                             st));
+      if (t + 1 < t1) {
+        rc = lbe_step(h, 1);
+        if (rc != LBE_OK) return rc;
+        ++recomputed;
+      }
+    }
+    ACK(h, poisson_reset_stats(h));
+    for (int t = t1 - 1; t >= t0; --t) {
+      const int64_t *qt = a->st_q + (size_t)(t - t0) * 2 * N;
+      const float *pt = a->st_phi + (size_t)(t - t0) * N;
+      k_adj_flux<<<nb, kBlock, 0, st>>>(g, h->phys, h->p32, h->mask, h->id, qt, pt, psi, a->lam, a->lam2, a->phibar,
+                                        a->chibar, a->part, nb);
+      k_adj_accumulate<<<kAdjSlots, 32, 0, st>>>(a->part, nb, a->acc);
+      ACK(h, cudaGetLastError());
+      std::swap(a->lam, a->lam2);
+      rc = adj_poisson(h, pt, psi, soft_electrode);
+      if (rc != LBE_OK) return rc;
+    }
+    if ((rc = count()) != LBE_OK) return rc;
+  }
+  k_adj_init<<<nb, kBlock, 0, st>>>(N, h->mask, h->prm.rho_bulk[0], a->lam, a->chibar, a->part, nb);
+  k_adj_accumulate<<<kAdjSlots, 32, 0, st>>>(a->part, nb, a->acc);
+  ACK(h, cudaGetLastError());
+  double acc[kAdjSlots];
+  ACK(h, cudaMemcpyAsync(acc, a->acc, sizeof(acc), cudaMemcpyDeviceToHost, st));
+  if (dchi)
+    ACK(h, cudaMemcpyAsync(dchi, a->chibar, sizeof(double) * N,
+                           dchi_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  ACK(h, cudaStreamSynchronize(st));
+  memset(out, 0, sizeof(*out));
+  for (int e = 0; e < h->n_elec; ++e) out->dpsi[e] = acc[e];
+  for (int k = 0; k < 2; ++k) out->dD[k] = acc[kSlotD + k];
+  out->drho_bulk = acc[kSlotRho];
+  out->poisson_iters = adj_iters;
+  out->recomputed_steps = recomputed;
+  // leave the handle as the forward pass left it
+  rc = load_ck(h, a->nseg);
+  if (rc != LBE_OK) return rc;
+  ACK(h, cudaStreamSynchronize(st));
+  h->gen = a->gen;
+  return LBE_OK;
+}
+
+}  // extern "C"

@@ -47,6 +47,7 @@ void free_all(lbe_handle *h) {
   if (h->qhost) cudaFreeHost(h->qhost);
   lbe::poisson_free(h);
   lbe::mg_free(h);
+  lbe::adjoint_free(h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   h->ev_pool.clear();
 }
@@ -244,6 +245,7 @@ int lbe_destroy(lbe_handle *h) {
 
 int lbe_set_geometry(lbe_handle *h, const uint8_t *node_id, int n_electrodes, int on_device) {
   if (!h) return LBE_ERR_ARG;
+  h->gen += 1;
   if (!node_id || n_electrodes < 0 || n_electrodes > LBE_MAX_ELECTRODES)
     return fail(h, LBE_ERR_ARG, "set_geometry: bad arguments");
   StreamGuard sg{h, h->owns_stream};
@@ -286,6 +288,7 @@ static int solve_now(lbe_handle *h) {
 
 int lbe_set_voltage(lbe_handle *h, const double *psi) {
   if (!h) return LBE_ERR_ARG;
+  h->gen += 1;
   if (!h->have_geometry) return fail(h, LBE_ERR_STATE, "set_voltage: no geometry");
   if (!psi && h->n_elec > 0) return fail(h, LBE_ERR_ARG, "set_voltage: NULL psi");
   StreamGuard sg{h, h->owns_stream};
@@ -301,6 +304,7 @@ int lbe_set_voltage(lbe_handle *h, const double *psi) {
 
 int lbe_init(lbe_handle *h) {
   if (!h) return LBE_ERR_ARG;
+  h->gen += 1;
   if (!h->have_geometry) return fail(h, LBE_ERR_STATE, "init: no geometry");
   StreamGuard sg{h, h->owns_stream};
   h->stats = lbe_stats{};
@@ -329,6 +333,7 @@ static int check_flags(lbe_handle *h) {
 
 int lbe_step(lbe_handle *h, int nsteps) {
   if (!h) return LBE_ERR_ARG;
+  h->gen += 1;
   if (!h->initialised) return fail(h, LBE_ERR_STATE, "step: call lbe_init first");
   if (nsteps < 0) return fail(h, LBE_ERR_ARG, "step: negative step count");
   StreamGuard sg{h, h->owns_stream};
@@ -438,6 +443,7 @@ int lbe_fields(lbe_handle *h, int which, void *out, int out_on_device) {
 
 int lbe_set_state(lbe_handle *h, const double *n, const double *phi, int on_device) {
   if (!h) return LBE_ERR_ARG;
+  h->gen += 1;
   if (!h->initialised) return fail(h, LBE_ERR_STATE, "set_state: call lbe_init first");
   StreamGuard sg{h, h->owns_stream};
   const long long N = h->geo.N;
@@ -521,6 +527,7 @@ int lbe_save_state(lbe_handle *h, void *blob, size_t *size) {
 }
 
 int lbe_load_state(lbe_handle *h, const void *blob, size_t size) {
+  if (h) h->gen += 1;
   if (!h || !blob) return LBE_ERR_ARG;
   if (!h->have_geometry) return fail(h, LBE_ERR_STATE, "load_state: no geometry");
   size_t fb, nb, pb, ub;

@@ -188,6 +188,7 @@ struct PoissonCtl {
   int outer_done, inner_done, rounds, status, sticky_status, arrive;
   long long solve_iters, total_iters, total_rounds, solves, max_solve_iters;
   double res, res0, alpha, beta, gamma;
+  double ref;  // linear solves: max |rhs|/diag, the scale of the relative test
 };
 
 struct PoissonWork {
@@ -198,6 +199,8 @@ struct PoissonWork {
   Launch L{};                 // launch of the CG kernels (<= kMaxPartials blocks)
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   const void *exec_key[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec_lin = nullptr;  // linear solve A x = rhs (adjoint)
+  const void *lin_key[2] = {nullptr, nullptr};
   bool graph_ok = false;
   double *phi_prev = nullptr;  // phi of the previous step (warm start)
   bool have_history = false;
@@ -219,6 +222,8 @@ struct MGWork {
   float *t0 = nullptr;  // fine-level scratch
   float *inv0 = nullptr;  // inverse diagonal of the fine operator
 };
+
+struct AdjWork;  // adjoint.cu
 
 }  // namespace lbe
 
@@ -269,6 +274,12 @@ struct lbe_handle {
   size_t ev_used = 0;
   long long launches = 0;     // kernels launched since profile_begin
   long long prof_iters = 0, prof_solves = 0, prof_steps = 0;
+
+  // reverse-mode derivative (lbe_adjoint_*): checkpoints and work arrays;
+  // gen counts the calls that change the state, so a backward pass can tell
+  // whether the state it differentiates is still the forward pass's
+  lbe::AdjWork *adj = nullptr;
+  long long gen = 0;
 };
 
 namespace lbe {
@@ -298,12 +309,20 @@ int poisson_enqueue(lbe_handle *h, bool extrapolate);
 // synchronise and read the solves' status/statistics since the last reset;
 // *kernels (optional) receives the kernels the graph path launched
 int poisson_status(lbe_handle *h, lbe_stats *st, long long *kernels);
+// enqueue a solve of A x = rhs on fluid nodes (A = -lap_mod with zero
+// Dirichlet values on solid nodes; FP32 form): iterative refinement with an
+// FP64 residual from x, stopping when max |res|/diag <= max(tol_abs,
+// tol_rel * max |rhs|/diag).  x (FP64, N) is the warm start on entry and
+// must hold 0 on solid nodes; rhs (FP64, N) is read on fluid nodes.
+int poisson_solve_linear(lbe_handle *h, const double *rhs, double *x, double tol_abs, double tol_rel);
 cudaError_t poisson_reset_stats(lbe_handle *h);
 void poisson_drop_graphs(lbe_handle *h);
 // lbe_api.cu: message returned by lbe_last_error(NULL) (thread-local)
 void set_static_error(const char *msg);
 // lbe_api.cu: derived constants (Phys, P32) of h->prm
 void fill_constants(lbe_handle *h);
+// adjoint.cu
+void adjoint_free(lbe_handle *h);
 // mg.cu
 cudaError_t mg_setup(lbe_handle *h);
 void mg_free(lbe_handle *h);

@@ -208,16 +208,21 @@ __global__ void k_solve_reset(PoissonCtl *c) {
 
 // FP64 residual of the current potential; seeds the inner solve:
 // r = (T)res, u = r/diag, x = p = s = 0.  Partial max |res|/diag.
-template <typename T, bool FIXED>
+// MODE: 0 charge density from FP64 n, 1 from fixed-point q, 2 a given rhs
+// (linear solve A x = rhs; its relative test also needs max |rhs|/diag,
+// kept in the otherwise idle (r,u) partial slots).
+enum { R_N64 = 0, R_FIXED = 1, R_RHS = 2 };
+template <typename T, int MODE>
 __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys P, const P32 P3,
                                                 const uint32_t *__restrict__ mask, const double *__restrict__ n64,
-                                                const int64_t *__restrict__ nq, const double *__restrict__ phi,
-                                                T *__restrict__ r, T *__restrict__ u, T *__restrict__ x,
-                                                T *__restrict__ p, T *__restrict__ s, double *__restrict__ part,
-                                                int nblk, PoissonCtl *c, double tol, int maxit,
+                                                const int64_t *__restrict__ nq, const double *__restrict__ rhs,
+                                                const double *__restrict__ phi, T *__restrict__ r,
+                                                T *__restrict__ u, T *__restrict__ x, T *__restrict__ p,
+                                                T *__restrict__ s, double *__restrict__ part, int nblk,
+                                                PoissonCtl *c, double tol, double tol_rel, int maxit,
                                                 cudaGraphConditionalHandle hout, cudaGraphConditionalHandle hin,
                                                 int use_cond) {
-  float mx = 0.f;
+  float mx = 0.f, mb = 0.f;
   for (int kz = 0; kz < zpt; ++kz) {
     int X, Y, Z;
     long long i;
@@ -227,32 +232,45 @@ __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys
       r[i] = u[i] = x[i] = p[i] = s[i] = (T)0;
       continue;
     }
-    double q;
-    if (FIXED && P3.salt11) {
+    double b;
+    if (MODE == R_RHS) {
+      b = rhs[i];
+    } else if (MODE == R_FIXED && P3.salt11) {
       // 1:1 salt with one bulk value: rho_el = s (q+ - q-), exact integer difference
-      q = P3.sd[0] * (double)(nq[i] - nq[g.N + i]);
+      b = P.four_pi_lb * (P3.sd[0] * (double)(nq[i] - nq[g.N + i]));
     } else {
-      q = 0.0;
+      double q = 0.0;
       for (int k = 0; k < P.ns; ++k)
-        q += P.z[k] * (FIXED ? P3.rbd[k] + P3.sd[k] * (double)nq[k * g.N + i] : n64[k * g.N + i]);
+        q += P.z[k] * (MODE == R_FIXED ? P3.rbd[k] + P3.sd[k] * (double)nq[k * g.N + i] : n64[k * g.N + i]);
+      b = P.four_pi_lb * q;
     }
-    const double rr = P.four_pi_lb * q + lap_at(g, (int)i, X, Y, Z, m, phi);
+    const double rr = b + lap_at(g, (int)i, X, Y, Z, m, phi);
     const T rt = (T)rr;
     const T dinv = (T)1 / diag_t<T>(m, P.selfmask);
     r[i] = rt;
     u[i] = rt * dinv;
     x[i] = p[i] = s[i] = (T)0;
     mx = fmaxf(mx, fabsf((float)rr) * (float)dinv);  // the stopping test needs no FP64
+    if (MODE == R_RHS) mb = fmaxf(mb, fabsf((float)b) * (float)dinv);
   }
   mx = block_reduce<true, float>(mx);
   if (flat_tid() == 0) part[S_MAX * nblk + flat_bid()] = (double)mx;
+  if (MODE == R_RHS) {
+    mb = block_reduce<true, float>(mb);
+    if (flat_tid() == 0) part[S_RU * nblk + flat_bid()] = (double)mb;
+  }
   if (!last_block(c, nblk)) return;
-  double m = 0.0;
-  for (int i = flat_tid(); i < nblk; i += kBlock) m = fmax(m, __ldcg(part + S_MAX * nblk + i));
+  double m = 0.0, ref = 0.0;
+  for (int i = flat_tid(); i < nblk; i += kBlock) {
+    m = fmax(m, __ldcg(part + S_MAX * nblk + i));
+    if (MODE == R_RHS) ref = fmax(ref, __ldcg(part + S_RU * nblk + i));
+  }
   m = block_reduce<true>(m);
+  if (MODE == R_RHS) ref = block_reduce<true>(ref);
   if (flat_tid() == 0) {
     c->arrive = 0;
-    outer_check(c, m, tol, maxit, hout, hin, use_cond);
+    if (MODE == R_RHS) c->ref = ref;
+    outer_check(c, m, MODE == R_RHS ? fmax(tol, tol_rel * ref) : tol, maxit, hout, hin, use_cond);
   }
 }
 
@@ -372,10 +390,11 @@ struct Args {
   Phys P;
   P32 P3;
   uint32_t selfmask;
-  double tol, eta, tol_inner;
+  double tol, tol_rel = 0.0, eta, tol_inner;
   const uint32_t *mask;
   const double *n64;
   const int64_t *nq;
+  const double *rhs = nullptr;
   double *phi;
   float *phi32;
   void *r, *u, *w, *x, *p, *s;
@@ -452,15 +471,16 @@ cudaError_t build_graph(lbe_handle *h, Args &A, cudaGraphExec_t *exec) {
   const Launch L1 = make_launch(h->geo);
   const dim3 one(1);
   const bool fixed = h->prm.precision == LBE_FP32;
-  void *f_res = fixed ? (void *)k_res<T, true> : (void *)k_res<T, false>;
+  void *f_res = A.rhs ? (void *)k_res<T, R_RHS> : (fixed ? (void *)k_res<T, R_FIXED> : (void *)k_res<T, R_N64>);
   cudaGraph_t G = nullptr;
   cudaError_t e = cudaGraphCreate(&G, 0);
   if (e != cudaSuccess) return e;
   cudaGraphNode_t last = nullptr, lo = nullptr, li = nullptr;
   cudaGraph_t body_out = nullptr, body_in = nullptr;
   void *a_reset[] = {&A.c};
-  void *a_res[] = {&A.g, &A.zpt, &A.P, &A.P3, &A.mask, &A.n64, &A.nq, &A.phi, &A.r, &A.u, &A.x, &A.p, &A.s,
-                   &A.part, &A.nblk, &A.c, &A.tol, &A.maxit, &A.hout, &A.hin, &A.use_cond};
+  void *a_res[] = {&A.g,     &A.zpt,  &A.P,    &A.P3,  &A.mask, &A.n64, &A.nq,      &A.rhs,
+                   &A.phi,   &A.r,    &A.u,    &A.x,   &A.p,    &A.s,   &A.part,    &A.nblk,
+                   &A.c,     &A.tol,  &A.tol_rel, &A.maxit, &A.hout, &A.hin, &A.use_cond};
   void *a_bi[] = {&A.g, &A.zpt, &A.selfmask, &A.mask, &A.u, &A.r, &A.w, &A.part, &A.nblk, &A.c,
                   &A.eta, &A.tol_inner, &A.maxit, &A.mode_init, &A.hin, &A.use_cond};
   void *a_bt[] = {&A.g, &A.zpt, &A.selfmask, &A.mask, &A.u, &A.r, &A.w, &A.part, &A.nblk, &A.c,
@@ -497,14 +517,12 @@ int solve_polled(lbe_handle *h, Args &A) {
   k_solve_reset<<<1, 1, 0, st>>>(A.c);
   h->launches += 1;
   for (int round = 0; round <= kMaxOuter; ++round) {
-    if (fixed)
-      k_res<T, true><<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.P, A.P3, A.mask, A.n64, A.nq, A.phi, (T *)A.r,
-                                                  (T *)A.u, (T *)A.x, (T *)A.p, (T *)A.s, A.part, A.nblk, A.c,
-                                                  A.tol, A.maxit, 0, 0, 0);
-    else
-      k_res<T, false><<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.P, A.P3, A.mask, A.n64, A.nq, A.phi, (T *)A.r,
-                                                   (T *)A.u, (T *)A.x, (T *)A.p, (T *)A.s, A.part, A.nblk, A.c,
-                                                   A.tol, A.maxit, 0, 0, 0);
+    {
+      auto kres = A.rhs ? k_res<T, R_RHS> : (fixed ? k_res<T, R_FIXED> : k_res<T, R_N64>);
+      kres<<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.P, A.P3, A.mask, A.n64, A.nq, A.rhs, A.phi, (T *)A.r,
+                                        (T *)A.u, (T *)A.x, (T *)A.p, (T *)A.s, A.part, A.nblk, A.c, A.tol,
+                                        A.tol_rel, A.maxit, 0, 0, 0);
+    }
     const bool mg = sizeof(T) == 4 && h->mg.nlev >= 2;
     if (mg && mg_vcycle(h, (const float *)A.r, (float *)A.u, A.c, nullptr, nullptr, st) != cudaSuccess)
       return LBE_ERR_CUDA;
@@ -599,6 +617,7 @@ void poisson_free(lbe_handle *h) {
   PoissonWork &w = h->pw;
   for (int k = 0; k < 2; ++k)
     if (w.exec[k]) cudaGraphExecDestroy(w.exec[k]);
+  if (w.exec_lin) cudaGraphExecDestroy(w.exec_lin);
   cudaFree(w.vec);
   cudaFree(w.partial);
   cudaFree(w.phi_prev);
@@ -614,6 +633,44 @@ void poisson_drop_graphs(lbe_handle *h) {
     w.exec[k] = nullptr;
     w.exec_key[k] = nullptr;
   }
+  if (w.exec_lin) cudaGraphExecDestroy(w.exec_lin);
+  w.exec_lin = nullptr;
+  w.lin_key[0] = w.lin_key[1] = nullptr;
+}
+
+int poisson_solve_linear(lbe_handle *h, const double *rhs, double *x, double tol_abs, double tol_rel) {
+  if (h->prm.precision != LBE_FP32) {
+    h->err = "linear solve: FP32 form only";
+    return LBE_ERR_STATE;
+  }
+  PoissonWork &w = h->pw;
+  Args A;
+  fill_args<float>(h, A);
+  A.rhs = rhs;
+  A.phi = x;
+  A.phi32 = nullptr;
+  A.tol = tol_abs;
+  A.tol_rel = tol_rel;
+  A.tol_inner = 0.25 * tol_abs;
+  if (!w.graph_ok) return solve_polled<float>(h, A);
+  if (!w.exec_lin || w.lin_key[0] != rhs || w.lin_key[1] != x) {
+    if (w.exec_lin) cudaGraphExecDestroy(w.exec_lin);
+    w.exec_lin = nullptr;
+    cudaError_t e = build_graph<float>(h, A, &w.exec_lin);
+    if (e != cudaSuccess) {
+      h->err = std::string("linear solve graph: ") + cudaGetErrorString(e);
+      w.exec_lin = nullptr;
+      return LBE_ERR_CUDA;
+    }
+    w.lin_key[0] = rhs;
+    w.lin_key[1] = x;
+  }
+  cudaError_t e = cudaGraphLaunch(w.exec_lin, h->stream);
+  if (e != cudaSuccess) {
+    h->err = std::string("linear solve graph launch: ") + cudaGetErrorString(e);
+    return LBE_ERR_CUDA;
+  }
+  return LBE_OK;
 }
 
 int poisson_enqueue(lbe_handle *h, bool extrapolate) {

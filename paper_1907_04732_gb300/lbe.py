@@ -40,7 +40,8 @@ EXPORTED = ["lbe_default_params", "lbe_create", "lbe_destroy", "lbe_last_error",
             "lbe_batch_create", "lbe_batch_destroy", "lbe_batch_last_error", "lbe_batch_set_geometry",
             "lbe_batch_set_voltage", "lbe_batch_init", "lbe_batch_step", "lbe_batch_charge",
             "lbe_batch_fields", "lbe_batch_get_stats", "lbe_batch_tuning",
-            "lbe_batch_profile_begin", "lbe_batch_profile_end"]
+            "lbe_batch_profile_begin", "lbe_batch_profile_end",
+            "lbe_adjoint_forward", "lbe_adjoint_backward"]
 LBE_BATCH_MAX_ELECTRODES = 4
 LBE_BATCH_TUNE_CANDIDATES = 6
 
@@ -64,6 +65,12 @@ class lbe_profile(ctypes.Structure):
                 ("advect_ms", ctypes.c_double), ("advect_launches", ctypes.c_longlong),
                 ("poisson_ms", ctypes.c_double), ("poisson_solves", ctypes.c_longlong),
                 ("poisson_iters", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong)]
+
+
+class lbe_adjoint_grad(ctypes.Structure):
+    _fields_ = [("dpsi", ctypes.c_double * LBE_MAX_ELECTRODES), ("drho_bulk", ctypes.c_double),
+                ("dD", ctypes.c_double * LBE_MAX_SPECIES), ("poisson_iters", ctypes.c_longlong),
+                ("recomputed_steps", ctypes.c_longlong)]
 
 
 _lib = None
@@ -116,6 +123,8 @@ def load(path: str = LIB_PATH):
     lib.lbe_batch_fields.argtypes = [vp, ip, ip, vp, ip]
     lib.lbe_batch_get_stats.argtypes = [vp, ctypes.POINTER(lbe_stats)]
     lib.lbe_batch_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp]
+    lib.lbe_adjoint_forward.argtypes = [vp, ip, ip, dp]
+    lib.lbe_adjoint_backward.argtypes = [vp, dp, ip, ctypes.POINTER(lbe_adjoint_grad), vp, ip]
     lib.lbe_batch_profile_begin.argtypes = [vp]
     lib.lbe_batch_profile_end.argtypes = [vp, ctypes.POINTER(lbe_profile)]
     for name in EXPORTED:
@@ -212,6 +221,18 @@ def lbe_induced_charge_static(phi_ptr: int, node_id_ptr: int, shape, periodic, b
                                           per, float(bjerrum), int(n_electrodes), q_out_ptr,
                                           ctypes.c_void_p(stream or None))
     return _check(None, rc)
+
+
+def lbe_adjoint_forward(h, nsteps: int, every: int, q_out=None):
+    return _check(h, load().lbe_adjoint_forward(h, int(nsteps), int(every), q_out))
+
+
+def lbe_adjoint_backward(h, dq, soft_electrode: int, dchi_ptr, dchi_on_device: bool) -> lbe_adjoint_grad:
+    g = lbe_adjoint_grad()
+    arr = (ctypes.c_double * max(len(dq), 1))(*[float(v) for v in dq])
+    _check(h, load().lbe_adjoint_backward(h, arr, int(soft_electrode), ctypes.byref(g), dchi_ptr,
+                                          int(dchi_on_device)))
+    return g
 
 
 def _bcheck(b, rc):
@@ -416,6 +437,23 @@ class Lattice:
 
     def profile_end(self) -> lbe_profile:
         return lbe_profile_end(self.h)
+
+    def adjoint_forward(self, nsteps: int, every: int) -> np.ndarray:
+        """lbe_init + nsteps steps with checkpoints; returns Q(T)."""
+        q = np.zeros(max(self.n_elec, 1))
+        lbe_adjoint_forward(self.h, nsteps, every, q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return q[: self.n_elec]
+
+    def adjoint_backward(self, dq, soft_electrode: int = 1, dchi=None):
+        """Gradient of sum_e dq[e] Q_e(T); dchi: a CUDA float64 tensor of N
+        values to receive the occupancy gradient (or None: returned as a host
+        array)."""
+        if dchi is None:
+            out = np.zeros(self.N)
+            g = lbe_adjoint_backward(self.h, dq, soft_electrode, out.ctypes.data, False)
+            return g, out
+        g = lbe_adjoint_backward(self.h, dq, soft_electrode, dchi.data_ptr(), True)
+        return g, dchi
 
 
 class Batch:
