@@ -247,6 +247,8 @@ def batch_leg(args, lbe, torch, stream, peak):
     sizes = [w.nodes for w in ws]
     sample = sorted({int(np.argmax(sizes)), int(np.argmin(sizes))} |
                     set(int(i) for i in rng.choice(len(ws), 4, replace=False)))
+    if args.compare_steps == 0:
+        sample = []
     t64, n64 = 0.0, 0
     for i in sample:
         w = ws[i]
@@ -263,7 +265,7 @@ def batch_leg(args, lbe, torch, stream, peak):
         t64 += ev0.elapsed_time(ev1) / 3
         n64 += w.nodes
         lat.close()
-    fp64_mlups = n64 / (t64 * 1e-3) / 1e6
+    fp64_mlups = n64 / (t64 * 1e-3) / 1e6 if sample else None
     value = nodes / (ms * 1e-3) / 1e6
     return {"workload": "256 plate/coax capacitors (seeded gaps 32-512, sides 8-64, Debye 2-32, "
                         "voltages -0.5..0.5)",
@@ -278,9 +280,64 @@ def batch_leg(args, lbe, torch, stream, peak):
                                "achieved": sweep_gbs, "peak": peak, "unit": "GB/s", "frac": sweep_gbs / peak},
             "cg_iters_per_step_summed_over_instances": st.poisson_iters / max(st.poisson_solves, 1),
             "cg_iters_per_step_max_instance": st.poisson_max_iters,
-            "fp64_plain": {"value": fp64_mlups, "unit": UNIT, "speedup_batched_fp32": value / fp64_mlups,
+            "fp64_plain": {"value": fp64_mlups, "unit": UNIT,
+                           "speedup_batched_fp32": value / fp64_mlups if fp64_mlups else None,
                            "sample": f"instances {sample}, one lattice at a time, 3 timed steps each"},
             "charge_finite": bool(np.all(np.isfinite(q)))}
+
+
+def adjoint_leg(args, lbe, torch, stream):
+    """Gradient of the induced charge after T steps on the 256x256x128
+    porous electrode (solvent at rest): FP32 forward with checkpoints every
+    K steps, then the reverse sweep (recomputation, adjoint Poisson solves),
+    timed with CUDA events; the plain FP64 forward step on the same lattice
+    for comparison."""
+    import numpy as np
+    w = wl.porous_electrode()
+    p = lbe.params_for(w, tol=args.tol, precision=lbe.LBE_FP32)
+    lat = lbe.Lattice(p, stream=stream.cuda_stream)
+    lat.set_geometry(w.ids, w.n_elec)
+    lat.set_voltage(w.psi)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    q = lat.adjoint_forward(args.adjoint_steps, args.adjoint_every)
+    ev[1].record(stream)
+    g, dchi = lat.adjoint_backward([1.0, 0.0], 1)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms, bwd_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    lat.close()
+    T = args.adjoint_steps
+    nseg = -(-T // args.adjoint_every)
+    # plain FP64 forward on the same lattice
+    p64 = lbe.params_for(w, tol=args.tol, precision=lbe.LBE_FP64)
+    l64 = lbe.Lattice(p64, stream=stream.cuda_stream)
+    l64.set_geometry(w.ids, w.n_elec)
+    l64.set_voltage(w.psi)
+    l64.init()
+    l64.step(3)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    l64.step(5)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms64 = ev[0].elapsed_time(ev[1]) / 5
+    l64.close()
+    node_steps = w.nodes * T
+    return {"workload": w.name + " (200 seeded spheres r 6-12 on a backing plate, counter plate; flow off)",
+            "objective": "Q_1 after T steps", "steps": T, "checkpoint_every": args.adjoint_every,
+            "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+            "forward_mlups": node_steps / (fwd_ms * 1e-3) / 1e6,
+            "gradient_mlups": node_steps / ((fwd_ms + bwd_ms) * 1e-3) / 1e6,
+            "backward_over_forward": bwd_ms / fwd_ms,
+            "recomputed_steps": int(g.recomputed_steps), "adjoint_cg_iters": int(g.poisson_iters),
+            "checkpoint_bytes": (nseg + 1) * 32 * w.nodes, "segment_bytes": args.adjoint_every * 20 * w.nodes,
+            "Q": [float(v) for v in q], "dQ1_dpsi": [float(v) for v in g.dpsi[:2]],
+            "dQ1_drho_bulk": float(g.drho_bulk), "dQ1_dD": [float(v) for v in g.dD[:2]],
+            "dQ1_dchi_absmax": float(np.abs(dchi).max()),
+            "fp64_plain_forward": {"ms_per_step": ms64, "value": w.nodes / (ms64 * 1e-3) / 1e6, "unit": UNIT,
+                                   "gradient_vs_fp64_forward_time": (fwd_ms + bwd_ms) / (ms64 * T)}}
 
 
 def main():
@@ -299,6 +356,9 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=5,
                     help="timed steps of the 256-instance batched form (0 = skip)")
     ap.add_argument("--batch-warmup", type=int, default=3)
+    ap.add_argument("--adjoint-steps", type=int, default=2000,
+                    help="steps of the porous-electrode gradient run (0 = skip)")
+    ap.add_argument("--adjoint-every", type=int, default=100)
     args = ap.parse_args()
     w = make_workload(args.workload)
     if args.impl == "reference":
@@ -439,6 +499,8 @@ def main():
         l64.close()
     if args.batch_steps > 0:
         line["batched"] = batch_leg(args, lbe, torch, stream, peak)
+    if args.adjoint_steps > 0:
+        line["adjoint"] = adjoint_leg(args, lbe, torch, stream)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.tol)
     if world > 1:

@@ -28,9 +28,13 @@ One step (Sec. "Lattice Boltzmann Electrokinetics", solvent at rest):
 n <- n - sum_i J_i(n, phi), then phi <- Poisson(n); phi at t = 0 solves the
 Poisson equation of the initial ions.  Q is evaluated after the last step.
 
-The Poisson equation is linear in phi with a matrix that depends on chi
-only; it is solved by a sparse LU factorisation (scipy), and its tangent by
-phi' = M^-1 (b' - M' phi) with the same factors.
+The Poisson equation is linear in phi with a matrix M that depends on chi
+only; its tangent is phi' = M^-1 (b' - M' phi).  Small boxes (or a
+non-binary chi) use a sparse LU factorisation (scipy); larger boxes at a
+binary chi eliminate the solid rows (phi_s = psi) and solve the symmetric
+positive definite fluid block by Jacobi-preconditioned conjugate gradients
+(scipy) to a relative residual of 1e-13, warm-started from the previous
+step.
 """
 from __future__ import annotations
 
@@ -186,15 +190,43 @@ class SoftLBE:
         psi_l = psi[self.label - 1] if not isinstance(psi, Dual) else psi[self.label - 1]
         return -(1.0 - chi) * (4.0 * math.pi * self.bjerrum) * rho - chi * psi_l
 
-    def _solve(self, lu, Md, rhs, dual):
+    LU_MAX = 6000  # larger boxes at a binary occupancy use conjugate gradients
+
+    def _factor(self, chi_v, Mv):
+        binary = bool(np.all((chi_v == 0.0) | (chi_v == 1.0)))
+        if self.g.N <= self.LU_MAX or not binary:
+            return {"lu": spla.splu(Mv)}
+        fl = chi_v == 0.0
+        Mr = Mv.tocsr()
+        A = (-Mr[fl][:, fl]).tocsr()
+        return {"fl": fl, "A": A, "C": Mr[fl][:, ~fl].tocsr(),
+                "P": sp.diags(1.0 / A.diagonal()), "warm": {}}
+
+    def _lin(self, fac, b, key):
+        if "lu" in fac:
+            return fac["lu"].solve(b)
+        fl = fac["fl"]
+        x = np.empty_like(b)
+        xs = -b[~fl]
+        x[~fl] = xs
+        rhs = fac["C"] @ xs - b[fl]
+        x0 = fac["warm"].get(key)
+        xf, info = spla.cg(fac["A"], rhs, x0=x0, rtol=1e-13, atol=0.0, M=fac["P"], maxiter=50000)
+        if info != 0:
+            raise RuntimeError("soft oracle: CG did not converge")
+        fac["warm"][key] = xf
+        x[fl] = xf
+        return x
+
+    def _solve(self, fac, Md, rhs, dual):
         if not dual:
-            return lu.solve(rhs)
+            return self._lin(fac, np.asarray(rhs, dtype=np.float64) * np.ones(self.g.N), "v")
         rhs = lift(rhs)
-        pv = lu.solve(np.asarray(rhs.v, dtype=np.float64) * np.ones(self.g.N))
+        pv = self._lin(fac, np.asarray(rhs.v, dtype=np.float64) * np.ones(self.g.N), "v")
         rd = np.asarray(rhs.d, dtype=np.float64) * np.ones(self.g.N)
         if Md is not None:
             rd = rd - Md @ pv
-        return Dual(pv, lu.solve(rd))
+        return Dual(pv, self._lin(fac, rd, "d"))
 
     def _flux_step(self, n, phi, chi, d):
         g = self.g
@@ -236,7 +268,7 @@ class SoftLBE:
         rho_b = 1.0 / (8.0 * math.pi * self.bjerrum * (debye * debye))
         d = [D[0] / A0, D[1] / A0] if not isinstance(D, Dual) else [D[0] / A0, D[1] / A0]
         coef = self._link_coef(chi)
-        lu = spla.splu(self._assemble(coef, chi, "v"))
+        lu = self._factor(val(chi), self._assemble(coef, chi, "v"))
         Md = self._assemble(coef, chi, "d") if isinstance(chi, Dual) else None
         n0 = rho_b * (1.0 - chi)
         n = [n0, n0]

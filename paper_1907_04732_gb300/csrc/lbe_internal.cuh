@@ -215,12 +215,12 @@ struct MGLevel {
   long long N = 0;
   float *A = nullptr;  // 27-point Galerkin operator [27][N]
   float *r = nullptr, *e = nullptr, *t = nullptr;
+  float *z = nullptr;  // pre-smoothed iterate omega r/diag
 };
 struct MGWork {
   MGLevel lv[kMaxLevels];
   int nlev = 0;        // 0: no hierarchy (Jacobi preconditioning)
   float *t0 = nullptr;  // fine-level scratch
-  float *inv0 = nullptr;  // inverse diagonal of the fine operator
 };
 
 struct AdjWork;  // adjoint.cu

@@ -30,13 +30,6 @@ __device__ __forceinline__ bool lnode(const MgLevel &L, int &x, int &y, int &z, 
 }
 
 // --- set-up: level-0 inverse diagonal, Galerkin coarse operators -------------
-__global__ void k_invdiag0(const Geo g, uint32_t selfmask, const uint32_t *__restrict__ mask, float *__restrict__ inv) {
-  int x, y, z;
-  long long il;
-  if (!node_of(g, 1, 0, x, y, z, il)) return;
-  inv[il] = inv_diag0(mask[il], selfmask);
-}
-
 // level 1 from the fine lattice (mask-defined operator)
 __global__ void k_galerkin0(const Geo g, uint32_t selfmask, const uint32_t *__restrict__ mask, const MgLevel C,
                             float *__restrict__ A) {
@@ -60,7 +53,8 @@ __global__ void k_galerkin(const MgLevel F, const float *__restrict__ AF, const 
 
 // --- V-cycle kernels ---------------------------------------------------------
 // Restriction with 8 threads per coarse node (one per child) and a fixed-order
-// shuffle sum of the children's pre-smoothed residuals.
+// shuffle sum of the children's pre-smoothed residuals.  The coarse node's
+// residual rc and its pre-smoothed iterate zc = omega rc/diag are stored.
 __device__ __forceinline__ void coarse_of_thread(const MgLevel &C, int &I, int &X, int &Y, int &Z, int &ch) {
   const int t = threadIdx.x;
   I = blockIdx.x * (blockDim.x / 8) + (t >> 3);
@@ -69,62 +63,89 @@ __device__ __forceinline__ void coarse_of_thread(const MgLevel &C, int &I, int &
   if (I < C.N) level_coords(C, I, X, Y, Z);
 }
 
+__device__ __forceinline__ void store_coarse(const MgLevel &C, int I, float v, const float *__restrict__ AC,
+                                             float *__restrict__ rc, float *__restrict__ zc) {
+  const float d = AC[13 * C.S + I];
+  rc[I] = v;
+  zc[I] = d != 0.f ? kOmega * v / d : 0.f;
+}
+
+// level 1: a fluid child's pre-smoothed residual is r - omega A u, u = r/diag
+// being the Jacobi vector the CG formed
 __global__ void __launch_bounds__(256) k_restrict0(const Geo g, uint32_t selfmask, const uint32_t *__restrict__ mask,
-                                                   const float *__restrict__ r, const float *__restrict__ inv,
-                                                   const MgLevel C, float *__restrict__ rc, const PoissonCtl *c) {
+                                                   const float *__restrict__ r, const float *__restrict__ u,
+                                                   const MgLevel C, const float *__restrict__ AC,
+                                                   float *__restrict__ rc, float *__restrict__ zc,
+                                                   const PoissonCtl *c) {
   if (c->inner_done) return;
   int I, X, Y, Z, ch, x, y, z;
   coarse_of_thread(C, I, X, Y, Z, ch);
   float v = 0.f;
-  if (I < C.N && child_of(C, X, Y, Z, ch, g.nx, g.ny, g.nz, x, y, z))
-    v = presmoothed_res0(g, selfmask, mask, r, inv, x, y, z);
+  if (I < C.N && child_of(C, X, Y, Z, ch, g.nx, g.ny, g.nz, x, y, z)) {
+    const int i = x + g.nx * (y + g.ny * z);
+    const uint32_t m = mask[i];
+    if (m & kFluidBit) {
+      const float s6 = nbsum6(m, selfmask, offsets_of(g, x, y, z), i, u);
+      v = r[i] - kOmega * ((float)diag6(m, selfmask) * u[i] - s6) * (1.f / 6.f);
+    }
+  }
   v = sum8(v);
-  if (ch == 0 && I < C.N) rc[I] = v;
+  if (ch == 0 && I < C.N) store_coarse(C, I, v, AC, rc, zc);
 }
 
 __global__ void __launch_bounds__(256) k_restrict(const MgLevel F, const float *__restrict__ AF,
-                                                  const float *__restrict__ r, const MgLevel C,
-                                                  float *__restrict__ rc, const PoissonCtl *c) {
+                                                  const float *__restrict__ r, const float *__restrict__ zf,
+                                                  const MgLevel C, const float *__restrict__ AC,
+                                                  float *__restrict__ rc, float *__restrict__ zc,
+                                                  const PoissonCtl *c) {
   if (c->inner_done) return;
   int I, X, Y, Z, ch, x, y, z;
   coarse_of_thread(C, I, X, Y, Z, ch);
   float v = 0.f;
-  if (I < C.N && child_of(C, X, Y, Z, ch, F.nx, F.ny, F.nz, x, y, z)) v = presmoothed_res(F, AF, r, x, y, z);
+  if (I < C.N && child_of(C, X, Y, Z, ch, F.nx, F.ny, F.nz, x, y, z)) v = presmoothed_res_z(F, AF, r, zf, x, y, z);
   v = sum8(v);
-  if (ch == 0 && I < C.N) rc[I] = v;
+  if (ch == 0 && I < C.N) store_coarse(C, I, v, AC, rc, zc);
 }
 
 // fused prolongation + post-smoothing on a 27-point level
-__global__ void k_post(const MgLevel L, const float *__restrict__ A, const float *__restrict__ r, const MgLevel C,
-                       const float *__restrict__ ec, float *__restrict__ out, const PoissonCtl *c) {
+__global__ void k_post(const MgLevel L, const float *__restrict__ A, const float *__restrict__ r,
+                       const float *__restrict__ z, const MgLevel C, const float *__restrict__ ec,
+                       float *__restrict__ out, const PoissonCtl *c) {
   if (c->inner_done) return;
   int X, Y, Z, I;
   if (!lnode(L, X, Y, Z, I)) return;
-  out[I] = post_value(L, A, r, C, ec, X, Y, Z);
+  out[I] = post_value_z(L, A, r, z, C, ec, X, Y, Z);
 }
 
-// level 0: t = omega r/diag + alpha P e_1 (fluid nodes), then
+// level 0: t = omega u + alpha P e_1 (fluid nodes), then
 // u = t + omega (r - A t)/diag
-__global__ void k_prolong0(const Geo g, const uint32_t *__restrict__ mask, const float *__restrict__ r,
-                           const float *__restrict__ inv, const MgLevel C, const float *__restrict__ ec,
-                           float *__restrict__ t, const PoissonCtl *c) {
+__global__ void k_prolong0(const Geo g, const uint32_t *__restrict__ mask, const float *__restrict__ u,
+                           const MgLevel C, const float *__restrict__ ec, float *__restrict__ t,
+                           const PoissonCtl *c) {
   if (c->inner_done) return;
   int x, y, z;
   long long il;
   if (!node_of(g, 1, 0, x, y, z, il)) return;
   const int i = (int)il;
-  t[i] = (mask[i] & kFluidBit) ? kOmega * r[i] * inv[i] + kAlpha * ec[agg_index(C, x, y, z)] : 0.f;
+  t[i] = (mask[i] & kFluidBit) ? fmaf(kAlpha, ec[agg_index(C, x, y, z)], kOmega * u[i]) : 0.f;
 }
 
 __global__ void k_post0(const Geo g, uint32_t selfmask, const uint32_t *__restrict__ mask, const float *__restrict__ r,
-                        const float *__restrict__ inv, const float *__restrict__ t, float *__restrict__ u,
-                        const PoissonCtl *c) {
+                        const float *__restrict__ t, float *__restrict__ u, const PoissonCtl *c) {
   if (c->inner_done) return;
   int x, y, z;
   long long il;
   if (!node_of(g, 1, 0, x, y, z, il)) return;
   const int i = (int)il;
-  u[i] = post_value0(g, selfmask, mask[i], x, y, z, i, r, inv, t);
+  const uint32_t m = mask[i];
+  if (!(m & kFluidBit)) {
+    u[i] = 0.f;
+    return;
+  }
+  const float d6 = (float)diag6(m, selfmask);
+  const float s6 = nbsum6(m, selfmask, offsets_of(g, x, y, z), i, t);
+  const float ti = t[i];
+  u[i] = ti + kOmega * __fdividef(6.f * r[i] - (d6 * ti - s6), d6);
 }
 
 // coarsest level in one block
@@ -165,20 +186,18 @@ cudaError_t mg_setup(lbe_handle *h) {
     L.sz = shp[l].sz;
     L.N = shp[l].N;
   }
-  cudaError_t e = cudaMalloc(&mg.inv0, sizeof(float) * g.N);
-  if (e == cudaSuccess) e = cudaMalloc(&mg.t0, sizeof(float) * g.N);
+  cudaError_t e = cudaMalloc(&mg.t0, sizeof(float) * g.N);
   for (int l = 1; l < mg.nlev && e == cudaSuccess; ++l) {
     MGLevel &L = mg.lv[l];
     e = cudaMalloc(&L.A, sizeof(float) * 27 * L.N);
     if (e == cudaSuccess) e = cudaMalloc(&L.r, sizeof(float) * L.N);
     if (e == cudaSuccess) e = cudaMalloc(&L.e, sizeof(float) * L.N);
+    if (e == cudaSuccess) e = cudaMalloc(&L.z, sizeof(float) * L.N);
   }
   if (e != cudaSuccess) {
     mg_free(h);
     return e;
   }
-  const Launch L0 = make_launch(g);
-  k_invdiag0<<<L0.grid, L0.block, 0, h->stream>>>(g, h->phys.selfmask, h->mask, mg.inv0);
   for (int l = 1; l < mg.nlev; ++l) {
     const MgLevel C = level_dev(mg.lv[l]);
     dim3 blk;
@@ -198,9 +217,9 @@ void mg_free(lbe_handle *h) {
     cudaFree(mg.lv[l].r);
     cudaFree(mg.lv[l].e);
     cudaFree(mg.lv[l].t);
+    cudaFree(mg.lv[l].z);
   }
   cudaFree(mg.t0);
-  cudaFree(mg.inv0);
   mg = MGWork{};
 }
 
@@ -218,7 +237,7 @@ cudaError_t mg_vcycle(lbe_handle *h, const float *r0, float *u0, const PoissonCt
   struct Node {
     void *f;
     dim3 grid, block;
-    void *args[9];
+    void *args[12];
   };
   std::vector<Node> nodes;
   std::vector<MgLevel> lv(kMaxLevels);
@@ -233,10 +252,12 @@ cudaError_t mg_vcycle(lbe_handle *h, const float *r0, float *u0, const PoissonCt
   auto cgrid = [](const MgLevel &C) { return dim3((unsigned)((C.N * 8 + 255) / 256)); };
   // down: restrictions (pre-smoothing on the fly)
   nodes.push_back(Node{(void *)k_restrict0, cgrid(lv[1]), dim3(256),
-                       {(void *)pg, (void *)psm, P(h->mask), P(r0), P(mg.inv0), &lv[1], P(mg.lv[1].r), P(c)}});
+                       {(void *)pg, (void *)psm, P(h->mask), P(r0), P(u0), &lv[1], P(mg.lv[1].A), P(mg.lv[1].r),
+                        P(mg.lv[1].z), P(c)}});
   for (int l = 1; l < nl - 1; ++l)
     nodes.push_back(Node{(void *)k_restrict, cgrid(lv[l + 1]), dim3(256),
-                         {&lv[l], P(mg.lv[l].A), P(mg.lv[l].r), &lv[l + 1], P(mg.lv[l + 1].r), P(c)}});
+                         {&lv[l], P(mg.lv[l].A), P(mg.lv[l].r), P(mg.lv[l].z), &lv[l + 1], P(mg.lv[l + 1].A),
+                          P(mg.lv[l + 1].r), P(mg.lv[l + 1].z), P(c)}});
   // coarsest
   nodes.push_back(Node{(void *)k_coarsest, dim3(1), dim3(kCoarseMax),
                        {&lv[nl - 1], P(mg.lv[nl - 1].A), P(mg.lv[nl - 1].r), P(mg.lv[nl - 1].e), P(c)}});
@@ -245,14 +266,14 @@ cudaError_t mg_vcycle(lbe_handle *h, const float *r0, float *u0, const PoissonCt
     dim3 blk;
     const dim3 grd = lgrid(lv[l], blk);
     nodes.push_back(Node{(void *)k_post, grd, blk,
-                         {&lv[l], P(mg.lv[l].A), P(mg.lv[l].r), &lv[l + 1], P(mg.lv[l + 1].e), P(mg.lv[l].e),
-                          P(c)}});
+                         {&lv[l], P(mg.lv[l].A), P(mg.lv[l].r), P(mg.lv[l].z), &lv[l + 1], P(mg.lv[l + 1].e),
+                          P(mg.lv[l].e), P(c)}});
   }
   // finest level
   nodes.push_back(Node{(void *)k_prolong0, L0.grid, L0.block,
-                       {(void *)pg, P(h->mask), P(r0), P(mg.inv0), &lv[1], P(mg.lv[1].e), P(mg.t0), P(c)}});
+                       {(void *)pg, P(h->mask), P(u0), &lv[1], P(mg.lv[1].e), P(mg.t0), P(c)}});
   nodes.push_back(Node{(void *)k_post0, L0.grid, L0.block,
-                       {(void *)pg, (void *)psm, P(h->mask), P(r0), P(mg.inv0), P(mg.t0), P(u0), P(c)}});
+                       {(void *)pg, (void *)psm, P(h->mask), P(r0), P(mg.t0), P(u0), P(c)}});
   cudaError_t e = cudaSuccess;
   for (Node &n : nodes) {
     if (gr) {

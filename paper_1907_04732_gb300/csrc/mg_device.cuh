@@ -98,18 +98,6 @@ __device__ __forceinline__ bool child_of(const MgLevel &C, int X, int Y, int Z, 
 }
 
 // --- set-up ------------------------------------------------------------------
-__device__ __forceinline__ float inv_diag0(uint32_t m, uint32_t selfmask) {
-  if (!(m & kFluidBit)) return 0.f;
-  float dg = 0.f;
-#pragma unroll
-  for (int l = 1; l < kQ; ++l) {
-    const uint32_t b = 1u << (l - 1);
-    if (selfmask & b) continue;
-    dg += (m & b) ? (float)lapc_of(l) : 2.f * (float)lapc_of(l);
-  }
-  return 1.f / dg;
-}
-
 // Galerkin row of coarse node (X,Y,Z) of level 1 from the fine lattice
 // (mask-defined operator); mask points at the lattice's node 0
 __device__ __forceinline__ void galerkin0_row(const Geo &g, uint32_t selfmask, const uint32_t *__restrict__ mask,
@@ -166,100 +154,6 @@ __device__ __forceinline__ float sum8(float v) {
   v += __shfl_xor_sync(0xffffffffu, v, 2);
   v += __shfl_xor_sync(0xffffffffu, v, 4);
   return v;
-}
-
-// Residual after pre-smoothing from zero (e = omega r/diag) at fine node
-// (x,y,z) of the lattice: r - A e.  Pointers at the lattice's node 0.
-__device__ __forceinline__ float presmoothed_res0(const Geo &g, uint32_t selfmask, const uint32_t *__restrict__ mask,
-                                                  const float *__restrict__ r, const float *__restrict__ inv, int x,
-                                                  int y, int z) {
-  const int i = x + g.nx * (y + g.ny * z);
-  const uint32_t m = mask[i];
-  if (!(m & kFluidBit)) return 0.f;
-  const Offs o = offsets_of(g, x, y, z);
-  float s = 0.f, dg = 0.f;
-#pragma unroll
-  for (int l = 1; l < kQ; ++l) {
-    const uint32_t b = 1u << (l - 1);
-    if (selfmask & b) continue;
-    const float w = (float)lapc_of(l);
-    if (m & b) {
-      dg += w;
-      const int j = i + o.at(cx_of(l), cy_of(l), cz_of(l));
-      s += w * (kOmega * r[j] * inv[j]);
-    } else {
-      dg += 2.f * w;
-    }
-  }
-  const float ri = r[i];
-  return ri - (dg * (kOmega * ri * inv[i]) - s);
-}
-
-// the same on a 27-point level
-__device__ __forceinline__ float presmoothed_res(const MgLevel &L, const float *__restrict__ A,
-                                                 const float *__restrict__ r, int X, int Y, int Z) {
-  const int I = X + L.nx * (Y + L.ny * Z);
-  if (A[13 * L.S + I] == 0.f) return 0.f;
-  float s = 0.f;
-#pragma unroll
-  for (int d = 0; d < 27; ++d) {
-    const float a = A[d * L.S + I];
-    if (a == 0.f) continue;
-    const int jx = wrap(X + d % 3 - 1, L.nx), jy = wrap(Y + (d / 3) % 3 - 1, L.ny), jz = wrap(Z + d / 9 - 1, L.nz);
-    const int j = jx + L.nx * (jy + L.ny * jz);
-    s += a * (kOmega * r[j] / A[13 * L.S + j]);
-  }
-  return r[I] - s;
-}
-
-// corrected iterate of a 27-point level at node j: e = omega r/diag + alpha e_c
-__device__ __forceinline__ float corrected(const MgLevel &L, const float *__restrict__ A, const float *__restrict__ r,
-                                           const MgLevel &C, const float *__restrict__ ec, int x, int y, int z,
-                                           int j) {
-  const float d = A[13 * L.S + j];
-  return d != 0.f ? kOmega * r[j] / d + kAlpha * ec[agg_index(C, x, y, z)] : 0.f;
-}
-
-// fused prolongation + post-smoothing on a 27-point level:
-// e + omega (r - A e)/diag with e as in corrected()
-__device__ __forceinline__ float post_value(const MgLevel &L, const float *__restrict__ A, const float *__restrict__ r,
-                                           const MgLevel &C, const float *__restrict__ ec, int X, int Y, int Z) {
-  const int I = X + L.nx * (Y + L.ny * Z);
-  const float d = A[13 * L.S + I];
-  if (d == 0.f) return 0.f;
-  float s = 0.f;
-#pragma unroll
-  for (int q = 0; q < 27; ++q) {
-    const float a = A[q * L.S + I];
-    if (a == 0.f) continue;
-    const int jx = wrap(X + q % 3 - 1, L.nx), jy = wrap(Y + (q / 3) % 3 - 1, L.ny), jz = wrap(Z + q / 9 - 1, L.nz);
-    s += a * corrected(L, A, r, C, ec, jx, jy, jz, jx + L.nx * (jy + L.ny * jz));
-  }
-  const float e = corrected(L, A, r, C, ec, X, Y, Z, I);
-  return e + kOmega * (r[I] - s) / d;
-}
-
-// level 0 after the prolongation t: t + omega (r - A t)/diag
-__device__ __forceinline__ float post_value0(const Geo &g, uint32_t selfmask, uint32_t m, int x, int y, int z, int i,
-                                            const float *__restrict__ r, const float *__restrict__ inv,
-                                            const float *__restrict__ t) {
-  if (!(m & kFluidBit)) return 0.f;
-  const Offs o = offsets_of(g, x, y, z);
-  float s = 0.f, dg = 0.f;
-#pragma unroll
-  for (int l = 1; l < kQ; ++l) {
-    const uint32_t b = 1u << (l - 1);
-    if (selfmask & b) continue;
-    const float w = (float)lapc_of(l);
-    if (m & b) {
-      dg += w;
-      s += w * t[i + o.at(cx_of(l), cy_of(l), cz_of(l))];
-    } else {
-      dg += 2.f * w;
-    }
-  }
-  const float ti = t[i];
-  return ti + kOmega * (r[i] - (dg * ti - s)) * inv[i];
 }
 
 // coarsest level: kCoarseSweeps weighted Jacobi sweeps from zero by one

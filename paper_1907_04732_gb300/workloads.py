@@ -179,3 +179,13 @@ def batch_instances(count=256, seed=SEED):
                                psi=(0.0, volt))
         out.append(w.with_(name="inst%03d_%s" % (k, w.name)))
     return out
+
+
+def porous_crop(nx=32, ny=32, nz=16, *, seed=SEED, debye=8.0, bjerrum=1.44, voltage=0.1,
+                steps=2000, **kw) -> Workload:
+    """32x32x16 crop of the porous electrode made by the same generator
+    (spheres on a backing plate, counter plate at z = nz-1), scaled to the
+    box: 2 spheres of radius 3-5 in z < 8.  Used for the gradient checks."""
+    ids = porous(nx, ny, nz, 2, 3.0, 5.0, min(8.0, nz / 2.0), seed)
+    return Workload("porous_crop_%dx%dx%d" % (nx, ny, nz), ids, 2, (1, 1, 0), (0.0, voltage),
+                    bjerrum, debye, flow=False, steps=steps, **kw)

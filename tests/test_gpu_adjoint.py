@@ -154,3 +154,28 @@ def test_adjoint_errors(lbe):
     g.adjoint_backward([1.0, 0.0])
     g.adjoint_backward([0.0, 1.0])  # the handle is left in the forward pass's final state
     np.testing.assert_array_equal(g.charge(), q)
+
+
+def test_adjoint_porous_crop_2000_steps_vs_stored_tangent(lbe):
+    """The 32x32x16 porous crop, 2000 FP32 steps with checkpoints every 100,
+    against the FP64 oracle tangent stored by tests/golden/make_adjoint_golden.py."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "adjoint_porous_crop32x32x16.json")
+    ref = json.load(open(path))
+    w = wl.porous_crop()
+    assert list(w.shape) == ref["shape"] and w.steps == ref["steps"] == 2000
+    q, dpsi, ddebye, dD, dchi, g, _ = gpu_grad(lbe, w, w.steps, 100, np.array([1.0, 0.0]))
+    dQ = {k: np.array(v)[0] for k, v in ref["dQ"].items()}
+    np.testing.assert_allclose(q, ref["Q"], rtol=1e-5)
+    assert abs(dpsi[1] - dQ["psi2"]) <= TOL * abs(dQ["psi2"])
+    assert abs(dpsi[0] + dQ["psi2"]) <= TOL * abs(dQ["psi2"])  # a common shift changes nothing
+    assert abs(ddebye - dQ["debye"]) <= TOL * abs(dQ["debye"])
+    assert abs(dD[0] - dQ["D+"]) <= TOL * max(abs(dQ["D+"]), abs(dQ["D-"]))
+    assert abs(dD[1] - dQ["D-"]) <= TOL * max(abs(dQ["D+"]), abs(dQ["D-"]))
+    rng = np.random.Generator(np.random.PCG64(ref["chi_random_seed"]))
+    v = rng.standard_normal(dchi.size)
+    assert abs(float(np.dot(dchi, v)) - dQ["chi_random"]) <= TOL * np.abs(dchi).max() * np.sqrt(dchi.size)
+    for key in ("chi_fluid_node", "chi_interface_node"):
+        assert abs(dchi[ref[key]] - dQ[key]) <= TOL * np.abs(dchi).max(), key
+    assert g.recomputed_steps == 2000 - 20
