@@ -64,6 +64,25 @@ def section(w, side=16):
     return None
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest value of x over the ranks (the slowest rank's time); the
+    process group is NCCL on the GPU box (device "cuda"), gloo in the CPU
+    tests (device "cpu")."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world: int, nodes_per_rank: int, steps: int, seconds: float) -> float:
+    """Lattice updates of all ranks (one replica each) over the slowest
+    rank's time."""
+    return world * nodes_per_rank * steps / seconds / 1e6
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -412,13 +431,9 @@ def main():
     prof = lat.profile_end()
     barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     ms_step = ms / args.steps
-    value = world * w.nodes * args.steps / (ms * 1e-3) / 1e6
+    value = whole_job_mlups(world, w.nodes, args.steps, ms * 1e-3)
 
     # e2e through the public API with host buffers: per step the electrode
     # potentials go host->device, the induced charges device->host
@@ -430,8 +445,8 @@ def main():
         lat.step(1)
         q = lat.charge()
     torch.cuda.synchronize()
-    e2e_dt = time.perf_counter() - t0
-    e2e_val = world * w.nodes * args.e2e_steps / e2e_dt / 1e6
+    e2e_dt = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_val = whole_job_mlups(world, w.nodes, args.e2e_steps, e2e_dt)
 
     peak, peak_kind = load_peaks()
     ns = len(w.z)

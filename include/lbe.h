@@ -59,6 +59,10 @@ extern "C" {
                            velocity order c_0 = (0,0,0);
                            c_1..c_9 = (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,-1,0)
                            (1,0,1) (1,0,-1) (0,1,1) (0,1,-1); c_{i+9} = -c_i */
+#define LBE_FIELD_QNODE 5 /* induced charge of each electrode node, N doubles:
+                             the node's term of Eq. Qelec (links to fluid,
+                             doubled weights); 0 on fluid nodes.  Summed over
+                             the nodes of electrode e it is Q_e. */
 
 typedef struct lbe_handle lbe_handle;
 

@@ -315,6 +315,25 @@ __global__ void k_charge_final(int nblk, int n_elec, const double *__restrict__ 
   if (threadIdx.x == 0) q[e] = v;
 }
 
+// per-node term of Eq. Qelec (the map behind lbe_induced_charge)
+__global__ void k_charge_node(const Geo g, const Phys P, const uint8_t *__restrict__ id,
+                              const uint32_t *__restrict__ mask, const double *__restrict__ phi,
+                              double *__restrict__ out) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= g.N) return;
+  const uint32_t m = mask[r];
+  if (!id[r] || !(m & ((1u << 18) - 1))) {
+    out[r] = 0.0;
+    return;
+  }
+  int x, y, z;
+  coords(g, r, x, y, z);
+  double s = 0.0;
+  for (int i = 1; i < kQ; ++i)
+    if (m & (1u << (i - 1))) s += lapc_of(i) * 2.0 * (phi[nbr_i(g, x, y, z, i)] - phi[r]);
+  out[r] = -P.eps * s;
+}
+
 inline unsigned grid_for(long long N) { return (unsigned)((N + kBlock - 1) / kBlock); }
 #define LAUNCH3(h) make_launch((h)->geo).grid, make_launch((h)->geo).block
 
@@ -384,6 +403,11 @@ cudaError_t launch_moments(lbe_handle *h, double *rho_out, double *u_out) {
 
 cudaError_t launch_gather_f(lbe_handle *h, double *out) {
   k_gather_f<<<LAUNCH3(h), 0, h->stream>>>(h->geo, h->mask, h->f[h->cur], out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_charge_node(lbe_handle *h, double *out) {
+  k_charge_node<<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->phys, h->id, h->mask, h->phi, out);
   return cudaGetLastError();
 }
 

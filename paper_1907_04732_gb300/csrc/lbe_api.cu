@@ -407,6 +407,7 @@ int lbe_fields(lbe_handle *h, int which, void *out, int out_on_device) {
     case LBE_FIELD_RHO: count = (size_t)N; break;
     case LBE_FIELD_U: count = (size_t)N * 3; break;
     case LBE_FIELD_F: count = (size_t)N * lbe::kQ; break;
+    case LBE_FIELD_QNODE: count = (size_t)N; break;
     default: return fail(h, LBE_ERR_ARG, "fields: unknown field");
   }
   const size_t bytes = count * sizeof(double);
@@ -433,6 +434,7 @@ int lbe_fields(lbe_handle *h, int which, void *out, int out_on_device) {
     case LBE_FIELD_F:
       e = f32 ? lbe::launch_moments32(h, nullptr, nullptr, dst) : lbe::launch_gather_f(h, dst);
       break;
+    case LBE_FIELD_QNODE: e = lbe::launch_charge_node(h, dst); break;
   }
   if (e == cudaSuccess && !out_on_device) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess && !out_on_device) e = cudaStreamSynchronize(h->stream);

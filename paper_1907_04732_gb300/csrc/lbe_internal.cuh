@@ -293,6 +293,7 @@ cudaError_t launch_advect(lbe_handle *h);
 cudaError_t launch_moments(lbe_handle *h, double *rho_out, double *u_out);
 cudaError_t launch_gather_f(lbe_handle *h, double *out);
 cudaError_t launch_charge(lbe_handle *h);
+cudaError_t launch_charge_node(lbe_handle *h, double *out);
 // kernels_fp32.cu
 cudaError_t launch_init32(lbe_handle *h);
 cudaError_t launch_sweep32(lbe_handle *h);

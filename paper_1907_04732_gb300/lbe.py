@@ -28,7 +28,7 @@ LBE_ERR_GEOMETRY = -6
 LBE_FP64, LBE_FP32 = 0, 1
 LBE_MAX_SPECIES = 4
 LBE_MAX_ELECTRODES = 16
-FIELD_PHI, FIELD_N, FIELD_RHO, FIELD_U, FIELD_F = 0, 1, 2, 3, 4
+FIELD_PHI, FIELD_N, FIELD_RHO, FIELD_U, FIELD_F, FIELD_QNODE = 0, 1, 2, 3, 4, 5
 # order of the 19 populations in FIELD_F (as documented in lbe.h)
 _HALF = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, -1, 0), (1, 0, 1), (1, 0, -1), (0, 1, 1), (0, 1, -1)]
 VELOCITIES = [(0, 0, 0)] + _HALF + [(-a, -b, -c) for (a, b, c) in _HALF]
@@ -387,7 +387,7 @@ class Lattice:
 
     def field(self, which: int, device: bool = False):
         import torch
-        size = {FIELD_PHI: 1, FIELD_N: self.ns, FIELD_RHO: 1, FIELD_U: 3, FIELD_F: 19}[which]
+        size = {FIELD_PHI: 1, FIELD_N: self.ns, FIELD_RHO: 1, FIELD_U: 3, FIELD_F: 19, FIELD_QNODE: 1}[which]
         shape = (self.nz, self.ny, self.nx) if size == 1 else (size, self.nz, self.ny, self.nx)
         if device:
             t = torch.empty(shape, dtype=torch.float64, device="cuda")
@@ -411,6 +411,10 @@ class Lattice:
 
     def populations(self):
         return self.field(FIELD_F)
+
+    def charge_map(self):
+        """Induced charge of every electrode node (0 on fluid nodes)."""
+        return self.field(FIELD_QNODE)
 
     def set_state(self, n=None, phi=None):
         conv = lambda a: None if a is None else np.ascontiguousarray(np.asarray(a).reshape(-1), dtype=np.float64)

@@ -183,3 +183,23 @@ def test_full_size_vs_reduced_oracle(lbe, which):
     np.testing.assert_allclose(n_g, np.tile(n_o, (1,) + reps), rtol=1e-9, atol=1e-12 * n_o.max())
     area = full.nodes // red.nodes
     np.testing.assert_allclose(g.charge(), o.charge() * area, rtol=1e-7)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_charge_map_sums_to_electrode_charges(lbe, precision):
+    """The per-node charge map (LBE_FIELD_QNODE): nonzero only on electrode
+    nodes with fluid neighbours; its sum over each electrode is Q_e, and
+    over all electrodes minus the ionic charge (Gauss)."""
+    ids = wl.porous(15, 14, 13, 3, 1.5, 2.5, 6.0, seed=21)  # electrodes do not touch
+    w = wl.Workload("porous", ids, 2, (1, 1, 0), (0.0, 0.2), 1.0, 2.5, e_app=(1e-3, 0.0, 0.0))
+    prec = lbe.LBE_FP64 if precision == "fp64" else lbe.LBE_FP32
+    g = lbe.Lattice.from_workload(w, precision=prec, tol=1e-13)
+    g.init()
+    g.step(20)
+    qmap, q = g.charge_map(), g.charge()
+    assert np.all(qmap[ids == 0] == 0.0)
+    for e in range(1, 3):
+        assert abs(qmap[ids == e].sum() - q[e - 1]) <= 1e-12 * np.abs(q).max()
+    n = g.n()
+    ionic = (n[0] - n[1]).sum()
+    assert abs(qmap.sum() + ionic) <= 1e-9 * np.abs(q).max()
