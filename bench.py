@@ -351,6 +351,8 @@ def adjoint_leg(args, lbe, torch, stream):
             "gradient_mlups": node_steps / ((fwd_ms + bwd_ms) * 1e-3) / 1e6,
             "backward_over_forward": bwd_ms / fwd_ms,
             "recomputed_steps": int(g.recomputed_steps), "adjoint_cg_iters": int(g.poisson_iters),
+            "backward_phases_ms": {"recompute": g.recompute_ms, "flux_transpose": g.flux_ms,
+                                   "adjoint_solves": g.solve_ms},
             "checkpoint_bytes": (nseg + 1) * 32 * w.nodes, "segment_bytes": args.adjoint_every * 20 * w.nodes,
             "Q": [float(v) for v in q], "dQ1_dpsi": [float(v) for v in g.dpsi[:2]],
             "dQ1_drho_bulk": float(g.drho_bulk), "dQ1_dD": [float(v) for v in g.dD[:2]],

@@ -284,6 +284,9 @@ typedef struct {
   double dD[LBE_MAX_SPECIES];      /* dS/dD_k (species order of lbe_params) */
   long long poisson_iters;         /* CG iterations of the adjoint Poisson solves */
   long long recomputed_steps;      /* forward steps recomputed from checkpoints */
+  double recompute_ms;             /* device time: forward recomputation */
+  double flux_ms;                  /* device time: transposed flux steps */
+  double solve_ms;                 /* device time: adjoint Poisson solves */
 } lbe_adjoint_grad;
 
 /* Forward pass for a later lbe_adjoint_backward: lbe_init, then nsteps

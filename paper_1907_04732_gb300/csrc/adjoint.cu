@@ -50,8 +50,11 @@ struct AdjWork {
   float *lam = nullptr, *lam2 = nullptr;  // nbar [2][N]
   float *phibar = nullptr;
   double *mu = nullptr, *rhs = nullptr, *chibar = nullptr;
+  double *mu_prev = nullptr;  // mu of the previous solve (warm start by extrapolation)
+  int nsolved = 0;            // solves since the seed
   double *part = nullptr, *acc = nullptr;  // [kAdjSlots][nblk], [kAdjSlots]
   double q[LBE_MAX_ELECTRODES] = {};
+  std::vector<cudaEvent_t> ev;  // phase timing: 2 + 2 per step of a segment
 };
 
 namespace {
@@ -72,21 +75,31 @@ __device__ __forceinline__ float phi_at(long long j, const uint8_t *__restrict__
   return e ? (float)psi.c[e] : phi[j];
 }
 
-// block partial sums of kAdjSlots values in a fixed order (thread 0 writes)
-__device__ __forceinline__ void block_partials(double *v, double *__restrict__ part, int nblk) {
-  __shared__ double sh[kBlock / 32][kAdjSlots];
+// block partial sums of the slots [S0, S1) in a fixed order
+template <int S0, int S1>
+__device__ __forceinline__ void block_partials(const double *v, double *__restrict__ part, int nblk) {
+  __shared__ double sh[kBlock / 32][S1 - S0];
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  for (int k = 0; k < kAdjSlots; ++k) {
+#pragma unroll
+  for (int k = 0; k < S1 - S0; ++k) {
     double a = v[k];
     for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
     if (lane == 0) sh[wid][k] = a;
   }
   __syncthreads();
-  if (t < kAdjSlots) {
+  if (t < S1 - S0) {
     double a = 0.0;
     for (int w = 0; w < kBlock / 32; ++w) a += sh[w][t];
-    part[(long long)t * nblk + blockIdx.x] = a;
+    part[(long long)(S0 + t) * nblk + blockIdx.x] = a;
   }
+}
+
+// coordinates of node r (32-bit arithmetic; lattices have < 2^31 nodes)
+__device__ __forceinline__ void coords32(const Geo &g, int r, int &x, int &y, int &z) {
+  x = r % g.nx;
+  const int t = r / g.nx;
+  y = t % g.ny;
+  z = t / g.ny;
 }
 
 // seed of the backward pass: phibar = dS/dphi^T and the direct chi terms of
@@ -97,7 +110,7 @@ __global__ void __launch_bounds__(kBlock) k_adj_seed(const Geo g, const Phys P, 
                                                      float *__restrict__ phibar, double *__restrict__ chibar) {
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < g.N; r += (long long)gridDim.x * blockDim.x) {
     int x, y, z;
-    coords(g, r, x, y, z);
+    coords32(g, (int)r, x, y, z);
     const uint32_t m = mask[r];
     const int e = id[r];
     const double pr = phi_at(r, id, phi, psi);
@@ -131,6 +144,19 @@ __global__ void __launch_bounds__(kBlock) k_adj_seed(const Geo g, const Phys P, 
   }
 }
 
+// warm start of the adjoint solve: mu <- 2 mu(t+1) - mu(t+2) on fluid nodes
+// (linear extrapolation in time, as the forward solve does for phi; the
+// solution does not depend on the start), remembering mu(t+1)
+__global__ void k_adj_extrapolate(long long N, const uint32_t *__restrict__ mask, double *__restrict__ mu,
+                                  double *__restrict__ prev, int have) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x) {
+    if (!(mask[r] & kFluidBit)) continue;
+    const double v = mu[r];
+    if (have) mu[r] = 2.0 * v - prev[r];
+    prev[r] = v;
+  }
+}
+
 // right-hand side of the adjoint Poisson solve: -phibar on fluid nodes
 __global__ void k_adj_rhs(long long N, const uint32_t *__restrict__ mask, const float *__restrict__ phibar,
                           double *__restrict__ rhs) {
@@ -146,11 +172,11 @@ __global__ void __launch_bounds__(kBlock) k_adj_post(const Geo g, const Phys P, 
                                                      const Weights psi, int soft, float *__restrict__ lam,
                                                      double *__restrict__ chibar, double *__restrict__ part,
                                                      int nblk) {
-  double acc[kAdjSlots];
-  for (int k = 0; k < kAdjSlots; ++k) acc[k] = 0.0;
+  double acc[LBE_MAX_ELECTRODES];  // psibar
+  for (int k = 0; k < LBE_MAX_ELECTRODES; ++k) acc[k] = 0.0;
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < g.N; r += (long long)gridDim.x * blockDim.x) {
     int x, y, z;
-    coords(g, r, x, y, z);
+    coords32(g, (int)r, x, y, z);
     const uint32_t m = mask[r];
     const int e = id[r];
     if (!e) {
@@ -186,7 +212,7 @@ __global__ void __launch_bounds__(kBlock) k_adj_post(const Geo g, const Phys P, 
       chibar[r] += mus * lphi - nb;
     }
   }
-  block_partials(acc, part, nblk);
+  block_partials<0, LBE_MAX_ELECTRODES>(acc, part, nblk);
 }
 
 // transpose of one flux step: lam_in = nbar^{t+1}, state (q, phi) of time t
@@ -199,12 +225,11 @@ __global__ void __launch_bounds__(kBlock) k_adj_flux(const Geo g, const Phys P, 
                                                      double *__restrict__ chibar, double *__restrict__ part,
                                                      int nblk) {
   const float a0inv = 1.f / (1.f + 2.f * sqrtf(2.f));  // d = D / A0
-  double acc[kAdjSlots];
-  for (int k = 0; k < kAdjSlots; ++k) acc[k] = 0.0;
+  double acc[2] = {0.0, 0.0};  // Dbar of the two species
   const float unit = ldexpf(1.f, -kFixBits);
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < g.N; r += (long long)gridDim.x * blockDim.x) {
     int x, y, z;
-    coords(g, r, x, y, z);
+    coords32(g, (int)r, x, y, z);
     const uint32_t m = mask[r];
     const int e = id[r];
     if (!e) {
@@ -238,7 +263,7 @@ __global__ void __launch_bounds__(kBlock) k_adj_flux(const Geo g, const Phys P, 
       }
       for (int k = 0; k < 2; ++k) {
         lam_out[k * g.N + r] = nbar[k];
-        acc[kSlotD + k] += dD[k];
+        acc[k] += dD[k];
       }
       phibar[r] = pb;
       chibar[r] += cb;
@@ -265,27 +290,26 @@ __global__ void __launch_bounds__(kBlock) k_adj_flux(const Geo g, const Phys P, 
       chibar[r] += cb;
     }
   }
-  block_partials(acc, part, nblk);
+  block_partials<kSlotD, kSlotD + 2>(acc, part, nblk);
 }
 
 // t = 0: n^0 = rho_b (1 - chi)
 __global__ void __launch_bounds__(kBlock) k_adj_init(long long N, const uint32_t *__restrict__ mask, double rho_b,
                                                      const float *__restrict__ lam, double *__restrict__ chibar,
                                                      double *__restrict__ part, int nblk) {
-  double acc[kAdjSlots];
-  for (int k = 0; k < kAdjSlots; ++k) acc[k] = 0.0;
+  double acc[1] = {0.0};  // rho_bbar
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x) {
     if (!(mask[r] & kFluidBit)) continue;
     const double s = (double)lam[r] + (double)lam[N + r];
-    acc[kSlotRho] += s;
+    acc[0] += s;
     chibar[r] += -rho_b * s;
   }
-  block_partials(acc, part, nblk);
+  block_partials<kSlotRho, kSlotRho + 1>(acc, part, nblk);
 }
 
-// acc[k] += sum of the block partials, in block order
-__global__ void k_adj_accumulate(const double *__restrict__ part, int nblk, double *__restrict__ acc) {
-  const int k = blockIdx.x;
+// acc[k] += sum of the block partials of slot k = s0 + block, in block order
+__global__ void k_adj_accumulate(const double *__restrict__ part, int nblk, int s0, double *__restrict__ acc) {
+  const int k = s0 + blockIdx.x;
   double a = 0.0;
   for (int b = threadIdx.x; b < nblk; b += 32) a += part[(long long)k * nblk + b];
   for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
@@ -329,6 +353,7 @@ int adj_alloc(lbe_handle *h, int T, int every) {
     alloc((void **)&a->lam2, sizeof(float) * 2 * N);
     alloc((void **)&a->phibar, sizeof(float) * N);
     alloc((void **)&a->mu, sizeof(double) * N);
+    alloc((void **)&a->mu_prev, sizeof(double) * N);
     alloc((void **)&a->rhs, sizeof(double) * N);
     alloc((void **)&a->chibar, sizeof(double) * N);
     alloc((void **)&a->part, sizeof(double) * kAdjSlots * a->nblk);
@@ -375,12 +400,16 @@ int adj_poisson(lbe_handle *h, const float *phi_t, const Weights &psi, int soft)
   const Geo g = h->geo;
   const int nb = a->nblk;
   k_adj_rhs<<<nb, kBlock, 0, h->stream>>>(g.N, h->mask, a->phibar, a->rhs);
+  if (a->nsolved > 0)
+    k_adj_extrapolate<<<nb, kBlock, 0, h->stream>>>(g.N, h->mask, a->mu, a->mu_prev, a->nsolved > 1 ? 1 : 0);
+  a->nsolved += 1;
   ACK(h, cudaGetLastError());
-  const int rc = poisson_solve_linear(h, a->rhs, a->mu, 1e-30, 1e-9);
+  // relative 1e-7: below the FP32 resolution of the ion adjoint it feeds
+  const int rc = poisson_solve_linear(h, a->rhs, a->mu, 1e-30, 1e-7);
   if (rc != LBE_OK) return rc;
   k_adj_post<<<nb, kBlock, 0, h->stream>>>(g, h->phys, h->mask, h->id, phi_t, a->phibar, a->mu, psi, soft, a->lam,
                                            a->chibar, a->part, nb);
-  k_adj_accumulate<<<kAdjSlots, 32, 0, h->stream>>>(a->part, nb, a->acc);
+  k_adj_accumulate<<<LBE_MAX_ELECTRODES, 32, 0, h->stream>>>(a->part, nb, 0, a->acc);
   ACK(h, cudaGetLastError());
   return LBE_OK;
 }
@@ -400,8 +429,9 @@ bool adjoint_supported(const lbe_handle *h, std::string *why) {
 void adjoint_free(lbe_handle *h) {
   AdjWork *a = h->adj;
   if (!a) return;
+  for (cudaEvent_t e : a->ev) cudaEventDestroy(e);
   void *ptrs[] = {a->ck_q, a->ck_phi, a->ck_prev, a->st_q, a->st_phi, a->lam, a->lam2, a->phibar,
-                  a->mu,   a->rhs,    a->chibar,  a->part, a->acc};
+                  a->mu,   a->rhs,    a->chibar,  a->part, a->acc, a->mu_prev};
   for (void *p : ptrs) cudaFree(p);
   delete a;
   h->adj = nullptr;
@@ -466,6 +496,8 @@ int lbe_adjoint_backward(lbe_handle *h, const double *dq, int soft_electrode, lb
   cudaStream_t st = h->stream;
   ACK(h, cudaMemsetAsync(a->lam, 0, sizeof(float) * 2 * N, st));
   ACK(h, cudaMemsetAsync(a->mu, 0, sizeof(double) * N, st));
+  ACK(h, cudaMemsetAsync(a->mu_prev, 0, sizeof(double) * N, st));
+  a->nsolved = 0;
   ACK(h, cudaMemsetAsync(a->chibar, 0, sizeof(double) * N, st));
   ACK(h, cudaMemsetAsync(a->acc, 0, sizeof(double) * kAdjSlots, st));
   // CG iterations of the adjoint solves: the recomputing steps reset the
@@ -488,8 +520,15 @@ int lbe_adjoint_backward(lbe_handle *h, const double *dq, int soft_electrode, lb
   if (rc != LBE_OK) return rc;
   if ((rc = count()) != LBE_OK) return rc;
   long long recomputed = 0;
+  double ms_re = 0.0, ms_flux = 0.0, ms_solve = 0.0;
+  while ((int)a->ev.size() < 2 * a->every + 3) {
+    cudaEvent_t e;
+    ACK(h, cudaEventCreate(&e));
+    a->ev.push_back(e);
+  }
   for (int s = a->nseg - 1; s >= 0; --s) {
     const int t0 = s * a->every, t1 = std::min(a->T, t0 + a->every);
+    ACK(h, cudaEventRecord(a->ev[0], st));
     rc = load_ck(h, s);
     if (rc != LBE_OK) return rc;
     for (int t = t0; t < t1; ++t) {
@@ -503,22 +542,36 @@ int lbe_adjoint_backward(lbe_handle *h, const double *dq, int soft_electrode, lb
         ++recomputed;
       }
     }
+    ACK(h, cudaEventRecord(a->ev[1], st));
     ACK(h, poisson_reset_stats(h));
+    int k = 2;
     for (int t = t1 - 1; t >= t0; --t) {
       const int64_t *qt = a->st_q + (size_t)(t - t0) * 2 * N;
       const float *pt = a->st_phi + (size_t)(t - t0) * N;
+      ACK(h, cudaEventRecord(a->ev[k++], st));
       k_adj_flux<<<nb, kBlock, 0, st>>>(g, h->phys, h->p32, h->mask, h->id, qt, pt, psi, a->lam, a->lam2, a->phibar,
                                         a->chibar, a->part, nb);
-      k_adj_accumulate<<<kAdjSlots, 32, 0, st>>>(a->part, nb, a->acc);
+      k_adj_accumulate<<<2, 32, 0, st>>>(a->part, nb, kSlotD, a->acc);
       ACK(h, cudaGetLastError());
+      ACK(h, cudaEventRecord(a->ev[k++], st));
       std::swap(a->lam, a->lam2);
       rc = adj_poisson(h, pt, psi, soft_electrode);
       if (rc != LBE_OK) return rc;
     }
-    if ((rc = count()) != LBE_OK) return rc;
+    ACK(h, cudaEventRecord(a->ev[k], st));
+    if ((rc = count()) != LBE_OK) return rc;  // synchronises
+    float ms = 0.f;
+    ACK(h, cudaEventElapsedTime(&ms, a->ev[0], a->ev[1]));
+    ms_re += ms;
+    for (int j = 2; j < k; j += 2) {
+      ACK(h, cudaEventElapsedTime(&ms, a->ev[j], a->ev[j + 1]));
+      ms_flux += ms;
+      ACK(h, cudaEventElapsedTime(&ms, a->ev[j + 1], a->ev[j + 2]));
+      ms_solve += ms;
+    }
   }
   k_adj_init<<<nb, kBlock, 0, st>>>(N, h->mask, h->prm.rho_bulk[0], a->lam, a->chibar, a->part, nb);
-  k_adj_accumulate<<<kAdjSlots, 32, 0, st>>>(a->part, nb, a->acc);
+  k_adj_accumulate<<<1, 32, 0, st>>>(a->part, nb, kSlotRho, a->acc);
   ACK(h, cudaGetLastError());
   double acc[kAdjSlots];
   ACK(h, cudaMemcpyAsync(acc, a->acc, sizeof(acc), cudaMemcpyDeviceToHost, st));
@@ -532,6 +585,9 @@ int lbe_adjoint_backward(lbe_handle *h, const double *dq, int soft_electrode, lb
   out->drho_bulk = acc[kSlotRho];
   out->poisson_iters = adj_iters;
   out->recomputed_steps = recomputed;
+  out->recompute_ms = ms_re;
+  out->flux_ms = ms_flux;
+  out->solve_ms = ms_solve;
   // leave the handle as the forward pass left it
   rc = load_ck(h, a->nseg);
   if (rc != LBE_OK) return rc;

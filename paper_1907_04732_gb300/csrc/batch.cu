@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(kBlock) kb_init(const InstDev *__restrict__ in
   }
 }
 
-template <bool FLOW>
+template <bool FLOW, bool WIDE>
 __global__ void __launch_bounds__(kBlock) kb_sweep(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
                                                    int T, int Ntot, const uint32_t *__restrict__ mask,
                                                    const float *__restrict__ fin, float *__restrict__ fout,
@@ -363,10 +363,20 @@ __global__ void __launch_bounds__(kBlock) kb_sweep(const InstDev *__restrict__ i
       const int r = I.off + lo;
       const uint32_t m = mask[r];
       if (!(m & kFluidBit)) continue;
-      sweep_node<FLOW, true>(I.P, Ntot, r, offsets_of(I.g, x, y, z), m, fin, fout, q, qstar, phi, u, over);
+      sweep_node<FLOW, true, WIDE>(I.P, Ntot, r, offsets_of(I.g, x, y, z), m, fin, fout, q, qstar, phi, u, over);
     }
   }
   if (over) atomicOr(flag, 1);
+}
+
+using SweepKern = void (*)(const InstDev *, const int *, int, int, const uint32_t *, const float *, float *,
+                          const int64_t *, int64_t *, const float *, float *, int *);
+// the sweep for the batch's flow mode and size (64-bit population offsets
+// when 19 components pass 2^31)
+inline SweepKern sweep_kernel(bool flow, long long Ntot) {
+  const bool wide = (long long)kQ * Ntot >= (1LL << 31);
+  return flow ? (wide ? kb_sweep<true, true> : kb_sweep<true, false>)
+              : (wide ? kb_sweep<false, true> : kb_sweep<false, false>);
 }
 
 __global__ void __launch_bounds__(kBlock) kb_advect(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
@@ -1265,7 +1275,7 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   void *a_a[] = {&A.inst, &A.n, &A.pref0, &A.T, &A.mask, &A.v, &A.part, &A.c};
   void *a_cor[] = {&A.inst, &A.tile_inst, &A.T, &A.mask, &A.vx, &A.phi, &A.phi32, &A.c};
   if (step) {
-    void *sweep = b->flow ? (void *)kb_sweep<true> : (void *)kb_sweep<false>;
+    void *sweep = (void *)sweep_kernel(b->flow, b->Ntot);
     if (prof) e = add_event(g, &last, b->ev[0]);
     if (e == cudaSuccess) e = add_node(g, &last, sweep, G, B, a_sw);
     if (e == cudaSuccess && prof) e = add_event(g, &last, b->ev[1]);
@@ -1314,12 +1324,8 @@ int run_polled(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *
   long long &nl = b->prof_launches;
   if (step) {
     BCK(b, rec(0));
-    if (b->flow)
-      kb_sweep<true><<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, fin, fout, qin, qmid, A.phi32,
-                                           A.u, A.flag);
-    else
-      kb_sweep<false><<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, fin, fout, qin, qmid, A.phi32,
-                                            A.u, A.flag);
+    sweep_kernel(b->flow, b->Ntot)<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, fin, fout, qin,
+                                                         qmid, A.phi32, A.u, A.flag);
     BCK(b, rec(1));
     if (b->flow) kb_advect<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, qmid, A.u, qin);
     BCK(b, rec(2));
@@ -1487,12 +1493,9 @@ int autotune(lbe_batch *b) {
     float ms = 0.f;
     for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
       err = cudaEventRecord(e0, b->stream);
-      if (b->flow)
-        kb_sweep<true><<<grid, kBlock, 0, b->stream>>>(b->inst_d, b->tile_inst, b->T, (int)b->Ntot, b->mask,
-                                                       b->f[b->cur], fout, b->q, b->qstar, b->phi32, b->u, b->flag);
-      else
-        kb_sweep<false><<<grid, kBlock, 0, b->stream>>>(b->inst_d, b->tile_inst, b->T, (int)b->Ntot, b->mask,
-                                                        b->f[b->cur], fout, b->q, b->qstar, b->phi32, b->u, b->flag);
+      sweep_kernel(b->flow, b->Ntot)<<<grid, kBlock, 0, b->stream>>>(b->inst_d, b->tile_inst, b->T, (int)b->Ntot,
+                                                                     b->mask, b->f[b->cur], fout, b->q, b->qstar,
+                                                                     b->phi32, b->u, b->flag);
       if (err == cudaSuccess) err = cudaGetLastError();
       if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
       if (err == cudaSuccess) err = cudaEventSynchronize(e1);

@@ -4,6 +4,8 @@
 // offsets.
 #pragma once
 
+#include <type_traits>
+
 #include "lbe_internal.cuh"
 
 namespace lbe {
@@ -51,15 +53,20 @@ __device__ __forceinline__ float tterm(float a, float nu) { return __fmaf_rn(2.f
 
 __device__ __forceinline__ int nb_of(const Offs &o, int r, int i) { return r + o.at(cx_of(i), cy_of(i), cz_of(i)); }
 
+// Population component offsets: 32-bit while 19 N < 2^31, else 64-bit
+// (WIDE; a large lattice or batch passes 2^31 over 19 components).
+template <bool WIDE>
+using PopIdx = typename std::conditional<WIDE, long long, int>::type;
+
 // pull streaming with halfway bounce-back (see kernels_fp64.cu)
+template <bool WIDE>
 __device__ __forceinline__ void gather32(int N, int r, const Offs &o, uint32_t m, const float *__restrict__ fin,
                                          float f[kQ]) {
   f[0] = fin[r];
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     const int io = opp_of(i);
-    // component offsets in 64 bits: 19 components of a large lattice pass 2^31
-    f[i] = (m & (1u << (io - 1))) ? fin[(long long)i * N + nb_of(o, r, io)] : fin[(long long)io * N + r];
+    f[i] = (m & (1u << (io - 1))) ? fin[(PopIdx<WIDE>)i * N + nb_of(o, r, io)] : fin[(PopIdx<WIDE>)io * N + r];
   }
 }
 
@@ -140,7 +147,7 @@ __device__ __forceinline__ long long share(float totf, float ux, float uy, float
 
 // Fused step at one fluid node: quantised link fluxes and q* = q - sum Jq,
 // solvent force, and (FLOW) BGK + Guo collision with pull streaming.
-template <bool FLOW, bool SALT11>
+template <bool FLOW, bool SALT11, bool WIDE>
 __device__ __forceinline__ void sweep_node(const P32 &P, int N, int r, const Offs &o, uint32_t m,
                                            const float *__restrict__ fin, float *__restrict__ fout,
                                            const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
@@ -159,7 +166,7 @@ __device__ __forceinline__ void sweep_node(const P32 &P, int N, int r, const Off
   if (!FLOW) return;
 
   float f[kQ];
-  gather32(N, r, o, m, fin, f);
+  gather32<WIDE>(N, r, o, m, fin, f);
   float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
@@ -194,8 +201,8 @@ __device__ __forceinline__ void sweep_node(const P32 &P, int N, int r, const Off
     const float src_even = P.guo * w * (9.f * cu * cF - 3.f * uF);
     const float src_odd = P.guo * w * 3.f * cF;
     const int io = i + 9;
-    fout[(long long)i * N + r] = f[i] - P.omega * (f[i] - (eq_even + eq_odd)) + (src_even + src_odd);
-    fout[(long long)io * N + r] = f[io] - P.omega * (f[io] - (eq_even - eq_odd)) + (src_even - src_odd);
+    fout[(PopIdx<WIDE>)i * N + r] = f[i] - P.omega * (f[i] - (eq_even + eq_odd)) + (src_even + src_odd);
+    fout[(PopIdx<WIDE>)io * N + r] = f[io] - P.omega * (f[io] - (eq_even - eq_odd)) + (src_even - src_odd);
   }
 }
 

@@ -37,7 +37,7 @@ __global__ void k_init32(const Geo g, const P32 P, const uint8_t *__restrict__ i
 // Fused step kernel: link fluxes (quantised), solute update q* = q - sum Jq,
 // solvent force, and (FLOW) BGK + Guo collision and pull streaming with
 // halfway bounce-back, all in FP32 deviations.
-template <bool FLOW, bool SALT11>
+template <bool FLOW, bool SALT11, bool WIDE>
 __global__ void __launch_bounds__(kBlock) k_sweep32(const Geo g, const P32 P, const uint32_t *__restrict__ mask,
                                                     const float *__restrict__ fin, float *__restrict__ fout,
                                                     const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep32(const Geo g, const P32 P, co
   const uint32_t m = mask[r];
   if (!(m & kFluidBit)) return;
   bool over = false;
-  sweep_node<FLOW, SALT11>(P, N, r, offsets_of(g, x, y, z), m, fin, fout, q, qstar, phi, u, over);
+  sweep_node<FLOW, SALT11, WIDE>(P, N, r, offsets_of(g, x, y, z), m, fin, fout, q, qstar, phi, u, over);
   if (over) atomicOr(flag, 1);
 }
 
@@ -123,7 +123,7 @@ __global__ void k_moments32(const Geo g, const P32 P, int flow, const uint32_t *
   }
   const Offs o = offsets_of(g, x, y, z);
   float f[kQ];
-  gather32(N, r, o, m, fin, f);
+  gather32<true>(N, r, o, m, fin, f);
   if (f_out) {
     for (int i = 0; i < kQ; ++i) f_out[(long long)i * N + r] = w_of(i) + (double)f[i];
     return;
@@ -170,8 +170,12 @@ cudaError_t launch_sweep32(lbe_handle *h) {
   const bool salt11 = P.ns == 2 && P.zi[0] == 1 && P.zi[1] == -1;
   using Kern = void (*)(const Geo, const P32, const uint32_t *, const float *, float *, const int64_t *, int64_t *,
                         const float *, float *, int *);
-  Kern kern = h->prm.flow ? (salt11 ? k_sweep32<true, true> : k_sweep32<true, false>)
-                          : (salt11 ? k_sweep32<false, true> : k_sweep32<false, false>);
+  // 32-bit population offsets while the 19 components fit
+  const bool wide = (long long)kQ * h->geo.N >= (1LL << 31);
+  Kern kern = wide ? (h->prm.flow ? (salt11 ? k_sweep32<true, true, true> : k_sweep32<true, false, true>)
+                                  : (salt11 ? k_sweep32<false, true, true> : k_sweep32<false, false, true>))
+                   : (h->prm.flow ? (salt11 ? k_sweep32<true, true, false> : k_sweep32<true, false, false>)
+                                  : (salt11 ? k_sweep32<false, true, false> : k_sweep32<false, false, false>));
   kern<<<LAUNCH3(h), 0, h->stream>>>(h->geo, P, h->mask, h->f32[h->cur], h->f32[nxt], h->q, h->qstar, h->phi32,
                                      h->u32, h->flag);
   if (h->prm.flow) h->cur = nxt;

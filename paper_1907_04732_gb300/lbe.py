@@ -70,7 +70,8 @@ class lbe_profile(ctypes.Structure):
 class lbe_adjoint_grad(ctypes.Structure):
     _fields_ = [("dpsi", ctypes.c_double * LBE_MAX_ELECTRODES), ("drho_bulk", ctypes.c_double),
                 ("dD", ctypes.c_double * LBE_MAX_SPECIES), ("poisson_iters", ctypes.c_longlong),
-                ("recomputed_steps", ctypes.c_longlong)]
+                ("recomputed_steps", ctypes.c_longlong), ("recompute_ms", ctypes.c_double),
+                ("flux_ms", ctypes.c_double), ("solve_ms", ctypes.c_double)]
 
 
 _lib = None
