@@ -30,7 +30,7 @@
 #include <string>
 #include <vector>
 
-#include "lbe_internal.cuh"
+#include "fp32_device.cuh"
 
 namespace lbe {
 
@@ -216,7 +216,9 @@ __global__ void __launch_bounds__(kBlock) k_adj_post(const Geo g, const Phys P, 
 }
 
 // transpose of one flux step: lam_in = nbar^{t+1}, state (q, phi) of time t
-// -> nbar^t, phibar^t, Dbar, chibar (openness)
+// -> nbar^t, phibar^t, Dbar, chibar (openness).  1:1 salt: with
+// x = phi_j - phi_r - E.c the two ions see dmu = +x and -x, so one pair
+// (e^x - 1, e^-x - 1) serves both.  Per-node sums in FP32, across nodes FP64.
 __global__ void __launch_bounds__(kBlock) k_adj_flux(const Geo g, const Phys P, const P32 P3,
                                                      const uint32_t *__restrict__ mask, const uint8_t *__restrict__ id,
                                                      const int64_t *__restrict__ q, const float *__restrict__ phi,
@@ -225,69 +227,84 @@ __global__ void __launch_bounds__(kBlock) k_adj_flux(const Geo g, const Phys P, 
                                                      double *__restrict__ chibar, double *__restrict__ part,
                                                      int nblk) {
   const float a0inv = 1.f / (1.f + 2.f * sqrtf(2.f));  // d = D / A0
-  double acc[2] = {0.0, 0.0};  // Dbar of the two species
+  const float d0 = (float)P.d[0], d1 = (float)P.d[1];
+  const float rb0 = (float)P3.rbd[0], rb1 = (float)P3.rbd[1];
   const float unit = ldexpf(1.f, -kFixBits);
-  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < g.N; r += (long long)gridDim.x * blockDim.x) {
+  const int N = (int)g.N;
+  double acc[2] = {0.0, 0.0};  // Dbar of the two species
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < N; r += gridDim.x * blockDim.x) {
     int x, y, z;
-    coords32(g, (int)r, x, y, z);
+    coords32(g, r, x, y, z);
     const uint32_t m = mask[r];
     const int e = id[r];
     if (!e) {
+      const Offs o = offsets_of(g, x, y, z);
       const float pr = phi[r];
-      float nbar[2], pb = 0.f;
-      double cb = 0.0, dD[2] = {0.0, 0.0};
-      for (int k = 0; k < 2; ++k) nbar[k] = lam_in[k * g.N + r];
+      const float l0 = lam_in[r], l1 = lam_in[N + r];
+      const float nu0 = unit * (float)q[r], nu1 = unit * (float)q[N + r];
+      float nb0 = l0, nb1 = l1, pb = 0.f, cb = 0.f, dD0 = 0.f, dD1 = 0.f;
+#pragma unroll
       for (int l = 1; l < kQ; ++l) {
         const uint32_t b = 1u << (l - 1);
         if ((P.selfmask & b) || !(m & b)) continue;
-        const long long j = link_nbr(g, x, y, z, l);
-        const float dl_len = (float)invlen_of(l);
-        for (int k = 0; k < 2; ++k) {
-          const float zk = (float)P.z[k], dk = (float)P.d[k];
-          const float dlam = lam_in[k * g.N + j] - lam_in[k * g.N + r];
-          const float dmu = zk * (phi[j] - pr - (float)P.e_dot_c[l]);
-          const float ep = expf(dmu), em = expf(-dmu), epm1 = expm1f(dmu);
-          const float avg = 0.5f * (1.f + em);
-          // n = rho_b (1 + nu), nu = 2^-40 q: n' e^dmu - n = rho_b ((nu' - nu) + (1 + nu') (e^dmu - 1))
-          const float nur = unit * (float)q[k * g.N + r], nuj = unit * (float)q[k * g.N + j];
-          const float dnu = unit * (float)(q[k * g.N + j] - q[k * g.N + r]);
-          const float rb = (float)P3.rbd[k];
-          const float bracket = rb * (dnu + (1.f + nuj) * epm1);
-          const float nr = rb * (1.f + nur), nj = rb * (1.f + nuj);
-          const float J = -dk * dl_len * avg * bracket;
-          nbar[k] += dlam * dk * dl_len * avg;                               // dJ/dn_r
-          pb += dlam * (-dk * dl_len * 0.5f * (nr * em + nj * ep)) * (-zk);  // dJ/ddmu ddmu/dphi_r
-          dD[k] += 0.5 * (double)(dlam * (-a0inv * dl_len * avg * bracket));  // dJ/dD_k (each link seen twice)
-          cb += (double)(dlam * -J);                                          // d openness / d chi_r
+        const int j = r + o.at(cx_of(l), cy_of(l), cz_of(l));
+        const float il = (float)invlen_of(l);
+        float Pp, Mm;
+        fp32::em1_pair(phi[j] - pr - (float)P.e_dot_c[l], Pp, Mm);
+        const float ep = 1.f + Pp, em = 1.f + Mm;
+        // n = rho_b (1 + nu): n' e^dmu - n = rho_b ((nu' - nu) + (1 + nu') (e^dmu - 1))
+        const float nuj0 = unit * (float)q[j], nuj1 = unit * (float)q[N + j];
+        const float dnu0 = unit * (float)(q[j] - q[r]), dnu1 = unit * (float)(q[N + j] - q[N + r]);
+        // species 0 (z = +1): dmu = x
+        {
+          const float dlam = lam_in[j] - l0;
+          const float avg = 0.5f * (1.f + em), br = rb0 * (dnu0 + (1.f + nuj0) * Pp);
+          const float J = -d0 * il * avg * br;
+          nb0 += dlam * d0 * il * avg;                                                   // dJ/dn_r
+          pb -= dlam * (-d0 * il * 0.5f * (rb0 * (1.f + nu0) * em + rb0 * (1.f + nuj0) * ep));  // dJ/dphi_r
+          dD0 += dlam * (-a0inv * il * avg * br);                                       // dJ/dD
+          cb -= dlam * J;                                                                // openness
+        }
+        // species 1 (z = -1): dmu = -x
+        {
+          const float dlam = lam_in[N + j] - l1;
+          const float avg = 0.5f * (1.f + ep), br = rb1 * (dnu1 + (1.f + nuj1) * Mm);
+          const float J = -d1 * il * avg * br;
+          nb1 += dlam * d1 * il * avg;
+          pb += dlam * (-d1 * il * 0.5f * (rb1 * (1.f + nu1) * ep + rb1 * (1.f + nuj1) * em));
+          dD1 += dlam * (-a0inv * il * avg * br);
+          cb -= dlam * J;
         }
       }
-      for (int k = 0; k < 2; ++k) {
-        lam_out[k * g.N + r] = nbar[k];
-        acc[k] += dD[k];
-      }
+      lam_out[r] = nb0;
+      lam_out[N + r] = nb1;
       phibar[r] = pb;
-      chibar[r] += cb;
+      chibar[r] += (double)cb;
+      acc[0] += 0.5 * (double)dD0;  // each link is seen from both ends
+      acc[1] += 0.5 * (double)dD1;
     } else {
-      lam_out[r] = lam_out[g.N + r] = 0.f;
+      lam_out[r] = lam_out[N + r] = 0.f;
       phibar[r] = 0.f;
       if (!(m & ((1u << 18) - 1))) continue;
+      const Offs o = offsets_of(g, x, y, z);
       const float ps = (float)psi.c[e];
-      double cb = 0.0;
+      float cb = 0.f;
+#pragma unroll
       for (int l = 1; l < kQ; ++l) {
         const uint32_t b = 1u << (l - 1);
         if ((P.selfmask & b) || !(m & b)) continue;
-        const long long j = link_nbr(g, x, y, z, l);
-        const float dl_len = (float)invlen_of(l);
-        for (int k = 0; k < 2; ++k) {
-          const float zk = (float)P.z[k], dk = (float)P.d[k];
-          const float dmu = zk * (phi[j] - ps - (float)P.e_dot_c[l]);
-          const float nj = (float)P3.rbd[k] * (1.f + unit * (float)q[k * g.N + j]);
-          // flux a link from this node (no ions) to fluid j would carry
-          const float Jt = -dk * dl_len * 0.5f * (1.f + expf(-dmu)) * nj * expf(dmu);
-          cb += (double)(lam_in[k * g.N + j] * -Jt);
-        }
+        const int j = r + o.at(cx_of(l), cy_of(l), cz_of(l));
+        const float il = (float)invlen_of(l);
+        float Pp, Mm;
+        fp32::em1_pair(phi[j] - ps - (float)P.e_dot_c[l], Pp, Mm);
+        const float ep = 1.f + Pp, em = 1.f + Mm;
+        const float n0 = rb0 * (1.f + unit * (float)q[j]), n1 = rb1 * (1.f + unit * (float)q[N + j]);
+        // the flux a link from this node (no ions) to fluid j would carry
+        const float J0 = -d0 * il * 0.5f * (1.f + em) * n0 * ep;
+        const float J1 = -d1 * il * 0.5f * (1.f + ep) * n1 * em;
+        cb -= lam_in[j] * J0 + lam_in[N + j] * J1;
       }
-      chibar[r] += cb;
+      chibar[r] += (double)cb;
     }
   }
   block_partials<kSlotD, kSlotD + 2>(acc, part, nblk);

@@ -1,0 +1,157 @@
+"""Rows beyond the hot path's core, on the same kernels:
+
+* charging time: the decay rate of Q(t) - Q_inf of a plate column equals the
+  slowest non-conserved eigenvalue of the linearised step map, computed from
+  the oracle (finite-difference Jacobian of one oracle step in the charge
+  sector, dense eigenvalues);
+* coaxial capacitance at steady state against Eq. CYLcapaDH for the setup of
+  Table CapaErrorCoaxial (54x54x3, R1 = 2, R2 = 25, l_B = 1.2, voltage 0.1,
+  lambda_D = 3, 6, 9, 12), the four lattices advanced together by the
+  batched form; the table's printed errors are 2.3, 1.2, 1.0, 0.94 %;
+* coaxial electro-osmosis (Eq. DHcoaxialEOF): the steady axial velocity of
+  the charged 128x128x4 coaxial capacitor (R1 = 10, R2 = 50, lambda_D = 5,
+  l_B = 1.2, voltage 0.1) under E_z = 1e-4.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1907_04732_gb300 import workloads as wl
+import analytic as an
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def oracle_charge_mode_rate(w):
+    """Largest non-unit eigenvalue of the linearised step map restricted to
+    the charge density rho = n+ - n- (uniform salt), from the oracle."""
+    from oracle import Oracle
+    o = Oracle(w.shape, w.periodic, tau=w.tau, bjerrum=w.bjerrum, z=w.z, D=w.D, rho_bulk=w.rho_bulk,
+               e_app=w.e_app, flow=False, tol=1e-14)
+    o.set_geometry(w.ids, w.n_elec)
+    o.set_voltage(w.psi)
+    o.init()
+    rb = w.rho_bulk[0]
+    idx = np.flatnonzero((w.ids == 0).reshape(-1))
+
+    def step_map(rho):
+        n = np.zeros((2, w.ids.size))
+        n[0, idx] = rb + rho / 2
+        n[1, idx] = rb - rho / 2
+        o.set_state(n=n)
+        o.poisson((n[0] - n[1]).reshape(w.ids.shape))
+        o.step(1)
+        m = o.n().reshape(2, -1)
+        return m[0, idx] - m[1, idx]
+
+    L = idx.size
+    h = 1e-6 * rb
+    base = step_map(np.zeros(L))
+    J = np.empty((L, L))
+    for i in range(L):
+        e = np.zeros(L)
+        e[i] = h
+        J[:, i] = (step_map(e) - base) / h
+    ev = np.sort(np.abs(np.linalg.eigvals(J)))[::-1]
+    assert abs(ev[0] - 1.0) < 1e-9  # the conserved total charge
+    return ev[1]
+
+
+@pytest.mark.parametrize("debye,dt", [(4.0, 100), (8.0, 200), (16.0, 400)])
+def test_charging_rate_matches_linearised_step(lbe, debye, dt):
+    """Charging-time study (Fig. 5's tau against 2 lambda_D / L): the decay
+    rate of the electrode charge for three Debye lengths."""
+    w = wl.plate_capacitor(1, 1, 64, debye=debye, psi=(0.1, 0.2), flow=False)
+    lam2 = oracle_charge_mode_rate(w)
+    g = lbe.Lattice.from_workload(w, precision=lbe.LBE_FP64, tol=1e-13)
+    g.init()
+    q = []
+    for _ in range(100):
+        g.step(dt)
+        q.append(g.charge()[1])
+    q = np.array(q)
+    d = np.diff(q)
+    ratio = d[40:] / d[39:-1]  # = lambda^dt once the slowest mode dominates
+    lam_gpu = float(np.median(ratio)) ** (1.0 / dt)
+    print("charging rate (lambda_D = %g): gpu" % debye, 1 - lam_gpu, "oracle eigenvalue", 1 - lam2)
+    assert abs((1 - lam_gpu) - (1 - lam2)) <= 2e-3 * (1 - lam2)
+
+
+def test_coax_capacitance_error_table(lbe):
+    """Reproduces the paper's printed errors to their printed precision
+    (half a unit of the last printed digit)."""
+    ref = json.load(open(os.path.join(GOLDEN, "coax_capacitance_table.json")))
+    ws = [wl.coax_capacitor(54, 54, 3, r1=2.0, r2=25.0, debye=float(d), bjerrum=1.2, psi=(0.0, 0.1),
+                            flow=False) for d in ref["debye_over_dx"]]
+    b = lbe.Batch(ws, tol=1e-12)
+    b.init()
+    b.step(30000)
+    q1 = b.charge()[:, 0]
+    b.step(2000)
+    q2 = b.charge()[:, 0]
+    errs = []
+    for w, qa, qb in zip(ws, q1, q2):
+        assert abs(qb - qa) <= 1e-4 * abs(qb)  # steady state
+        eps = an.eps_of(w.bjerrum)
+        c_dh = an.coax_cdh_per_length(eps, 2.0, 25.0, 1.0 / w.debye)
+        c = abs(qb) / (w.shape[2] * 0.1)  # per unit length
+        errs.append(100.0 * abs(c - c_dh) / c_dh)
+    print("coax capacitance errors %", [round(e, 3) for e in errs])
+    for e, p, dec in zip(errs, ref["relative_error_percent"], ref["printed_decimals"]):
+        assert abs(e - p) <= 0.5 * 10.0 ** (-dec) + 1e-9, (errs, ref["relative_error_percent"])
+
+
+def test_coax_electro_osmosis_profile(lbe):
+    base = wl.coax_capacitor(128, 128, 4, r1=10.0, r2=50.0, debye=5.0, bjerrum=1.2, psi=(0.0, 0.1), flow=False)
+    g0 = lbe.Lattice.from_workload(base, precision=lbe.LBE_FP32, tol=1e-12)
+    g0.init()
+    g0.step(12000)
+    n, phi = g0.n(), g0.phi()
+    w = base.with_(flow=True, e_app=(0.0, 0.0, 1e-4))
+    g = lbe.Lattice.from_workload(w, precision=lbe.LBE_FP32, tol=1e-12)
+    g.init()
+    g.set_state(n=n, phi=phi)
+    g.step(8000)
+    u = g.u()[2].mean(axis=0)  # u_z averaged along the axis, [y, x]
+    ny, nx = u.shape
+    y, x = np.mgrid[0:ny, 0:nx]
+    r = np.hypot(x - (nx - 1) / 2, y - (ny - 1) / 2)
+    fluid = (base.ids[0] == 0)
+    eps, eta = an.eps_of(base.bjerrum), 1.0 / 6.0
+    uref = eps * 1e-4 * 0.1 / eta
+    th = an.coax_dh_eof(r[fluid], 10.0, 50.0, 1.0 / base.debye, eps, eta, 1e-4, 0.1)
+    dev = np.abs(u[fluid] - th).max() / uref
+    print("coax EOF: max |u - u_DH| / u_ref =", dev, " u_max/u_ref", np.abs(u[fluid]).max() / uref)
+    assert dev < 0.05
+
+
+def test_time_dependent_voltage(lbe):
+    """A voltage that changes every step (variant A15): the potential is the
+    Poisson solution of the new voltage at once; FP32 form against the
+    oracle re-solved after each change."""
+    from oracle import Oracle
+    ids = wl.random_blobs(16, 15, 14, 2, 0.2, seed=13)
+    w = wl.Workload("blob", ids, 2, (1, 1, 1), (0.0, 0.1), 1.0, 2.5, e_app=(1e-3, 0.0, 0.0))
+    o = Oracle(w.shape, w.periodic, tau=w.tau, bjerrum=w.bjerrum, z=w.z, D=w.D, rho_bulk=w.rho_bulk,
+               e_app=w.e_app, flow=w.flow, tol=1e-14)
+    o.set_geometry(w.ids, w.n_elec)
+    o.set_voltage(w.psi)
+    o.init()
+    g = lbe.Lattice.from_workload(w, precision=lbe.LBE_FP32, tol=1e-12)
+    g.init()
+    for t in range(30):
+        psi = (0.0, 0.1 + 0.05 * math.sin(2 * math.pi * t / 30))
+        o.set_voltage(psi)
+        n = o.n()
+        o.poisson((n[0] - n[1]).reshape(ids.shape))
+        g.set_voltage(psi)
+        o.step(1)
+        g.step(1)
+    assert np.abs(g.phi() - o.phi()).max() <= 1e-6 * 0.15
+    qo = o.charge()
+    assert np.all(np.abs(g.charge() - qo) <= 1e-5 * np.abs(qo).max())
