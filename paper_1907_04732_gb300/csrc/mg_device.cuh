@@ -27,9 +27,26 @@
 namespace lbe {
 namespace mgd {
 
-constexpr float kOmega = 0.7f;     // Jacobi weight
-constexpr float kAlpha = 1.6f;     // coarse-correction scaling
-constexpr int kCoarseSweeps = 32;  // Jacobi sweeps on the coarsest level
+// Smoother and correction constants (compile-time).  Measured on the
+// electro-osmosis, porous-electrode and coaxial lattices (CG iterations per
+// step, omega / alpha): 0.7/1.6 10.7, 14.9, 12.2; 0.9/1.8 7.6, 14.0, 9.5;
+// 1.0/1.8 7.0, 12.2, 8.0; 1.1/1.8 6.0, 10.3, 7.9; at 1.15/1.8 the V-cycle
+// stops being positive definite on the porous lattice (the CG stalls).
+// The Jacobi-scaled 19-point operator has its largest eigenvalue near 4/3
+// (smoothing needs omega below ~1.5), and alpha = 2 is where the coarse
+// correction stops contracting: 1.0/1.8 keeps a margin from both.
+#ifndef LBE_MG_OMEGA
+#define LBE_MG_OMEGA 1.0f
+#endif
+#ifndef LBE_MG_ALPHA
+#define LBE_MG_ALPHA 1.8f
+#endif
+#ifndef LBE_MG_COARSE_SWEEPS
+#define LBE_MG_COARSE_SWEEPS 32
+#endif
+constexpr float kOmega = LBE_MG_OMEGA;               // Jacobi weight
+constexpr float kAlpha = LBE_MG_ALPHA;               // coarse-correction scaling
+constexpr int kCoarseSweeps = LBE_MG_COARSE_SWEEPS;  // Jacobi sweeps on the coarsest level
 constexpr int kCoarseTarget = 256; // coarsening stops at or below this size
 constexpr int kCoarseMax = 1024;   // the coarsest solve owns one node per thread
 
