@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(kBlock) kb_outer(const InstDev *__restrict__ i
                                                    const double *__restrict__ part, InstCtl *c, BatchCtl *b,
                                                    double tol, int maxit, int nfam, const int *__restrict__ fam_cnt,
                                                    int *__restrict__ fam_pref, cudaGraphConditionalHandle hout,
-                                                   cudaGraphConditionalHandle hin, int use_cond) {
+                                                   cudaGraphConditionalHandle hin, int use_cond, int set_hin) {
   const int ii = blockIdx.x;
   if (!c[ii].outer_done) {
     const InstDev &I = inst[ii];
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(kBlock) kb_outer(const InstDev *__restrict__ i
     int any = 0;
     for (int i = 0; i < n; ++i) any |= !__ldcg(&c[i].outer_done);
     set_cond(hout, use_cond, any ? 1u : 0u);
-    if (!any) set_cond(hin, use_cond, 0u);
+    if (!any && set_hin) set_cond(hin, use_cond, 0u);
     b->any_outer = any;
     if (!any) b->any_inner = 0;
   }
@@ -1188,7 +1188,7 @@ int vcycle_kernels(const lbe_batch *b) { return b->mg_nlev >= 2 ? 2 * (b->mg_nle
 struct SolveArgs {
   const lbe::InstDev *inst;
   const int *tile_inst, *pref0, *fam_cnt;
-  int T, Ntot, n, maxit, nfam, use = 1, init1 = 1, init0 = 0, set_hist;
+  int T, Ntot, n, maxit, nfam, use = 1, init1 = 1, init0 = 0, set_hist, hin_no = 0, hin_yes = 1;
   const uint32_t *mask;
   const float *fin;
   float *fout;
@@ -1265,8 +1265,12 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   void *a_ext[] = {&A.inst, &A.tile_inst, &A.T, &A.mask, &A.phi, &A.phi_prev, &A.phi32, &A.hist};
   void *a_reset[] = {&A.n, &A.c, &A.bc, &A.hist, &A.set_hist};
   void *a_res[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.qsolve, &A.phi, &A.v, &A.part, &A.c};
-  void *a_out[] = {&A.inst, &A.n,       &A.T,        &A.part, &A.c,   &A.bc,  &A.tol,
-                   &A.maxit, &A.nfam,   &A.fam_cnt,  &A.fam_pref, &A.hout, &A.hin, &A.use};
+  // the test before the round loop must not touch the inner loop's
+  // condition (it belongs to the loop body); the one closing a round does
+  void *a_out0[] = {&A.inst, &A.n,    &A.T,       &A.part,     &A.c,    &A.bc,  &A.tol,
+                    &A.maxit, &A.nfam, &A.fam_cnt, &A.fam_pref, &A.hout, &A.hin, &A.use, &A.hin_no};
+  void *a_out[] = {&A.inst, &A.n,    &A.T,       &A.part,     &A.c,    &A.bc,  &A.tol,
+                   &A.maxit, &A.nfam, &A.fam_cnt, &A.fam_pref, &A.hout, &A.hin, &A.use, &A.hin_yes};
   void *a_b[] = {&A.inst, &A.n, &A.pref0, &A.T, &A.mask, &A.vr, &A.vu, &A.vw, &A.part};
   void *a_si[] = {&A.inst, &A.n,     &A.T,    &A.part,    &A.c,        &A.bc,  &A.eta, &A.tol_abs,
                   &A.maxit, &A.init1, &A.nfam, &A.fam_cnt, &A.fam_pref, &A.hin, &A.use};
@@ -1284,11 +1288,13 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
     if (e == cudaSuccess) e = add_node(g, &last, (void *)kb_extrapolate, G, B, a_ext);
   }
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&A.hout, g, 1, cudaGraphCondAssignDefault);
+  // reset -> residual test -> while (any instance unconverged) { V-cycle ->
+  // CG -> correct -> residual test }
   if (e == cudaSuccess) e = add_node(g, &last, (void *)kb_solve_reset, rb, dim3(256), a_reset);
+  if (e == cudaSuccess) e = add_node(g, &last, (void *)kb_res, G, B, a_res);
+  if (e == cudaSuccess) e = add_node(g, &last, (void *)kb_outer, NB, B, a_out0);
   if (e == cudaSuccess) e = add_while(g, &last, A.hout, &bo);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&A.hin, bo, 0, 0);
-  if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_res, G, B, a_res);
-  if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_outer, NB, B, a_out);
   if (e == cudaSuccess) e = add_vcycle(b, bo, &lo);
   if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_cg_b, G, B, a_b);
   if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_scal, NB, B, a_si);
@@ -1298,6 +1304,8 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   if (e == cudaSuccess) e = add_node(bi, &li, (void *)kb_cg_b, G, B, a_b);
   if (e == cudaSuccess) e = add_node(bi, &li, (void *)kb_scal, NB, B, a_st);
   if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_correct, G, B, a_cor);
+  if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_res, G, B, a_res);
+  if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_outer, NB, B, a_out);
   if (e == cudaSuccess && prof) e = add_event(g, &last, b->ev[3]);
   if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
   cudaGraphDestroy(g);
@@ -1358,7 +1366,7 @@ int run_polled(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *
   while (any_outer && err == cudaSuccess) {
     kb_res<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, A.qsolve, A.phi, A.v, A.part, A.c);
     kb_outer<<<n, kBlock, 0, st>>>(A.inst, n, A.T, A.part, A.c, A.bc, A.tol, A.maxit, A.nfam, A.fam_cnt, A.fam_pref,
-                                   h0, h0, 0);
+                                   h0, h0, 0, 0);
     nl += 2;
     flags(&any_outer, nullptr);
     if (!any_outer) break;

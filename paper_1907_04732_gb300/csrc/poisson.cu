@@ -134,7 +134,7 @@ __device__ __forceinline__ void reduce_partials(const double *part, int nblk, do
 // outer test of a refinement round (thread 0 of the last block of k_res):
 // converged, out of rounds or out of iterations?
 __device__ void outer_check(PoissonCtl *c, double m, double tol, int maxit, cudaGraphConditionalHandle hout,
-                            cudaGraphConditionalHandle hin, int use_cond) {
+                            cudaGraphConditionalHandle hin, int use_cond, int set_hin) {
   c->res = m;
   int done = 0;
   if (m <= tol) {
@@ -151,7 +151,7 @@ __device__ void outer_check(PoissonCtl *c, double m, double tol, int maxit, cuda
   c->rounds += 1;
   c->total_rounds += 1;
   set_cond(hout, use_cond, done ? 0u : 1u);
-  if (done) set_cond(hin, use_cond, 0u);
+  if (done && set_hin) set_cond(hin, use_cond, 0u);
 }
 
 // scalar recurrence of the Chronopoulos-Gear CG and the inner stopping test
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys
                                                 T *__restrict__ s, double *__restrict__ part, int nblk,
                                                 PoissonCtl *c, double tol, double tol_rel, int maxit,
                                                 cudaGraphConditionalHandle hout, cudaGraphConditionalHandle hin,
-                                                int use_cond) {
+                                                int use_cond, int set_hin) {
   float mx = 0.f, mb = 0.f;
   for (int kz = 0; kz < zpt; ++kz) {
     int X, Y, Z;
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys
   if (flat_tid() == 0) {
     c->arrive = 0;
     if (MODE == R_RHS) c->ref = ref;
-    outer_check(c, m, MODE == R_RHS ? fmax(tol, tol_rel * ref) : tol, maxit, hout, hin, use_cond);
+    outer_check(c, m, MODE == R_RHS ? fmax(tol, tol_rel * ref) : tol, maxit, hout, hin, use_cond, set_hin);
   }
 }
 
@@ -357,13 +357,17 @@ __global__ void __launch_bounds__(kBlock) k_cg_a(const Geo g, int zpt, uint32_t 
 // (linear extrapolation in time; the converged potential does not depend on
 // the starting guess), and remember phi(t)
 __global__ void k_extrapolate(const Geo g, const uint32_t *__restrict__ mask, double *__restrict__ phi,
-                              double *__restrict__ prev, int have_history) {
+                              double *__restrict__ prev, float *__restrict__ phi32, int have_history) {
   int X, Y, Z;
   long long i;
   if (!node_of(g, 1, 0, X, Y, Z, i)) return;
   if (!(mask[i] & kFluidBit)) return;
   const double v = phi[i];
-  if (have_history) phi[i] = 2.0 * v - prev[i];
+  if (have_history) {
+    const double e = 2.0 * v - prev[i];
+    phi[i] = e;
+    if (phi32) phi32[i] = (float)e;  // the FP32 copy follows: the solve may stop at once
+  }
   prev[i] = v;
 }
 
@@ -386,7 +390,7 @@ __global__ void k_correct(const Geo g, const uint32_t *__restrict__ mask, const 
 // kernel argument storage for graph nodes (values are copied at node creation)
 struct Args {
   Geo g;
-  int zpt, nblk, maxit, use_cond = 1, mode_init = C_INIT, mode_iter = C_ITER;
+  int zpt, nblk, maxit, use_cond = 1, mode_init = C_INIT, mode_iter = C_ITER, hin_no = 0, hin_yes = 1;
   Phys P;
   P32 P3;
   uint32_t selfmask;
@@ -478,21 +482,29 @@ cudaError_t build_graph(lbe_handle *h, Args &A, cudaGraphExec_t *exec) {
   cudaGraphNode_t last = nullptr, lo = nullptr, li = nullptr;
   cudaGraph_t body_out = nullptr, body_in = nullptr;
   void *a_reset[] = {&A.c};
-  void *a_res[] = {&A.g,     &A.zpt,  &A.P,    &A.P3,  &A.mask, &A.n64, &A.nq,      &A.rhs,
-                   &A.phi,   &A.r,    &A.u,    &A.x,   &A.p,    &A.s,   &A.part,    &A.nblk,
-                   &A.c,     &A.tol,  &A.tol_rel, &A.maxit, &A.hout, &A.hin, &A.use_cond};
+  // the residual before the round loop must not touch the inner loop's
+  // condition (it belongs to the loop body); the one closing a round does
+  void *a_res0[] = {&A.g,   &A.zpt, &A.P,       &A.P3,    &A.mask, &A.n64, &A.nq,       &A.rhs,
+                    &A.phi, &A.r,   &A.u,       &A.x,     &A.p,    &A.s,   &A.part,     &A.nblk,
+                    &A.c,   &A.tol, &A.tol_rel, &A.maxit, &A.hout, &A.hin, &A.use_cond, &A.hin_no};
+  void *a_res[] = {&A.g,   &A.zpt, &A.P,       &A.P3,    &A.mask, &A.n64, &A.nq,       &A.rhs,
+                   &A.phi, &A.r,   &A.u,       &A.x,     &A.p,    &A.s,   &A.part,     &A.nblk,
+                   &A.c,   &A.tol, &A.tol_rel, &A.maxit, &A.hout, &A.hin, &A.use_cond, &A.hin_yes};
   void *a_bi[] = {&A.g, &A.zpt, &A.selfmask, &A.mask, &A.u, &A.r, &A.w, &A.part, &A.nblk, &A.c,
                   &A.eta, &A.tol_inner, &A.maxit, &A.mode_init, &A.hin, &A.use_cond};
   void *a_bt[] = {&A.g, &A.zpt, &A.selfmask, &A.mask, &A.u, &A.r, &A.w, &A.part, &A.nblk, &A.c,
                   &A.eta, &A.tol_inner, &A.maxit, &A.mode_iter, &A.hin, &A.use_cond};
   void *a_a[] = {&A.g, &A.zpt, &A.selfmask, &A.mask, &A.x, &A.r, &A.u, &A.w, &A.p, &A.s, &A.part, &A.nblk, &A.c};
   void *a_cor[] = {&A.g, &A.mask, &A.x, &A.phi, &A.phi32};
+  // reset -> residual test -> while (not converged) { V-cycle -> CG -> correct
+  // -> residual test }: a converged test ends the solve without running the
+  // rest of a round
   e = cudaGraphConditionalHandleCreate(&A.hout, G, 1, cudaGraphCondAssignDefault);
   if (e == cudaSuccess) e = add_kernel(G, &last, (void *)k_solve_reset, one, one, a_reset);
+  if (e == cudaSuccess) e = add_kernel(G, &last, f_res, L.grid, L.block, a_res0);
   if (e == cudaSuccess) e = add_while(G, &last, A.hout, &body_out);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&A.hin, body_out, 0, 0);
   const bool mg = sizeof(T) == 4 && h->mg.nlev >= 2;
-  if (e == cudaSuccess) e = add_kernel(body_out, &lo, f_res, L.grid, L.block, a_res);
   if (e == cudaSuccess && mg) e = mg_vcycle(h, (const float *)A.r, (float *)A.u, A.c, body_out, &lo, nullptr);
   if (e == cudaSuccess) e = add_kernel(body_out, &lo, (void *)k_cg_b<T>, L.grid, L.block, a_bi);
   if (e == cudaSuccess) e = add_while(body_out, &lo, A.hin, &body_in);
@@ -500,6 +512,7 @@ cudaError_t build_graph(lbe_handle *h, Args &A, cudaGraphExec_t *exec) {
   if (e == cudaSuccess && mg) e = mg_vcycle(h, (const float *)A.r, (float *)A.u, A.c, body_in, &li, nullptr);
   if (e == cudaSuccess) e = add_kernel(body_in, &li, (void *)k_cg_b<T>, L.grid, L.block, a_bt);
   if (e == cudaSuccess) e = add_kernel(body_out, &lo, (void *)k_correct<T>, L1.grid, L1.block, a_cor);
+  if (e == cudaSuccess) e = add_kernel(body_out, &lo, f_res, L.grid, L.block, a_res);
   if (e == cudaSuccess) e = cudaGraphInstantiate(exec, G, 0);
   cudaGraphDestroy(G);
   return e;
@@ -521,7 +534,7 @@ int solve_polled(lbe_handle *h, Args &A) {
       auto kres = A.rhs ? k_res<T, R_RHS> : (fixed ? k_res<T, R_FIXED> : k_res<T, R_N64>);
       kres<<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.P, A.P3, A.mask, A.n64, A.nq, A.rhs, A.phi, (T *)A.r,
                                         (T *)A.u, (T *)A.x, (T *)A.p, (T *)A.s, A.part, A.nblk, A.c, A.tol,
-                                        A.tol_rel, A.maxit, 0, 0, 0);
+                                        A.tol_rel, A.maxit, 0, 0, 0, 0);
     }
     const bool mg = sizeof(T) == 4 && h->mg.nlev >= 2;
     if (mg && mg_vcycle(h, (const float *)A.r, (float *)A.u, A.c, nullptr, nullptr, st) != cudaSuccess)
@@ -677,7 +690,9 @@ int poisson_enqueue(lbe_handle *h, bool extrapolate) {
   PoissonWork &w = h->pw;
   if (extrapolate) {
     const Launch L1 = make_launch(h->geo);
-    k_extrapolate<<<L1.grid, L1.block, 0, h->stream>>>(h->geo, h->mask, h->phi, w.phi_prev, w.have_history ? 1 : 0);
+    k_extrapolate<<<L1.grid, L1.block, 0, h->stream>>>(h->geo, h->mask, h->phi, w.phi_prev,
+                                                       h->prm.precision == LBE_FP32 ? h->phi32 : nullptr,
+                                                       w.have_history ? 1 : 0);
     h->launches += 1;
     w.have_history = true;
   } else {
@@ -704,9 +719,11 @@ int poisson_status(lbe_handle *h, lbe_stats *st, long long *kernels) {
   // kernels of the graph path: reset + per round (residual, stencil,
   // correct) + per iteration (update, stencil)
   if (kernels && w.graph_ok) {
-    // a V-cycle after every residual and every iteration when multigrid is on
+    // per solve: reset and the residual tests; per round that ran (every
+    // test but the last of a solve): V-cycle, CG stencil, correction; per
+    // iteration: update, V-cycle, stencil (a V-cycle only with multigrid)
     const long long vc = h->prm.precision == LBE_FP32 ? mg_kernels_per_cycle(h) : 0;
-    *kernels = c.solves + (3 + vc) * c.total_rounds + (2 + vc) * c.total_iters;
+    *kernels = c.solves + c.total_rounds + (2 + vc) * (c.total_rounds - c.solves) + (2 + vc) * c.total_iters;
   }
   if (c.sticky_status == LBE_ERR_NOCONVERGE || c.status == LBE_ERR_NOCONVERGE) {
     h->err = "poisson: no convergence within poisson_max_iter";
