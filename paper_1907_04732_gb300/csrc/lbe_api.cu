@@ -42,7 +42,7 @@ bool fp32(const lbe_handle *h) { return h->prm.precision == LBE_FP32; }
 
 void free_all(lbe_handle *h) {
   void *ptrs[] = {h->id, h->mask, h->f[0], h->f[1], h->n, h->nstar, h->phi, h->u, h->qpart, h->qout, h->psi_dev,
-                  h->f32[0], h->f32[1], h->q, h->qstar, h->phi32, h->u32, h->flag};
+                  h->f32[0], h->f32[1], h->q, h->qstar, h->phi32, h->phi_lo, h->u32, h->flag};
   for (void *p : ptrs) cudaFree(p);
   if (h->qhost) cudaFreeHost(h->qhost);
   lbe::poisson_free(h);
@@ -205,6 +205,7 @@ int lbe_create(const lbe_params *p, void *cuda_stream, lbe_handle **out) {
     alloc((void **)&h->q, sizeof(int64_t) * (size_t)N * p->nspecies);
     alloc((void **)&h->qstar, sizeof(int64_t) * (size_t)N * p->nspecies);
     alloc((void **)&h->phi32, nf);
+    alloc((void **)&h->phi_lo, nf);
     alloc((void **)&h->u32, nf * 3);
     alloc((void **)&h->flag, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(h->u32, 0, nf * 3, h->stream);

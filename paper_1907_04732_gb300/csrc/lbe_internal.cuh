@@ -262,7 +262,8 @@ struct lbe_handle {
   float *f32[2] = {nullptr, nullptr};  // population deviations f_i - w_i
   int64_t *q = nullptr;                // fixed-point solute amounts [k][r]
   int64_t *qstar = nullptr;
-  float *phi32 = nullptr;              // FP32 copy of phi
+  float *phi32 = nullptr;              // FP32 copy of phi (its high part)
+  float *phi_lo = nullptr;             // low part: phi = phi32 + phi_lo to ~2^-48
   float *u32 = nullptr;                // velocity of the last collision
   int *flag = nullptr;                 // device error flags (fixed-point range)
   float *pw32 = nullptr;               // FP32 Poisson work: res, p, q, e [4][N]

@@ -25,7 +25,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#include "lbe_internal.cuh"
+#include "fp32_device.cuh"
 
 namespace lbe {
 
@@ -75,6 +75,38 @@ __device__ __forceinline__ double lap_at(const Geo &g, int r, int x, int y, int 
     wsum += w;
   }
   return (s1 + 2.0 * s2 + 4.0 * s4 - (double)wsum * v[r]) * (1.0 / 6.0);
+}
+
+// Error-free sum (Knuth): s + e = a + b exactly, s = fl(a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// 6 lap_mod(phi)(r) for phi = hi + lo (two floats per node), accumulated in
+// float-float on the FP32 pipes: per link the difference of the high parts
+// is split exactly (two_sum), the low parts and the rounding errors go to the
+// error word.  Returns S + E ~ 6 lap to ~2^-46 of the terms; the FP64 form
+// of lap_at needs 18 FP64 adds, which are slow on this GPU.
+__device__ __forceinline__ void lap6_ff(const Geo &g, int r, int x, int y, int z, uint32_t m,
+                                        const float *__restrict__ hi, const float *__restrict__ lo, float &S,
+                                        float &E) {
+  const Offs o = offsets_of(g, x, y, z);
+  const float h0 = hi[r], l0 = lo[r];
+  S = 0.f;
+  E = 0.f;
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    const int j = r + o.at(cx_of(i), cy_of(i), cz_of(i));
+    const float w = (float)((c2_of(i) == 1 ? 2 : 1) * ((m & (1u << (i - 1))) ? 1 : 2));
+    float d, de;
+    two_sum(hi[j], -h0, d, de);  // d + de = hi_j - hi_r exactly
+    float t, te;
+    two_sum(S, w * d, t, te);  // w is a power of two: w d is exact
+    S = t;
+    E += te + w * (de + (lo[j] - l0));
+  }
 }
 
 // block-wide sum or max in a fixed order; result valid in thread 0.  The
@@ -211,12 +243,14 @@ __global__ void k_solve_reset(PoissonCtl *c) {
 // MODE: 0 charge density from FP64 n, 1 from fixed-point q, 2 a given rhs
 // (linear solve A x = rhs; its relative test also needs max |rhs|/diag,
 // kept in the otherwise idle (r,u) partial slots).
-enum { R_N64 = 0, R_FIXED = 1, R_RHS = 2 };
+enum { R_N64 = 0, R_FIXED = 1, R_RHS = 2, R_FF = 3 };  // R_FF: R_FIXED, 1:1 salt, float-float residual
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys P, const P32 P3,
                                                 const uint32_t *__restrict__ mask, const double *__restrict__ n64,
                                                 const int64_t *__restrict__ nq, const double *__restrict__ rhs,
-                                                const double *__restrict__ phi, T *__restrict__ r,
+                                                const double *__restrict__ phi, const float *__restrict__ phi_hi,
+                                                const float *__restrict__ phi_lo, float c6_hi, float c6_lo,
+                                                T *__restrict__ r,
                                                 T *__restrict__ u, T *__restrict__ x, T *__restrict__ p,
                                                 T *__restrict__ s, double *__restrict__ part, int nblk,
                                                 PoissonCtl *c, double tol, double tol_rel, int maxit,
@@ -230,6 +264,25 @@ __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys
     const uint32_t m = mask[i];
     if (!(m & kFluidBit)) {
       r[i] = u[i] = x[i] = p[i] = s[i] = (T)0;
+      continue;
+    }
+    if (MODE == R_FF) {
+      // 6 res = 6 lap + 6 (4 pi l_B s) (q+ - q-), both in float-float
+      float S, E;
+      lap6_ff(g, (int)i, X, Y, Z, m, phi_hi, phi_lo, S, E);
+      const long long dq = nq[i] - nq[g.N + i];
+      const float dq_hi = fp32::ll2f(dq);
+      const float dq_lo = fp32::ll2f(dq - fp32::f2ll_rn(dq_hi));  // exact remainder
+      const float B = c6_hi * dq_hi;
+      const float Be = fmaf(c6_hi, dq_hi, -B) + (c6_hi * dq_lo + c6_lo * dq_hi);  // product error and tails
+      float t, te;
+      two_sum(S, B, t, te);
+      const float rt = (t + (te + (E + Be))) * (1.f / 6.f);
+      const float dinv = 1.f / diag_t<float>(m, P.selfmask);
+      r[i] = (T)rt;
+      u[i] = (T)(rt * dinv);
+      x[i] = p[i] = s[i] = (T)0;
+      mx = fmaxf(mx, fabsf(rt) * dinv);
       continue;
     }
     double b;
@@ -357,7 +410,8 @@ __global__ void __launch_bounds__(kBlock) k_cg_a(const Geo g, int zpt, uint32_t 
 // (linear extrapolation in time; the converged potential does not depend on
 // the starting guess), and remember phi(t)
 __global__ void k_extrapolate(const Geo g, const uint32_t *__restrict__ mask, double *__restrict__ phi,
-                              double *__restrict__ prev, float *__restrict__ phi32, int have_history) {
+                              double *__restrict__ prev, float *__restrict__ phi32, float *__restrict__ phi_lo,
+                              int have_history) {
   int X, Y, Z;
   long long i;
   if (!node_of(g, 1, 0, X, Y, Z, i)) return;
@@ -366,7 +420,11 @@ __global__ void k_extrapolate(const Geo g, const uint32_t *__restrict__ mask, do
   if (have_history) {
     const double e = 2.0 * v - prev[i];
     phi[i] = e;
-    if (phi32) phi32[i] = (float)e;  // the FP32 copy follows: the solve may stop at once
+    if (phi32) {  // the FP32 copies follow: the solve may stop at once
+      const float hi = (float)e;
+      phi32[i] = hi;
+      if (phi_lo) phi_lo[i] = (float)(e - (double)hi);
+    }
   }
   prev[i] = v;
 }
@@ -374,7 +432,7 @@ __global__ void k_extrapolate(const Geo g, const uint32_t *__restrict__ mask, do
 // phi64 += e on fluid nodes; the FP32 form refreshes its FP32 copy
 template <typename T>
 __global__ void k_correct(const Geo g, const uint32_t *__restrict__ mask, const T *__restrict__ e,
-                          double *__restrict__ phi, float *__restrict__ phi32) {
+                          double *__restrict__ phi, float *__restrict__ phi32, float *__restrict__ phi_lo) {
   int X, Y, Z;
   long long i;
   if (!node_of(g, 1, 0, X, Y, Z, i)) return;
@@ -383,7 +441,11 @@ __global__ void k_correct(const Geo g, const uint32_t *__restrict__ mask, const 
     v += (double)e[i];
     phi[i] = v;
   }
-  if (phi32) phi32[i] = (float)v;
+  if (phi32) {
+    const float hi = (float)v;
+    phi32[i] = hi;
+    if (phi_lo) phi_lo[i] = (float)(v - (double)hi);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -400,7 +462,8 @@ struct Args {
   const int64_t *nq;
   const double *rhs = nullptr;
   double *phi;
-  float *phi32;
+  float *phi32, *phi_lo = nullptr;
+  float c6_hi = 0.f, c6_lo = 0.f;  // 6 * 4 pi l_B * s, as two floats (R_FF)
   void *r, *u, *w, *x, *p, *s;
   double *part;
   PoissonCtl *c;
@@ -459,6 +522,12 @@ void fill_args(lbe_handle *h, Args &A) {
   A.nq = h->q;
   A.phi = h->phi;
   A.phi32 = h->phi32;
+  A.phi_lo = h->phi_lo;
+  {
+    const double c6 = 6.0 * h->phys.four_pi_lb * h->p32.sd[0];
+    A.c6_hi = (float)c6;
+    A.c6_lo = (float)(c6 - (double)A.c6_hi);
+  }
   A.r = base;
   A.u = base + N;
   A.w = base + 2 * N;
@@ -475,7 +544,9 @@ cudaError_t build_graph(lbe_handle *h, Args &A, cudaGraphExec_t *exec) {
   const Launch L1 = make_launch(h->geo);
   const dim3 one(1);
   const bool fixed = h->prm.precision == LBE_FP32;
-  void *f_res = A.rhs ? (void *)k_res<T, R_RHS> : (fixed ? (void *)k_res<T, R_FIXED> : (void *)k_res<T, R_N64>);
+  const bool ff = fixed && sizeof(T) == 4 && h->p32.salt11 && A.phi_lo && !A.rhs;
+  void *f_res = A.rhs ? (void *)k_res<T, R_RHS>
+                      : (ff ? (void *)k_res<T, R_FF> : (fixed ? (void *)k_res<T, R_FIXED> : (void *)k_res<T, R_N64>));
   cudaGraph_t G = nullptr;
   cudaError_t e = cudaGraphCreate(&G, 0);
   if (e != cudaSuccess) return e;
@@ -484,18 +555,20 @@ cudaError_t build_graph(lbe_handle *h, Args &A, cudaGraphExec_t *exec) {
   void *a_reset[] = {&A.c};
   // the residual before the round loop must not touch the inner loop's
   // condition (it belongs to the loop body); the one closing a round does
-  void *a_res0[] = {&A.g,   &A.zpt, &A.P,       &A.P3,    &A.mask, &A.n64, &A.nq,       &A.rhs,
-                    &A.phi, &A.r,   &A.u,       &A.x,     &A.p,    &A.s,   &A.part,     &A.nblk,
-                    &A.c,   &A.tol, &A.tol_rel, &A.maxit, &A.hout, &A.hin, &A.use_cond, &A.hin_no};
-  void *a_res[] = {&A.g,   &A.zpt, &A.P,       &A.P3,    &A.mask, &A.n64, &A.nq,       &A.rhs,
-                   &A.phi, &A.r,   &A.u,       &A.x,     &A.p,    &A.s,   &A.part,     &A.nblk,
-                   &A.c,   &A.tol, &A.tol_rel, &A.maxit, &A.hout, &A.hin, &A.use_cond, &A.hin_yes};
+  void *a_res0[] = {&A.g,     &A.zpt,   &A.P,      &A.P3,      &A.mask,  &A.n64, &A.nq, &A.rhs,
+                    &A.phi,   &A.phi32, &A.phi_lo, &A.c6_hi,   &A.c6_lo, &A.r,   &A.u,  &A.x,
+                    &A.p,     &A.s,     &A.part,   &A.nblk,    &A.c,     &A.tol, &A.tol_rel,
+                    &A.maxit, &A.hout,  &A.hin,    &A.use_cond, &A.hin_no};
+  void *a_res[] = {&A.g,     &A.zpt,   &A.P,      &A.P3,      &A.mask,  &A.n64, &A.nq, &A.rhs,
+                   &A.phi,   &A.phi32, &A.phi_lo, &A.c6_hi,   &A.c6_lo, &A.r,   &A.u,  &A.x,
+                   &A.p,     &A.s,     &A.part,   &A.nblk,    &A.c,     &A.tol, &A.tol_rel,
+                   &A.maxit, &A.hout,  &A.hin,    &A.use_cond, &A.hin_yes};
   void *a_bi[] = {&A.g, &A.zpt, &A.selfmask, &A.mask, &A.u, &A.r, &A.w, &A.part, &A.nblk, &A.c,
                   &A.eta, &A.tol_inner, &A.maxit, &A.mode_init, &A.hin, &A.use_cond};
   void *a_bt[] = {&A.g, &A.zpt, &A.selfmask, &A.mask, &A.u, &A.r, &A.w, &A.part, &A.nblk, &A.c,
                   &A.eta, &A.tol_inner, &A.maxit, &A.mode_iter, &A.hin, &A.use_cond};
   void *a_a[] = {&A.g, &A.zpt, &A.selfmask, &A.mask, &A.x, &A.r, &A.u, &A.w, &A.p, &A.s, &A.part, &A.nblk, &A.c};
-  void *a_cor[] = {&A.g, &A.mask, &A.x, &A.phi, &A.phi32};
+  void *a_cor[] = {&A.g, &A.mask, &A.x, &A.phi, &A.phi32, &A.phi_lo};
   // reset -> residual test -> while (not converged) { V-cycle -> CG -> correct
   // -> residual test }: a converged test ends the solve without running the
   // rest of a round
@@ -531,10 +604,11 @@ int solve_polled(lbe_handle *h, Args &A) {
   h->launches += 1;
   for (int round = 0; round <= kMaxOuter; ++round) {
     {
-      auto kres = A.rhs ? k_res<T, R_RHS> : (fixed ? k_res<T, R_FIXED> : k_res<T, R_N64>);
-      kres<<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.P, A.P3, A.mask, A.n64, A.nq, A.rhs, A.phi, (T *)A.r,
-                                        (T *)A.u, (T *)A.x, (T *)A.p, (T *)A.s, A.part, A.nblk, A.c, A.tol,
-                                        A.tol_rel, A.maxit, 0, 0, 0, 0);
+      const bool ff = fixed && sizeof(T) == 4 && h->p32.salt11 && A.phi_lo && !A.rhs;
+      auto kres = A.rhs ? k_res<T, R_RHS> : (ff ? k_res<T, R_FF> : (fixed ? k_res<T, R_FIXED> : k_res<T, R_N64>));
+      kres<<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.P, A.P3, A.mask, A.n64, A.nq, A.rhs, A.phi, A.phi32, A.phi_lo,
+                                        A.c6_hi, A.c6_lo, (T *)A.r, (T *)A.u, (T *)A.x, (T *)A.p, (T *)A.s, A.part,
+                                        A.nblk, A.c, A.tol, A.tol_rel, A.maxit, 0, 0, 0, 0);
     }
     const bool mg = sizeof(T) == 4 && h->mg.nlev >= 2;
     if (mg && mg_vcycle(h, (const float *)A.r, (float *)A.u, A.c, nullptr, nullptr, st) != cudaSuccess)
@@ -561,7 +635,7 @@ int solve_polled(lbe_handle *h, Args &A) {
       }
       h->launches += 2 * kChunk;
     }
-    k_correct<T><<<L1.grid, L1.block, 0, st>>>(A.g, A.mask, (const T *)A.x, A.phi, A.phi32);
+    k_correct<T><<<L1.grid, L1.block, 0, st>>>(A.g, A.mask, (const T *)A.x, A.phi, A.phi32, A.phi_lo);
     h->launches += 1;
     if (w.ctl_host->outer_done) break;
   }
@@ -662,6 +736,7 @@ int poisson_solve_linear(lbe_handle *h, const double *rhs, double *x, double tol
   A.rhs = rhs;
   A.phi = x;
   A.phi32 = nullptr;
+  A.phi_lo = nullptr;
   A.tol = tol_abs;
   A.tol_rel = tol_rel;
   A.tol_inner = 0.25 * tol_abs;
@@ -692,6 +767,7 @@ int poisson_enqueue(lbe_handle *h, bool extrapolate) {
     const Launch L1 = make_launch(h->geo);
     k_extrapolate<<<L1.grid, L1.block, 0, h->stream>>>(h->geo, h->mask, h->phi, w.phi_prev,
                                                        h->prm.precision == LBE_FP32 ? h->phi32 : nullptr,
+                                                       h->prm.precision == LBE_FP32 ? h->phi_lo : nullptr,
                                                        w.have_history ? 1 : 0);
     h->launches += 1;
     w.have_history = true;
@@ -740,7 +816,7 @@ cudaError_t poisson_reset_stats(lbe_handle *h) { return cudaMemsetAsync(h->pw.ct
 
 cudaError_t launch_phi32_sync(lbe_handle *h) {
   const Launch L = make_launch(h->geo);
-  k_correct<float><<<L.grid, L.block, 0, h->stream>>>(h->geo, h->mask, nullptr, h->phi, h->phi32);
+  k_correct<float><<<L.grid, L.block, 0, h->stream>>>(h->geo, h->mask, nullptr, h->phi, h->phi32, h->phi_lo);
   return cudaGetLastError();
 }
 
