@@ -90,6 +90,7 @@ struct InstDev {
   uint32_t selfmask;
   int mg_levels;      // multigrid levels incl. the lattice (0: Jacobi)
   FastDiv fx, fxy;    // division by nx and by nx*ny
+  float c6_hi, c6_lo;  // 6 * 4 pi l_B * s (fixed-point unit), as two floats
   double four_pi_lb, eps;
   P32 P;
 };
@@ -156,6 +157,7 @@ struct lbe_batch {
   int64_t *q = nullptr, *qstar = nullptr;
   double *phi = nullptr, *phi_prev = nullptr;
   float *phi32 = nullptr, *u = nullptr;
+  float *phi_lo = nullptr;  // phi = phi32 + phi_lo to ~2^-48 (float-float residual)
   float *vec = nullptr;     // CG vectors [6][Ntot]
   double *part = nullptr;   // per-tile partials [3][T]
   double *psi_d = nullptr;  // [n][kBE + 1]
@@ -325,7 +327,8 @@ __global__ void __launch_bounds__(kBlock) kb_init(const InstDev *__restrict__ in
                                                   int T, long long Ntot, const uint8_t *__restrict__ id,
                                                   const double *__restrict__ psi, float *__restrict__ f,
                                                   int64_t *__restrict__ q, double *__restrict__ phi,
-                                                  float *__restrict__ phi32, double *__restrict__ phi_prev,
+                                                  float *__restrict__ phi32, float *__restrict__ phi_lo,
+                                                  double *__restrict__ phi_prev,
                                                   float *__restrict__ u) {
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
     const int ii = tile_inst[t];
@@ -340,6 +343,7 @@ __global__ void __launch_bounds__(kBlock) kb_init(const InstDev *__restrict__ in
       const double p = e ? psi[ii * (kBE + 1) + e] : 0.0;
       phi[r] = p;
       phi32[r] = (float)p;
+      phi_lo[r] = (float)(p - (double)(float)p);
       phi_prev[r] = p;
       u[r] = u[Ntot + r] = u[2 * Ntot + r] = 0.f;
     }
@@ -405,7 +409,8 @@ __global__ void __launch_bounds__(kBlock) kb_advect(const InstDev *__restrict__ 
 // the previous solution is there (*hist); the FP32 copy follows
 __global__ void kb_extrapolate(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst, int T,
                                const uint32_t *__restrict__ mask, double *__restrict__ phi,
-                               double *__restrict__ prev, float *__restrict__ phi32, const int *__restrict__ hist) {
+                               double *__restrict__ prev, float *__restrict__ phi32, float *__restrict__ phi_lo,
+                               const int *__restrict__ hist) {
   const int have = *hist;
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
     const InstDev &I = inst[tile_inst[t]];
@@ -419,6 +424,7 @@ __global__ void kb_extrapolate(const InstDev *__restrict__ inst, const int *__re
         const double e = 2.0 * v - prev[r];
         phi[r] = e;
         phi32[r] = (float)e;
+        phi_lo[r] = (float)(e - (double)(float)e);
       }
       prev[r] = v;
     }
@@ -446,9 +452,9 @@ __global__ void kb_solve_reset(int n, InstCtl *c, BatchCtl *b, int *hist, int se
 // r/diag, x = p = s = 0); per-tile max |r|/diag
 __global__ void __launch_bounds__(kBlock) kb_res(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
                                                  int T, int Ntot, const uint32_t *__restrict__ mask,
-                                                 const int64_t *__restrict__ qn, const double *__restrict__ phi,
-                                                 const CgVec v, double *__restrict__ part,
-                                                 const InstCtl *__restrict__ c) {
+                                                 const int64_t *__restrict__ qn, const float *__restrict__ phi_hi,
+                                                 const float *__restrict__ phi_lo, const CgVec v,
+                                                 double *__restrict__ part, const InstCtl *__restrict__ c) {
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
     const int ii = tile_inst[t];
     if (c[ii].outer_done) continue;  // block-uniform
@@ -465,21 +471,17 @@ __global__ void __launch_bounds__(kBlock) kb_res(const InstDev *__restrict__ ins
         v.r[r] = v.u[r] = v.x[r] = v.p[r] = v.s[r] = 0.f;
         continue;
       }
-      const Offs o = offsets_of(I.g, x, y, z);
-      double s1 = 0.0, s2 = 0.0, s4 = 0.0;
-      int wsum = 0;
-#pragma unroll
-      for (int l = 1; l < kQ; ++l) {
-        const double vi = phi[r + o.at(cx_of(l), cy_of(l), cz_of(l))];
-        const int w = (c2_of(l) == 1 ? 2 : 1) * ((m & (1u << (l - 1))) ? 1 : 2);
-        if (w == 1) s1 += vi;
-        else if (w == 2) s2 += vi;
-        else s4 += vi;
-        wsum += w;
-      }
-      const double lap = (s1 + 2.0 * s2 + 4.0 * s4 - (double)wsum * phi[r]) * (1.0 / 6.0);
-      const double rho = I.P.sd[0] * (double)(qn[r] - qn[Ntot + r]);  // 1:1 salt, one bulk value
-      const float rf = (float)(I.four_pi_lb * rho + lap);
+      // 6 res = 6 lap(phi) + 6 (4 pi l_B s)(q+ - q-) in float-float (phi =
+      // hi + lo; FP64 adds are slow on this GPU)
+      float S, E;
+      fp32::lap6_ff(I.g, r, x, y, z, m, phi_hi, phi_lo, S, E);
+      const long long dq = qn[r] - qn[Ntot + r];  // 1:1 salt, one bulk value
+      const float dq_hi = ll2f(dq), dq_lo = ll2f(dq - f2ll_rn(dq_hi));
+      const float Bv = I.c6_hi * dq_hi;
+      const float Be = fmaf(I.c6_hi, dq_hi, -Bv) + (I.c6_hi * dq_lo + I.c6_lo * dq_hi);
+      float t6, te6;
+      fp32::two_sum(S, Bv, t6, te6);
+      const float rf = (t6 + (te6 + (E + Be))) * (1.f / 6.f);
       const float dinv = __fdividef(6.f, (float)mgd::diag6(m, I.selfmask));
       v.r[r] = rf;
       v.u[r] = rf * dinv;
@@ -670,7 +672,8 @@ __global__ void __launch_bounds__(kBlock) kb_cg_a(const InstDev *__restrict__ in
 // phi64 += x for instances that solved this round; FP32 copy refreshed
 __global__ void kb_correct(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst, int T,
                            const uint32_t *__restrict__ mask, const float *__restrict__ x_,
-                           double *__restrict__ phi, float *__restrict__ phi32, const InstCtl *__restrict__ c) {
+                           double *__restrict__ phi, float *__restrict__ phi32, float *__restrict__ phi_lo,
+                           const InstCtl *__restrict__ c) {
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
     const int ii = tile_inst[t];
     if (!c[ii].solving) continue;
@@ -685,6 +688,7 @@ __global__ void kb_correct(const InstDev *__restrict__ inst, const int *__restri
         phi[r] = v;
       }
       phi32[r] = (float)v;
+      phi_lo[r] = (float)(v - (double)(float)v);
     }
   }
 }
@@ -974,7 +978,8 @@ void mg_release(lbe_batch *b) {
 
 void bfree(lbe_batch *b) {
   void *ptrs[] = {b->inst_d, b->tile_inst, b->id,   b->mask, b->f[0],  b->f[1], b->q,    b->qstar, b->phi,
-                  b->phi_prev, b->phi32,  b->u, b->vec,  b->part, b->psi_d, b->ictl, b->bctl, b->qpart, b->qout,
+                  b->phi_prev, b->phi32,  b->phi_lo, b->u, b->vec, b->part, b->psi_d, b->ictl, b->bctl, b->qpart,
+                  b->qout,
                   b->flag,     b->hist};
   for (void *p : ptrs) cudaFree(p);
   mg_release(b);
@@ -1194,7 +1199,7 @@ struct SolveArgs {
   float *fout;
   int64_t *qin, *qmid, *qsolve;
   double *phi, *phi_prev;
-  float *phi32, *u;
+  float *phi32, *phi_lo, *u;
   lbe::CgVec v;
   const float *vr, *vu, *vx;
   float *vw;
@@ -1229,6 +1234,7 @@ void solve_args(lbe_batch *b, bool step, const float *fin, float *fout, int64_t 
   A.phi = b->phi;
   A.phi_prev = b->phi_prev;
   A.phi32 = b->phi32;
+  A.phi_lo = b->phi_lo;
   A.u = b->u;
   A.v = b->cg();
   A.vr = A.v.r;
@@ -1262,9 +1268,9 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   void *a_sw[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.fin, &A.fout, &A.qin, &A.qmid, &A.phi32, &A.u,
                   &A.flag};
   void *a_adv[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.qmid, &A.u, &A.qin};
-  void *a_ext[] = {&A.inst, &A.tile_inst, &A.T, &A.mask, &A.phi, &A.phi_prev, &A.phi32, &A.hist};
+  void *a_ext[] = {&A.inst, &A.tile_inst, &A.T, &A.mask, &A.phi, &A.phi_prev, &A.phi32, &A.phi_lo, &A.hist};
   void *a_reset[] = {&A.n, &A.c, &A.bc, &A.hist, &A.set_hist};
-  void *a_res[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.qsolve, &A.phi, &A.v, &A.part, &A.c};
+  void *a_res[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.qsolve, &A.phi32, &A.phi_lo, &A.v, &A.part, &A.c};
   // the test before the round loop must not touch the inner loop's
   // condition (it belongs to the loop body); the one closing a round does
   void *a_out0[] = {&A.inst, &A.n,    &A.T,       &A.part,     &A.c,    &A.bc,  &A.tol,
@@ -1277,7 +1283,7 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   void *a_st[] = {&A.inst, &A.n,     &A.T,    &A.part,    &A.c,        &A.bc,  &A.eta, &A.tol_abs,
                   &A.maxit, &A.init0, &A.nfam, &A.fam_cnt, &A.fam_pref, &A.hin, &A.use};
   void *a_a[] = {&A.inst, &A.n, &A.pref0, &A.T, &A.mask, &A.v, &A.part, &A.c};
-  void *a_cor[] = {&A.inst, &A.tile_inst, &A.T, &A.mask, &A.vx, &A.phi, &A.phi32, &A.c};
+  void *a_cor[] = {&A.inst, &A.tile_inst, &A.T, &A.mask, &A.vx, &A.phi, &A.phi32, &A.phi_lo, &A.c};
   if (step) {
     void *sweep = (void *)sweep_kernel(b->flow, b->Ntot);
     if (prof) e = add_event(g, &last, b->ev[0]);
@@ -1337,7 +1343,8 @@ int run_polled(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *
     BCK(b, rec(1));
     if (b->flow) kb_advect<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, qmid, A.u, qin);
     BCK(b, rec(2));
-    kb_extrapolate<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.mask, A.phi, A.phi_prev, A.phi32, A.hist);
+    kb_extrapolate<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.mask, A.phi, A.phi_prev, A.phi32, A.phi_lo,
+                                         A.hist);
     nl += b->flow ? 3 : 2;
   }
   kb_solve_reset<<<(n + 255) / 256, 256, 0, st>>>(n, A.c, A.bc, A.hist, A.set_hist);
@@ -1364,7 +1371,8 @@ int run_polled(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *
   const cudaGraphConditionalHandle h0 = 0;
   int any_outer = 1;
   while (any_outer && err == cudaSuccess) {
-    kb_res<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, A.qsolve, A.phi, A.v, A.part, A.c);
+    kb_res<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, A.qsolve, A.phi32, A.phi_lo, A.v,
+                                 A.part, A.c);
     kb_outer<<<n, kBlock, 0, st>>>(A.inst, n, A.T, A.part, A.c, A.bc, A.tol, A.maxit, A.nfam, A.fam_cnt, A.fam_pref,
                                    h0, h0, 0, 0);
     nl += 2;
@@ -1386,7 +1394,7 @@ int run_polled(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *
       nl += 3;
       flags(nullptr, &any_inner);
     }
-    kb_correct<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.mask, A.vx, A.phi, A.phi32, A.c);
+    kb_correct<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.mask, A.vx, A.phi, A.phi32, A.phi_lo, A.c);
     nl += 1;
   }
   if (vc) cudaGraphExecDestroy(vc);
@@ -1585,6 +1593,11 @@ int lbe_batch_create(const lbe_params *params, int n, void *cuda_stream, lbe_bat
     I.n_elec = 0;
     I.selfmask = tmp.phys.selfmask;
     I.four_pi_lb = tmp.phys.four_pi_lb;
+    {
+      const double c6 = 6.0 * tmp.phys.four_pi_lb * tmp.p32.sd[0];
+      I.c6_hi = (float)c6;
+      I.c6_lo = (float)(c6 - (double)I.c6_hi);
+    }
     I.eps = tmp.phys.eps;
     I.P = tmp.p32;
     for (int k = 0; k < I.ntiles; ++k) tile_inst[(size_t)(t0 + k)] = i;
@@ -1617,6 +1630,7 @@ int lbe_batch_create(const lbe_params *params, int n, void *cuda_stream, lbe_bat
   alloc((void **)&b->phi, 8 * N);
   alloc((void **)&b->phi_prev, 8 * N);
   alloc((void **)&b->phi32, 4 * N);
+  alloc((void **)&b->phi_lo, 4 * N);
   alloc((void **)&b->u, 4 * N * 3);
   alloc((void **)&b->vec, 4 * N * 6);
   alloc((void **)&b->part, sizeof(double) * 3 * T);
@@ -1710,7 +1724,7 @@ int lbe_batch_init(lbe_batch *b) {
   BCK(b, cudaMemcpyAsync(b->psi_d, b->psi.data(), sizeof(double) * b->psi.size(), cudaMemcpyHostToDevice, b->stream));
   b->cur = 0;
   kb_init<<<b->grid, kBlock, 0, b->stream>>>(b->inst_d, b->tile_inst, b->T, b->Ntot, b->id, b->psi_d, b->f[0], b->q,
-                                             b->phi, b->phi32, b->phi_prev, b->u);
+                                             b->phi, b->phi32, b->phi_lo, b->phi_prev, b->u);
   BCK(b, cudaGetLastError());
   BCK(b, cudaMemsetAsync(b->hist, 0, sizeof(int), b->stream));
   BCK(b, cudaStreamSynchronize(b->stream));

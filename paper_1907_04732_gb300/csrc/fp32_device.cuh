@@ -242,5 +242,37 @@ __device__ __forceinline__ void advect_node(int ns, int N, int r, const Offs &o,
   for (int k = 0; k < ns; ++k) qout[k * N + r] = acc[k] - base;
 }
 
+// Error-free sum (Knuth): s + e = a + b exactly, s = fl(a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// 6 lap_mod(phi)(r) for phi = hi + lo (two floats per node), accumulated in
+// float-float on the FP32 pipes: per link the difference of the high parts
+// is split exactly (two_sum), the low parts and the rounding errors go to the
+// error word.  Returns S + E ~ 6 lap to ~2^-46 of the terms; the FP64 form
+// of lap_at needs 18 FP64 adds, which are slow on this GPU.
+__device__ __forceinline__ void lap6_ff(const Geo &g, int r, int x, int y, int z, uint32_t m,
+                                        const float *__restrict__ hi, const float *__restrict__ lo, float &S,
+                                        float &E) {
+  const Offs o = offsets_of(g, x, y, z);
+  const float h0 = hi[r], l0 = lo[r];
+  S = 0.f;
+  E = 0.f;
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    const int j = r + o.at(cx_of(i), cy_of(i), cz_of(i));
+    const float w = (float)((c2_of(i) == 1 ? 2 : 1) * ((m & (1u << (i - 1))) ? 1 : 2));
+    float d, de;
+    two_sum(hi[j], -h0, d, de);  // d + de = hi_j - hi_r exactly
+    float t, te;
+    two_sum(S, w * d, t, te);  // w is a power of two: w d is exact
+    S = t;
+    E += te + w * (de + (lo[j] - l0));
+  }
+}
+
 }  // namespace fp32
 }  // namespace lbe

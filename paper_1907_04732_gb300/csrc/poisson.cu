@@ -77,38 +77,6 @@ __device__ __forceinline__ double lap_at(const Geo &g, int r, int x, int y, int 
   return (s1 + 2.0 * s2 + 4.0 * s4 - (double)wsum * v[r]) * (1.0 / 6.0);
 }
 
-// Error-free sum (Knuth): s + e = a + b exactly, s = fl(a + b).
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// 6 lap_mod(phi)(r) for phi = hi + lo (two floats per node), accumulated in
-// float-float on the FP32 pipes: per link the difference of the high parts
-// is split exactly (two_sum), the low parts and the rounding errors go to the
-// error word.  Returns S + E ~ 6 lap to ~2^-46 of the terms; the FP64 form
-// of lap_at needs 18 FP64 adds, which are slow on this GPU.
-__device__ __forceinline__ void lap6_ff(const Geo &g, int r, int x, int y, int z, uint32_t m,
-                                        const float *__restrict__ hi, const float *__restrict__ lo, float &S,
-                                        float &E) {
-  const Offs o = offsets_of(g, x, y, z);
-  const float h0 = hi[r], l0 = lo[r];
-  S = 0.f;
-  E = 0.f;
-#pragma unroll
-  for (int i = 1; i < kQ; ++i) {
-    const int j = r + o.at(cx_of(i), cy_of(i), cz_of(i));
-    const float w = (float)((c2_of(i) == 1 ? 2 : 1) * ((m & (1u << (i - 1))) ? 1 : 2));
-    float d, de;
-    two_sum(hi[j], -h0, d, de);  // d + de = hi_j - hi_r exactly
-    float t, te;
-    two_sum(S, w * d, t, te);  // w is a power of two: w d is exact
-    S = t;
-    E += te + w * (de + (lo[j] - l0));
-  }
-}
-
 // block-wide sum or max in a fixed order; result valid in thread 0.  The
 // FP32 kernels reduce in FP32 within the block (FP64 is slow on this GPU);
 // block partials are stored and combined in FP64.
@@ -269,14 +237,14 @@ __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys
     if (MODE == R_FF) {
       // 6 res = 6 lap + 6 (4 pi l_B s) (q+ - q-), both in float-float
       float S, E;
-      lap6_ff(g, (int)i, X, Y, Z, m, phi_hi, phi_lo, S, E);
+      fp32::lap6_ff(g, (int)i, X, Y, Z, m, phi_hi, phi_lo, S, E);
       const long long dq = nq[i] - nq[g.N + i];
       const float dq_hi = fp32::ll2f(dq);
       const float dq_lo = fp32::ll2f(dq - fp32::f2ll_rn(dq_hi));  // exact remainder
       const float B = c6_hi * dq_hi;
       const float Be = fmaf(c6_hi, dq_hi, -B) + (c6_hi * dq_lo + c6_lo * dq_hi);  // product error and tails
       float t, te;
-      two_sum(S, B, t, te);
+      fp32::two_sum(S, B, t, te);
       const float rt = (t + (te + (E + Be))) * (1.f / 6.f);
       const float dinv = 1.f / diag_t<float>(m, P.selfmask);
       r[i] = (T)rt;
