@@ -110,7 +110,9 @@ int lbe_set_geometry(lbe_handle *h, const uint8_t *node_id, int n_electrodes, in
 
 /* Electrode potentials psi_e (reduced, host array of n_electrodes doubles).
  * Only differences matter (Sec. "Parallel plate capacitor").  After lbe_init
- * the potential is re-solved at once so that the state stays consistent. */
+ * the potential is re-solved at once so that the state stays consistent;
+ * potentials equal to the current ones are uploaded and nothing else is done
+ * (the state is already consistent). */
 int lbe_set_voltage(lbe_handle *h, const double *psi);
 
 /* Initial state (Sec. "Potential and concentration profiles"): uncharged

@@ -289,13 +289,23 @@ static int solve_now(lbe_handle *h) {
 
 int lbe_set_voltage(lbe_handle *h, const double *psi) {
   if (!h) return LBE_ERR_ARG;
-  h->gen += 1;
   if (!h->have_geometry) return fail(h, LBE_ERR_STATE, "set_voltage: no geometry");
   if (!psi && h->n_elec > 0) return fail(h, LBE_ERR_ARG, "set_voltage: NULL psi");
   StreamGuard sg{h, h->owns_stream};
   for (int e = 0; e < h->n_elec; ++e)
     if (!isfinite(psi[e])) return fail(h, LBE_ERR_ARG, "set_voltage: non-finite potential");
-  for (int e = 0; e < h->n_elec; ++e) h->psi[e] = psi[e];
+  bool same = h->initialised;
+  for (int e = 0; e < h->n_elec; ++e) {
+    same = same && h->psi[e] == psi[e];
+    h->psi[e] = psi[e];
+  }
+  if (same) {
+    // the electrodes already hold these potentials: upload them (the solid
+    // nodes are rewritten with the same values) and keep the consistent state
+    LBE_CK(h, lbe::launch_set_solid_phi(h));
+    return LBE_OK;
+  }
+  h->gen += 1;
   if (!h->initialised) return LBE_OK;
   h->stats = lbe_stats{};
   LBE_CK(h, lbe::launch_set_solid_phi(h));

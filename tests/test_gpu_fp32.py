@@ -117,3 +117,19 @@ def test_fp32_determinism_and_checkpoint(lbe):
     np.testing.assert_array_equal(c.populations(), a.populations())
     np.testing.assert_array_equal(c.n(), a.n())
     np.testing.assert_array_equal(c.charge(), a.charge())
+
+
+def test_set_voltage_unchanged_keeps_state(lbe):
+    """Setting the potentials the electrodes already hold uploads them and
+    leaves the trajectory bitwise unchanged; a new value re-solves at once."""
+    ids = wl.random_blobs(14, 13, 12, 2, 0.2, seed=23)
+    w = wl.Workload("blob", ids, 2, (1, 1, 1), (0.0, 0.15), 1.0, 2.5, e_app=(1e-3, 0.0, 0.0))
+    a, b = gpu_for(lbe, w), gpu_for(lbe, w)
+    for _ in range(6):
+        a.set_voltage(w.psi)
+        a.step(1)
+        b.step(1)
+    np.testing.assert_array_equal(a.phi(), b.phi())
+    np.testing.assert_array_equal(a.n(), b.n())
+    a.set_voltage((0.0, 0.2))
+    assert np.abs(a.phi() - b.phi()).max() > 1e-3  # re-solved for the new voltage
