@@ -355,7 +355,7 @@ def adjoint_leg(args, lbe, torch, stream):
             "recomputed_steps": int(g.recomputed_steps), "adjoint_cg_iters": int(g.poisson_iters),
             "backward_phases_ms": {"recompute": g.recompute_ms, "flux_transpose": g.flux_ms,
                                    "adjoint_solves": g.solve_ms},
-            "checkpoint_bytes": (nseg + 1) * 32 * w.nodes, "segment_bytes": args.adjoint_every * 20 * w.nodes,
+            "checkpoint_bytes": (nseg + 1) * 40 * w.nodes, "segment_bytes": args.adjoint_every * 20 * w.nodes,
             "Q": [float(v) for v in q], "dQ1_dpsi": [float(v) for v in g.dpsi[:2]],
             "dQ1_drho_bulk": float(g.drho_bulk), "dQ1_dD": [float(v) for v in g.dD[:2]],
             "dQ1_dchi_absmax": float(np.abs(dchi).max()),
@@ -489,7 +489,7 @@ def main():
         "roofline": roof,
         "phases_ms": phases, "phase_shares": shares,
         "poisson": {"ms_per_step": phases["poisson"], "cg_iters_per_step": iters,
-                    "note": "FP64-residual refinement, multigrid-preconditioned CG (FP32 form), one CUDA graph"},
+                    "note": "refinement on a float-float residual, multigrid-preconditioned FP32 CG, quadratic warm start in time, one CUDA graph"},
         "lb_part_hbm_frac": step_bytes / ((phases["sweep"] + phases["advect"]) * 1e-3) / 1e9 / peak,
         "advect_gbs": adv_bytes / (phases["advect"] * 1e-3) / 1e9 if phases["advect"] > 0 else None,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * w.n_elec,

@@ -43,7 +43,8 @@ struct AdjWork {
   long long gen = -1;  // handle generation after the forward pass
   bool ready = false;
   int64_t *ck_q = nullptr;  // checkpoints [nseg + 1][2N] (the last: time T)
-  double *ck_phi = nullptr, *ck_prev = nullptr;  // [nseg + 1][N]
+  double *ck_phi = nullptr;   // [nseg + 1][N]
+  double *ck_prev = nullptr;  // [nseg + 1][2N]: the warm start's history
   std::vector<char> ck_hist;
   int64_t *st_q = nullptr;  // states of one segment [every][2N]
   float *st_phi = nullptr;  // [every][N]
@@ -145,8 +146,10 @@ __global__ void __launch_bounds__(kBlock) k_adj_seed(const Geo g, const Phys P, 
 }
 
 // warm start of the adjoint solve: mu <- 2 mu(t+1) - mu(t+2) on fluid nodes
-// (linear extrapolation in time, as the forward solve does for phi; the
-// solution does not depend on the start), remembering mu(t+1)
+// (linear extrapolation in time; the solution does not depend on the start),
+// remembering mu(t+1).  Unlike the forward potential, the quadratic start
+// measured worse here: 25.5 k instead of 19.0 k adjoint CG iterations over
+// 2000 steps of the porous electrode.
 __global__ void k_adj_extrapolate(long long N, const uint32_t *__restrict__ mask, double *__restrict__ mu,
                                   double *__restrict__ prev, int have) {
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x) {
@@ -363,7 +366,7 @@ int adj_alloc(lbe_handle *h, int T, int every) {
     const size_t ns1 = (size_t)nseg + 1;
     alloc((void **)&a->ck_q, sizeof(int64_t) * 2 * N * ns1);
     alloc((void **)&a->ck_phi, sizeof(double) * N * ns1);
-    alloc((void **)&a->ck_prev, sizeof(double) * N * ns1);
+    alloc((void **)&a->ck_prev, sizeof(double) * 2 * N * ns1);
     alloc((void **)&a->st_q, sizeof(int64_t) * 2 * N * std::max(every, 1));
     alloc((void **)&a->st_phi, sizeof(float) * N * std::max(every, 1));
     alloc((void **)&a->lam, sizeof(float) * 2 * N);
@@ -392,9 +395,9 @@ int save_ck(lbe_handle *h, int k) {
   ACK(h, cudaMemcpyAsync(a->ck_q + (size_t)k * 2 * N, h->q, sizeof(int64_t) * 2 * N, cudaMemcpyDeviceToDevice,
                          h->stream));
   ACK(h, cudaMemcpyAsync(a->ck_phi + (size_t)k * N, h->phi, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
-  ACK(h, cudaMemcpyAsync(a->ck_prev + (size_t)k * N, h->pw.phi_prev, sizeof(double) * N, cudaMemcpyDeviceToDevice,
-                         h->stream));
-  a->ck_hist[k] = h->pw.have_history ? 1 : 0;
+  ACK(h, cudaMemcpyAsync(a->ck_prev + (size_t)k * 2 * N, h->pw.phi_prev, sizeof(double) * 2 * N,
+                         cudaMemcpyDeviceToDevice, h->stream));
+  a->ck_hist[k] = (char)h->pw.history;
   return LBE_OK;
 }
 
@@ -404,9 +407,9 @@ int load_ck(lbe_handle *h, int k) {
   ACK(h, cudaMemcpyAsync(h->q, a->ck_q + (size_t)k * 2 * N, sizeof(int64_t) * 2 * N, cudaMemcpyDeviceToDevice,
                          h->stream));
   ACK(h, cudaMemcpyAsync(h->phi, a->ck_phi + (size_t)k * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
-  ACK(h, cudaMemcpyAsync(h->pw.phi_prev, a->ck_prev + (size_t)k * N, sizeof(double) * N, cudaMemcpyDeviceToDevice,
-                         h->stream));
-  h->pw.have_history = a->ck_hist[k] != 0;
+  ACK(h, cudaMemcpyAsync(h->pw.phi_prev, a->ck_prev + (size_t)k * 2 * N, sizeof(double) * 2 * N,
+                         cudaMemcpyDeviceToDevice, h->stream));
+  h->pw.history = a->ck_hist[k];
   ACK(h, launch_phi32_sync(h));
   return LBE_OK;
 }

@@ -155,7 +155,7 @@ struct lbe_batch {
   uint32_t *mask = nullptr;
   float *f[2] = {nullptr, nullptr};
   int64_t *q = nullptr, *qstar = nullptr;
-  double *phi = nullptr, *phi_prev = nullptr;
+  double *phi = nullptr, *phi_prev = nullptr;  // phi_prev [2][Ntot]: the previous two solutions
   float *phi32 = nullptr, *u = nullptr;
   float *phi_lo = nullptr;  // phi = phi32 + phi_lo to ~2^-48 (float-float residual)
   float *vec = nullptr;     // CG vectors [6][Ntot]
@@ -165,7 +165,7 @@ struct lbe_batch {
   lbe::BatchCtl *bctl = nullptr, *bctl_h = nullptr;
   double *qpart = nullptr, *qout = nullptr, *qhost = nullptr;
   int *flag = nullptr;
-  int *hist = nullptr;  // device: phi_prev holds the previous solution
+  int *hist = nullptr;  // device: how many solutions phi_prev holds (0..2)
   // tile lists of active instances: family f counts, prefix sums
   int nfam = 0;
   int *fam_cnt = nullptr;   // [nfam][n]
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(kBlock) kb_init(const InstDev *__restrict__ in
       phi[r] = p;
       phi32[r] = (float)p;
       phi_lo[r] = (float)(p - (double)(float)p);
-      phi_prev[r] = p;
+      phi_prev[r] = phi_prev[Ntot + r] = p;
       u[r] = u[Ntot + r] = u[2 * Ntot + r] = 0.f;
     }
   }
@@ -405,10 +405,12 @@ __global__ void __launch_bounds__(kBlock) kb_advect(const InstDev *__restrict__ 
   }
 }
 
-// warm start phi <- 2 phi(t) - phi(t-1) on fluid nodes (all instances), once
-// the previous solution is there (*hist); the FP32 copy follows
+// warm start on fluid nodes (all instances) from the *hist previous
+// solutions: phi <- 3 phi(t) - 3 phi(t-1) + phi(t-2) with two of them,
+// 2 phi(t) - phi(t-1) with one; the FP32 copies follow, and the history
+// shifts: prev = [phi(t), phi(t-1)]
 __global__ void kb_extrapolate(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst, int T,
-                               const uint32_t *__restrict__ mask, double *__restrict__ phi,
+                               int Ntot, const uint32_t *__restrict__ mask, double *__restrict__ phi,
                                double *__restrict__ prev, float *__restrict__ phi32, float *__restrict__ phi_lo,
                                const int *__restrict__ hist) {
   const int have = *hist;
@@ -419,13 +421,14 @@ __global__ void kb_extrapolate(const InstDev *__restrict__ inst, const int *__re
       if (lo >= I.g.N) break;
       const int r = I.off + lo;
       if (!(mask[r] & kFluidBit)) continue;
-      const double v = phi[r];
+      const double v = phi[r], p1 = prev[r];
       if (have) {
-        const double e = 2.0 * v - prev[r];
+        const double e = have > 1 ? prev[Ntot + r] + 3.0 * (v - p1) : 2.0 * v - p1;
         phi[r] = e;
         phi32[r] = (float)e;
         phi_lo[r] = (float)(e - (double)(float)e);
       }
+      prev[Ntot + r] = p1;
       prev[r] = v;
     }
   }
@@ -434,7 +437,7 @@ __global__ void kb_extrapolate(const InstDev *__restrict__ inst, const int *__re
 // --- batched Poisson ---------------------------------------------------------
 __global__ void kb_solve_reset(int n, InstCtl *c, BatchCtl *b, int *hist, int set_hist) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0 && set_hist) *hist = 1;
+  if (i == 0 && set_hist && *hist < 2) *hist += 1;
   if (i < n) {
     if (c[i].status && !b->sticky_status) b->sticky_status = c[i].status;
     atomicMax((unsigned long long *)&b->max_iters, (unsigned long long)c[i].iters);
@@ -1268,7 +1271,7 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   void *a_sw[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.fin, &A.fout, &A.qin, &A.qmid, &A.phi32, &A.u,
                   &A.flag};
   void *a_adv[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.qmid, &A.u, &A.qin};
-  void *a_ext[] = {&A.inst, &A.tile_inst, &A.T, &A.mask, &A.phi, &A.phi_prev, &A.phi32, &A.phi_lo, &A.hist};
+  void *a_ext[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.phi, &A.phi_prev, &A.phi32, &A.phi_lo, &A.hist};
   void *a_reset[] = {&A.n, &A.c, &A.bc, &A.hist, &A.set_hist};
   void *a_res[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.qsolve, &A.phi32, &A.phi_lo, &A.v, &A.part, &A.c};
   // the test before the round loop must not touch the inner loop's
@@ -1343,8 +1346,8 @@ int run_polled(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *
     BCK(b, rec(1));
     if (b->flow) kb_advect<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, qmid, A.u, qin);
     BCK(b, rec(2));
-    kb_extrapolate<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.mask, A.phi, A.phi_prev, A.phi32, A.phi_lo,
-                                         A.hist);
+    kb_extrapolate<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, A.phi, A.phi_prev, A.phi32,
+                                         A.phi_lo, A.hist);
     nl += b->flow ? 3 : 2;
   }
   kb_solve_reset<<<(n + 255) / 256, 256, 0, st>>>(n, A.c, A.bc, A.hist, A.set_hist);
@@ -1628,7 +1631,7 @@ int lbe_batch_create(const lbe_params *params, int n, void *cuda_stream, lbe_bat
   alloc((void **)&b->q, 8 * N * 2);
   alloc((void **)&b->qstar, 8 * N * 2);
   alloc((void **)&b->phi, 8 * N);
-  alloc((void **)&b->phi_prev, 8 * N);
+  alloc((void **)&b->phi_prev, 8 * 2 * N);
   alloc((void **)&b->phi32, 4 * N);
   alloc((void **)&b->phi_lo, 4 * N);
   alloc((void **)&b->u, 4 * N * 3);

@@ -476,7 +476,7 @@ int lbe_set_state(lbe_handle *h, const double *n, const double *phi, int on_devi
     if (tmp) cudaFree(tmp);
     LBE_CK(h, e);
   }
-  h->pw.have_history = false;  // no warm-start extrapolation across a state change
+  h->pw.history = 0;  // no warm-start extrapolation across a state change
   if (phi) {
     LBE_CK(h, cudaMemcpyAsync(h->phi, phi, sizeof(double) * N, kind, h->stream));
     LBE_CK(h, lbe::launch_set_solid_phi(h));
@@ -487,14 +487,15 @@ int lbe_set_state(lbe_handle *h, const double *n, const double *phi, int on_devi
 }
 
 // blob: header | populations (19N) | solute (ns N) | phi (N doubles) |
-// velocity (3N) | previous-step phi (N doubles, warm start of the next
-// solve); populations, solute and velocity in the form's own types
+// velocity (3N) | phi of the previous two steps (2N doubles, warm start of
+// the next solve; header.history of them valid); populations, solute and
+// velocity in the form's own types
 struct BlobHeader {
   uint64_t magic;
   int64_t N;
   int32_t ns, flow, precision, history;
 };
-static const uint64_t kMagic = 0x4c42457374763034ULL;
+static const uint64_t kMagic = 0x4c42457374763035ULL;
 
 static void blob_sizes(const lbe_handle *h, size_t *fb, size_t *nb, size_t *pb, size_t *ub) {
   const size_t N = (size_t)h->geo.N;
@@ -502,7 +503,7 @@ static void blob_sizes(const lbe_handle *h, size_t *fb, size_t *nb, size_t *pb, 
   *fb = N * lbe::kQ * (f32 ? sizeof(float) : sizeof(double));
   *nb = N * h->prm.nspecies * (f32 ? sizeof(int64_t) : sizeof(double));
   *pb = N * sizeof(double);
-  *ub = N * 3 * (f32 ? sizeof(float) : sizeof(double)) + N * sizeof(double);
+  *ub = N * 3 * (f32 ? sizeof(float) : sizeof(double)) + 2 * N * sizeof(double);
 }
 
 int lbe_save_state(lbe_handle *h, void *blob, size_t *size) {
@@ -518,7 +519,7 @@ int lbe_save_state(lbe_handle *h, void *blob, size_t *size) {
   if (*size < need) return fail(h, LBE_ERR_ARG, "save_state: blob too small");
   StreamGuard sg{h, h->owns_stream};
   const bool f32 = fp32(h);
-  BlobHeader hd{kMagic, h->geo.N, h->prm.nspecies, h->prm.flow, h->prm.precision, h->pw.have_history ? 1 : 0};
+  BlobHeader hd{kMagic, h->geo.N, h->prm.nspecies, h->prm.flow, h->prm.precision, h->pw.history};
   char *p = (char *)blob;
   memcpy(p, &hd, sizeof(hd));
   p += sizeof(hd);
@@ -529,10 +530,10 @@ int lbe_save_state(lbe_handle *h, void *blob, size_t *size) {
   p += nb;
   LBE_CK(h, cudaMemcpyAsync(p, h->phi, pb, cudaMemcpyDeviceToHost, h->stream));
   p += pb;
-  const size_t vb = ub - (size_t)h->geo.N * sizeof(double);
+  const size_t vb = ub - 2 * (size_t)h->geo.N * sizeof(double);
   LBE_CK(h, cudaMemcpyAsync(p, f32 ? (void *)h->u32 : (void *)h->u, vb, cudaMemcpyDeviceToHost, h->stream));
   p += vb;
-  LBE_CK(h, cudaMemcpyAsync(p, h->pw.phi_prev, (size_t)h->geo.N * sizeof(double), cudaMemcpyDeviceToHost,
+  LBE_CK(h, cudaMemcpyAsync(p, h->pw.phi_prev, 2 * (size_t)h->geo.N * sizeof(double), cudaMemcpyDeviceToHost,
                             h->stream));
   LBE_CK(h, cudaStreamSynchronize(h->stream));
   *size = need;
@@ -556,19 +557,19 @@ int lbe_load_state(lbe_handle *h, const void *blob, size_t size) {
   const bool f32 = fp32(h);
   const char *p = (const char *)blob + sizeof(hd);
   h->cur = 0;
-  h->pw.have_history = false;
+  h->pw.history = 0;
   LBE_CK(h, cudaMemcpyAsync(f32 ? (void *)h->f32[0] : (void *)h->f[0], p, fb, cudaMemcpyHostToDevice, h->stream));
   p += fb;
   LBE_CK(h, cudaMemcpyAsync(f32 ? (void *)h->q : (void *)h->n, p, nb, cudaMemcpyHostToDevice, h->stream));
   p += nb;
   LBE_CK(h, cudaMemcpyAsync(h->phi, p, pb, cudaMemcpyHostToDevice, h->stream));
   p += pb;
-  const size_t vb = ub - (size_t)h->geo.N * sizeof(double);
+  const size_t vb = ub - 2 * (size_t)h->geo.N * sizeof(double);
   LBE_CK(h, cudaMemcpyAsync(f32 ? (void *)h->u32 : (void *)h->u, p, vb, cudaMemcpyHostToDevice, h->stream));
   p += vb;
-  LBE_CK(h, cudaMemcpyAsync(h->pw.phi_prev, p, (size_t)h->geo.N * sizeof(double), cudaMemcpyHostToDevice,
+  LBE_CK(h, cudaMemcpyAsync(h->pw.phi_prev, p, 2 * (size_t)h->geo.N * sizeof(double), cudaMemcpyHostToDevice,
                             h->stream));
-  h->pw.have_history = hd.history != 0;
+  h->pw.history = hd.history < 0 ? 0 : (hd.history > 2 ? 2 : hd.history);
   if (f32) LBE_CK(h, lbe::launch_phi32_sync(h));
   LBE_CK(h, cudaStreamSynchronize(h->stream));
   h->initialised = true;

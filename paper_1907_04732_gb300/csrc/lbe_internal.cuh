@@ -202,8 +202,8 @@ struct PoissonWork {
   cudaGraphExec_t exec_lin = nullptr;  // linear solve A x = rhs (adjoint)
   const void *lin_key[2] = {nullptr, nullptr};
   bool graph_ok = false;
-  double *phi_prev = nullptr;  // phi of the previous step (warm start)
-  bool have_history = false;
+  double *phi_prev = nullptr;  // [2][N]: phi of the previous two steps (warm start)
+  int history = 0;             // how many of them hold a solution (0..2)
 };
 constexpr int kMaxPartials = 2048;
 

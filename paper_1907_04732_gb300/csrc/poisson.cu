@@ -374,19 +374,23 @@ __global__ void __launch_bounds__(kBlock) k_cg_a(const Geo g, int zpt, uint32_t 
   if (flat_tid() == 0) part[S_MAX * nblk + flat_bid()] = (double)v;
 }
 
-// warm start of a step's solve: phi <- 2 phi(t) - phi(t-1) on fluid nodes
-// (linear extrapolation in time; the converged potential does not depend on
-// the starting guess), and remember phi(t)
+// warm start of a step's solve on fluid nodes: the polynomial in time through
+// the last history + 1 solutions, evaluated one step ahead,
+//   history 2: phi <- 3 phi(t) - 3 phi(t-1) + phi(t-2)
+//   history 1: phi <- 2 phi(t) - phi(t-1)
+// (the converged potential does not depend on the starting guess; the
+// quadratic start is 30-300 times closer to it than the linear one while the
+// capacitor charges), then shift the history: prev = [phi(t), phi(t-1)]
 __global__ void k_extrapolate(const Geo g, const uint32_t *__restrict__ mask, double *__restrict__ phi,
                               double *__restrict__ prev, float *__restrict__ phi32, float *__restrict__ phi_lo,
-                              int have_history) {
+                              int history) {
   int X, Y, Z;
   long long i;
   if (!node_of(g, 1, 0, X, Y, Z, i)) return;
   if (!(mask[i] & kFluidBit)) return;
-  const double v = phi[i];
-  if (have_history) {
-    const double e = 2.0 * v - prev[i];
+  const double v = phi[i], p1 = prev[i];
+  if (history > 0) {
+    const double e = history > 1 ? prev[g.N + i] + 3.0 * (v - p1) : 2.0 * v - p1;
     phi[i] = e;
     if (phi32) {  // the FP32 copies follow: the solve may stop at once
       const float hi = (float)e;
@@ -394,6 +398,7 @@ __global__ void k_extrapolate(const Geo g, const uint32_t *__restrict__ mask, do
       if (phi_lo) phi_lo[i] = (float)(e - (double)hi);
     }
   }
+  prev[g.N + i] = p1;
   prev[i] = v;
 }
 
@@ -657,7 +662,7 @@ cudaError_t poisson_alloc(lbe_handle *h) {
   cudaError_t e;
   if ((e = cudaMalloc(&w.vec, tsz * 6 * N)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&w.partial, sizeof(double) * 3 * w.L.nblk())) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&w.phi_prev, sizeof(double) * N)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.phi_prev, sizeof(double) * 2 * N)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&w.ctl, sizeof(PoissonCtl))) != cudaSuccess) return e;
   if ((e = cudaMemset(w.ctl, 0, sizeof(PoissonCtl))) != cudaSuccess) return e;
   if ((e = cudaMallocHost(&w.ctl_host, sizeof(PoissonCtl))) != cudaSuccess) return e;
@@ -736,11 +741,11 @@ int poisson_enqueue(lbe_handle *h, bool extrapolate) {
     k_extrapolate<<<L1.grid, L1.block, 0, h->stream>>>(h->geo, h->mask, h->phi, w.phi_prev,
                                                        h->prm.precision == LBE_FP32 ? h->phi32 : nullptr,
                                                        h->prm.precision == LBE_FP32 ? h->phi_lo : nullptr,
-                                                       w.have_history ? 1 : 0);
+                                                       w.history);
     h->launches += 1;
-    w.have_history = true;
+    if (w.history < 2) w.history += 1;
   } else {
-    w.have_history = false;
+    w.history = 0;
   }
   return h->prm.precision == LBE_FP32 ? solve_t<float>(h) : solve_t<double>(h);
 }
