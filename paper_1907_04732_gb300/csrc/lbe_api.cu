@@ -332,14 +332,26 @@ int lbe_init(lbe_handle *h) {
   return rc;
 }
 
-static int check_flags(lbe_handle *h) {
+// the FP32 form's range flag: copy_flag enqueues its read-back, flag_result
+// evaluates it once the stream has been synchronised
+static int copy_flag(lbe_handle *h) {
+  if (!fp32(h)) return LBE_OK;
+  LBE_CK(h, cudaMemcpyAsync(h->qhost, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  return LBE_OK;
+}
+static int flag_result(lbe_handle *h) {
   if (!fp32(h)) return LBE_OK;
   int flag = 0;
-  LBE_CK(h, cudaMemcpyAsync(h->qhost, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  LBE_CK(h, cudaStreamSynchronize(h->stream));
   memcpy(&flag, h->qhost, sizeof(int));
   if (flag) return fail(h, LBE_ERR_NONFINITE, "fixed-point solute range exceeded (|link flux| or |n| too large)");
   return LBE_OK;
+}
+static int check_flags(lbe_handle *h) {
+  if (!fp32(h)) return LBE_OK;
+  const int rc = copy_flag(h);
+  if (rc != LBE_OK) return rc;
+  LBE_CK(h, cudaStreamSynchronize(h->stream));
+  return flag_result(h);
 }
 
 int lbe_step(lbe_handle *h, int nsteps) {
@@ -374,7 +386,10 @@ int lbe_step(lbe_handle *h, int nsteps) {
     if (rc != LBE_OK) return rc;
   }
   // the solves ran without host synchronisation; their status and counts
-  // are read once here (a failed solve is reported at the end of the call)
+  // are read once here, with the range flag, under one synchronisation (a
+  // failed solve is reported at the end of the call)
+  const int frc = copy_flag(h);
+  if (frc != LBE_OK) return frc;
   long long graph_kernels = 0;
   int rc = lbe::poisson_status(h, &h->stats, &graph_kernels);
   h->launches += graph_kernels;
@@ -384,7 +399,7 @@ int lbe_step(lbe_handle *h, int nsteps) {
     h->prof_steps += nsteps;
   }
   if (rc != LBE_OK) return rc;
-  return check_flags(h);
+  return flag_result(h);
 }
 
 int lbe_induced_charge(lbe_handle *h, double *q_out, int out_on_device) {
