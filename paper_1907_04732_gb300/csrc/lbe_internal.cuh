@@ -221,6 +221,7 @@ struct MGWork {
   MGLevel lv[kMaxLevels];
   int nlev = 0;        // 0: no hierarchy (Jacobi preconditioning)
   float *t0 = nullptr;  // fine-level scratch
+  float *cinv = nullptr;  // inverse of the coarsest operator [N][N] (null: Jacobi sweeps)
 };
 
 struct AdjWork;  // adjoint.cu
