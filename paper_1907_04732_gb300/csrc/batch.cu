@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "fp32_device.cuh"
@@ -179,6 +180,8 @@ struct lbe_batch {
   lbe::LvSeg *mg_seg = nullptr;          // [kMaxLevels][n]
   lbe::LvPtrs mg_p{};
   float *mg_t0 = nullptr;
+  float *mg_cinv = nullptr;          // inverses of the coarsest operators, concatenated
+  long long *mg_cinv_off = nullptr;  // device [n]: an instance's inverse (-1: Jacobi sweeps)
   // step graphs keyed by (populations read, solute read); [4] = solve only;
   // [5..8] step graphs with profiling events
   cudaGraphExec_t exec[9] = {};
@@ -856,15 +859,34 @@ __global__ void __launch_bounds__(kBlock) kbm_restrict(int n, const int *__restr
   }
 }
 
-// every instance's coarsest level, one block each
+// every instance's coarsest level, one block each: exactly, through the
+// inverse formed at set-up (one warp per row, a fixed summation order), or
+// by Jacobi sweeps where its operator is not positive definite
 __global__ void __launch_bounds__(mgd::kCoarseMax) kbm_coarsest(const InstDev *__restrict__ inst, int n,
                                                                 const LvSeg *__restrict__ seg, const LvPtrs P,
-                                                                const InstCtl *__restrict__ c) {
+                                                                const InstCtl *__restrict__ c,
+                                                                const float *__restrict__ cinv,
+                                                                const long long *__restrict__ cinv_off) {
   const int ii = blockIdx.x;
   const int nl = inst[ii].mg_levels;
   if (nl < 2 || c[ii].inner_done) return;
   __shared__ float buf[2][mgd::kCoarseMax];
   const LvSeg S = seg[(nl - 1) * n + ii];
+  const long long off = cinv_off[ii];
+  if (off >= 0) {
+    const int N = S.L.N, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const float *r = P.r[nl - 1] + S.off;
+    float *e = P.e[nl - 1] + S.off;
+    for (int row = threadIdx.x >> 5; row < N; row += nw) {
+      const float *a = cinv + off + (long long)row * N;
+      float s = 0.f;
+      for (int j = lane; j < N; j += 32) s = fmaf(a[j], r[j], s);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) e[row] = s;
+    }
+    return;
+  }
   mgd::coarsest_solve(S.L, P.A[nl - 1] + S.off, P.r[nl - 1] + S.off, P.e[nl - 1] + S.off, buf);
 }
 
@@ -962,6 +984,8 @@ void mg_release(lbe_batch *b) {
   cudaFree(b->mg_tiles);
   cudaFree(b->mg_seg);
   cudaFree(b->mg_t0);
+  cudaFree(b->mg_cinv);
+  cudaFree(b->mg_cinv_off);
   cudaFree(b->fam_cnt);
   cudaFree(b->fam_pref);
   for (int l = 0; l < lbe::kMaxLevels; ++l) {
@@ -973,6 +997,8 @@ void mg_release(lbe_batch *b) {
   b->mg_tiles = nullptr;
   b->mg_seg = nullptr;
   b->mg_t0 = nullptr;
+  b->mg_cinv = nullptr;
+  b->mg_cinv_off = nullptr;
   b->fam_cnt = b->fam_pref = nullptr;
   b->mg_p = lbe::LvPtrs{};
   b->mg_nlev = 0;
@@ -1037,6 +1063,68 @@ int fam_levels(const lbe_batch *b) { return b->mg_nlev >= 2 ? b->mg_nlev : 1; }
 
 // Multigrid hierarchy of every instance (after the link masks): level shapes
 // per instance, the levels' concatenated arrays and tile lists, the active-
+// Exact coarsest solves: each instance's coarsest operator comes back to the
+// host, is inverted there (mgd::coarse_inverse, FP64 Cholesky; instances in
+// parallel threads) and the inverses go to the device concatenated.  An
+// instance whose operator is not positive definite keeps the Jacobi sweeps
+// (offset -1), as does every instance with LBE_MG_DIRECT=0.
+int coarse_inverses(lbe_batch *b, const std::vector<lbe::LvSeg> &seg) {
+  using namespace lbe;
+  const int n = b->n, L = b->mg_nlev;
+  std::vector<long long> off(n, -1);
+  const char *denv = getenv("LBE_MG_DIRECT");
+  const bool direct = !(denv && denv[0] == '0');
+  std::vector<std::vector<float>> inv(n);
+  if (direct) {
+    std::vector<std::vector<float>> Ah(L);
+    for (int i = 0; i < n; ++i) {
+      const int l = b->inst[i].mg_levels - 1;
+      if (l >= 1 && Ah[l].empty()) {
+        Ah[l].resize((size_t)27 * b->mg_M[l]);
+        BCK(b, cudaMemcpyAsync(Ah[l].data(), b->mg_p.A[l], sizeof(float) * Ah[l].size(), cudaMemcpyDeviceToHost,
+                               b->stream));
+      }
+    }
+    BCK(b, cudaStreamSynchronize(b->stream));
+    std::vector<char> ok(n, 0);
+    auto work = [&](int t, int nt) {
+      for (int i = t; i < n; i += nt) {
+        const int l = b->inst[i].mg_levels - 1;
+        if (l < 1) continue;
+        const LvSeg &S = seg[(size_t)l * n + i];
+        mgd::MgLevel Lc = S.L;
+        Lc.S = Lc.N;
+        std::vector<float> a27((size_t)27 * Lc.N);
+        for (int q = 0; q < 27; ++q)
+          for (int I = 0; I < Lc.N; ++I) a27[(size_t)q * Lc.N + I] = Ah[l][(size_t)q * S.L.S + S.off + I];
+        ok[i] = mgd::coarse_inverse(Lc, a27, inv[i]) ? 1 : 0;
+      }
+    };
+    const int nt = std::max(1, std::min<int>(n, (int)std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(work, t, nt);
+    work(0, nt);
+    for (auto &t : th) t.join();
+    long long tot = 0;
+    for (int i = 0; i < n; ++i)
+      if (ok[i]) {
+        off[i] = tot;
+        tot += (long long)inv[i].size();
+      }
+    if (tot > 0) {
+      BCK(b, cudaMalloc(&b->mg_cinv, sizeof(float) * tot));
+      for (int i = 0; i < n; ++i)
+        if (ok[i])
+          BCK(b, cudaMemcpyAsync(b->mg_cinv + off[i], inv[i].data(), sizeof(float) * inv[i].size(),
+                                 cudaMemcpyHostToDevice, b->stream));
+    }
+  }
+  BCK(b, cudaMalloc(&b->mg_cinv_off, sizeof(long long) * n));
+  BCK(b, cudaMemcpyAsync(b->mg_cinv_off, off.data(), sizeof(long long) * n, cudaMemcpyHostToDevice, b->stream));
+  BCK(b, cudaStreamSynchronize(b->stream));  // the host buffers are released on return
+  return LBE_OK;
+}
+
 // tile families, then the inverse fine diagonal and the Galerkin operators on
 // the GPU.  Uploads the instance table (it carries each instance's level
 // count).
@@ -1120,7 +1208,7 @@ int mg_setup(lbe_batch *b) {
         b->mg_tiles + b->mg_tbase[l + 1], b->mg_T[l + 1], b->mg_seg + (size_t)l * n, b->mg_seg + (size_t)(l + 1) * n,
         b->mg_p.A[l], b->mg_p.A[l + 1]);
   BCK(b, cudaGetLastError());
-  return LBE_OK;
+  return coarse_inverses(b, seg);
 }
 
 // u = M r (one V-cycle over every active instance with a hierarchy) as graph
@@ -1159,7 +1247,9 @@ cudaError_t add_vcycle(lbe_batch *b, cudaGraph_t gr, cudaGraphNode_t *last) {
     if (e != cudaSuccess) return e;
   }
   {
-    void *a[] = {&inst, &n, &seg_all, &P, &c};
+    const float *cinv = b->mg_cinv;
+    const long long *cinv_off = b->mg_cinv_off;
+    void *a[] = {&inst, &n, &seg_all, &P, &c, &cinv, &cinv_off};
     e = add_node(gr, last, (void *)kbm_coarsest, dim3(n), dim3(mgd::kCoarseMax), a);
     if (e != cudaSuccess) return e;
   }

@@ -192,6 +192,10 @@ dim3 lgrid(const MgLevel &L, dim3 &block) {
 
 MgLevel level_dev(const MGLevel &L) { return MgLevel{L.nx, L.ny, L.nz, L.sx, L.sy, L.sz, (int)L.N, L.N}; }
 
+
+}  // namespace
+
+// build the hierarchy for the current geometry (after the link mask)
 // Inverse of the coarsest level's operator from its 27-point rows (host,
 // FP64): the operator restricted to the nodes with a non-zero diagonal
 // (aggregates holding fluid) is assembled densely, factored A = L L^T
@@ -199,7 +203,7 @@ MgLevel level_dev(const MGLevel &L) { return MgLevel{L.nx, L.ny, L.nz, L.sx, L.s
 // as the Jacobi sweeps leave them.  False when the operator is not
 // symmetric positive definite to working accuracy (e.g. a periodic lattice
 // without electrodes, whose operator is singular): the sweeps are used then.
-bool coarse_inverse(const MgLevel &L, const std::vector<float> &A27, std::vector<float> &inv) {
+bool mgd::coarse_inverse(const MgLevel &L, const std::vector<float> &A27, std::vector<float> &inv) {
   const int N = L.N;
   std::vector<int> act;  // active node -> level index
   std::vector<int> pos(N, -1);
@@ -265,9 +269,6 @@ bool coarse_inverse(const MgLevel &L, const std::vector<float> &A27, std::vector
   return true;
 }
 
-}  // namespace
-
-// build the hierarchy for the current geometry (after the link mask)
 cudaError_t mg_setup(lbe_handle *h) {
   MGWork &mg = h->mg;
   mg_free(h);

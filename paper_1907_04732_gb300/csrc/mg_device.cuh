@@ -22,6 +22,8 @@
 // functions is already offset to the lattice's first node of that level.
 #pragma once
 
+#include <vector>
+
 #include "lbe_internal.cuh"
 
 namespace lbe {
@@ -288,6 +290,12 @@ __device__ __forceinline__ float post_value_z(const MgLevel &L, const float *__r
   const float e = fmaf(kAlpha, ec[agg_index(C, X, Y, Z)], z[I]);
   return e + kOmega * (r[I] - s) / d;
 }
+
+// host (mg.cu): inverse of a coarsest level's operator, A27 its 27-point
+// rows [27][L.N]; inv [L.N][L.N] with zero rows and columns for the nodes
+// with a zero diagonal; false when the operator is not symmetric positive
+// definite to working accuracy
+bool coarse_inverse(const MgLevel &L, const std::vector<float> &A27, std::vector<float> &inv);
 
 }  // namespace mgd
 }  // namespace lbe
