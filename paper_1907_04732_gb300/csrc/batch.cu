@@ -354,15 +354,25 @@ __global__ void __launch_bounds__(kBlock) kb_init(const InstDev *__restrict__ in
 }
 
 template <bool FLOW, bool WIDE>
-__global__ void __launch_bounds__(kBlock) kb_sweep(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
+__global__ void __launch_bounds__(kBlock, 4) kb_sweep(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
                                                    int T, int Ntot, const uint32_t *__restrict__ mask,
                                                    const float *__restrict__ fin, float *__restrict__ fout,
                                                    const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
                                                    const float *__restrict__ phi, float *__restrict__ u,
                                                    int *__restrict__ flag) {
+  // the tile's instance constants are staged in shared memory: the link loop
+  // reads them for every link (shared loads instead of global ones)
+  __shared__ InstDev sI;
   bool over = false;
-  for (int t = blockIdx.x; t < T; t += gridDim.x) {
-    const InstDev &I = inst[tile_inst[t]];
+  for (int t = blockIdx.x; t < T; t += gridDim.x) {  // the same t for the whole block
+    __syncthreads();  // the previous tile's readers are done
+    {
+      const int *src = reinterpret_cast<const int *>(inst + tile_inst[t]);
+      int *dst = reinterpret_cast<int *>(&sI);
+      for (int w = threadIdx.x; w < (int)(sizeof(InstDev) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+    }
+    __syncthreads();
+    const InstDev &I = sI;
     for (int k = 0; k < kSub; ++k) {
       int x, y, z;
       const int lo = (t - I.tile0) * kTile + k * kBlock + threadIdx.x;

@@ -162,7 +162,10 @@ __device__ __forceinline__ void sweep_node(const P32 &P, int N, int r, const Off
   }
   float F[3];
   ion_links<true, SALT11>(P, N, r, o, m, q, phi, q0, q0f, dq, F, over);
-  for (int k = 0; k < (SALT11 ? 2 : P.ns); ++k) qstar[k * N + r] = q0[k] + dq[k];
+  // compile-time species indices keep q0/dq in registers
+#pragma unroll
+  for (int k = 0; k < (SALT11 ? 2 : LBE_MAX_SPECIES); ++k)
+    if (SALT11 || k < P.ns) qstar[k * N + r] = q0[k] + dq[k];
   if (!FLOW) return;
 
   float f[kQ];
@@ -212,10 +215,13 @@ __device__ __forceinline__ void advect_node(int ns, int N, int r, const Offs &o,
                                             int64_t *__restrict__ qout) {
   const float ux = u[r], uy = u[N + r], uz = u[2 * N + r];
   const long long base = 1LL << kFixBits;
+  // species loops run to the compile-time bound (guarded by ns) so that acc
+  // and totf stay in registers
   long long acc[LBE_MAX_SPECIES];
   float totf[LBE_MAX_SPECIES];
-  for (int k = 0; k < ns; ++k) {
-    acc[k] = base + qin[k * N + r];
+#pragma unroll
+  for (int k = 0; k < LBE_MAX_SPECIES; ++k) {
+    acc[k] = k < ns ? base + qin[k * N + r] : 0;
     totf[k] = ll2f(acc[k]);
   }
   // outgoing (the share is zero outside the octant of u); shares bound for
@@ -225,7 +231,9 @@ __device__ __forceinline__ void advect_node(int ns, int N, int r, const Offs &o,
     const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
     if (d == 13 || !(m & (1u << dir_bit(dx, dy, dz)))) continue;
     if ((dx && dx * ux <= 0.f) || (dy && dy * uy <= 0.f) || (dz && dz * uz <= 0.f)) continue;
-    for (int k = 0; k < ns; ++k) acc[k] -= share(totf[k], ux, uy, uz, dx, dy, dz);
+#pragma unroll
+    for (int k = 0; k < LBE_MAX_SPECIES; ++k)
+      if (k < ns) acc[k] -= share(totf[k], ux, uy, uz, dx, dy, dz);
   }
   // incoming from every fluid neighbour whose cell reaches r: the source at
   // r - s gives along +s
@@ -237,9 +245,13 @@ __device__ __forceinline__ void advect_node(int ns, int N, int r, const Offs &o,
     const float vx = u[s], vy = u[N + s], vz = u[2 * N + s];
     const float w = ov(dx, vx) * ov(dy, vy) * ov(dz, vz);
     if (w == 0.f) continue;
-    for (int k = 0; k < ns; ++k) acc[k] += share(ll2f(base + qin[k * N + s]), vx, vy, vz, dx, dy, dz);
+#pragma unroll
+    for (int k = 0; k < LBE_MAX_SPECIES; ++k)
+      if (k < ns) acc[k] += share(ll2f(base + qin[k * N + s]), vx, vy, vz, dx, dy, dz);
   }
-  for (int k = 0; k < ns; ++k) qout[k * N + r] = acc[k] - base;
+#pragma unroll
+  for (int k = 0; k < LBE_MAX_SPECIES; ++k)
+    if (k < ns) qout[k * N + r] = acc[k] - base;
 }
 
 // Error-free sum (Knuth): s + e = a + b exactly, s = fl(a + b).
