@@ -206,6 +206,15 @@ struct PoissonWork {
   int history = 0;             // how many of them hold a solution (0..2)
 };
 constexpr int kMaxPartials = 2048;
+// Launch size of the solve's lattice kernels: each thread handles zpt nodes
+// along z so that a kernel has at most this many blocks.  On this GPU a
+// dependent kernel costs about 0.6 ns per block to schedule (2.4 us for 4096
+// empty blocks of 256 threads, 0.4 us for one block), which the short
+// kernels of the solve pay dozens of times per step.
+#ifndef LBE_SOLVE_BLOCKS
+#define LBE_SOLVE_BLOCKS 1024
+#endif
+constexpr int kSolveBlocks = LBE_SOLVE_BLOCKS;
 
 // Multigrid hierarchy of the FP32 Poisson preconditioner (mg.cu); level 0 is
 // the lattice itself.

@@ -65,12 +65,17 @@ __global__ void k_galerkin(const MgLevel F, const float *__restrict__ AF, const 
 // Restriction with 8 threads per coarse node (one per child) and a fixed-order
 // shuffle sum of the children's pre-smoothed residuals.  The coarse node's
 // residual rc and its pre-smoothed iterate zc = omega rc/diag are stored.
-__device__ __forceinline__ void coarse_of_thread(const MgLevel &C, int &I, int &X, int &Y, int &Z, int &ch) {
-  const int t = threadIdx.x;
-  I = blockIdx.x * (blockDim.x / 8) + (t >> 3);
-  ch = t & 7;
+// Work item w (8 per coarse node); a block strides over the items in steps of
+// the grid, the same number of steps for all its threads (the shuffle sum).
+__device__ __forceinline__ void coarse_of_item(const MgLevel &C, long long w, int &I, int &X, int &Y, int &Z,
+                                               int &ch) {
+  I = (int)(w >> 3);
+  ch = (int)(w & 7);
   X = Y = Z = 0;
   if (I < C.N) level_coords(C, I, X, Y, Z);
+}
+__device__ __forceinline__ void coarse_of_thread(const MgLevel &C, int &I, int &X, int &Y, int &Z, int &ch) {
+  coarse_of_item(C, (long long)blockIdx.x * blockDim.x + threadIdx.x, I, X, Y, Z, ch);
 }
 
 __device__ __forceinline__ void store_coarse(const MgLevel &C, int I, float v, const float *__restrict__ AC,
@@ -88,19 +93,22 @@ __global__ void __launch_bounds__(256) k_restrict0(const Geo g, uint32_t selfmas
                                                    float *__restrict__ rc, float *__restrict__ zc,
                                                    const PoissonCtl *c) {
   if (c->inner_done) return;
-  int I, X, Y, Z, ch, x, y, z;
-  coarse_of_thread(C, I, X, Y, Z, ch);
-  float v = 0.f;
-  if (I < C.N && child_of(C, X, Y, Z, ch, g.nx, g.ny, g.nz, x, y, z)) {
-    const int i = x + g.nx * (y + g.ny * z);
-    const uint32_t m = mask[i];
-    if (m & kFluidBit) {
-      const float s6 = nbsum6(m, selfmask, offsets_of(g, x, y, z), i, u);
-      v = r[i] - kOmega * ((float)diag6(m, selfmask) * u[i] - s6) * (1.f / 6.f);
+  const long long items = 8LL * C.N, stride = (long long)gridDim.x * blockDim.x;
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w - threadIdx.x < items; w += stride) {
+    int I, X, Y, Z, ch, x, y, z;
+    coarse_of_item(C, w, I, X, Y, Z, ch);
+    float v = 0.f;
+    if (I < C.N && child_of(C, X, Y, Z, ch, g.nx, g.ny, g.nz, x, y, z)) {
+      const int i = x + g.nx * (y + g.ny * z);
+      const uint32_t m = mask[i];
+      if (m & kFluidBit) {
+        const float s6 = nbsum6(m, selfmask, offsets_of(g, x, y, z), i, u);
+        v = r[i] - kOmega * ((float)diag6(m, selfmask) * u[i] - s6) * (1.f / 6.f);
+      }
     }
+    v = sum8(v);
+    if (ch == 0 && I < C.N) store_coarse(C, I, v, AC, rc, zc);
   }
-  v = sum8(v);
-  if (ch == 0 && I < C.N) store_coarse(C, I, v, AC, rc, zc);
 }
 
 __global__ void __launch_bounds__(256) k_restrict(const MgLevel F, const float *__restrict__ AF,
@@ -129,33 +137,38 @@ __global__ void k_post(const MgLevel L, const float *__restrict__ A, const float
 
 // level 0: t = omega u + alpha P e_1 (fluid nodes), then
 // u = t + omega (r - A t)/diag
-__global__ void k_prolong0(const Geo g, const uint32_t *__restrict__ mask, const float *__restrict__ u,
+__global__ void k_prolong0(const Geo g, int zpt, const uint32_t *__restrict__ mask, const float *__restrict__ u,
                            const MgLevel C, const float *__restrict__ ec, float *__restrict__ t,
                            const PoissonCtl *c) {
   if (c->inner_done) return;
-  int x, y, z;
-  long long il;
-  if (!node_of(g, 1, 0, x, y, z, il)) return;
-  const int i = (int)il;
-  t[i] = (mask[i] & kFluidBit) ? fmaf(kAlpha, ec[agg_index(C, x, y, z)], kOmega * u[i]) : 0.f;
+  for (int kz = 0; kz < zpt; ++kz) {
+    int x, y, z;
+    long long il;
+    if (!node_of(g, zpt, kz, x, y, z, il)) continue;
+    const int i = (int)il;
+    t[i] = (mask[i] & kFluidBit) ? fmaf(kAlpha, ec[agg_index(C, x, y, z)], kOmega * u[i]) : 0.f;
+  }
 }
 
-__global__ void k_post0(const Geo g, uint32_t selfmask, const uint32_t *__restrict__ mask, const float *__restrict__ r,
-                        const float *__restrict__ t, float *__restrict__ u, const PoissonCtl *c) {
+__global__ void k_post0(const Geo g, int zpt, uint32_t selfmask, const uint32_t *__restrict__ mask,
+                        const float *__restrict__ r, const float *__restrict__ t, float *__restrict__ u,
+                        const PoissonCtl *c) {
   if (c->inner_done) return;
-  int x, y, z;
-  long long il;
-  if (!node_of(g, 1, 0, x, y, z, il)) return;
-  const int i = (int)il;
-  const uint32_t m = mask[i];
-  if (!(m & kFluidBit)) {
-    u[i] = 0.f;
-    return;
+  for (int kz = 0; kz < zpt; ++kz) {
+    int x, y, z;
+    long long il;
+    if (!node_of(g, zpt, kz, x, y, z, il)) continue;
+    const int i = (int)il;
+    const uint32_t m = mask[i];
+    if (!(m & kFluidBit)) {
+      u[i] = 0.f;
+      continue;
+    }
+    const float d6 = (float)diag6(m, selfmask);
+    const float s6 = nbsum6(m, selfmask, offsets_of(g, x, y, z), i, t);
+    const float ti = t[i];
+    u[i] = ti + kOmega * __fdividef(6.f * r[i] - (d6 * ti - s6), d6);
   }
-  const float d6 = (float)diag6(m, selfmask);
-  const float s6 = nbsum6(m, selfmask, offsets_of(g, x, y, z), i, t);
-  const float ti = t[i];
-  u[i] = ti + kOmega * __fdividef(6.f * r[i] - (d6 * ti - s6), d6);
 }
 
 // coarsest level solved exactly: e = A^-1 r with the inverse formed at
@@ -350,7 +363,9 @@ cudaError_t mg_vcycle(lbe_handle *h, const float *r0, float *u0, const PoissonCt
   MGWork &mg = h->mg;
   const int nl = mg.nlev;
   const Geo g = h->geo;
-  const Launch L0 = make_launch(g);
+  // finest-level kernels: the solve's launch (zpt nodes along z per thread)
+  const Launch L0 = h->pw.L;
+  int zpt0 = L0.zpt;
   const uint32_t sm = h->phys.selfmask;
   // kernel arguments live in these arrays until the nodes are created or the
   // kernels launched
@@ -371,7 +386,8 @@ cudaError_t mg_vcycle(lbe_handle *h, const float *r0, float *u0, const PoissonCt
   const void *pg = &g, *psm = &sm;
   auto cgrid = [](const MgLevel &C) { return dim3((unsigned)((C.N * 8 + 255) / 256)); };
   // down: restrictions (pre-smoothing on the fly)
-  nodes.push_back(Node{(void *)k_restrict0, cgrid(lv[1]), dim3(256),
+  const dim3 g1 = cgrid(lv[1]);
+  nodes.push_back(Node{(void *)k_restrict0, dim3(g1.x < (unsigned)kSolveBlocks ? g1.x : (unsigned)kSolveBlocks), dim3(256),
                        {(void *)pg, (void *)psm, P(h->mask), P(r0), P(u0), &lv[1], P(mg.lv[1].A), P(mg.lv[1].r),
                         P(mg.lv[1].z), P(c)}});
   for (int l = 1; l < nl - 1; ++l)
@@ -396,9 +412,9 @@ cudaError_t mg_vcycle(lbe_handle *h, const float *r0, float *u0, const PoissonCt
   }
   // finest level
   nodes.push_back(Node{(void *)k_prolong0, L0.grid, L0.block,
-                       {(void *)pg, P(h->mask), P(u0), &lv[1], P(mg.lv[1].e), P(mg.t0), P(c)}});
+                       {(void *)pg, &zpt0, P(h->mask), P(u0), &lv[1], P(mg.lv[1].e), P(mg.t0), P(c)}});
   nodes.push_back(Node{(void *)k_post0, L0.grid, L0.block,
-                       {(void *)pg, (void *)psm, P(h->mask), P(r0), P(mg.t0), P(u0), P(c)}});
+                       {(void *)pg, &zpt0, (void *)psm, P(h->mask), P(r0), P(mg.t0), P(u0), P(c)}});
   cudaError_t e = cudaSuccess;
   for (Node &n : nodes) {
     if (gr) {

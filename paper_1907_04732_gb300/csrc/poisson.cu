@@ -381,43 +381,47 @@ __global__ void __launch_bounds__(kBlock) k_cg_a(const Geo g, int zpt, uint32_t 
 // (the converged potential does not depend on the starting guess; the
 // quadratic start is 30-300 times closer to it than the linear one while the
 // capacitor charges), then shift the history: prev = [phi(t), phi(t-1)]
-__global__ void k_extrapolate(const Geo g, const uint32_t *__restrict__ mask, double *__restrict__ phi,
+__global__ void k_extrapolate(const Geo g, int zpt, const uint32_t *__restrict__ mask, double *__restrict__ phi,
                               double *__restrict__ prev, float *__restrict__ phi32, float *__restrict__ phi_lo,
                               int history) {
-  int X, Y, Z;
-  long long i;
-  if (!node_of(g, 1, 0, X, Y, Z, i)) return;
-  if (!(mask[i] & kFluidBit)) return;
-  const double v = phi[i], p1 = prev[i];
-  if (history > 0) {
-    const double e = history > 1 ? prev[g.N + i] + 3.0 * (v - p1) : 2.0 * v - p1;
-    phi[i] = e;
-    if (phi32) {  // the FP32 copies follow: the solve may stop at once
-      const float hi = (float)e;
-      phi32[i] = hi;
-      if (phi_lo) phi_lo[i] = (float)(e - (double)hi);
+  for (int kz = 0; kz < zpt; ++kz) {
+    int X, Y, Z;
+    long long i;
+    if (!node_of(g, zpt, kz, X, Y, Z, i)) continue;
+    if (!(mask[i] & kFluidBit)) continue;
+    const double v = phi[i], p1 = prev[i];
+    if (history > 0) {
+      const double e = history > 1 ? prev[g.N + i] + 3.0 * (v - p1) : 2.0 * v - p1;
+      phi[i] = e;
+      if (phi32) {  // the FP32 copies follow: the solve may stop at once
+        const float hi = (float)e;
+        phi32[i] = hi;
+        if (phi_lo) phi_lo[i] = (float)(e - (double)hi);
+      }
     }
+    prev[g.N + i] = p1;
+    prev[i] = v;
   }
-  prev[g.N + i] = p1;
-  prev[i] = v;
 }
 
 // phi64 += e on fluid nodes; the FP32 form refreshes its FP32 copy
 template <typename T>
-__global__ void k_correct(const Geo g, const uint32_t *__restrict__ mask, const T *__restrict__ e,
+__global__ void k_correct(const Geo g, int zpt, const uint32_t *__restrict__ mask, const T *__restrict__ e,
                           double *__restrict__ phi, float *__restrict__ phi32, float *__restrict__ phi_lo) {
-  int X, Y, Z;
-  long long i;
-  if (!node_of(g, 1, 0, X, Y, Z, i)) return;
-  double v = phi[i];
-  if (e && (mask[i] & kFluidBit)) {
-    v += (double)e[i];
-    phi[i] = v;
-  }
-  if (phi32) {
-    const float hi = (float)v;
-    phi32[i] = hi;
-    if (phi_lo) phi_lo[i] = (float)(v - (double)hi);
+  for (int kz = 0; kz < zpt; ++kz) {
+    int X, Y, Z;
+    long long i;
+    if (!node_of(g, zpt, kz, X, Y, Z, i)) continue;
+    double v = phi[i];
+    if (e && (mask[i] & kFluidBit)) {
+      v += (double)e[i];
+      phi[i] = v;
+    }
+    if (phi32) {
+      const float hi = (float)v;
+      phi32[i] = hi;
+      if (phi_lo) phi_lo[i] = (float)(v - (double)hi);
+    }
   }
 }
 
@@ -514,7 +518,6 @@ void fill_args(lbe_handle *h, Args &A) {
 template <typename T>
 cudaError_t build_graph(lbe_handle *h, Args &A, cudaGraphExec_t *exec) {
   const Launch &L = h->pw.L;
-  const Launch L1 = make_launch(h->geo);
   const dim3 one(1);
   const bool fixed = h->prm.precision == LBE_FP32;
   const bool ff = fixed && sizeof(T) == 4 && h->p32.salt11 && A.phi_lo && !A.rhs;
@@ -541,7 +544,7 @@ cudaError_t build_graph(lbe_handle *h, Args &A, cudaGraphExec_t *exec) {
   void *a_bt[] = {&A.g, &A.zpt, &A.selfmask, &A.mask, &A.u, &A.r, &A.w, &A.part, &A.nblk, &A.c,
                   &A.eta, &A.tol_inner, &A.maxit, &A.mode_iter, &A.hin, &A.use_cond};
   void *a_a[] = {&A.g, &A.zpt, &A.selfmask, &A.mask, &A.x, &A.r, &A.u, &A.w, &A.p, &A.s, &A.part, &A.nblk, &A.c};
-  void *a_cor[] = {&A.g, &A.mask, &A.x, &A.phi, &A.phi32, &A.phi_lo};
+  void *a_cor[] = {&A.g, &A.zpt, &A.mask, &A.x, &A.phi, &A.phi32, &A.phi_lo};
   // reset -> residual test -> while (not converged) { V-cycle -> CG -> correct
   // -> residual test }: a converged test ends the solve without running the
   // rest of a round
@@ -557,7 +560,7 @@ cudaError_t build_graph(lbe_handle *h, Args &A, cudaGraphExec_t *exec) {
   if (e == cudaSuccess) e = add_kernel(body_in, &li, (void *)k_cg_a<T>, L.grid, L.block, a_a);
   if (e == cudaSuccess && mg) e = mg_vcycle(h, (const float *)A.r, (float *)A.u, A.c, body_in, &li, nullptr);
   if (e == cudaSuccess) e = add_kernel(body_in, &li, (void *)k_cg_b<T>, L.grid, L.block, a_bt);
-  if (e == cudaSuccess) e = add_kernel(body_out, &lo, (void *)k_correct<T>, L1.grid, L1.block, a_cor);
+  if (e == cudaSuccess) e = add_kernel(body_out, &lo, (void *)k_correct<T>, L.grid, L.block, a_cor);
   if (e == cudaSuccess) e = add_kernel(body_out, &lo, f_res, L.grid, L.block, a_res);
   if (e == cudaSuccess) e = cudaGraphInstantiate(exec, G, 0);
   cudaGraphDestroy(G);
@@ -569,7 +572,6 @@ template <typename T>
 int solve_polled(lbe_handle *h, Args &A) {
   PoissonWork &w = h->pw;
   const Launch &L = w.L;
-  const Launch L1 = make_launch(h->geo);
   cudaStream_t st = h->stream;
   const bool fixed = h->prm.precision == LBE_FP32;
   A.use_cond = 0;
@@ -608,7 +610,7 @@ int solve_polled(lbe_handle *h, Args &A) {
       }
       h->launches += 2 * kChunk;
     }
-    k_correct<T><<<L1.grid, L1.block, 0, st>>>(A.g, A.mask, (const T *)A.x, A.phi, A.phi32, A.phi_lo);
+    k_correct<T><<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.mask, (const T *)A.x, A.phi, A.phi32, A.phi_lo);
     h->launches += 1;
     if (w.ctl_host->outer_done) break;
   }
@@ -657,7 +659,7 @@ int solve_t(lbe_handle *h) {
 cudaError_t poisson_alloc(lbe_handle *h) {
   PoissonWork &w = h->pw;
   const long long N = h->geo.N;
-  w.L = make_launch(h->geo, kMaxPartials);
+  w.L = make_launch(h->geo, kSolveBlocks);
   const size_t tsz = h->prm.precision == LBE_FP32 ? sizeof(float) : sizeof(double);
   cudaError_t e;
   if ((e = cudaMalloc(&w.vec, tsz * 6 * N)) != cudaSuccess) return e;
@@ -737,8 +739,7 @@ int poisson_solve_linear(lbe_handle *h, const double *rhs, double *x, double tol
 int poisson_enqueue(lbe_handle *h, bool extrapolate) {
   PoissonWork &w = h->pw;
   if (extrapolate) {
-    const Launch L1 = make_launch(h->geo);
-    k_extrapolate<<<L1.grid, L1.block, 0, h->stream>>>(h->geo, h->mask, h->phi, w.phi_prev,
+    k_extrapolate<<<w.L.grid, w.L.block, 0, h->stream>>>(h->geo, w.L.zpt, h->mask, h->phi, w.phi_prev,
                                                        h->prm.precision == LBE_FP32 ? h->phi32 : nullptr,
                                                        h->prm.precision == LBE_FP32 ? h->phi_lo : nullptr,
                                                        w.history);
@@ -789,7 +790,7 @@ cudaError_t poisson_reset_stats(lbe_handle *h) { return cudaMemsetAsync(h->pw.ct
 
 cudaError_t launch_phi32_sync(lbe_handle *h) {
   const Launch L = make_launch(h->geo);
-  k_correct<float><<<L.grid, L.block, 0, h->stream>>>(h->geo, h->mask, nullptr, h->phi, h->phi32, h->phi_lo);
+  k_correct<float><<<L.grid, L.block, 0, h->stream>>>(h->geo, 1, h->mask, nullptr, h->phi, h->phi32, h->phi_lo);
   return cudaGetLastError();
 }
 
