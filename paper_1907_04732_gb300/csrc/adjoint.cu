@@ -52,6 +52,7 @@ struct AdjWork {
   float *phibar = nullptr;
   double *mu = nullptr, *rhs = nullptr, *chibar = nullptr;
   double *mu_prev = nullptr;  // mu of the previous solve (warm start by extrapolation)
+  float *mu_hi = nullptr, *mu_lo = nullptr;  // mu as two floats (float-float residual)
   int nsolved = 0;            // solves since the seed
   double *part = nullptr, *acc = nullptr;  // [kAdjSlots][nblk], [kAdjSlots]
   double q[LBE_MAX_ELECTRODES] = {};
@@ -374,6 +375,8 @@ int adj_alloc(lbe_handle *h, int T, int every) {
     alloc((void **)&a->phibar, sizeof(float) * N);
     alloc((void **)&a->mu, sizeof(double) * N);
     alloc((void **)&a->mu_prev, sizeof(double) * N);
+    alloc((void **)&a->mu_hi, sizeof(float) * N);
+    alloc((void **)&a->mu_lo, sizeof(float) * N);
     alloc((void **)&a->rhs, sizeof(double) * N);
     alloc((void **)&a->chibar, sizeof(double) * N);
     alloc((void **)&a->part, sizeof(double) * kAdjSlots * a->nblk);
@@ -424,8 +427,9 @@ int adj_poisson(lbe_handle *h, const float *phi_t, const Weights &psi, int soft)
     k_adj_extrapolate<<<nb, kBlock, 0, h->stream>>>(g.N, h->mask, a->mu, a->mu_prev, a->nsolved > 1 ? 1 : 0);
   a->nsolved += 1;
   ACK(h, cudaGetLastError());
-  // relative 1e-7: below the FP32 resolution of the ion adjoint it feeds
-  const int rc = poisson_solve_linear(h, a->rhs, a->mu, 1e-30, 1e-7);
+  // relative 1e-7: below the FP32 resolution of the ion adjoint it feeds;
+  // the right-hand side -phibar holds floats: float-float residual
+  const int rc = poisson_solve_linear(h, a->rhs, a->mu, 1e-30, 1e-7, a->mu_hi, a->mu_lo);
   if (rc != LBE_OK) return rc;
   k_adj_post<<<nb, kBlock, 0, h->stream>>>(g, h->phys, h->mask, h->id, phi_t, a->phibar, a->mu, psi, soft, a->lam,
                                            a->chibar, a->part, nb);
@@ -451,7 +455,7 @@ void adjoint_free(lbe_handle *h) {
   if (!a) return;
   for (cudaEvent_t e : a->ev) cudaEventDestroy(e);
   void *ptrs[] = {a->ck_q, a->ck_phi, a->ck_prev, a->st_q, a->st_phi, a->lam, a->lam2, a->phibar,
-                  a->mu,   a->rhs,    a->chibar,  a->part, a->acc, a->mu_prev};
+                  a->mu,   a->rhs,    a->chibar,  a->part, a->acc, a->mu_prev, a->mu_hi, a->mu_lo};
   for (void *p : ptrs) cudaFree(p);
   delete a;
   h->adj = nullptr;

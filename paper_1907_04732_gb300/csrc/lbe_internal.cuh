@@ -200,7 +200,7 @@ struct PoissonWork {
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   const void *exec_key[2] = {nullptr, nullptr};
   cudaGraphExec_t exec_lin = nullptr;  // linear solve A x = rhs (adjoint)
-  const void *lin_key[2] = {nullptr, nullptr};
+  const void *lin_key[3] = {nullptr, nullptr, nullptr};
   bool graph_ok = false;
   double *phi_prev = nullptr;  // [2][N]: phi of the previous two steps (warm start)
   int history = 0;             // how many of them hold a solution (0..2)
@@ -326,7 +326,11 @@ int poisson_status(lbe_handle *h, lbe_stats *st, long long *kernels);
 // FP64 residual from x, stopping when max |res|/diag <= max(tol_abs,
 // tol_rel * max |rhs|/diag).  x (FP64, N) is the warm start on entry and
 // must hold 0 on solid nodes; rhs (FP64, N) is read on fluid nodes.
-int poisson_solve_linear(lbe_handle *h, const double *rhs, double *x, double tol_abs, double tol_rel);
+// A x = rhs to max(tol_abs, tol_rel max|rhs|/diag) from the given x; with
+// x_hi/x_lo (scratch, N floats each) the residual is evaluated in
+// float-float arithmetic, which needs every rhs value to be a float
+int poisson_solve_linear(lbe_handle *h, const double *rhs, double *x, double tol_abs, double tol_rel,
+                         float *x_hi = nullptr, float *x_lo = nullptr);
 cudaError_t poisson_reset_stats(lbe_handle *h);
 void poisson_drop_graphs(lbe_handle *h);
 // lbe_api.cu: message returned by lbe_last_error(NULL) (thread-local)

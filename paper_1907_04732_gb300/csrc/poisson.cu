@@ -210,8 +210,10 @@ __global__ void k_solve_reset(PoissonCtl *c) {
 // r = (T)res, u = r/diag, x = p = s = 0.  Partial max |res|/diag.
 // MODE: 0 charge density from FP64 n, 1 from fixed-point q, 2 a given rhs
 // (linear solve A x = rhs; its relative test also needs max |rhs|/diag,
-// kept in the otherwise idle (r,u) partial slots).
-enum { R_N64 = 0, R_FIXED = 1, R_RHS = 2, R_FF = 3 };  // R_FF: R_FIXED, 1:1 salt, float-float residual
+// kept in the otherwise idle (r,u) partial slots), 3 = 1 for a 1:1 salt in
+// float-float arithmetic, 4 = 2 in float-float arithmetic (rhs values that
+// are floats, x also held as two floats).
+enum { R_N64 = 0, R_FIXED = 1, R_RHS = 2, R_FF = 3, R_RHS_FF = 4 };
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys P, const P32 P3,
                                                 const uint32_t *__restrict__ mask, const double *__restrict__ n64,
@@ -224,6 +226,7 @@ __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys
                                                 PoissonCtl *c, double tol, double tol_rel, int maxit,
                                                 cudaGraphConditionalHandle hout, cudaGraphConditionalHandle hin,
                                                 int use_cond, int set_hin) {
+  constexpr bool RHS = MODE == R_RHS || MODE == R_RHS_FF;
   float mx = 0.f, mb = 0.f;
   for (int kz = 0; kz < zpt; ++kz) {
     int X, Y, Z;
@@ -253,6 +256,23 @@ __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys
       mx = fmaxf(mx, fabsf(rt) * dinv);
       continue;
     }
+    if (MODE == R_RHS_FF) {
+      // 6 res = 6 rhs + 6 lap(x), x = hi + lo, in float-float; rhs is a float
+      float S, E;
+      fp32::lap6_ff(g, (int)i, X, Y, Z, m, phi_hi, phi_lo, S, E);
+      const float bf = (float)rhs[i];
+      const float B = 6.f * bf, Be = fmaf(6.f, bf, -B);  // 6 rhs = B + Be exactly
+      float t, te;
+      fp32::two_sum(S, B, t, te);
+      const float rt = (t + (te + (E + Be))) * (1.f / 6.f);
+      const float dinv = 1.f / diag_t<float>(m, P.selfmask);
+      r[i] = (T)rt;
+      u[i] = (T)(rt * dinv);
+      x[i] = p[i] = s[i] = (T)0;
+      mx = fmaxf(mx, fabsf(rt) * dinv);
+      mb = fmaxf(mb, fabsf(bf) * dinv);
+      continue;
+    }
     double b;
     if (MODE == R_RHS) {
       b = rhs[i];
@@ -276,7 +296,7 @@ __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys
   }
   mx = block_reduce<true, float>(mx);
   if (flat_tid() == 0) part[S_MAX * nblk + flat_bid()] = (double)mx;
-  if (MODE == R_RHS) {
+  if (RHS) {
     mb = block_reduce<true, float>(mb);
     if (flat_tid() == 0) part[S_RU * nblk + flat_bid()] = (double)mb;
   }
@@ -284,14 +304,14 @@ __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys
   double m = 0.0, ref = 0.0;
   for (int i = flat_tid(); i < nblk; i += kBlock) {
     m = fmax(m, __ldcg(part + S_MAX * nblk + i));
-    if (MODE == R_RHS) ref = fmax(ref, __ldcg(part + S_RU * nblk + i));
+    if (RHS) ref = fmax(ref, __ldcg(part + S_RU * nblk + i));
   }
   m = block_reduce<true>(m);
-  if (MODE == R_RHS) ref = block_reduce<true>(ref);
+  if (RHS) ref = block_reduce<true>(ref);
   if (flat_tid() == 0) {
     c->arrive = 0;
-    if (MODE == R_RHS) c->ref = ref;
-    outer_check(c, m, MODE == R_RHS ? fmax(tol, tol_rel * ref) : tol, maxit, hout, hin, use_cond, set_hin);
+    if (RHS) c->ref = ref;
+    outer_check(c, m, RHS ? fmax(tol, tol_rel * ref) : tol, maxit, hout, hin, use_cond, set_hin);
   }
 }
 
@@ -521,7 +541,7 @@ cudaError_t build_graph(lbe_handle *h, Args &A, cudaGraphExec_t *exec) {
   const dim3 one(1);
   const bool fixed = h->prm.precision == LBE_FP32;
   const bool ff = fixed && sizeof(T) == 4 && h->p32.salt11 && A.phi_lo && !A.rhs;
-  void *f_res = A.rhs ? (void *)k_res<T, R_RHS>
+  void *f_res = A.rhs ? (A.phi32 && A.phi_lo ? (void *)k_res<T, R_RHS_FF> : (void *)k_res<T, R_RHS>)
                       : (ff ? (void *)k_res<T, R_FF> : (fixed ? (void *)k_res<T, R_FIXED> : (void *)k_res<T, R_N64>));
   cudaGraph_t G = nullptr;
   cudaError_t e = cudaGraphCreate(&G, 0);
@@ -580,7 +600,8 @@ int solve_polled(lbe_handle *h, Args &A) {
   for (int round = 0; round <= kMaxOuter; ++round) {
     {
       const bool ff = fixed && sizeof(T) == 4 && h->p32.salt11 && A.phi_lo && !A.rhs;
-      auto kres = A.rhs ? k_res<T, R_RHS> : (ff ? k_res<T, R_FF> : (fixed ? k_res<T, R_FIXED> : k_res<T, R_N64>));
+      auto kres = A.rhs ? (A.phi32 && A.phi_lo ? k_res<T, R_RHS_FF> : k_res<T, R_RHS>)
+                        : (ff ? k_res<T, R_FF> : (fixed ? k_res<T, R_FIXED> : k_res<T, R_N64>));
       kres<<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.P, A.P3, A.mask, A.n64, A.nq, A.rhs, A.phi, A.phi32, A.phi_lo,
                                         A.c6_hi, A.c6_lo, (T *)A.r, (T *)A.u, (T *)A.x, (T *)A.p, (T *)A.s, A.part,
                                         A.nblk, A.c, A.tol, A.tol_rel, A.maxit, 0, 0, 0, 0);
@@ -697,10 +718,11 @@ void poisson_drop_graphs(lbe_handle *h) {
   }
   if (w.exec_lin) cudaGraphExecDestroy(w.exec_lin);
   w.exec_lin = nullptr;
-  w.lin_key[0] = w.lin_key[1] = nullptr;
+  w.lin_key[0] = w.lin_key[1] = w.lin_key[2] = nullptr;
 }
 
-int poisson_solve_linear(lbe_handle *h, const double *rhs, double *x, double tol_abs, double tol_rel) {
+int poisson_solve_linear(lbe_handle *h, const double *rhs, double *x, double tol_abs, double tol_rel, float *x_hi,
+                         float *x_lo) {
   if (h->prm.precision != LBE_FP32) {
     h->err = "linear solve: FP32 form only";
     return LBE_ERR_STATE;
@@ -710,13 +732,17 @@ int poisson_solve_linear(lbe_handle *h, const double *rhs, double *x, double tol
   fill_args<float>(h, A);
   A.rhs = rhs;
   A.phi = x;
-  A.phi32 = nullptr;
-  A.phi_lo = nullptr;
+  A.phi32 = x_hi;
+  A.phi_lo = x_lo;
+  if (x_hi && x_lo) {  // the split of the starting x; the corrections keep it current
+    k_correct<float><<<w.L.grid, w.L.block, 0, h->stream>>>(h->geo, w.L.zpt, h->mask, nullptr, x, x_hi, x_lo);
+    if (cudaGetLastError() != cudaSuccess) return LBE_ERR_CUDA;
+  }
   A.tol = tol_abs;
   A.tol_rel = tol_rel;
   A.tol_inner = 0.25 * tol_abs;
   if (!w.graph_ok) return solve_polled<float>(h, A);
-  if (!w.exec_lin || w.lin_key[0] != rhs || w.lin_key[1] != x) {
+  if (!w.exec_lin || w.lin_key[0] != rhs || w.lin_key[1] != x || w.lin_key[2] != x_hi) {
     if (w.exec_lin) cudaGraphExecDestroy(w.exec_lin);
     w.exec_lin = nullptr;
     cudaError_t e = build_graph<float>(h, A, &w.exec_lin);
@@ -727,6 +753,7 @@ int poisson_solve_linear(lbe_handle *h, const double *rhs, double *x, double tol
     }
     w.lin_key[0] = rhs;
     w.lin_key[1] = x;
+    w.lin_key[2] = x_hi;
   }
   cudaError_t e = cudaGraphLaunch(w.exec_lin, h->stream);
   if (e != cudaSuccess) {
