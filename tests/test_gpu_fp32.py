@@ -133,3 +133,35 @@ def test_set_voltage_unchanged_keeps_state(lbe):
     np.testing.assert_array_equal(a.n(), b.n())
     a.set_voltage((0.0, 0.2))
     assert np.abs(a.phi() - b.phi()).max() > 1e-3  # re-solved for the new voltage
+
+
+def test_exact_coarsest_solve_matches_jacobi_sweeps(lbe, monkeypatch):
+    """The exact coarsest-level solve (inverse formed at set-up) and the 32
+    Jacobi sweeps it replaces are two preconditioners of the same CG: the
+    converged potentials agree to the solve tolerance, and the exact one
+    needs no more iterations."""
+    w = wl.Workload("plates", wl.plates(32, 32, 96), 2, (1, 1, 0), (0.0, 0.2), 1.44, 8.0,
+                    e_app=(1e-3, 0.0, 0.0))
+    runs = []
+    for direct in ("0", "1"):
+        monkeypatch.setenv("LBE_MG_DIRECT", direct)
+        g = gpu_for(lbe, w)
+        g.step(10)
+        runs.append((g.phi(), g.stats().poisson_iters))
+        g.close()
+    (p_jac, it_jac), (p_dir, it_dir) = runs
+    assert np.abs(p_dir - p_jac).max() <= 1e-9, np.abs(p_dir - p_jac).max()
+    assert it_dir <= it_jac, (it_dir, it_jac)
+
+
+def test_periodic_box_without_electrodes(lbe):
+    """A fully periodic lattice without electrodes has a singular coarsest
+    operator: the set-up keeps the Jacobi sweeps there, and with a uniform
+    salt the potential stays zero."""
+    ids = np.zeros((16, 12, 10), dtype=np.uint8)
+    w = wl.Workload("box", ids, 0, (1, 1, 1), (), 1.0, 4.0, e_app=(1e-3, 0.0, 0.0))
+    g = gpu_for(lbe, w)
+    g.step(5)
+    assert np.all(np.isfinite(g.phi()))
+    assert np.abs(g.phi()).max() <= 1e-12
+    g.close()
