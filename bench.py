@@ -109,8 +109,10 @@ BYTES["fp32"] = {
     # 19 FP32 deviations read + 19 written, int64 q_k read + q*_k written,
     # FP32 phi read, FP32 u written (3), link mask
     "sweep": lambda ns: 4 * (19 + 19 + 1 + 3) + 8 * 2 * ns + 4,
-    # int64 q*_k read, q_k written, u read (3), mask
-    "advect": lambda ns: 8 * 2 * ns + 4 * 3 + 4,
+    # int64 q*_k read, q_k written, u read (3), mask; plus the next solve's
+    # warm start fused into this kernel: phi and its two previous values read
+    # and written (FP64), the FP32 split of phi written
+    "advect": lambda ns: 8 * 2 * ns + 4 * 3 + 4 + 8 * 6 + 4 * 2,
     # one FP32 CG iteration of the inner correction solve: matvec (p read,
     # q write), update (e, res, p, q read; e, res write), direction (res, p
     # read; p write), mask read thrice

@@ -399,7 +399,10 @@ inline SweepKern sweep_kernel(bool flow, long long Ntot) {
 __global__ void __launch_bounds__(kBlock) kb_advect(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
                                                     int T, int Ntot, const uint32_t *__restrict__ mask,
                                                     const int64_t *__restrict__ qin, const float *__restrict__ u,
-                                                    int64_t *__restrict__ qout) {
+                                                    int64_t *__restrict__ qout, double *__restrict__ phi,
+                                                    double *__restrict__ prev, float *__restrict__ phi32,
+                                                    float *__restrict__ phi_lo, const int *__restrict__ hist) {
+  const int have = *hist;  // the next solve's warm start rides along (phi is not read here)
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
     const InstDev &I = inst[tile_inst[t]];
     for (int k = 0; k < kSub; ++k) {
@@ -414,6 +417,7 @@ __global__ void __launch_bounds__(kBlock) kb_advect(const InstDev *__restrict__ 
         continue;
       }
       advect_node(2, Ntot, r, offsets_of(I.g, x, y, z), m, qin, u, qout);
+      extrapolate_node(Ntot, r, phi, prev, phi32, phi_lo, have);
     }
   }
 }
@@ -434,15 +438,7 @@ __global__ void kb_extrapolate(const InstDev *__restrict__ inst, const int *__re
       if (lo >= I.g.N) break;
       const int r = I.off + lo;
       if (!(mask[r] & kFluidBit)) continue;
-      const double v = phi[r], p1 = prev[r];
-      if (have) {
-        const double e = have > 1 ? prev[Ntot + r] + 3.0 * (v - p1) : 2.0 * v - p1;
-        phi[r] = e;
-        phi32[r] = (float)e;
-        phi_lo[r] = (float)(e - (double)(float)e);
-      }
-      prev[Ntot + r] = p1;
-      prev[r] = v;
+      extrapolate_node(Ntot, r, phi, prev, phi32, phi_lo, have);
     }
   }
 }
@@ -1370,7 +1366,8 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   cudaGraph_t bo = nullptr, bi = nullptr;
   void *a_sw[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.fin, &A.fout, &A.qin, &A.qmid, &A.phi32, &A.u,
                   &A.flag};
-  void *a_adv[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.qmid, &A.u, &A.qin};
+  void *a_adv[] = {&A.inst, &A.tile_inst, &A.T,      &A.Ntot,  &A.mask, &A.qmid,
+                   &A.u,    &A.qin,       &A.phi, &A.phi_prev, &A.phi32, &A.phi_lo, &A.hist};
   void *a_ext[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.phi, &A.phi_prev, &A.phi32, &A.phi_lo, &A.hist};
   void *a_reset[] = {&A.n, &A.c, &A.bc, &A.hist, &A.set_hist};
   void *a_res[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.qsolve, &A.phi32, &A.phi_lo, &A.v, &A.part, &A.c};
@@ -1394,7 +1391,8 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
     if (e == cudaSuccess && prof) e = add_event(g, &last, b->ev[1]);
     if (e == cudaSuccess && b->flow) e = add_node(g, &last, (void *)kb_advect, G, B, a_adv);
     if (e == cudaSuccess && prof) e = add_event(g, &last, b->ev[2]);
-    if (e == cudaSuccess) e = add_node(g, &last, (void *)kb_extrapolate, G, B, a_ext);
+    // with flow the advection applies the warm start (kb_advect)
+    if (e == cudaSuccess && !b->flow) e = add_node(g, &last, (void *)kb_extrapolate, G, B, a_ext);
   }
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&A.hout, g, 1, cudaGraphCondAssignDefault);
   // reset -> residual test -> while (any instance unconverged) { V-cycle ->
@@ -1444,11 +1442,14 @@ int run_polled(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *
     sweep_kernel(b->flow, b->Ntot)<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, fin, fout, qin,
                                                          qmid, A.phi32, A.u, A.flag);
     BCK(b, rec(1));
-    if (b->flow) kb_advect<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, qmid, A.u, qin);
+    if (b->flow)  // the advection applies the warm start as well
+      kb_advect<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, qmid, A.u, qin, A.phi, A.phi_prev,
+                                      A.phi32, A.phi_lo, A.hist);
     BCK(b, rec(2));
-    kb_extrapolate<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, A.phi, A.phi_prev, A.phi32,
-                                         A.phi_lo, A.hist);
-    nl += b->flow ? 3 : 2;
+    if (!b->flow)
+      kb_extrapolate<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, A.phi, A.phi_prev, A.phi32,
+                                           A.phi_lo, A.hist);
+    nl += 2;
   }
   kb_solve_reset<<<(n + 255) / 256, 256, 0, st>>>(n, A.c, A.bc, A.hist, A.set_hist);
   nl += 1;

@@ -254,6 +254,31 @@ __device__ __forceinline__ void advect_node(int ns, int N, int r, const Offs &o,
     if (k < ns) qout[k * N + r] = acc[k] - base;
 }
 
+// Warm start of the next solve at fluid node i: the polynomial in time
+// through the last history + 1 solutions, one step ahead,
+//   history 2: phi <- 3 phi(t) - 3 phi(t-1) + phi(t-2)
+//   history 1: phi <- 2 phi(t) - phi(t-1)
+// (the converged potential does not depend on the starting guess; the
+// quadratic start is 30-300 times closer to it than the linear one while the
+// capacitor charges); its FP32 split follows when hi is given; the history
+// shifts: prev = [phi(t), phi(t-1)] with component stride N
+__device__ __forceinline__ void extrapolate_node(long long N, long long i, double *__restrict__ phi,
+                                                 double *__restrict__ prev, float *__restrict__ hi,
+                                                 float *__restrict__ lo, int history) {
+  const double v = phi[i], p1 = prev[i];
+  if (history > 0) {
+    const double e = history > 1 ? prev[N + i] + 3.0 * (v - p1) : 2.0 * v - p1;
+    phi[i] = e;
+    if (hi) {  // the FP32 copies follow: the solve may stop at once
+      const float h = (float)e;
+      hi[i] = h;
+      if (lo) lo[i] = (float)(e - (double)h);
+    }
+  }
+  prev[N + i] = p1;
+  prev[i] = v;
+}
+
 // Error-free sum (Knuth): s + e = a + b exactly, s = fl(a + b).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   s = __fadd_rn(a, b);

@@ -62,7 +62,9 @@ __global__ void __launch_bounds__(kBlock) k_sweep32(const Geo g, const P32 P, co
 // velocity points at it.
 __global__ void __launch_bounds__(kBlock) k_advect32(const Geo g, int ns, const uint32_t *__restrict__ mask,
                                                      const int64_t *__restrict__ qin, const float *__restrict__ u,
-                                                     int64_t *__restrict__ qout) {
+                                                     int64_t *__restrict__ qout, double *__restrict__ phi,
+                                                     double *__restrict__ prev, float *__restrict__ phi32,
+                                                     float *__restrict__ phi_lo, int history) {
   int x, y, z;
   long long rl;
   if (!node_of(g, 1, 0, x, y, z, rl)) return;
@@ -73,6 +75,8 @@ __global__ void __launch_bounds__(kBlock) k_advect32(const Geo g, int ns, const 
     return;
   }
   advect_node(ns, N, r, offsets_of(g, x, y, z), m, qin, u, qout);
+  // the next solve's warm start (phi is not read by the advection)
+  if (phi) extrapolate_node(N, r, phi, prev, phi32, phi_lo, history);
 }
 
 __global__ void k_n_to_double(const Geo g, const P32 P, const int64_t *__restrict__ q, const uint32_t *__restrict__ mask,
@@ -182,8 +186,10 @@ cudaError_t launch_sweep32(lbe_handle *h) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_advect32(lbe_handle *h) {
-  k_advect32<<<LAUNCH3(h), 0, h->stream>>>(h->geo, h->prm.nspecies, h->mask, h->qstar, h->u32, h->q);
+cudaError_t launch_advect32(lbe_handle *h, bool extrapolate) {
+  k_advect32<<<LAUNCH3(h), 0, h->stream>>>(h->geo, h->prm.nspecies, h->mask, h->qstar, h->u32, h->q,
+                                           extrapolate ? h->phi : nullptr, h->pw.phi_prev, h->phi32, h->phi_lo,
+                                           h->pw.history);
   return cudaGetLastError();
 }
 

@@ -368,8 +368,10 @@ int lbe_step(lbe_handle *h, int nsteps) {
     LBE_CK(h, f32 ? lbe::launch_sweep32(h) : lbe::launch_sweep(h));
     LBE_CK(h, mark(h));
     h->launches += 1;
+    // the FP32 form's advection also applies the next solve's warm start
+    const bool fused_extrapolation = f32 && h->prm.flow;
     if (h->prm.flow) {
-      LBE_CK(h, f32 ? lbe::launch_advect32(h) : lbe::launch_advect(h));
+      LBE_CK(h, f32 ? lbe::launch_advect32(h, true) : lbe::launch_advect(h));
       h->launches += 1;
     } else if (f32) {
       int64_t *t = h->q;
@@ -381,7 +383,7 @@ int lbe_step(lbe_handle *h, int nsteps) {
       h->nstar = t;
     }
     LBE_CK(h, mark(h));
-    int rc = lbe::poisson_enqueue(h, true);
+    int rc = lbe::poisson_enqueue(h, true, fused_extrapolation);
     LBE_CK(h, mark(h));
     if (rc != LBE_OK) return rc;
   }

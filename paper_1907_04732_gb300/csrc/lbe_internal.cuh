@@ -308,7 +308,9 @@ cudaError_t launch_charge_node(lbe_handle *h, double *out);
 // kernels_fp32.cu
 cudaError_t launch_init32(lbe_handle *h);
 cudaError_t launch_sweep32(lbe_handle *h);
-cudaError_t launch_advect32(lbe_handle *h);
+// extrapolate: also the warm start of the next solve (as k_extrapolate, with
+// the current history), the advection not reading the potential
+cudaError_t launch_advect32(lbe_handle *h, bool extrapolate = false);
 cudaError_t launch_n_to_double(lbe_handle *h, double *out);
 cudaError_t launch_n_from_double(lbe_handle *h, const double *n);
 cudaError_t launch_moments32(lbe_handle *h, double *rho_out, double *u_out, double *f_out);
@@ -317,7 +319,9 @@ cudaError_t poisson_alloc(lbe_handle *h);
 void poisson_free(lbe_handle *h);
 // enqueue one Poisson solve on the handle's stream (no host synchronisation
 // on the graph path)
-int poisson_enqueue(lbe_handle *h, bool extrapolate);
+// extrapolated: the warm start was already applied this step (by the
+// advection kernel); only the history count advances
+int poisson_enqueue(lbe_handle *h, bool extrapolate, bool extrapolated = false);
 // synchronise and read the solves' status/statistics since the last reset;
 // *kernels (optional) receives the kernels the graph path launched
 int poisson_status(lbe_handle *h, lbe_stats *st, long long *kernels);

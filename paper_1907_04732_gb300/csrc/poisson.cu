@@ -394,13 +394,8 @@ __global__ void __launch_bounds__(kBlock) k_cg_a(const Geo g, int zpt, uint32_t 
   if (flat_tid() == 0) part[S_MAX * nblk + flat_bid()] = (double)v;
 }
 
-// warm start of a step's solve on fluid nodes: the polynomial in time through
-// the last history + 1 solutions, evaluated one step ahead,
-//   history 2: phi <- 3 phi(t) - 3 phi(t-1) + phi(t-2)
-//   history 1: phi <- 2 phi(t) - phi(t-1)
-// (the converged potential does not depend on the starting guess; the
-// quadratic start is 30-300 times closer to it than the linear one while the
-// capacitor charges), then shift the history: prev = [phi(t), phi(t-1)]
+// warm start of a step's solve on fluid nodes (fp32::extrapolate_node); the
+// FP32 form with flow does this inside the advection kernel instead
 __global__ void k_extrapolate(const Geo g, int zpt, const uint32_t *__restrict__ mask, double *__restrict__ phi,
                               double *__restrict__ prev, float *__restrict__ phi32, float *__restrict__ phi_lo,
                               int history) {
@@ -408,19 +403,7 @@ __global__ void k_extrapolate(const Geo g, int zpt, const uint32_t *__restrict__
     int X, Y, Z;
     long long i;
     if (!node_of(g, zpt, kz, X, Y, Z, i)) continue;
-    if (!(mask[i] & kFluidBit)) continue;
-    const double v = phi[i], p1 = prev[i];
-    if (history > 0) {
-      const double e = history > 1 ? prev[g.N + i] + 3.0 * (v - p1) : 2.0 * v - p1;
-      phi[i] = e;
-      if (phi32) {  // the FP32 copies follow: the solve may stop at once
-        const float hi = (float)e;
-        phi32[i] = hi;
-        if (phi_lo) phi_lo[i] = (float)(e - (double)hi);
-      }
-    }
-    prev[g.N + i] = p1;
-    prev[i] = v;
+    if (mask[i] & kFluidBit) fp32::extrapolate_node(g.N, i, phi, prev, phi32, phi_lo, history);
   }
 }
 
@@ -763,14 +746,16 @@ int poisson_solve_linear(lbe_handle *h, const double *rhs, double *x, double tol
   return LBE_OK;
 }
 
-int poisson_enqueue(lbe_handle *h, bool extrapolate) {
+int poisson_enqueue(lbe_handle *h, bool extrapolate, bool extrapolated) {
   PoissonWork &w = h->pw;
   if (extrapolate) {
-    k_extrapolate<<<w.L.grid, w.L.block, 0, h->stream>>>(h->geo, w.L.zpt, h->mask, h->phi, w.phi_prev,
-                                                       h->prm.precision == LBE_FP32 ? h->phi32 : nullptr,
-                                                       h->prm.precision == LBE_FP32 ? h->phi_lo : nullptr,
-                                                       w.history);
-    h->launches += 1;
+    if (!extrapolated) {
+      k_extrapolate<<<w.L.grid, w.L.block, 0, h->stream>>>(h->geo, w.L.zpt, h->mask, h->phi, w.phi_prev,
+                                                         h->prm.precision == LBE_FP32 ? h->phi32 : nullptr,
+                                                         h->prm.precision == LBE_FP32 ? h->phi_lo : nullptr,
+                                                         w.history);
+      h->launches += 1;
+    }
     if (w.history < 2) w.history += 1;
   } else {
     w.history = 0;
