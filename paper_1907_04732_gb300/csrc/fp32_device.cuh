@@ -70,6 +70,46 @@ __device__ __forceinline__ void gather32(int N, int r, const Offs &o, uint32_t m
   }
 }
 
+// One link of a 1:1 salt (z = +1, -1) from a node with potential phi0 and
+// solute nu0 (nu = s q) to its neighbour r2: the flux terms J0, J1 of the two
+// species (Eq. LF2, relative form) and the link excess flux gs summed over
+// them.  A fixed rounding sequence: evaluated from the other end the link
+// gives exactly -J0, -J1, -gs.
+__device__ __forceinline__ void link_salt11(const P32 &P, int N, int r2, float phi0, float ec, float il,
+                                            const float nu0[2], const int64_t *__restrict__ q,
+                                            const float *__restrict__ phi, float &J0, float &J1, float &gs) {
+  const float dphi = __fsub_rn(__fsub_rn(phi[r2], phi0), ec);
+  float P1, M1;
+  em1_pair(dphi, P1, M1);
+  gs = 0.f;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float Pk = k == 0 ? P1 : M1, Mk = k == 0 ? M1 : P1;
+    const float nu1 = __fmul_rn(P.s[k], ll2f(q[k * N + r2]));
+    const float a1 = nE(P.rb[k], nu1, Pk), a0 = nE(P.rb[k], nu0[k], Mk);
+    const float J = __fsub_rn(tterm(a1, nu1), tterm(a0, nu0[k]));  // t1 - t0, exactly odd under link reversal
+    if (k == 0) J0 = J;
+    else J1 = J;
+    // link excess flux g = j/d + (n' - n)/|c| = -(n' (e^mu - 1) - n (e^-mu - 1))/(2|c|)
+    gs = __fmaf_rn(-(il * 0.5f), __fsub_rn(a1, a0), gs);
+  }
+}
+
+// The quantised solute update and the force of link i (1:1 salt) from its
+// flux terms: dq_k -= round(J_k kq_k), F += c_i gs.
+__device__ __forceinline__ void link_apply(const P32 &P, int i, float J0, float J1, float gs, long long dq[2],
+                                           float &Fx, float &Fy, float &Fz, bool &over) {
+  const float jq0 = __fmul_rn(J0, c2_of(i) == 1 ? P.kq1[0] : P.kq2[0]);
+  const float jq1 = __fmul_rn(J1, c2_of(i) == 1 ? P.kq1[1] : P.kq2[1]);
+  over |= fabsf(jq0) > 1.0e17f;
+  over |= fabsf(jq1) > 1.0e17f;
+  dq[0] -= f2ll_rn(jq0);
+  dq[1] -= f2ll_rn(jq1);
+  Fx += cx_of(i) * gs;
+  Fy += cy_of(i) * gs;
+  Fz += cz_of(i) * gs;
+}
+
 // Ion part of the step at one fluid node: quantised link fluxes -> dq, and
 // the solvent force from the link excess fluxes.
 template <bool QUANT, bool SALT11>
@@ -79,6 +119,20 @@ __device__ __forceinline__ void ion_links(const P32 &P, int N, int r, const Offs
                                           long long dq[LBE_MAX_SPECIES], float F[3], bool &over) {
   const float phi0 = phi[r];
   float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+  if (SALT11 && QUANT) {
+    const float nu0[2] = {q0f[0], q0f[1]};
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+      if (!(m & (1u << (i - 1)))) continue;
+      float J0, J1, gs;
+      link_salt11(P, N, nb_of(o, r, i), phi0, P.ec[i], (float)invlen_of(i), nu0, q, phi, J0, J1, gs);
+      link_apply(P, i, J0, J1, gs, dq, Fx, Fy, Fz, over);
+    }
+    F[0] = Fx * P.inv_2a0;
+    F[1] = Fy * P.inv_2a0;
+    F[2] = Fz * P.inv_2a0;
+    return;
+  }
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     if (!(m & (1u << (i - 1)))) continue;
@@ -114,7 +168,7 @@ __device__ __forceinline__ void ion_links(const P32 &P, int N, int r, const Offs
         dq[k] -= f2ll_rn(jq);
       }
       // link excess flux g = j/d + (n' - n)/|c| = -(n' (e^mu - 1) - n (e^-mu - 1))/(2|c|)
-      gs -= il * 0.5f * (a1 - a0);
+      gs = __fmaf_rn(-(il * 0.5f), __fsub_rn(a1, a0), gs);
     }
     Fx += cx_of(i) * gs;
     Fy += cy_of(i) * gs;
@@ -145,29 +199,12 @@ __device__ __forceinline__ long long share(float totf, float ux, float uy, float
 }
 
 
-// Fused step at one fluid node: quantised link fluxes and q* = q - sum Jq,
-// solvent force, and (FLOW) BGK + Guo collision with pull streaming.
-template <bool FLOW, bool SALT11, bool WIDE>
-__device__ __forceinline__ void sweep_node(const P32 &P, int N, int r, const Offs &o, uint32_t m,
-                                           const float *__restrict__ fin, float *__restrict__ fout,
-                                           const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
-                                           const float *__restrict__ phi, float *__restrict__ u, bool &over) {
-  long long q0[LBE_MAX_SPECIES], dq[LBE_MAX_SPECIES];
-  float q0f[LBE_MAX_SPECIES];
-#pragma unroll
-  for (int k = 0; k < LBE_MAX_SPECIES; ++k) {
-    q0[k] = k < P.ns ? q[k * N + r] : 0;
-    q0f[k] = k < P.ns ? __fmul_rn(P.s[k], ll2f(q0[k])) : 0.f;  // nu = s q
-    dq[k] = 0;
-  }
-  float F[3];
-  ion_links<true, SALT11>(P, N, r, o, m, q, phi, q0, q0f, dq, F, over);
-  // compile-time species indices keep q0/dq in registers
-#pragma unroll
-  for (int k = 0; k < (SALT11 ? 2 : LBE_MAX_SPECIES); ++k)
-    if (SALT11 || k < P.ns) qstar[k * N + r] = q0[k] + dq[k];
-  if (!FLOW) return;
-
+// BGK + Guo collision and pull streaming with halfway bounce-back at one
+// fluid node, given the solvent force F; the velocity is stored
+template <bool WIDE>
+__device__ __forceinline__ void lb_node(const P32 &P, int N, int r, const Offs &o, uint32_t m,
+                                        const float *__restrict__ fin, float *__restrict__ fout,
+                                        float *__restrict__ u, const float F[3]) {
   float f[kQ];
   gather32<WIDE>(N, r, o, m, fin, f);
   float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
@@ -207,6 +244,30 @@ __device__ __forceinline__ void sweep_node(const P32 &P, int N, int r, const Off
     fout[(PopIdx<WIDE>)i * N + r] = f[i] - P.omega * (f[i] - (eq_even + eq_odd)) + (src_even + src_odd);
     fout[(PopIdx<WIDE>)io * N + r] = f[io] - P.omega * (f[io] - (eq_even - eq_odd)) + (src_even - src_odd);
   }
+}
+
+// Fused step at one fluid node: quantised link fluxes and q* = q - sum Jq,
+// solvent force, and (FLOW) BGK + Guo collision with pull streaming.
+template <bool FLOW, bool SALT11, bool WIDE>
+__device__ __forceinline__ void sweep_node(const P32 &P, int N, int r, const Offs &o, uint32_t m,
+                                           const float *__restrict__ fin, float *__restrict__ fout,
+                                           const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
+                                           const float *__restrict__ phi, float *__restrict__ u, bool &over) {
+  long long q0[LBE_MAX_SPECIES], dq[LBE_MAX_SPECIES];
+  float q0f[LBE_MAX_SPECIES];
+#pragma unroll
+  for (int k = 0; k < LBE_MAX_SPECIES; ++k) {
+    q0[k] = k < P.ns ? q[k * N + r] : 0;
+    q0f[k] = k < P.ns ? __fmul_rn(P.s[k], ll2f(q0[k])) : 0.f;  // nu = s q
+    dq[k] = 0;
+  }
+  float F[3];
+  ion_links<true, SALT11>(P, N, r, o, m, q, phi, q0, q0f, dq, F, over);
+  // compile-time species indices keep q0/dq in registers
+#pragma unroll
+  for (int k = 0; k < (SALT11 ? 2 : LBE_MAX_SPECIES); ++k)
+    if (SALT11 || k < P.ns) qstar[k * N + r] = q0[k] + dq[k];
+  if (FLOW) lb_node<WIDE>(P, N, r, o, m, fin, fout, u, F);
 }
 
 // Cell-overlap advection at one fluid node (see k_advect32).
