@@ -122,7 +122,7 @@ BYTES_FP64 = BYTES["fp64"]
 
 # DRAM bytes per launch of the fused sweep from an ncu capture of the same
 # kernel code (profiles/), or absent when the kernel changed since
-SWEEP_TRAFFIC = {("fp32", "eof_64x64x256"): 104152320 + 64943616}  # profiles/fp32_eof64x64x256_k_sweep32_ncu_full.md
+SWEEP_TRAFFIC = {("fp32", "eof_64x64x256"): 104150016 + 64849920}  # profiles/fp32_eof64x64x256_k_sweep32_ncu_full.md
 
 
 class ClockSampler:
