@@ -110,9 +110,9 @@ BYTES["fp32"] = {
     # FP32 phi read, FP32 u written (3), link mask
     "sweep": lambda ns: 4 * (19 + 19 + 1 + 3) + 8 * 2 * ns + 4,
     # int64 q*_k read, q_k written, u read (3), mask; plus the next solve's
-    # warm start fused into this kernel: phi and its two previous values read
-    # and written (FP64), the FP32 split of phi written
-    "advect": lambda ns: 8 * 2 * ns + 4 * 3 + 4 + 8 * 6 + 4 * 2,
+    # warm start fused into this kernel: phi and its three previous values
+    # read and written (FP64, cubic extrapolation), the FP32 split written
+    "advect": lambda ns: 8 * 2 * ns + 4 * 3 + 4 + 8 * 8 + 4 * 2,
     # one FP32 CG iteration of the inner correction solve: matvec (p read,
     # q write), update (e, res, p, q read; e, res write), direction (res, p
     # read; p write), mask read thrice
@@ -357,7 +357,7 @@ def adjoint_leg(args, lbe, torch, stream):
             "recomputed_steps": int(g.recomputed_steps), "adjoint_cg_iters": int(g.poisson_iters),
             "backward_phases_ms": {"recompute": g.recompute_ms, "flux_transpose": g.flux_ms,
                                    "adjoint_solves": g.solve_ms},
-            "checkpoint_bytes": (nseg + 1) * 40 * w.nodes, "segment_bytes": args.adjoint_every * 20 * w.nodes,
+            "checkpoint_bytes": (nseg + 1) * 48 * w.nodes, "segment_bytes": args.adjoint_every * 20 * w.nodes,
             "Q": [float(v) for v in q], "dQ1_dpsi": [float(v) for v in g.dpsi[:2]],
             "dQ1_drho_bulk": float(g.drho_bulk), "dQ1_dD": [float(v) for v in g.dD[:2]],
             "dQ1_dchi_absmax": float(np.abs(dchi).max()),
@@ -490,7 +490,7 @@ def main():
         "roofline": roof,
         "phases_ms": phases, "phase_shares": shares,
         "poisson": {"ms_per_step": phases["poisson"], "cg_iters_per_step": iters,
-                    "note": "refinement on a float-float residual, multigrid-preconditioned FP32 CG, quadratic warm start in time, one CUDA graph"},
+                    "note": "refinement on a float-float residual, multigrid-preconditioned FP32 CG, cubic warm start in time, one CUDA graph"},
         "lb_part_hbm_frac": step_bytes / ((phases["sweep"] + phases["advect"]) * 1e-3) / 1e9 / peak,
         "advect_gbs": adv_bytes / (phases["advect"] * 1e-3) / 1e9 if phases["advect"] > 0 else None,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * w.n_elec,

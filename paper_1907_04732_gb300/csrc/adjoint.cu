@@ -44,7 +44,7 @@ struct AdjWork {
   bool ready = false;
   int64_t *ck_q = nullptr;  // checkpoints [nseg + 1][2N] (the last: time T)
   double *ck_phi = nullptr;   // [nseg + 1][N]
-  double *ck_prev = nullptr;  // [nseg + 1][2N]: the warm start's history
+  double *ck_prev = nullptr;  // [nseg + 1][kHist N]: the warm start's history
   std::vector<char> ck_hist;
   int64_t *st_q = nullptr;  // states of one segment [every][2N]
   float *st_phi = nullptr;  // [every][N]
@@ -367,7 +367,7 @@ int adj_alloc(lbe_handle *h, int T, int every) {
     const size_t ns1 = (size_t)nseg + 1;
     alloc((void **)&a->ck_q, sizeof(int64_t) * 2 * N * ns1);
     alloc((void **)&a->ck_phi, sizeof(double) * N * ns1);
-    alloc((void **)&a->ck_prev, sizeof(double) * 2 * N * ns1);
+    alloc((void **)&a->ck_prev, sizeof(double) * kHist * N * ns1);
     alloc((void **)&a->st_q, sizeof(int64_t) * 2 * N * std::max(every, 1));
     alloc((void **)&a->st_phi, sizeof(float) * N * std::max(every, 1));
     alloc((void **)&a->lam, sizeof(float) * 2 * N);
@@ -398,7 +398,7 @@ int save_ck(lbe_handle *h, int k) {
   ACK(h, cudaMemcpyAsync(a->ck_q + (size_t)k * 2 * N, h->q, sizeof(int64_t) * 2 * N, cudaMemcpyDeviceToDevice,
                          h->stream));
   ACK(h, cudaMemcpyAsync(a->ck_phi + (size_t)k * N, h->phi, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
-  ACK(h, cudaMemcpyAsync(a->ck_prev + (size_t)k * 2 * N, h->pw.phi_prev, sizeof(double) * 2 * N,
+  ACK(h, cudaMemcpyAsync(a->ck_prev + (size_t)k * kHist * N, h->pw.phi_prev, sizeof(double) * kHist * N,
                          cudaMemcpyDeviceToDevice, h->stream));
   a->ck_hist[k] = (char)h->pw.history;
   return LBE_OK;
@@ -410,7 +410,7 @@ int load_ck(lbe_handle *h, int k) {
   ACK(h, cudaMemcpyAsync(h->q, a->ck_q + (size_t)k * 2 * N, sizeof(int64_t) * 2 * N, cudaMemcpyDeviceToDevice,
                          h->stream));
   ACK(h, cudaMemcpyAsync(h->phi, a->ck_phi + (size_t)k * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
-  ACK(h, cudaMemcpyAsync(h->pw.phi_prev, a->ck_prev + (size_t)k * 2 * N, sizeof(double) * 2 * N,
+  ACK(h, cudaMemcpyAsync(h->pw.phi_prev, a->ck_prev + (size_t)k * kHist * N, sizeof(double) * kHist * N,
                          cudaMemcpyDeviceToDevice, h->stream));
   h->pw.history = a->ck_hist[k];
   ACK(h, launch_phi32_sync(h));

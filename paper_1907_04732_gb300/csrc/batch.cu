@@ -156,7 +156,7 @@ struct lbe_batch {
   uint32_t *mask = nullptr;
   float *f[2] = {nullptr, nullptr};
   int64_t *q = nullptr, *qstar = nullptr;
-  double *phi = nullptr, *phi_prev = nullptr;  // phi_prev [2][Ntot]: the previous two solutions
+  double *phi = nullptr, *phi_prev = nullptr;  // phi_prev [kHist][Ntot]: the previous solutions
   float *phi32 = nullptr, *u = nullptr;
   float *phi_lo = nullptr;  // phi = phi32 + phi_lo to ~2^-48 (float-float residual)
   float *vec = nullptr;     // CG vectors [6][Ntot]
@@ -166,7 +166,7 @@ struct lbe_batch {
   lbe::BatchCtl *bctl = nullptr, *bctl_h = nullptr;
   double *qpart = nullptr, *qout = nullptr, *qhost = nullptr;
   int *flag = nullptr;
-  int *hist = nullptr;  // device: how many solutions phi_prev holds (0..2)
+  int *hist = nullptr;  // device: how many solutions phi_prev holds (0..kHist)
   // tile lists of active instances: family f counts, prefix sums
   int nfam = 0;
   int *fam_cnt = nullptr;   // [nfam][n]
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(kBlock) kb_init(const InstDev *__restrict__ in
       phi[r] = p;
       phi32[r] = (float)p;
       phi_lo[r] = (float)(p - (double)(float)p);
-      phi_prev[r] = phi_prev[Ntot + r] = p;
+      for (int k = 0; k < kHist; ++k) phi_prev[k * Ntot + r] = p;
       u[r] = u[Ntot + r] = u[2 * Ntot + r] = 0.f;
     }
   }
@@ -446,7 +446,7 @@ __global__ void kb_extrapolate(const InstDev *__restrict__ inst, const int *__re
 // --- batched Poisson ---------------------------------------------------------
 __global__ void kb_solve_reset(int n, InstCtl *c, BatchCtl *b, int *hist, int set_hist) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0 && set_hist && *hist < 2) *hist += 1;
+  if (i == 0 && set_hist && *hist < kHist) *hist += 1;
   if (i < n) {
     if (c[i].status && !b->sticky_status) b->sticky_status = c[i].status;
     atomicMax((unsigned long long *)&b->max_iters, (unsigned long long)c[i].iters);
@@ -1732,7 +1732,7 @@ int lbe_batch_create(const lbe_params *params, int n, void *cuda_stream, lbe_bat
   alloc((void **)&b->q, 8 * N * 2);
   alloc((void **)&b->qstar, 8 * N * 2);
   alloc((void **)&b->phi, 8 * N);
-  alloc((void **)&b->phi_prev, 8 * 2 * N);
+  alloc((void **)&b->phi_prev, 8 * lbe::kHist * N);
   alloc((void **)&b->phi32, 4 * N);
   alloc((void **)&b->phi_lo, 4 * N);
   alloc((void **)&b->u, 4 * N * 3);

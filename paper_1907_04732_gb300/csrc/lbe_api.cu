@@ -504,15 +504,15 @@ int lbe_set_state(lbe_handle *h, const double *n, const double *phi, int on_devi
 }
 
 // blob: header | populations (19N) | solute (ns N) | phi (N doubles) |
-// velocity (3N) | phi of the previous two steps (2N doubles, warm start of
-// the next solve; header.history of them valid); populations, solute and
-// velocity in the form's own types
+// velocity (3N) | phi of the previous kHist steps (kHist N doubles, warm
+// start of the next solve; header.history of them valid); populations,
+// solute and velocity in the form's own types
 struct BlobHeader {
   uint64_t magic;
   int64_t N;
   int32_t ns, flow, precision, history;
 };
-static const uint64_t kMagic = 0x4c42457374763035ULL;
+static const uint64_t kMagic = 0x4c42457374763130ULL + lbe::kHist;  // format 1, history length
 
 static void blob_sizes(const lbe_handle *h, size_t *fb, size_t *nb, size_t *pb, size_t *ub) {
   const size_t N = (size_t)h->geo.N;
@@ -520,7 +520,7 @@ static void blob_sizes(const lbe_handle *h, size_t *fb, size_t *nb, size_t *pb, 
   *fb = N * lbe::kQ * (f32 ? sizeof(float) : sizeof(double));
   *nb = N * h->prm.nspecies * (f32 ? sizeof(int64_t) : sizeof(double));
   *pb = N * sizeof(double);
-  *ub = N * 3 * (f32 ? sizeof(float) : sizeof(double)) + 2 * N * sizeof(double);
+  *ub = N * 3 * (f32 ? sizeof(float) : sizeof(double)) + lbe::kHist * N * sizeof(double);
 }
 
 int lbe_save_state(lbe_handle *h, void *blob, size_t *size) {
@@ -547,10 +547,10 @@ int lbe_save_state(lbe_handle *h, void *blob, size_t *size) {
   p += nb;
   LBE_CK(h, cudaMemcpyAsync(p, h->phi, pb, cudaMemcpyDeviceToHost, h->stream));
   p += pb;
-  const size_t vb = ub - 2 * (size_t)h->geo.N * sizeof(double);
+  const size_t vb = ub - lbe::kHist * (size_t)h->geo.N * sizeof(double);
   LBE_CK(h, cudaMemcpyAsync(p, f32 ? (void *)h->u32 : (void *)h->u, vb, cudaMemcpyDeviceToHost, h->stream));
   p += vb;
-  LBE_CK(h, cudaMemcpyAsync(p, h->pw.phi_prev, 2 * (size_t)h->geo.N * sizeof(double), cudaMemcpyDeviceToHost,
+  LBE_CK(h, cudaMemcpyAsync(p, h->pw.phi_prev, lbe::kHist * (size_t)h->geo.N * sizeof(double), cudaMemcpyDeviceToHost,
                             h->stream));
   LBE_CK(h, cudaStreamSynchronize(h->stream));
   *size = need;
@@ -581,12 +581,12 @@ int lbe_load_state(lbe_handle *h, const void *blob, size_t size) {
   p += nb;
   LBE_CK(h, cudaMemcpyAsync(h->phi, p, pb, cudaMemcpyHostToDevice, h->stream));
   p += pb;
-  const size_t vb = ub - 2 * (size_t)h->geo.N * sizeof(double);
+  const size_t vb = ub - lbe::kHist * (size_t)h->geo.N * sizeof(double);
   LBE_CK(h, cudaMemcpyAsync(f32 ? (void *)h->u32 : (void *)h->u, p, vb, cudaMemcpyHostToDevice, h->stream));
   p += vb;
-  LBE_CK(h, cudaMemcpyAsync(h->pw.phi_prev, p, 2 * (size_t)h->geo.N * sizeof(double), cudaMemcpyHostToDevice,
+  LBE_CK(h, cudaMemcpyAsync(h->pw.phi_prev, p, lbe::kHist * (size_t)h->geo.N * sizeof(double), cudaMemcpyHostToDevice,
                             h->stream));
-  h->pw.history = hd.history < 0 ? 0 : (hd.history > 2 ? 2 : hd.history);
+  h->pw.history = hd.history < 0 ? 0 : (hd.history > lbe::kHist ? lbe::kHist : hd.history);
   if (f32) LBE_CK(h, lbe::launch_phi32_sync(h));
   LBE_CK(h, cudaStreamSynchronize(h->stream));
   h->initialised = true;

@@ -202,10 +202,17 @@ struct PoissonWork {
   cudaGraphExec_t exec_lin = nullptr;  // linear solve A x = rhs (adjoint)
   const void *lin_key[3] = {nullptr, nullptr, nullptr};
   bool graph_ok = false;
-  double *phi_prev = nullptr;  // [2][N]: phi of the previous two steps (warm start)
-  int history = 0;             // how many of them hold a solution (0..2)
+  double *phi_prev = nullptr;  // [kHist][N]: phi of the previous kHist steps (warm start)
+  int history = 0;             // how many of them hold a solution (0..kHist)
 };
 constexpr int kMaxPartials = 2048;
+// Order of the warm start's extrapolation in time = the number of earlier
+// solutions kept (fp32::extrapolate_node).
+#ifndef LBE_EXTRAP_ORDER
+#define LBE_EXTRAP_ORDER 3
+#endif
+constexpr int kHist = LBE_EXTRAP_ORDER;
+static_assert(kHist >= 1 && kHist <= 3, "extrapolation order 1..3");
 // Launch size of the solve's lattice kernels: each thread handles zpt nodes
 // along z so that a kernel has at most this many blocks.  On this GPU a
 // dependent kernel costs about 0.6 ns per block to schedule (2.4 us for 4096

@@ -668,7 +668,7 @@ cudaError_t poisson_alloc(lbe_handle *h) {
   cudaError_t e;
   if ((e = cudaMalloc(&w.vec, tsz * 6 * N)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&w.partial, sizeof(double) * 3 * w.L.nblk())) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&w.phi_prev, sizeof(double) * 2 * N)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&w.phi_prev, sizeof(double) * kHist * N)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&w.ctl, sizeof(PoissonCtl))) != cudaSuccess) return e;
   if ((e = cudaMemset(w.ctl, 0, sizeof(PoissonCtl))) != cudaSuccess) return e;
   if ((e = cudaMallocHost(&w.ctl_host, sizeof(PoissonCtl))) != cudaSuccess) return e;
@@ -756,7 +756,7 @@ int poisson_enqueue(lbe_handle *h, bool extrapolate, bool extrapolated) {
                                                          w.history);
       h->launches += 1;
     }
-    if (w.history < 2) w.history += 1;
+    if (w.history < kHist) w.history += 1;
   } else {
     w.history = 0;
   }
