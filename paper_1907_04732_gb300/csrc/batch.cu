@@ -423,9 +423,7 @@ __global__ void __launch_bounds__(kBlock) kb_advect(const InstDev *__restrict__ 
 }
 
 // warm start on fluid nodes (all instances) from the *hist previous
-// solutions: phi <- 3 phi(t) - 3 phi(t-1) + phi(t-2) with two of them,
-// 2 phi(t) - phi(t-1) with one; the FP32 copies follow, and the history
-// shifts: prev = [phi(t), phi(t-1)]
+// solutions (fp32::extrapolate_node; with flow, kb_advect does this)
 __global__ void kb_extrapolate(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst, int T,
                                int Ntot, const uint32_t *__restrict__ mask, double *__restrict__ phi,
                                double *__restrict__ prev, float *__restrict__ phi32, float *__restrict__ phi_lo,

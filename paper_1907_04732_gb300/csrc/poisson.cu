@@ -6,19 +6,24 @@
 // with Eq. SOR and keeps the converged potential; here the same fixed point is
 // reached by iterative refinement:
 //
-//   round:  res = 4 pi l_B rho_el + lap_mod(phi)      (FP64, from FP64 phi)
+//   round:  res = 4 pi l_B rho_el + lap_mod(phi)      (FP64 in the FP64 form;
+//           in the FP32 form float-float arithmetic on phi = hi + lo)
 //           stop when max_r |res(r)|/diag(r) <= poisson_tol
-//           solve A e = res approximately by Jacobi-preconditioned conjugate
-//           gradients (T = double in the FP64 form, float in the FP32 form)
+//           solve A e = res approximately by preconditioned conjugate
+//           gradients (FP64 and Jacobi in the FP64 form; FP32 and the
+//           multigrid V-cycle of mg.cu in the FP32 form)
 //           phi += e                                  (FP64)
 //
-// The CG is the Chronopoulos-Gear variant: both inner products of an
-// iteration come from one reduction phase, so an iteration is three kernels
-// (vector update, stencil + dot products, scalar recurrence).  The whole solve
-// is one CUDA graph: a device-side `while` over refinement rounds containing a
-// `while` over CG iterations; kernels set the loop conditions, bounded by the
-// round limit and poisson_max_iter.  Where conditional graph nodes are not
-// available the same kernels run from a host loop that polls the device.
+// Each step starts from the extrapolation in time of the previous solutions
+// (fp32::extrapolate_node).  The CG is the Chronopoulos-Gear variant: both
+// inner products of an iteration come from one reduction phase, so an
+// iteration is the vector update (k_cg_a), the preconditioner, and the
+// stencil with the dot products (k_cg_b, whose last block runs the scalar
+// recurrence).  The whole solve is one CUDA graph: a device-side `while`
+// over refinement rounds containing a `while` over CG iterations; kernels set
+// the loop conditions, bounded by the round limit and poisson_max_iter.
+// Where conditional graph nodes are not available the same kernels run from
+// a host loop that polls the device.
 //
 // Reductions are deterministic: each block reduces in a fixed tree order and
 // writes one partial; a single block sums the partials in block order.
