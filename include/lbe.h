@@ -44,8 +44,9 @@ extern "C" {
 #define LBE_ERR_GEOMETRY (-6)   /* fluid node on a non-periodic face, bad id */
 
 #define LBE_FP64 0 /* all state and arithmetic in FP64 */
-#define LBE_FP32 1 /* FP32 deviations from the rest state, FP64 Poisson
-                      residual/refinement and FP64 reductions */
+#define LBE_FP32 1 /* FP32 deviations from the rest state, int64 fixed-point
+                      solute, FP64 potential refined on a float-float
+                      residual, FP64 reductions */
 
 #define LBE_MAX_SPECIES 4
 #define LBE_MAX_ELECTRODES 16
@@ -123,8 +124,11 @@ int lbe_init(lbe_handle *h);
 /* Advance nsteps LBE time steps.  One step: link fluxes of Eq. LF2 and the
  * solvent force, BGK collision with forcing (Eq. LBpop) and streaming with
  * bounce-back, advection, then the Poisson solve of Eq. SOR's fixed point
- * with the modified Laplacian of Eq. DiscreteLaplacianModif.  Returns
- * LBE_ERR_NOCONVERGE if a Poisson solve reached poisson_max_iter. */
+ * with the modified Laplacian of Eq. DiscreteLaplacianModif, started from
+ * the extrapolation in time of the previous steps' potentials (the converged
+ * potential does not depend on the start).  The steps of one call run
+ * without host synchronisation; the solves' status is read once at the end.
+ * Returns LBE_ERR_NOCONVERGE if a Poisson solve reached poisson_max_iter. */
 int lbe_step(lbe_handle *h, int nsteps);
 
 /* Induced charge of every electrode, Eq. Qelec, from the current potential:
@@ -142,9 +146,11 @@ int lbe_fields(lbe_handle *h, int which, void *out, int out_on_device);
  * potential on solid nodes is reset to the electrode potentials. */
 int lbe_set_state(lbe_handle *h, const double *n, const double *phi, int on_device);
 
-/* Checkpoint: the complete dynamic state as an opaque blob.  With blob NULL,
+/* Checkpoint: the complete dynamic state (including the earlier potentials
+ * the next solve extrapolates from) as an opaque blob.  With blob NULL,
  * *size receives the needed size.  lbe_load_state restores a blob written by
- * a handle with the same parameters and geometry. */
+ * a handle with the same parameters and geometry, built with the same
+ * extrapolation order. */
 int lbe_save_state(lbe_handle *h, void *blob, size_t *size);
 int lbe_load_state(lbe_handle *h, const void *blob, size_t size);
 
