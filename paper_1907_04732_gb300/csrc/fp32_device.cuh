@@ -75,17 +75,17 @@ __device__ __forceinline__ void gather32(int N, int r, const Offs &o, uint32_t m
 // species (Eq. LF2, relative form) and the link excess flux gs summed over
 // them.  A fixed rounding sequence: evaluated from the other end the link
 // gives exactly -J0, -J1, -gs.
-__device__ __forceinline__ void link_salt11(const P32 &P, int N, int r2, float phi0, float ec, float il,
-                                            const float nu0[2], const int64_t *__restrict__ q,
-                                            const float *__restrict__ phi, float &J0, float &J1, float &gs) {
-  const float dphi = __fsub_rn(__fsub_rn(phi[r2], phi0), ec);
+__device__ __forceinline__ void link_salt11_nu(const P32 &P, float phi0, float phi2, float ec, float il,
+                                               const float nu0[2], const float nu2[2], float &J0, float &J1,
+                                               float &gs) {
+  const float dphi = __fsub_rn(__fsub_rn(phi2, phi0), ec);
   float P1, M1;
   em1_pair(dphi, P1, M1);
   gs = 0.f;
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const float Pk = k == 0 ? P1 : M1, Mk = k == 0 ? M1 : P1;
-    const float nu1 = __fmul_rn(P.s[k], ll2f(q[k * N + r2]));
+    const float nu1 = nu2[k];
     const float a1 = nE(P.rb[k], nu1, Pk), a0 = nE(P.rb[k], nu0[k], Mk);
     const float J = __fsub_rn(tterm(a1, nu1), tterm(a0, nu0[k]));  // t1 - t0, exactly odd under link reversal
     if (k == 0) J0 = J;
@@ -93,6 +93,13 @@ __device__ __forceinline__ void link_salt11(const P32 &P, int N, int r2, float p
     // link excess flux g = j/d + (n' - n)/|c| = -(n' (e^mu - 1) - n (e^-mu - 1))/(2|c|)
     gs = __fmaf_rn(-(il * 0.5f), __fsub_rn(a1, a0), gs);
   }
+}
+// the same with the neighbour's solute read from q (nu = s q)
+__device__ __forceinline__ void link_salt11(const P32 &P, int N, int r2, float phi0, float ec, float il,
+                                            const float nu0[2], const int64_t *__restrict__ q,
+                                            const float *__restrict__ phi, float &J0, float &J1, float &gs) {
+  const float nu2[2] = {__fmul_rn(P.s[0], ll2f(q[r2])), __fmul_rn(P.s[1], ll2f(q[N + r2]))};
+  link_salt11_nu(P, phi0, phi[r2], ec, il, nu0, nu2, J0, J1, gs);
 }
 
 // The quantised solute update and the force of link i (1:1 salt) from its
