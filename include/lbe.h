@@ -210,7 +210,7 @@ int lbe_profile_end(lbe_handle *h, lbe_profile *out);
  * Batched FP32 form: many independent lattices ("instances", each with its
  * own size, geometry, voltages, Debye length and diffusivities) advanced
  * together.  The instances' state is concatenated in device memory; every
- * kernel of a step is one persistent launch over all instances (tiles of 256
+ * kernel of a step is one persistent launch over all instances (tiles of 1024
  * consecutive nodes of one instance), and a whole step -- fused flux and
  * collide-stream sweep, advection, Poisson solve with per-instance
  * convergence -- runs as one CUDA graph launch.  The arithmetic per node is
@@ -236,9 +236,11 @@ int lbe_batch_set_geometry(lbe_batch *b, int i, const uint8_t *node_id, int n_el
 /* Potentials of instance i's electrodes: psi host, n_electrodes doubles.
  * Before lbe_batch_init (LBE_ERR_STATE after). */
 int lbe_batch_set_voltage(lbe_batch *b, int i, const double *psi);
-/* Equilibrium start of every instance (as lbe_init), the persistent grid
- * picked by timing candidate grids (autotuner), and the first Poisson
- * solves.  Every instance needs a geometry first. */
+/* Equilibrium start of every instance (as lbe_init), the multigrid
+ * hierarchies (with each coarsest operator inverted on the host where it is
+ * positive definite), the persistent grid picked by timing candidate grids
+ * (autotuner), and the first Poisson solves.  Every instance needs a
+ * geometry first. */
 int lbe_batch_init(lbe_batch *b);
 /* nsteps time steps of every instance; synchronises once at the end to read
  * the Poisson status (LBE_ERR_NOCONVERGE / LBE_ERR_NONFINITE if any
