@@ -106,7 +106,9 @@ const char *lbe_last_error(const lbe_handle *h);
  * electrode regions of Figs. 2 and 7).  node_id has N bytes: 0 = fluid node,
  * e in 1..n_electrodes = solid node of electrode e.  on_device selects where
  * node_id lives.  Fails with LBE_ERR_GEOMETRY if an id exceeds n_electrodes
- * or a fluid node lies on a non-periodic face. */
+ * or a fluid node lies on a non-periodic face.  In the FP32 form it also
+ * builds the multigrid hierarchy of the Poisson preconditioner and inverts
+ * its coarsest operator on the host (synchronising the stream). */
 int lbe_set_geometry(lbe_handle *h, const uint8_t *node_id, int n_electrodes, int on_device);
 
 /* Electrode potentials psi_e (reduced, host array of n_electrodes doubles).
