@@ -458,8 +458,8 @@ __global__ void kb_solve_reset(int n, InstCtl *c, BatchCtl *b, int *hist, int se
   if (i == 0) b->solves += 1;
 }
 
-// FP64 residual of the instances still solving; seeds their CG (r, u =
-// r/diag, x = p = s = 0); per-tile max |r|/diag
+// Residual (float-float, phi = hi + lo) of the instances still solving;
+// seeds their CG (r, u = r/diag, x = p = s = 0); per-tile max |r|/diag
 __global__ void __launch_bounds__(kBlock) kb_res(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
                                                  int T, int Ntot, const uint32_t *__restrict__ mask,
                                                  const int64_t *__restrict__ qn, const float *__restrict__ phi_hi,

@@ -14,7 +14,10 @@
 //               is symmetric)
 //   correction  e += alpha P e_c, alpha > 1 compensating the stiffness of
 //               piecewise-constant coarse spaces
-//   coarsest    a fixed number of Jacobi sweeps in one thread block
+//   coarsest    solved exactly with its inverse (formed on the host at
+//               set-up, coarse_inverse) where the operator is positive
+//               definite, else a fixed number of Jacobi sweeps in one
+//               thread block
 //
 // A coarse level is an MgLevel; its operator is stored component-major with
 // component stride S (S = N for one lattice, the level's total node count
