@@ -204,8 +204,28 @@ def cpu_baseline(w, tol, budget_s=15.0):
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", 0)) or os.cpu_count()
     return {"value": sub.nodes * steps / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu": cpu_model(),
             "sample": f"{steps} FP64 oracle steps of the {sub.shape[0]}x{sub.shape[1]}x{sub.shape[2]} "
                       f"periodic section of {w.name} after its init ({dt:.1f} s, OpenMP)"}
+
+
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (x86: model name; Arm: the
+    implementer and part codes), with the machine type."""
+    import platform
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k, _, v = ln.partition(":")
+                k, v = k.strip(), v.strip()
+                if k in ("model name", "CPU implementer", "CPU part") and k not in fields:
+                    fields[k] = v
+    except OSError:
+        pass
+    name = fields.get("model name") or " ".join(f"{k} {fields[k]}" for k in ("CPU implementer", "CPU part")
+                                                if k in fields)
+    return f"{platform.machine()} {name}".strip()
 
 
 def run_reference(args, w):
@@ -480,6 +500,7 @@ def main():
     step_bytes = sweep_bytes + adv_bytes
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "value_fluid_nodes": whole_job_mlups(world, fluid, args.steps, ms * 1e-3),
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": w.name, "lattice": list(w.shape), "nodes": w.nodes, "fluid_nodes": fluid,
