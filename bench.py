@@ -209,6 +209,22 @@ def cpu_baseline(w, tol, budget_s=15.0):
                       f"periodic section of {w.name} after its init ({dt:.1f} s, OpenMP)"}
 
 
+def cpu_baseline_single_thread(w, tol, budget_s=5.0):
+    """The same oracle timing on one host thread (a child process with
+    OMP_NUM_THREADS=1); None if it cannot run."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "from paper_1907_04732_gb300 import workloads as wl; "
+            "w = [x for x in [wl.eof_plates()] if x.name == %r]; "
+            "print(json.dumps(bench.cpu_baseline(w[0], %r, %r)['value']) if w else 'null')"
+            % (os.path.dirname(os.path.abspath(__file__)), w.name, tol, budget_s))
+    try:
+        p = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, OMP_NUM_THREADS="1"),
+                           capture_output=True, text=True, timeout=120)
+        return json.loads(p.stdout.strip().splitlines()[-1]) if p.returncode == 0 else None
+    except Exception:
+        return None
+
+
 def cpu_model() -> str:
     """The host CPU as /proc/cpuinfo names it (x86: model name; Arm: the
     implementer and part codes), with the machine type."""
@@ -544,6 +560,7 @@ def main():
         line["adjoint"] = adjoint_leg(args, lbe, torch, stream)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.tol)
+        line["cpu_baseline"]["single_thread_value"] = cpu_baseline_single_thread(w, args.tol)
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
