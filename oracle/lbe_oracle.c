@@ -86,6 +86,7 @@ typedef struct {
   int ns;
   double z[ORC_MAXS], D[ORC_MAXS], rho_bulk[ORC_MAXS];
   double e_app[3];
+  double g_body[3];   /* external body force density on the solvent (0 unless set) */
   int flow;
   double tol;
   int maxit;
@@ -336,7 +337,7 @@ static void ion_fluxes(const orc *o, double *nstar, double *F) {
       }
       for (int a = 0; a < 3; ++a) force[a] += CV[i][a] * g;
     }
-    for (int a = 0; a < 3; ++a) F[(size_t)a * N + r] = force[a] / (2.0 * A0);
+    for (int a = 0; a < 3; ++a) F[(size_t)a * N + r] = force[a] / (2.0 * A0) + o->g_body[a];
   }
 }
 
@@ -514,6 +515,15 @@ int orc_fields(orc *o, int which, double *out) {
     return 0;
   }
   return -1;
+}
+
+/* A uniform external body force density g on the solvent, added on every
+ * fluid node to the ion force of step 2 (the force term of Eq. LBpop does not
+ * care where the force comes from).  Zero unless set; it lets the pins drive
+ * the lattice Boltzmann part alone (Poiseuille flow, momentum budget). */
+int orc_set_body_force(orc *o, const double *g) {
+  for (int a = 0; a < 3; ++a) o->g_body[a] = g[a];
+  return 0;
 }
 
 /* Overwrite the dynamic state (any pointer may be NULL to keep it). */

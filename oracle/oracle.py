@@ -62,6 +62,7 @@ def _load():
     lib.orc_laplacian.argtypes = [vp, dp, dp]
     lib.orc_poisson.argtypes = [vp, dp]
     lib.orc_set_state.argtypes = [vp, dp, dp, dp]
+    lib.orc_set_body_force.argtypes = [vp, dp]
     lib.orc_force.argtypes = [vp, dp]
     lib.orc_advect.argtypes = [vp, dp, dp, dp]
     lib.orc_last_iters.argtypes = [vp]
@@ -183,6 +184,13 @@ class Oracle:
         self.lib.orc_set_state(self.h, _dp(f) if f is not None else nul,
                                _dp(n) if n is not None else nul,
                                _dp(phi) if phi is not None else nul)
+
+    def set_body_force(self, g):
+        """Uniform external body force density on the solvent (3 values),
+        added to the ion force; zero unless set."""
+        self._g = np.ascontiguousarray(np.asarray(g, dtype=np.float64))
+        assert self._g.size == 3
+        self.lib.orc_set_body_force(self.h, _dp(self._g))
 
     def force(self) -> np.ndarray:
         out = np.zeros(3 * self.N)

@@ -353,3 +353,126 @@ def test_plate_eof_profile():
     ref = an.dh_plate_eof(zc, L, 1 / lam, eps, eta, E, dV)
     uref = eps * E * dV / eta
     assert np.abs(ux - ref).max() < 0.04 * uref, (np.abs(ux - ref).max() / uref)
+
+
+# ---------------------------------------------------------------------------
+# The lattice Boltzmann part away from tau = 1 (Eq. LBpop with BGK relaxation
+# 1/tau, second-order equilibrium, Guo forcing, halfway bounce-back).  At
+# tau = 1 the relaxation erases the pre-collision populations and the Guo
+# prefactor (1 - 1/(2 tau)) equals several plausible mis-writings of it, so
+# these pins run at tau in {0.7, 1.3, 1.8} as well.
+_CV = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1), (1, 1, 0),
+       (-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 0, 1), (-1, 0, -1), (1, 0, -1), (-1, 0, 1), (0, 1, 1),
+       (0, -1, -1), (0, 1, -1), (0, -1, 1)]  # the oracle's population order
+_W = [1 / 3] + [1 / 18] * 6 + [1 / 36] * 12
+
+
+def _fluid_box(shape, tau):
+    """A periodic box of neutral 1:1 salt without electrodes: uniform ions,
+    zero potential, no ion force -- the solvent alone."""
+    nx, ny, nz = shape
+    o = Oracle(shape, (1, 1, 1), tau=tau, bjerrum=1.0, rho_bulk=(0.01, 0.01), flow=True, tol=1e-14)
+    o.set_geometry(np.zeros((nz, ny, nx), np.uint8), 0)
+    o.set_voltage([])
+    o.init()
+    return o
+
+
+def _shear_wave(tau, L, U=0.0, amp=1e-4, steps=200):
+    """Transverse wave u_x = amp sin(k z) (k = 2 pi / L) carried by a uniform
+    flow U along z; returns (decay rate per step, phase speed) measured over
+    the last 100 steps.  The start is the first-order state w_i (1 + 3 c.u);
+    its non-hydrodynamic part dies out within a few steps."""
+    o = _fluid_box((1, 1, L), tau)
+    z = np.arange(L)
+    k = 2 * math.pi / L
+    ux, uz = amp * np.sin(k * z), np.full(L, U)
+    f = np.zeros((19, L, 1, 1))
+    for i, c in enumerate(_CV):
+        f[i, :, 0, 0] = _W[i] * (1 + 3 * (c[0] * ux + c[2] * uz))
+    o.set_state(f=f)
+    a = []
+    for _ in range(steps):
+        a.append(np.sum(o.u()[0, :, 0, 0] * np.exp(-1j * k * z)) * 2 / L)
+        o.step(1)
+    r = np.array(a[steps - 99:]) / np.array(a[steps - 100:-1])
+    return -np.log(np.abs(r)).mean(), -np.angle(r).mean() / k
+
+
+@pytest.mark.parametrize("tau", [0.7, 1.0, 1.3, 1.8])
+def test_shear_wave_viscosity_and_galilean_advection(tau):
+    """A shear wave decays at nu k^2 with the kinematic viscosity
+    nu = (tau - 1/2)/3 of the BGK collision, up to O(k^2) relative (the
+    error falls by 4 when L doubles); carried by a uniform flow it moves at
+    that flow's speed (the momentum flux rho u u of the second-order
+    equilibrium)."""
+    nu = (tau - 0.5) / 3.0
+    err = {}
+    for L in (32, 64):
+        rate, _ = _shear_wave(tau, L)
+        err[L] = rate / (nu * (2 * math.pi / L) ** 2) - 1.0
+    assert abs(err[64]) < 6e-3, err
+    if tau != 1.0:  # at tau = 1 both errors are ~1e-6
+        assert 3.5 < err[32] / err[64] < 4.5, err
+    rate, speed = _shear_wave(tau, 64, U=0.05)
+    assert abs(speed / 0.05 - 1.0) < 1e-3, speed
+    assert abs(rate / (nu * (2 * math.pi / 64) ** 2) - 1.0) < 2e-2, rate  # O(U^2) Galilean error
+
+
+def _poiseuille(tau, H, g=1e-6):
+    """Steady flow driven by a uniform body force g along x between the
+    electrode layers z = 0 and z = H+1 (both at potential 0, halfway
+    bounce-back), run for 30 times the slowest decay time H^2/(pi^2 nu)."""
+    nz = H + 2
+    ids = np.zeros((nz, 1, 1), np.uint8)
+    ids[0], ids[-1] = 1, 2
+    o = Oracle((1, 1, nz), (1, 1, 0), tau=tau, bjerrum=1.0, rho_bulk=(0.01, 0.01), flow=True, tol=1e-14)
+    o.set_geometry(ids, 2)
+    o.set_voltage([0.0, 0.0])
+    o.init()
+    o.set_body_force([g, 0.0, 0.0])
+    nu = (tau - 0.5) / 3.0
+    o.step(int(30 * H * H / (math.pi ** 2 * nu)))
+    return o.u()[0, 1:-1, 0, 0], nu
+
+
+@pytest.mark.parametrize("tau", [0.7, 1.0, 1.3, 1.8])
+def test_body_force_poiseuille(tau):
+    """Plane Poiseuille flow (the textbook special case for the forcing and
+    the walls): the steady profile has the curvature -g/(rho nu) of the
+    Navier-Stokes solution exactly (a unidirectional flow has no other term),
+    and it equals the parabola vanishing at the halfway walls z = 1/2 and
+    z = H + 1/2 up to the constant slip of bounce-back, whose share of the
+    centre velocity falls as 1/H^2."""
+    g = 1e-6
+    dev = {}
+    for H in (16, 32):
+        u, nu = _poiseuille(tau, H, g)
+        curv = u[2:] - 2 * u[1:-1] + u[:-2]
+        np.testing.assert_allclose(curv, -g / nu, rtol=1e-8)
+        z = np.arange(1, H + 1)
+        exact = g / (2 * nu) * (z - 0.5) * (H + 0.5 - z)
+        dev[H] = (u - exact).max() / exact.max()
+        assert np.ptp(u - exact) < 1e-9 * exact.max()  # a constant slip
+    assert abs(dev[32]) < 1e-2, dev
+    if tau != 1.0:
+        assert 3.8 < dev[16] / dev[32] < 4.2, dev
+
+
+@pytest.mark.parametrize("tau", [0.7, 1.3])
+def test_body_force_momentum_budget(tau):
+    """With Guo forcing and u = (sum f c + F/2)/rho, each step adds exactly
+    F to the momentum of every node, whatever tau: after t steps from rest a
+    periodic box holds t N g (the flow is uniform, so collisions move
+    nothing)."""
+    o = _fluid_box((3, 2, 4), tau)
+    g = np.array([2e-5, -1e-5, 3e-5])
+    o.set_body_force(g)
+    t = 40
+    o.step(t)
+    f = o.populations().reshape(19, -1)
+    mom = np.array([sum(c[a] * f[i].sum() for i, c in enumerate(_CV)) for a in range(3)])
+    np.testing.assert_allclose(mom, t * 24 * g, rtol=1e-11)
+    # the velocity read-out includes the half-step force
+    np.testing.assert_allclose(o.u().reshape(3, -1), ((t + 0.5) * g)[:, None] / o.rho().reshape(1, -1),
+                               rtol=1e-10)
