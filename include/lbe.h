@@ -173,7 +173,9 @@ int lbe_get_stats(const lbe_handle *h, lbe_stats *out);
  * for instance during CUDA stream capture.)
  *   phi      device, N doubles: potential of every node (solid nodes hold
  *            their electrode potential), layout as lbe_fields(LBE_FIELD_PHI)
- *   node_id  device, N bytes: 0 fluid, e = 1..n_electrodes electrode e
+ *   node_id  device, N bytes: 0 fluid, e = 1..n_electrodes electrode e; an
+ *            id above n_electrodes is not checked: such a node counts as
+ *            solid for its neighbours and its own charge is not reported
  *   nx,ny,nz lattice size (nx*ny*nz < 2^31); periodic[3] host flags
  *   bjerrum  l_B > 0; q_out device, n_electrodes doubles (written)
  *   cuda_stream  stream the work is ordered on (NULL = legacy stream)
@@ -182,7 +184,9 @@ int lbe_get_stats(const lbe_handle *h, lbe_stats *out);
  * library keeps until the process exits; any lattice size fits it, while
  * n_electrodes above LBE_MAX_ELECTRODES is rejected with LBE_ERR_ARG.  The
  * first call on a device looks up that array's device address (and caches
- * it), so make that first call outside any stream capture.  Every call
+ * it for the life of the process), so make that first call outside any
+ * stream capture, and do not reset the device (cudaDeviceReset) between
+ * calls: the cached address would then be stale.  Every call
  * rewrites the partials it reads, but all calls share the one array: calls
  * that can overlap on the GPU (different streams, or threads without
  * ordering) race and must be serialised by the caller.  Returns LBE_OK,

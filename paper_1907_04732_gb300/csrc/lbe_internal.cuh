@@ -140,6 +140,11 @@ __device__ __forceinline__ Offs offsets_of(const Geo &g, int x, int y, int z) {
   return o;
 }
 
+// A term of a max |residual| stopping test with NaN read as +infinity: fmax
+// drops NaN operands, so a NaN residual would otherwise vanish from the test.
+__device__ __forceinline__ float finite_or_inf(float v) { return v == v ? v : __int_as_float(0x7f800000); }
+__device__ __forceinline__ double finite_or_inf(double v) { return v == v ? v : __longlong_as_double(0x7ff0000000000000LL); }
+
 __device__ __forceinline__ int flat_tid() {
   return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
 }
@@ -176,6 +181,8 @@ struct P32 {
   double rbd[LBE_MAX_SPECIES], sd[LBE_MAX_SPECIES];
   float kq1[LBE_MAX_SPECIES], kq2[LBE_MAX_SPECIES];  // -d_k/(2|c| s_k), |c| = 1, sqrt 2
   float ec[kQ];                                      // E_app . c_i, ec[opp] = -ec
+  float kem[kQ], kep[kQ];                            // e^{-E.c_i} - 1, e^{E.c_i} - 1 (link factors)
+  int field;                                         // E_app != 0
   float omega, guo, inv_2a0;
   int salt11;  // two species, z = +1 and -1, equal bulk concentrations
 };
@@ -283,6 +290,7 @@ struct lbe_handle {
   float *phi_lo = nullptr;             // low part: phi = phi32 + phi_lo to ~2^-48
   float *u32 = nullptr;                // velocity of the last collision
   int *flag = nullptr;                 // device error flags (fixed-point range)
+  float4 *lf = nullptr;                // 1:1 salt link records, 2 per node (fp32::link_factors)
   float *pw32 = nullptr;               // FP32 Poisson work: res, p, q, e [4][N]
 
   // profiling (lbe_profile_begin/end): events [sweep start, sweep end,

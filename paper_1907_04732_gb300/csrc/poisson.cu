@@ -176,7 +176,7 @@ __device__ void cg_scalars(PoissonCtl *c, double gam, double del, double mx, dou
     c->total_iters += 1;
     if (mx <= fmax(eta * c->res0, tol_abs)) {
       done = 1;
-    } else if (!(mx == mx) || !(del == del)) {
+    } else if (!(mx == mx) || mx > 1e300 || !(del == del)) {
       done = 1;
       c->status = LBE_ERR_NONFINITE;
       c->outer_done = 1;
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys
       r[i] = (T)rt;
       u[i] = (T)(rt * dinv);
       x[i] = p[i] = s[i] = (T)0;
-      mx = fmaxf(mx, fabsf(rt) * dinv);
+      mx = fmaxf(mx, finite_or_inf(fabsf(rt) * dinv));
       continue;
     }
     if (MODE == R_RHS_FF) {
@@ -274,8 +274,8 @@ __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys
       r[i] = (T)rt;
       u[i] = (T)(rt * dinv);
       x[i] = p[i] = s[i] = (T)0;
-      mx = fmaxf(mx, fabsf(rt) * dinv);
-      mb = fmaxf(mb, fabsf(bf) * dinv);
+      mx = fmaxf(mx, finite_or_inf(fabsf(rt) * dinv));
+      mb = fmaxf(mb, finite_or_inf(fabsf(bf) * dinv));
       continue;
     }
     double b;
@@ -296,8 +296,8 @@ __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys
     r[i] = rt;
     u[i] = rt * dinv;
     x[i] = p[i] = s[i] = (T)0;
-    mx = fmaxf(mx, fabsf((float)rr) * (float)dinv);  // the stopping test needs no FP64
-    if (MODE == R_RHS) mb = fmaxf(mb, fabsf((float)b) * (float)dinv);
+    mx = fmaxf(mx, finite_or_inf(fabsf((float)rr) * (float)dinv));  // the stopping test needs no FP64
+    if (MODE == R_RHS) mb = fmaxf(mb, finite_or_inf(fabsf((float)b) * (float)dinv));
   }
   mx = block_reduce<true, float>(mx);
   if (flat_tid() == 0) part[S_MAX * nblk + flat_bid()] = (double)mx;
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_a(const Geo g, int zpt, uint32_t 
     r[i] = rv;
     const T dinv = (T)1 / diag_t<T>(m, selfmask);
     u[i] = rv * dinv;
-    mx = fmax(mx, fabs(rv) * dinv);
+    mx = fmax(mx, finite_or_inf(fabs(rv) * dinv));
   }
   const T v = block_reduce<true, T>(mx);
   if (flat_tid() == 0) part[S_MAX * nblk + flat_bid()] = (double)v;

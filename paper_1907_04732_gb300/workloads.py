@@ -77,15 +77,22 @@ def random_blobs(nx: int, ny: int, nz: int, n_elec: int, fill: float, seed: int)
     directions periodic)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     ids = np.zeros((nz, ny, nx), dtype=np.uint8)
-    zz, yy, xx = np.mgrid[0:nz, 0:ny, 0:nx]
     target = int(fill * ids.size)
-    while (ids > 0).sum() < target:
+    solid = 0
+    while solid < target:
         c = rng.integers(0, [nz, ny, nx])
         r = rng.uniform(0.8, 2.5)
         e = rng.integers(1, n_elec + 1)
-        d2 = ((zz - c[0] + nz // 2) % nz - nz // 2) ** 2 + ((yy - c[1] + ny // 2) % ny - ny // 2) ** 2 \
-            + ((xx - c[2] + nx // 2) % nx - nx // 2) ** 2
-        ids[(d2 <= r * r) & (ids == 0)] = e
+        # the ball touches only nodes within 2 of its centre (r < 2.5);
+        # periodic distances as the minimum image
+        win = [np.unique(np.arange(c[a] - 2, c[a] + 3) % n) for a, n in enumerate((nz, ny, nx))]
+        dd = [((w - c[a] + n // 2) % n - n // 2) ** 2 for a, (w, n) in enumerate(zip(win, (nz, ny, nx)))]
+        d2 = dd[0][:, None, None] + dd[1][None, :, None] + dd[2][None, None, :]
+        sub = ids[np.ix_(*win)]
+        hit = (d2 <= r * r) & (sub == 0)
+        sub[hit] = e
+        ids[np.ix_(*win)] = sub
+        solid += int(hit.sum())
     return ids
 
 

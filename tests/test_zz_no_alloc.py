@@ -14,18 +14,29 @@ from paper_1907_04732_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 
+def _case(name):
+    if name == "blob_23x18x15":
+        ids = wl.random_blobs(23, 18, 15, 2, 0.2, seed=21)
+        return wl.Workload("blob", ids, 2, (1, 1, 1), (-0.05, 0.3), 1.2, 2.5, e_app=(1e-3, 0.0, 0.0))
+    # parallel plates, z not periodic (links leaving the box are skipped);
+    # 331,776 nodes: more than the 1024 x 256 threads of the static grid, so
+    # every block strides over several nodes
+    return wl.Workload("plates", wl.plates(72, 72, 64), 2, (1, 1, 0), (0.0, 0.2), 1.44, 8.0,
+                       e_app=(1e-3, 0.0, 0.0))
+
+
+@pytest.mark.parametrize("case", ["blob_23x18x15", "plates_72x72x64"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_static_charge_matches_lattice_charge(lbe, precision):
+def test_static_charge_matches_lattice_charge(lbe, precision, case):
     import torch
-    ids = wl.random_blobs(23, 18, 15, 2, 0.2, seed=21)
-    w = wl.Workload("blob", ids, 2, (1, 1, 1), (-0.05, 0.3), 1.2, 2.5, e_app=(1e-3, 0.0, 0.0))
+    w = _case(case)
     prec = lbe.LBE_FP32 if precision == "fp32" else lbe.LBE_FP64
     lat = lbe.Lattice.from_workload(w, precision=prec, tol=1e-13)
     lat.init()
     lat.step(8)
     q_ref = lat.charge()
     phi = lat.field(lbe.FIELD_PHI, device=True).contiguous()
-    node_id = torch.from_numpy(np.ascontiguousarray(ids.reshape(-1))).to("cuda")
+    node_id = torch.from_numpy(np.ascontiguousarray(w.ids.reshape(-1))).to("cuda")
     outs = []
     for _ in range(2):
         q = torch.full((w.n_elec,), float("nan"), dtype=torch.float64, device="cuda")
