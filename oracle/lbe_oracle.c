@@ -87,6 +87,7 @@ typedef struct {
   double z[ORC_MAXS], D[ORC_MAXS], rho_bulk[ORC_MAXS];
   double e_app[3];
   double g_body[3];   /* external body force density on the solvent (0 unless set) */
+  int node_rule;      /* 1: the first-order rule (solid nodes at psi, plain Laplacian) */
   int flow;
   double tol;
   int maxit;
@@ -190,6 +191,15 @@ int orc_set_voltage(orc *o, const double *psi) {
 }
 
 /* ---------------------------------------------------------------------- */
+/* Link factor of the Laplacian: 1 + |chi(r+c_i) - chi(r)| in Eq.
+ * DiscreteLaplacianModif; 1 on every link under the first-order rule that
+ * the paper describes before it (Eq. DiscreteLaplacian, solid nodes simply
+ * held at their potential, which puts the interface on the solid node). */
+static double link_factor(const orc *o, long r, long r2) {
+  if (o->node_rule) return 1.0;
+  return 1.0 + fabs((double)solid(o, r2) - (double)solid(o, r));
+}
+
 /* Eq. DiscreteLaplacianModif: (2/c_s^2) sum_i w_i [phi(r+c_i) - phi(r)] *
  * [1 + |chi(r+c_i) - chi(r)|], evaluated at any node r.  Links that leave a
  * non-periodic box are skipped (they only exist at solid faces and join
@@ -199,7 +209,7 @@ static double laplacian_at(const orc *o, const double *phi, size_t r) {
   for (int i = 1; i < ORC_Q; ++i) {
     long r2 = nbr(o, r, i);
     if (r2 < 0) continue;
-    double factor = 1.0 + fabs((double)solid(o, r2) - (double)solid(o, (long)r));
+    double factor = link_factor(o, (long)r, r2);
     s += (2.0 / CS2) * weight(i) * (phi[r2] - phi[r]) * factor;
   }
   return s;
@@ -225,7 +235,7 @@ static double diag_at(const orc *o, size_t r) {
   for (int i = 1; i < ORC_Q; ++i) {
     long r2 = nbr(o, r, i);
     if (r2 < 0 || (size_t)r2 == r) continue;
-    double factor = 1.0 + fabs((double)solid(o, r2) - (double)solid(o, (long)r));
+    double factor = link_factor(o, (long)r, r2);
     d += (2.0 / CS2) * weight(i) * factor;
   }
   return d;
@@ -471,8 +481,9 @@ int orc_step(orc *o, int nsteps) {
 }
 
 /* Eq. Qelec: Q_e = -(1/(4 pi l_B)) sum_{r in e} laplacian(phi)(r), with the
- * modified Laplacian; only links from electrode e to fluid nodes are taken
- * (links between two electrodes carry no induced charge of either). */
+ * modified Laplacian (the plain one under the first-order rule); only links
+ * from electrode e to fluid nodes are taken (links between two electrodes
+ * carry no induced charge of either). */
 int orc_charge(const orc *o, double *q) {
   double eps = 1.0 / (4.0 * M_PI * o->bjerrum);
   for (int e = 0; e < o->n_elec; ++e) q[e] = 0.0;
@@ -483,7 +494,7 @@ int orc_charge(const orc *o, double *q) {
     for (int i = 1; i < ORC_Q; ++i) {
       long r2 = nbr(o, r, i);
       if (r2 < 0 || o->id[r2]) continue;
-      s += (2.0 / CS2) * weight(i) * (o->phi[r2] - o->phi[r]) * 2.0;
+      s += (2.0 / CS2) * weight(i) * (o->phi[r2] - o->phi[r]) * link_factor(o, (long)r, r2);
     }
     q[e - 1] += -eps * s;
   }
@@ -515,6 +526,15 @@ int orc_fields(orc *o, int which, double *out) {
     return 0;
   }
   return -1;
+}
+
+/* Boundary rule of the Poisson solve: 0 (default) the paper's rule, Eq.
+ * DiscreteLaplacianModif; 1 the first-order rule it improves on (plain Eq.
+ * DiscreteLaplacian with the solid nodes held at their potential).  Set it
+ * before orc_init. */
+int orc_set_boundary_rule(orc *o, int node_rule) {
+  o->node_rule = node_rule ? 1 : 0;
+  return 0;
 }
 
 /* A uniform external body force density g on the solvent, added on every

@@ -63,6 +63,7 @@ def _load():
     lib.orc_poisson.argtypes = [vp, dp]
     lib.orc_set_state.argtypes = [vp, dp, dp, dp]
     lib.orc_set_body_force.argtypes = [vp, dp]
+    lib.orc_set_boundary_rule.argtypes = [vp, ctypes.c_int]
     lib.orc_force.argtypes = [vp, dp]
     lib.orc_advect.argtypes = [vp, dp, dp, dp]
     lib.orc_last_iters.argtypes = [vp]
@@ -184,6 +185,12 @@ class Oracle:
         self.lib.orc_set_state(self.h, _dp(f) if f is not None else nul,
                                _dp(n) if n is not None else nul,
                                _dp(phi) if phi is not None else nul)
+
+    def set_boundary_rule(self, node_rule: int):
+        """0: the paper's rule (Eq. DiscreteLaplacianModif, the default); 1:
+        the first-order rule it replaces (plain Laplacian, solid nodes held
+        at their potential).  Call before init()."""
+        self.lib.orc_set_boundary_rule(self.h, int(node_rule))
 
     def set_body_force(self, g):
         """Uniform external body force density on the solvent (3 values),

@@ -476,3 +476,61 @@ def test_body_force_momentum_budget(tau):
     # the velocity read-out includes the half-step force
     np.testing.assert_allclose(o.u().reshape(3, -1), ((t + 0.5) * g)[:, None] / o.rho().reshape(1, -1),
                                rtol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# The first-order rule of Sec. "Imposing conducting boundary conditions" (the
+# one Eq. DiscreteLaplacianModif improves on): the plain Laplacian of Eq.
+# DiscreteLaplacian with the solid nodes held at their potential puts the
+# interface on the last solid node, so the empty capacitor's Laplace
+# solution is linear between the solid layers (gap nz - 1 instead of the
+# mid-plane gap nz - 2) and Q(0) = eps dV/(nz - 1).
+@pytest.mark.parametrize("nx,nz,psi", [(1, 20, (0.1, 0.2)), (3, 33, (-0.3, 0.25))])
+def test_first_order_rule_laplace_between_solid_layers(nx, nz, psi):
+    w = wl.plate_capacitor(nx, nx, nz, psi=psi)
+    o = make(w)
+    o.set_boundary_rule(1)
+    o.init()
+    zc = np.arange(nz, dtype=float)
+    exact = psi[0] + (psi[1] - psi[0]) * zc / (nz - 1)
+    phi = o.phi()
+    np.testing.assert_allclose(phi, np.broadcast_to(exact[:, None, None], phi.shape), rtol=0, atol=1e-12)
+    qexp = an.dielectric_plate_charge_per_area(an.eps_of(w.bjerrum), nz - 1, psi[1] - psi[0]) * nx * nx
+    np.testing.assert_allclose(o.charge(), [-qexp, qexp], rtol=1e-11)
+
+
+@pytest.mark.slow
+def test_first_order_rule_converges_first_order():
+    """The capacitance error of the first-order rule falls about as
+    dx/lambda_D (halving it divides the error by about 2), where the paper's
+    rule falls as (dx/lambda_D)^2 (the pin above its slope-2 test)."""
+    errs = []
+    for lam, L in ((3.0, 24), (6.0, 48)):
+        w = wl.plate_capacitor(1, 1, L + 2, debye=lam, bjerrum=1.0, psi=(0.0, 0.01), flow=False, D=(0.15, 0.15))
+        o = make(w)
+        o.set_boundary_rule(1)
+        o.init()
+        o.step(int(9 * L * lam / (2 * 0.15)))
+        qdh = an.dh_plate_charge_per_area(an.eps_of(1.0), 1 / lam, L, 0.01)
+        errs.append(abs(o.charge()[1] - qdh) / qdh)
+    ratio = errs[0] / errs[1]
+    assert errs[0] > 0.05 and 1.6 < ratio < 2.5, (errs, ratio)
+
+
+# ---------------------------------------------------------------------------
+# Reading c8: the steady state reached by the scheme is the discrete
+# nonlinear Poisson-Boltzmann solution (Boltzmann distributions make every
+# link flux vanish; conservation fixes their prefactors), exactly, not only
+# to O(dx^2).  The helper solves those equations by Newton's method.
+def test_oracle_steady_state_is_discrete_pb():
+    from discrete_pb import plate_column_steady
+    L, lam, lB = 32, 4.0, 1.0
+    w = wl.plate_capacitor(1, 1, L + 2, debye=lam, bjerrum=lB, psi=(0.0, 0.5), flow=False, D=(0.2, 0.2))
+    o = make(w)
+    o.init()
+    # 30 decay times of the slowest mode (salt diffusion across the gap,
+    # L^2/(pi^2 D) = 520 steps, beside the charging time L lambda/(2D) = 320)
+    o.step(16000)
+    phi, n = plate_column_steady(L, 0.0, 0.5, lB, w.rho_bulk)
+    np.testing.assert_allclose(o.phi()[1:-1, 0, 0], phi, rtol=0, atol=1e-9 * 0.5)
+    np.testing.assert_allclose(o.n()[:, 1:-1, 0, 0], n, rtol=1e-8)
