@@ -48,6 +48,9 @@ extern "C" {
                       solute, FP64 potential refined on a float-float
                       residual, FP64 reductions */
 
+#define LBE_RULE_MIDPLANE 0 /* lbe_params.boundary_rule */
+#define LBE_RULE_NODE 1
+
 #define LBE_MAX_SPECIES 4
 #define LBE_MAX_ELECTRODES 16
 
@@ -86,10 +89,19 @@ typedef struct {
   int precision;        /* LBE_FP64 or LBE_FP32 */
   double poisson_tol;   /* stop when max_r |residual(r)|/diag(r) <= tol */
   int poisson_max_iter; /* iteration cap per Poisson solve */
+  int boundary_rule;    /* LBE_RULE_MIDPLANE (default): the paper's rule, Eq.
+                           DiscreteLaplacianModif (links to solid doubled, the
+                           interface half-way between solid and fluid nodes);
+                           LBE_RULE_NODE: the first-order rule the paper starts
+                           from in Sec. "Imposing conducting boundary
+                           conditions" (plain Eq. DiscreteLaplacian, solid
+                           nodes held at their potential), for comparison;
+                           FP64 form only (LBE_ERR_ARG otherwise) */
 } lbe_params;
 
 /* Defaults: 1x1x1, periodic, tau 1, l_B 1, 1:1 salt with D = 0.05 and
- * rho = 0.01, no field, flow on, FP64, tol 1e-13, 100000 iterations. */
+ * rho = 0.01, no field, flow on, FP64, tol 1e-13, 100000 iterations, the
+ * paper's boundary rule. */
 void lbe_default_params(lbe_params *p);
 
 /* Create a lattice.  cuda_stream is a cudaStream_t (may be NULL).  On
@@ -129,8 +141,11 @@ int lbe_init(lbe_handle *h);
  * with the modified Laplacian of Eq. DiscreteLaplacianModif, started from
  * the extrapolation in time of the previous steps' potentials (the converged
  * potential does not depend on the start).  The steps of one call run
- * without host synchronisation; the solves' status is read once at the end.
- * Returns LBE_ERR_NOCONVERGE if a Poisson solve reached poisson_max_iter. */
+ * without host synchronisation, except that the solves' status is read
+ * every 1024 steps (a failed solve ends the call there) and at the end.
+ * Returns LBE_ERR_NOCONVERGE if a Poisson solve reached poisson_max_iter or
+ * a refinement round failed to halve the residual (a tolerance below what
+ * the form's arithmetic resolves). */
 int lbe_step(lbe_handle *h, int nsteps);
 
 /* Induced charge of every electrode, Eq. Qelec, from the current potential:
@@ -307,11 +322,22 @@ typedef struct {
 
 /* Forward pass for a later lbe_adjoint_backward: lbe_init, then nsteps
  * steps, keeping the state every checkpoint_every steps in device memory
- * (32 bytes per node per checkpoint, plus 20 bytes per node per step of one
- * segment during the backward pass).  q_out (host, n_electrodes doubles,
- * may be NULL) receives Q(T).  LBE_ERR_STATE when the handle is not an FP32,
+ * (48 bytes per node per checkpoint: solute, potential and the warm start's
+ * three earlier potentials; plus 20 bytes per node per step of one segment
+ * during the backward pass).  q_out (host, n_electrodes doubles, may be
+ * NULL) receives Q(T).  LBE_ERR_STATE when the handle is not an FP32,
  * flow-off, 1:1-salt lattice with a geometry. */
 int lbe_adjoint_forward(lbe_handle *h, int nsteps, int checkpoint_every, double *q_out);
+
+/* The same forward pass with the checkpoints placed by the binomial schedule
+ * of Griewank and Walther ("revolve") within device_bytes of checkpoint
+ * memory (48 bytes per node per checkpoint slot; at least two slots, the
+ * initial and the final state; LBE_ERR_ARG below).  With s = slots - 2 the
+ * backward pass recomputes every forward step at most r times, r the
+ * smallest integer with C(s + r, s) >= nsteps, and keeps no per-step states;
+ * the gradient is bitwise that of lbe_adjoint_forward.  The schedule's
+ * first checkpoints are taken during this pass, so its steps are reused. */
+int lbe_adjoint_forward_budget(lbe_handle *h, int nsteps, size_t device_bytes, double *q_out);
 
 /* Backward pass of the last lbe_adjoint_forward (LBE_ERR_STATE if the state
  * changed since): dq (host, n_electrodes weights), soft_electrode in

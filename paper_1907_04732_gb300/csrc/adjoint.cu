@@ -20,9 +20,13 @@
 //   t > 0: the flux step's transpose gives nbar^{t-1}, phibar^{t-1}, Dbar,
 //          chibar (openness)
 //   t = 0: rho_bbar += sum nbar^0, chibar -= rho_b sum_k nbar^0
-// The forward states of a step are recomputed from checkpoints taken every
-// K steps (two-level checkpointing: the states of one segment are kept while
-// it is differentiated).  Parameter sums are FP64, in a fixed order.
+// The forward states of a step are recomputed from checkpoints: either
+// taken every K steps (two-level checkpointing: the states of one segment
+// are kept while it is differentiated), or placed by the binomial schedule
+// of Griewank and Walther ("revolve") within a device-memory budget, which
+// reverses T steps with s checkpoint slots by recomputing each step at most
+// r times, r the smallest with C(s + r, s) >= T.  Parameter sums are FP64,
+// in a fixed order.
 #include <math.h>
 #include <string.h>
 
@@ -42,6 +46,10 @@ struct AdjWork {
   int T = 0, every = 0, nseg = 0, nblk = 0;
   long long gen = -1;  // handle generation after the forward pass
   bool ready = false;
+  // binomial schedule: checkpoint slots (ck_* hold nseg + 1 of them then:
+  // slot 0 the initial state, slots 1.. the forward pass's first descent,
+  // slot nseg the final state); 0 = uniform checkpoints
+  int revolve_slots = 0;
   int64_t *ck_q = nullptr;  // checkpoints [nseg + 1][2N] (the last: time T)
   double *ck_phi = nullptr;   // [nseg + 1][N]
   double *ck_prev = nullptr;  // [nseg + 1][kHist N]: the warm start's history
@@ -348,10 +356,12 @@ int afail(lbe_handle *h, int code, const std::string &m) {
     if (e_ != cudaSuccess) return afail((h), LBE_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-int adj_alloc(lbe_handle *h, int T, int every) {
+// every > 0: uniform checkpoints; every = 0: slots checkpoint slots of the
+// binomial schedule (nseg = slots - 1, no segment states)
+int adj_alloc(lbe_handle *h, int T, int every, int slots = 0) {
   AdjWork *a = h->adj;
   const long long N = h->geo.N;
-  const int nseg = T > 0 ? (T + every - 1) / every : 0;
+  const int nseg = every > 0 ? (T > 0 ? (T + every - 1) / every : 0) : slots - 1;
   const bool same = a && a->N == N && a->nseg == nseg && a->every == every;
   if (!same) {
     adjoint_free(h);
@@ -368,8 +378,10 @@ int adj_alloc(lbe_handle *h, int T, int every) {
     alloc((void **)&a->ck_q, sizeof(int64_t) * 2 * N * ns1);
     alloc((void **)&a->ck_phi, sizeof(double) * N * ns1);
     alloc((void **)&a->ck_prev, sizeof(double) * kHist * N * ns1);
-    alloc((void **)&a->st_q, sizeof(int64_t) * 2 * N * std::max(every, 1));
-    alloc((void **)&a->st_phi, sizeof(float) * N * std::max(every, 1));
+    if (every > 0) {
+      alloc((void **)&a->st_q, sizeof(int64_t) * 2 * N * every);
+      alloc((void **)&a->st_phi, sizeof(float) * N * every);
+    }
     alloc((void **)&a->lam, sizeof(float) * 2 * N);
     alloc((void **)&a->lam2, sizeof(float) * 2 * N);
     alloc((void **)&a->phibar, sizeof(float) * N);
@@ -388,7 +400,27 @@ int adj_alloc(lbe_handle *h, int T, int every) {
     }
   }
   a->T = T;
+  a->revolve_slots = every > 0 ? 0 : slots;
   return LBE_OK;
+}
+
+// binomial schedule: beta(s, r) = C(s + r, s) steps can be reversed with s
+// free slots and r recomputations of each step; the smallest r for n steps,
+// and the first checkpoint's distance d (the right part n - d then fits s - 1
+// slots with r recomputations, the left part d fits s slots with r - 1)
+long long beta(int s, int r) {
+  long long b = 1;
+  for (int i = 1; i <= s; ++i) {
+    b = b * (r + i) / i;  // exact: a binomial coefficient at every i
+    if (b > (1LL << 40)) return 1LL << 40;
+  }
+  return b;
+}
+int revolve_d(int n, int s) {
+  int r = 0;
+  while (beta(s, r) < n) ++r;
+  const long long right = beta(s - 1, r);
+  return (int)std::max<long long>(1, n - std::min<long long>(right, n - 1));
 }
 
 // checkpoint k <-> the handle's state (solute, potential, warm-start history)
@@ -437,6 +469,98 @@ int adj_poisson(lbe_handle *h, const float *phi_t, const Weights &psi, int soft)
   ACK(h, cudaGetLastError());
   return LBE_OK;
 }
+
+// The reverse sweep under the binomial schedule.  The handle's state is
+// moved between checkpoint slots and recomputed steps; each backward step
+// reads the forward state at its time directly from the handle.
+struct RevSweep {
+  lbe_handle *h;
+  Weights psi;
+  int soft;
+  long long recomputed = 0, adj_iters = 0;
+  double ms_re = 0.0, ms_flux = 0.0, ms_solve = 0.0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+
+  // CG iterations of the adjoint solves since the last reset (the
+  // recomputing steps reset the solver's counters)
+  int count() {
+    ACK(h, cudaMemcpyAsync(h->pw.ctl_host, h->pw.ctl, sizeof(PoissonCtl), cudaMemcpyDeviceToHost, h->stream));
+    ACK(h, cudaStreamSynchronize(h->stream));
+    adj_iters += h->pw.ctl_host->total_iters;
+    const int status = h->pw.ctl_host->status ? h->pw.ctl_host->status : h->pw.ctl_host->sticky_status;
+    if (status) return afail(h, status, "adjoint: Poisson solve failed");
+    return LBE_OK;
+  }
+  int timed(double *acc, int (*f)(RevSweep *, int), int arg) {
+    ACK(h, cudaEventRecord(e0, h->stream));
+    const int rc = f(this, arg);
+    if (rc != LBE_OK) return rc;
+    ACK(h, cudaEventRecord(e1, h->stream));
+    ACK(h, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    ACK(h, cudaEventElapsedTime(&ms, e0, e1));
+    *acc += ms;
+    return LBE_OK;
+  }
+  static int advance(RevSweep *R, int n) {
+    R->recomputed += n;
+    return n > 0 ? lbe_step(R->h, n) : LBE_OK;
+  }
+  static int flux(RevSweep *R, int) {
+    AdjWork *a = R->h->adj;
+    const int nb = a->nblk;
+    k_adj_flux<<<nb, kBlock, 0, R->h->stream>>>(R->h->geo, R->h->phys, R->h->p32, R->h->mask, R->h->id, R->h->q,
+                                                R->h->phi32, R->psi, a->lam, a->lam2, a->phibar, a->chibar, a->part,
+                                                nb);
+    k_adj_accumulate<<<2, 32, 0, R->h->stream>>>(a->part, nb, kSlotD, a->acc);
+    ACK(R->h, cudaGetLastError());
+    std::swap(a->lam, a->lam2);
+    return LBE_OK;
+  }
+  static int solve(RevSweep *R, int) {
+    ACK(R->h, poisson_reset_stats(R->h));
+    const int rc = adj_poisson(R->h, R->h->phi32, R->psi, R->soft);
+    if (rc != LBE_OK) return rc;
+    return R->count();
+  }
+  // the transposed flux step t -> t+1 and the adjoint solve at time t, from
+  // the forward state at t (in the handle)
+  int back(int) {
+    int rc = timed(&ms_flux, flux, 0);
+    if (rc != LBE_OK) return rc;
+    return timed(&ms_solve, solve, 0);
+  }
+  int step(int n) { return timed(&ms_re, advance, n); }
+
+  // Reverse the steps t1-1 .. t0; slot `base` holds x(t0), slots above it
+  // are free, s of them usable.  On the first descent (first) the forward
+  // pass already stored the next checkpoint in slot base + 1.
+  int reverse(int t0, int t1, int base, int s, bool first) {
+    const int n = t1 - t0;
+    int rc;
+    if (n <= 0) return LBE_OK;
+    if (n == 1) {
+      if ((rc = load_ck(h, base)) != LBE_OK) return rc;
+      return back(t0);
+    }
+    if (s == 0) {  // no free slot: recompute from x(t0) for every step
+      for (int t = t1 - 1; t >= t0; --t) {
+        if ((rc = load_ck(h, base)) != LBE_OK) return rc;
+        if ((rc = step(t - t0)) != LBE_OK) return rc;
+        if ((rc = back(t)) != LBE_OK) return rc;
+      }
+      return LBE_OK;
+    }
+    const int d = revolve_d(n, s);
+    if (!first) {
+      if ((rc = load_ck(h, base)) != LBE_OK) return rc;
+      if ((rc = step(d)) != LBE_OK) return rc;
+      if ((rc = save_ck(h, base + 1)) != LBE_OK) return rc;
+    }
+    if ((rc = reverse(t0 + d, t1, base + 1, s - 1, first)) != LBE_OK) return rc;
+    return reverse(t0, t0 + d, base, s, false);
+  }
+};
 
 bool adjoint_supported(const lbe_handle *h, std::string *why) {
   const lbe_params &p = h->prm;
@@ -500,6 +624,51 @@ int lbe_adjoint_forward(lbe_handle *h, int nsteps, int checkpoint_every, double 
   return LBE_OK;
 }
 
+int lbe_adjoint_forward_budget(lbe_handle *h, int nsteps, size_t device_bytes, double *q_out) {
+  using namespace lbe;
+  if (!h) return LBE_ERR_ARG;
+  std::string why;
+  if (!adjoint_supported(h, &why)) return afail(h, LBE_ERR_STATE, why);
+  if (nsteps < 0) return afail(h, LBE_ERR_ARG, "adjoint_forward_budget: bad step count");
+  const size_t N = (size_t)h->geo.N;
+  const size_t per_slot = N * (2 * sizeof(int64_t) + sizeof(double) + kHist * sizeof(double));
+  const size_t slots = device_bytes / per_slot;
+  if (slots < 2) return afail(h, LBE_ERR_ARG, "adjoint_forward_budget: budget below two checkpoints");
+  const int nslot = (int)std::min<size_t>(slots, (size_t)nsteps + 2);
+  int rc = adj_alloc(h, nsteps, 0, nslot);
+  if (rc != LBE_OK) return rc;
+  AdjWork *a = h->adj;
+  a->ready = false;
+  rc = lbe_init(h);
+  if (rc != LBE_OK) return rc;
+  if ((rc = save_ck(h, 0)) != LBE_OK) return rc;
+  // the first descent of the schedule, as the reverse sweep will expect it
+  int t0 = 0, s = nslot - 2, k = 0;
+  while (nsteps - t0 > 1 && s > 0) {
+    const int d = revolve_d(nsteps - t0, s);
+    if ((rc = lbe_step(h, d)) != LBE_OK) return rc;
+    if ((rc = save_ck(h, k + 1)) != LBE_OK) return rc;
+    t0 += d;
+    ++k;
+    --s;
+  }
+  if ((rc = lbe_step(h, nsteps - t0)) != LBE_OK) return rc;
+  if ((rc = save_ck(h, a->nseg)) != LBE_OK) return rc;  // time T
+  double q[LBE_MAX_ELECTRODES] = {};
+  if (h->n_elec) {
+    rc = lbe_induced_charge(h, q, 0);
+    if (rc != LBE_OK) return rc;
+  }
+  for (int e = 0; e < h->n_elec; ++e) {
+    a->q[e] = q[e];
+    if (q_out) q_out[e] = q[e];
+  }
+  ACK(h, cudaStreamSynchronize(h->stream));
+  a->gen = h->gen;
+  a->ready = true;
+  return LBE_OK;
+}
+
 int lbe_adjoint_backward(lbe_handle *h, const double *dq, int soft_electrode, lbe_adjoint_grad *out, double *dchi,
                          int dchi_on_device) {
   using namespace lbe;
@@ -545,12 +714,26 @@ int lbe_adjoint_backward(lbe_handle *h, const double *dq, int soft_electrode, lb
   if ((rc = count()) != LBE_OK) return rc;
   long long recomputed = 0;
   double ms_re = 0.0, ms_flux = 0.0, ms_solve = 0.0;
+  if (a->revolve_slots > 0) {  // binomial schedule
+    RevSweep R{h, psi, soft_electrode};
+    ACK(h, cudaEventCreate(&R.e0));
+    ACK(h, cudaEventCreate(&R.e1));
+    rc = R.reverse(0, a->T, 0, a->revolve_slots - 2, true);
+    cudaEventDestroy(R.e0);
+    cudaEventDestroy(R.e1);
+    if (rc != LBE_OK) return rc;
+    recomputed = R.recomputed;
+    adj_iters += R.adj_iters;
+    ms_re = R.ms_re;
+    ms_flux = R.ms_flux;
+    ms_solve = R.ms_solve;
+  }
   while ((int)a->ev.size() < 2 * a->every + 3) {
     cudaEvent_t e;
     ACK(h, cudaEventCreate(&e));
     a->ev.push_back(e);
   }
-  for (int s = a->nseg - 1; s >= 0; --s) {
+  for (int s = a->revolve_slots > 0 ? -1 : a->nseg - 1; s >= 0; --s) {
     const int t0 = s * a->every, t1 = std::min(a->T, t0 + a->every);
     ACK(h, cudaEventRecord(a->ev[0], st));
     rc = load_ck(h, s);

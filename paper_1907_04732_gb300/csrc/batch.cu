@@ -157,8 +157,10 @@ struct lbe_batch {
   float *f[2] = {nullptr, nullptr};
   int64_t *q = nullptr, *qstar = nullptr;
   double *phi = nullptr, *phi_prev = nullptr;  // phi_prev [kHist][Ntot]: the previous solutions
-  float *phi32 = nullptr, *u = nullptr;
+  float *phi32 = nullptr;
+  float4 *u = nullptr;      // velocity records (fp32::octant_code)
   float *phi_lo = nullptr;  // phi = phi32 + phi_lo to ~2^-48 (float-float residual)
+  float4 *lf = nullptr;     // link records, one per node (fp32::link_record)
   float *vec = nullptr;     // CG vectors [6][Ntot]
   double *part = nullptr;   // per-tile partials [3][T]
   double *psi_d = nullptr;  // [n][kBE + 1]
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(kBlock) kb_init(const InstDev *__restrict__ in
                                                   int64_t *__restrict__ q, double *__restrict__ phi,
                                                   float *__restrict__ phi32, float *__restrict__ phi_lo,
                                                   double *__restrict__ phi_prev,
-                                                  float *__restrict__ u) {
+                                                  float4 *__restrict__ u) {
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
     const int ii = tile_inst[t];
     const InstDev &I = inst[ii];
@@ -348,7 +350,24 @@ __global__ void __launch_bounds__(kBlock) kb_init(const InstDev *__restrict__ in
       phi32[r] = (float)p;
       phi_lo[r] = (float)(p - (double)(float)p);
       for (int k = 0; k < kHist; ++k) phi_prev[k * Ntot + r] = p;
-      u[r] = u[Ntot + r] = u[2 * Ntot + r] = 0.f;
+      u[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+// link records of every fluid node (fp32::link_record) from the potential
+// and solute of the step about to run
+template <bool WIDE>
+__global__ void __launch_bounds__(kBlock) kb_prep(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
+                                                  int T, int Ntot, const float *__restrict__ phi,
+                                                  const int64_t *__restrict__ q, float4 *__restrict__ lf) {
+  for (int t = blockIdx.x; t < T; t += gridDim.x) {
+    const InstDev &I = inst[tile_inst[t]];
+    for (int k = 0; k < kSub; ++k) {
+      const int lo = (t - I.tile0) * kTile + k * kBlock + threadIdx.x;
+      if (lo >= I.g.N) break;
+      const int r = I.off + lo;
+      lf[r] = link_record(I.P, phi[r], q[r], q[Ntot + r]);  // solid records are never read
     }
   }
 }
@@ -358,7 +377,7 @@ __global__ void __launch_bounds__(kBlock, 4) kb_sweep(const InstDev *__restrict_
                                                    int T, int Ntot, const uint32_t *__restrict__ mask,
                                                    const float *__restrict__ fin, float *__restrict__ fout,
                                                    const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
-                                                   const float *__restrict__ phi, float *__restrict__ u,
+                                                   const float4 *__restrict__ lf, float4 *__restrict__ u,
                                                    int *__restrict__ flag) {
   // the tile's instance constants are staged in shared memory: the link loop
   // reads them for every link (shared loads instead of global ones)
@@ -380,25 +399,27 @@ __global__ void __launch_bounds__(kBlock, 4) kb_sweep(const InstDev *__restrict_
       const int r = I.off + lo;
       const uint32_t m = mask[r];
       if (!(m & kFluidBit)) continue;
-      sweep_node<FLOW, true, WIDE>(I.P, Ntot, r, offsets_of(I.g, x, y, z), m, fin, fout, q, qstar, phi, u, over);
+      sweep_node_lf<FLOW, WIDE>(I.P, Ntot, r, offsets_of(I.g, x, y, z), m, fin, fout, q, qstar, lf, u, over);
     }
   }
   if (over) atomicOr(flag, 1);
 }
 
 using SweepKern = void (*)(const InstDev *, const int *, int, int, const uint32_t *, const float *, float *,
-                          const int64_t *, int64_t *, const float *, float *, int *);
-// the sweep for the batch's flow mode and size (64-bit population offsets
-// when 19 components pass 2^31)
+                          const int64_t *, int64_t *, const float4 *, float4 *, int *);
+using PrepKern = void (*)(const InstDev *, const int *, int, int, const float *, const int64_t *, float4 *);
+// 64-bit population and record offsets when 19 components pass 2^31
+inline bool wide_batch(long long Ntot) { return (long long)kQ * Ntot >= (1LL << 31); }
+// the sweep for the batch's flow mode and size
 inline SweepKern sweep_kernel(bool flow, long long Ntot) {
-  const bool wide = (long long)kQ * Ntot >= (1LL << 31);
-  return flow ? (wide ? kb_sweep<true, true> : kb_sweep<true, false>)
-              : (wide ? kb_sweep<false, true> : kb_sweep<false, false>);
+  const SweepKern k[2][2] = {{kb_sweep<false, false>, kb_sweep<false, true>}, {kb_sweep<true, false>, kb_sweep<true, true>}};
+  return k[flow][wide_batch(Ntot)];
 }
+inline PrepKern prep_kernel(long long Ntot) { return wide_batch(Ntot) ? kb_prep<true> : kb_prep<false>; }
 
 __global__ void __launch_bounds__(kBlock) kb_advect(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
                                                     int T, int Ntot, const uint32_t *__restrict__ mask,
-                                                    const int64_t *__restrict__ qin, const float *__restrict__ u,
+                                                    const int64_t *__restrict__ qin, const float4 *__restrict__ u,
                                                     int64_t *__restrict__ qout, double *__restrict__ phi,
                                                     double *__restrict__ prev, float *__restrict__ phi32,
                                                     float *__restrict__ phi_lo, const int *__restrict__ hist) {
@@ -496,7 +517,7 @@ __global__ void __launch_bounds__(kBlock) kb_res(const InstDev *__restrict__ ins
       v.r[r] = rf;
       v.u[r] = rf * dinv;
       v.x[r] = v.p[r] = v.s[r] = 0.f;
-      mx = fmaxf(mx, fabsf(rf) * dinv);
+      mx = fmaxf(mx, finite_or_inf(fabsf(rf) * dinv));
     }
     mx = breducef<true>(mx);
     if (threadIdx.x == 0) part[2LL * T + t] = (double)mx;
@@ -519,11 +540,17 @@ __global__ void __launch_bounds__(kBlock) kb_outer(const InstDev *__restrict__ i
     m = breduce<true>(m);
     if (threadIdx.x == 0) {
       InstCtl &C = c[ii];
+      const double prev = C.res;
       C.res = m;
       int done = 0;
       if (m <= tol) done = 1;
       else if (!(m == m) || m > 1e300) { done = 1; C.status = LBE_ERR_NONFINITE; }
-      else if (C.rounds >= kMaxOuterB || C.iters >= maxit) { done = 1; C.status = LBE_ERR_NOCONVERGE; }
+      // out of rounds or iterations, or a round that did not halve the
+      // residual (the tolerance is below what the arithmetic resolves)
+      else if (C.rounds >= kMaxOuterB || C.iters >= maxit || (C.rounds >= 1 && m > 0.5 * prev)) {
+        done = 1;
+        C.status = LBE_ERR_NOCONVERGE;
+      }
       C.outer_done = done;
       C.inner_done = done;
       C.solving = !done;
@@ -615,7 +642,7 @@ __global__ void __launch_bounds__(kBlock) kb_scal(const InstDev *__restrict__ in
         C.iters += 1;
         atomicAdd((unsigned long long *)&b->total_iters, 1ULL);
         if (m <= fmax(eta * C.res0, tol_abs)) done = 1;
-        else if (!(m == m) || !(d == d)) { done = 1; C.status = LBE_ERR_NONFINITE; C.outer_done = 1; }
+        else if (!(m == m) || m > 1e300 || !(d == d)) { done = 1; C.status = LBE_ERR_NONFINITE; C.outer_done = 1; }
         else if (C.iters >= maxit) done = 1;
         else {
           const double beta = g / C.gamma;
@@ -672,7 +699,7 @@ __global__ void __launch_bounds__(kBlock) kb_cg_a(const InstDev *__restrict__ in
       r_[r] = rv;
       const float dinv = __fdividef(6.f, (float)mgd::diag6(m, I.selfmask));
       u_[r] = rv * dinv;
-      mx = fmaxf(mx, fabsf(rv) * dinv);
+      mx = fmaxf(mx, finite_or_inf(fabsf(rv) * dinv));
     }
     mx = breducef<true>(mx);
     if (threadIdx.x == 0) part[2LL * T + I.tile0 + j] = (double)mx;
@@ -1013,7 +1040,7 @@ void bfree(lbe_batch *b) {
   void *ptrs[] = {b->inst_d, b->tile_inst, b->id,   b->mask, b->f[0],  b->f[1], b->q,    b->qstar, b->phi,
                   b->phi_prev, b->phi32,  b->phi_lo, b->u, b->vec, b->part, b->psi_d, b->ictl, b->bctl, b->qpart,
                   b->qout,
-                  b->flag,     b->hist};
+                  b->flag,     b->hist,   b->lf};
   for (void *p : ptrs) cudaFree(p);
   mg_release(b);
   if (b->bctl_h) cudaFreeHost(b->bctl_h);
@@ -1296,7 +1323,8 @@ struct SolveArgs {
   float *fout;
   int64_t *qin, *qmid, *qsolve;
   double *phi, *phi_prev;
-  float *phi32, *phi_lo, *u;
+  float *phi32, *phi_lo;
+  float4 *u, *lf;
   lbe::CgVec v;
   const float *vr, *vu, *vx;
   float *vw;
@@ -1333,6 +1361,7 @@ void solve_args(lbe_batch *b, bool step, const float *fin, float *fout, int64_t 
   A.phi32 = b->phi32;
   A.phi_lo = b->phi_lo;
   A.u = b->u;
+  A.lf = b->lf;
   A.v = b->cg();
   A.vr = A.v.r;
   A.vu = A.v.u;
@@ -1345,7 +1374,7 @@ void solve_args(lbe_batch *b, bool step, const float *fin, float *fout, int64_t 
   A.hist = b->hist;
   A.tol = b->prm[0].poisson_tol;
   A.eta = 1e-4;
-  A.tol_abs = 0.25 * A.tol;
+  A.tol_abs = 0.8 * A.tol;  // as the single-lattice solve (fewer CG iterations, same outer test)
 }
 
 // One graph per step: [sweep -> advect ->] extrapolate -> Poisson solve
@@ -1362,7 +1391,8 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   if (e != cudaSuccess) return e;
   cudaGraphNode_t last = nullptr, lo = nullptr, li = nullptr;
   cudaGraph_t bo = nullptr, bi = nullptr;
-  void *a_sw[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.fin, &A.fout, &A.qin, &A.qmid, &A.phi32, &A.u,
+  void *a_prep[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.phi32, &A.qin, &A.lf};
+  void *a_sw[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.fin, &A.fout, &A.qin, &A.qmid, &A.lf, &A.u,
                   &A.flag};
   void *a_adv[] = {&A.inst, &A.tile_inst, &A.T,      &A.Ntot,  &A.mask, &A.qmid,
                    &A.u,    &A.qin,       &A.phi, &A.phi_prev, &A.phi32, &A.phi_lo, &A.hist};
@@ -1385,6 +1415,7 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   if (step) {
     void *sweep = (void *)sweep_kernel(b->flow, b->Ntot);
     if (prof) e = add_event(g, &last, b->ev[0]);
+    if (e == cudaSuccess) e = add_node(g, &last, (void *)prep_kernel(b->Ntot), G, B, a_prep);
     if (e == cudaSuccess) e = add_node(g, &last, sweep, G, B, a_sw);
     if (e == cudaSuccess && prof) e = add_event(g, &last, b->ev[1]);
     if (e == cudaSuccess && b->flow) e = add_node(g, &last, (void *)kb_advect, G, B, a_adv);
@@ -1437,8 +1468,9 @@ int run_polled(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *
   long long &nl = b->prof_launches;
   if (step) {
     BCK(b, rec(0));
-    sweep_kernel(b->flow, b->Ntot)<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, fin, fout, qin,
-                                                         qmid, A.phi32, A.u, A.flag);
+    prep_kernel(b->Ntot)<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.phi32, qin, A.lf);
+    sweep_kernel(b->flow, b->Ntot)<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, fin,
+                                                                   fout, qin, qmid, A.lf, A.u, A.flag);
     BCK(b, rec(1));
     if (b->flow)  // the advection applies the warm start as well
       kb_advect<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, qmid, A.u, qin, A.phi, A.phi_prev,
@@ -1447,7 +1479,7 @@ int run_polled(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *
     if (!b->flow)
       kb_extrapolate<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, A.phi, A.phi_prev, A.phi32,
                                            A.phi_lo, A.hist);
-    nl += 2;
+    nl += 3;
   }
   kb_solve_reset<<<(n + 255) / 256, 256, 0, st>>>(n, A.c, A.bc, A.hist, A.set_hist);
   nl += 1;
@@ -1584,7 +1616,7 @@ int read_status(lbe_batch *b) {
 int flags(lbe_batch *b) {
   int v = 0;
   BCK(b, cudaMemcpy(&v, b->flag, sizeof(int), cudaMemcpyDeviceToHost));
-  if (v) return bfail(b, LBE_ERR_NONFINITE, "fixed-point solute range exceeded");
+  if (v) return bfail(b, LBE_ERR_NONFINITE, "state out of range: fixed-point solute, solvent density or a NaN");
   return LBE_OK;
 }
 
@@ -1605,15 +1637,18 @@ int autotune(lbe_batch *b) {
   float best = 1e30f;
   int best_grid = 4 * sms;
   float *fout = b->flow ? b->f[b->cur ^ 1] : b->f[b->cur];
-  cudaError_t err = cudaSuccess;
+  // the sweep reads the link records of the current state
+  prep_kernel(b->Ntot)<<<4 * sms, kBlock, 0, b->stream>>>(b->inst_d, b->tile_inst, b->T, (int)b->Ntot, b->phi32,
+                                                         b->q, b->lf);
+  cudaError_t err = cudaGetLastError();
   for (int c = 0; c < LBE_BATCH_TUNE_CANDIDATES && err == cudaSuccess; ++c) {
     const int grid = cand[c] * sms;
     float ms = 0.f;
     for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
       err = cudaEventRecord(e0, b->stream);
-      sweep_kernel(b->flow, b->Ntot)<<<grid, kBlock, 0, b->stream>>>(b->inst_d, b->tile_inst, b->T, (int)b->Ntot,
-                                                                     b->mask, b->f[b->cur], fout, b->q, b->qstar,
-                                                                     b->phi32, b->u, b->flag);
+      sweep_kernel(b->flow, b->Ntot)<<<grid, kBlock, 0, b->stream>>>(
+          b->inst_d, b->tile_inst, b->T, (int)b->Ntot, b->mask, b->f[b->cur], fout, b->q, b->qstar, b->lf, b->u,
+          b->flag);
       if (err == cudaSuccess) err = cudaGetLastError();
       if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
       if (err == cudaSuccess) err = cudaEventSynchronize(e1);
@@ -1732,8 +1767,9 @@ int lbe_batch_create(const lbe_params *params, int n, void *cuda_stream, lbe_bat
   alloc((void **)&b->phi, 8 * N);
   alloc((void **)&b->phi_prev, 8 * lbe::kHist * N);
   alloc((void **)&b->phi32, 4 * N);
+  alloc((void **)&b->lf, sizeof(float4) * N);
   alloc((void **)&b->phi_lo, 4 * N);
-  alloc((void **)&b->u, 4 * N * 3);
+  alloc((void **)&b->u, sizeof(float4) * N);
   alloc((void **)&b->vec, 4 * N * 6);
   alloc((void **)&b->part, sizeof(double) * 3 * T);
   alloc((void **)&b->psi_d, sizeof(double) * n * (kBE + 1));
@@ -1750,7 +1786,7 @@ int lbe_batch_create(const lbe_params *params, int n, void *cuda_stream, lbe_bat
   if (e == cudaSuccess) e = cudaMemset(b->bctl, 0, sizeof(lbe::BatchCtl));
   if (e == cudaSuccess) e = cudaMemset(b->flag, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(b->hist, 0, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(b->u, 0, 4 * N * 3);
+  if (e == cudaSuccess) e = cudaMemset(b->u, 0, sizeof(float4) * N);
   if (e != cudaSuccess) {
     bfree(b);
     if (own) cudaStreamDestroy(b->stream);
@@ -1857,8 +1893,9 @@ int lbe_batch_step(lbe_batch *b, int nsteps) {
     b->prof_iters += b->stats.poisson_iters;
     b->prof_solves += b->stats.poisson_solves;
   }
-  if (rc != LBE_OK) return rc;
-  return flags(b);
+  // a state out of range (range flag) explains a solve that failed after it
+  const int frc = flags(b);
+  return frc != LBE_OK ? frc : rc;
 }
 
 int lbe_batch_charge(lbe_batch *b, double *q_out, int out_on_device) {

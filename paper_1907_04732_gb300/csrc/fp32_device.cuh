@@ -58,88 +58,109 @@ __device__ __forceinline__ int nb_of(const Offs &o, int r, int i) { return r + o
 template <bool WIDE>
 using PopIdx = typename std::conditional<WIDE, long long, int>::type;
 
-// pull streaming with halfway bounce-back (see kernels_fp64.cu)
-template <bool WIDE>
+// pull streaming with halfway bounce-back (see kernels_fp64.cu); ALL: every
+// link joins fluid (no bounce-back to select)
+template <bool WIDE, bool ALL = false>
 __device__ __forceinline__ void gather32(int N, int r, const Offs &o, uint32_t m, const float *__restrict__ fin,
                                          float f[kQ]) {
   f[0] = fin[r];
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     const int io = opp_of(i);
-    f[i] = (m & (1u << (io - 1))) ? fin[(PopIdx<WIDE>)i * N + nb_of(o, r, io)] : fin[(PopIdx<WIDE>)io * N + r];
+    f[i] = (ALL || (m & (1u << (io - 1)))) ? fin[(PopIdx<WIDE>)i * N + nb_of(o, r, io)]
+                                           : fin[(PopIdx<WIDE>)io * N + r];
   }
 }
 
-// One link of a 1:1 salt (z = +1, -1) from a node with potential phi0 and
-// solute nu0 (nu = s q) to its neighbour r2: the flux terms J0, J1 of the two
-// species (Eq. LF2, relative form) and the link excess flux gs summed over
-// them.  A fixed rounding sequence: evaluated from the other end the link
-// gives exactly -J0, -J1, -gs.
-__device__ __forceinline__ void link_salt11_nu(const P32 &P, float phi0, float phi2, float ec, float il,
-                                               const float nu0[2], const float nu2[2], float &J0, float &J1,
-                                               float &gs) {
-  const float dphi = __fsub_rn(__fsub_rn(phi2, phi0), ec);
-  float P1, M1;
-  em1_pair(dphi, P1, M1);
-  gs = 0.f;
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const float Pk = k == 0 ? P1 : M1, Mk = k == 0 ? M1 : P1;
-    const float nu1 = nu2[k];
-    const float a1 = nE(P.rb[k], nu1, Pk), a0 = nE(P.rb[k], nu0[k], Mk);
-    const float J = __fsub_rn(tterm(a1, nu1), tterm(a0, nu0[k]));  // t1 - t0, exactly odd under link reversal
-    if (k == 0) J0 = J;
-    else J1 = J;
-    // link excess flux g = j/d + (n' - n)/|c| = -(n' (e^mu - 1) - n (e^-mu - 1))/(2|c|)
-    gs = __fmaf_rn(-(il * 0.5f), __fsub_rn(a1, a0), gs);
+// ---------------------------------------------------------------------------
+// Link records of a 1:1 salt (z = +1, -1): one float4 per fluid node,
+// (phi, nu_+, nu_-, 0) with nu = s q, written before each sweep so that the
+// link loop reads one record per neighbour instead of converting its 64-bit
+// solute amounts.
+__device__ __forceinline__ float4 link_record(const P32 &P, float phi, long long q0, long long q1) {
+  return make_float4(phi, __fmul_rn(P.s[0], ll2f(q0)), __fmul_rn(P.s[1], ll2f(q1)), 0.f);
+}
+
+// sinh x and cosh x - 1 from expm1f, for the rare link with |x| > 1/4 (a
+// call, so that the common path does not carry it)
+static __device__ __noinline__ float2 shch_wide(float x) {
+  const float ep = expm1f(x), em = expm1f(-x);
+  return make_float2(__fmul_rn(0.5f, __fsub_rn(ep, em)), __fmul_rn(0.5f, __fadd_rn(ep, em)));
+}
+
+// Flux terms of both species on the link from its owner a to b (Eq. LF2 in
+// the relative form), with x = dmu_+ = phi_b - phi_a - E.c (dmu_- = -x):
+//   A_k = n_b (e^{dmu} - 1) - n_a (e^{-dmu} - 1) = S_k sinh(dmu) + D_k (cosh(dmu) - 1)
+//   J_k = n_b (1 + e^{dmu}) - n_a (1 + e^{-dmu}) = 2 D_k + A_k
+// with S = n_a + n_b, D = n_b - n_a (j = -d J/(2|c|); A is the link excess
+// flux of the force up to the factor -1/(2|c|)).  sinh and
+// cosh - 1 come from their Taylor series for |x| <= 1/4 (relative error
+// below 5e-8) and from expm1f beyond.  Every link is evaluated in this one
+// orientation (a = the end from which it points along one of c_1..c_9), by
+// both of its end nodes from the same records: the two are bitwise equal.
+__device__ __forceinline__ void link_pair(const P32 &P, const float4 &ra, const float4 &rb, float ec, float &Jp,
+                                          float &Ap, float &Jm, float &Am) {
+  const float x = __fsub_rn(__fsub_rn(rb.x, ra.x), ec);
+  float sh, ch;
+  if (fabsf(x) <= 0.25f) {
+    const float x2 = __fmul_rn(x, x);
+    sh = __fmul_rn(x, __fmaf_rn(x2, __fmaf_rn(x2, 1.f / 120.f, 1.f / 6.f), 1.f));
+    ch = __fmul_rn(x2, __fmaf_rn(x2, 1.f / 24.f, 0.5f));
+  } else {
+    const float2 w = shch_wide(x);
+    sh = w.x;
+    ch = w.y;
+  }
+  const float Dp = __fsub_rn(rb.y, ra.y), Dm = __fsub_rn(rb.z, ra.z);
+  const float Sp = __fadd_rn(2.f * P.rb[0], __fadd_rn(ra.y, rb.y));
+  const float Sm = __fadd_rn(2.f * P.rb[1], __fadd_rn(ra.z, rb.z));
+  Ap = __fmaf_rn(Sp, sh, __fmul_rn(Dp, ch));
+  Am = __fmaf_rn(-Sm, sh, __fmul_rn(Dm, ch));
+  Jp = __fmaf_rn(2.f, Dp, Ap);
+  Jm = __fmaf_rn(2.f, Dm, Am);
+}
+
+// Rounding a link's flux x (fixed-point units, |x| < 2^44) to an integer and
+// adding it to (SIGN > 0) or subtracting it from (SIGN < 0) a 64-bit amount
+// kept as two 32-bit sums hi 2^22 + lo, with FP32 and integer adds only (no
+// conversion instructions): h = round(x 2^-22) read off the float grid of
+// unit spacing at 1.5 2^23 (kMagic), lo = x - h 2^22 (exact), l = round(lo)
+// likewise.  The sums carry kMagicBits per term, removed once per node
+// (mod 2^32).  Both roundings are round-half-even, an odd function of x, so
+// a link's two ends move exactly opposite amounts.
+constexpr float kMagic = 12582912.f;  // 1.5 * 2^23
+constexpr unsigned kMagicBits = 0x4B400000u;
+template <int SIGN>
+__device__ __forceinline__ void acc_round(float x, unsigned &ah, unsigned &al) {
+  const float h = __fmaf_rn(x, 2.384185791015625e-07f, kMagic);  // 2^-22
+  const float lo = __fmaf_rn(-__fsub_rn(h, kMagic), 4194304.f, x);  // 2^22
+  const float l = __fadd_rn(lo, kMagic);
+  if (SIGN > 0) {
+    ah += (unsigned)__float_as_int(h);
+    al += (unsigned)__float_as_int(l);
+  } else {
+    ah -= (unsigned)__float_as_int(h);
+    al -= (unsigned)__float_as_int(l);
   }
 }
-// the same with the neighbour's solute read from q (nu = s q)
-__device__ __forceinline__ void link_salt11(const P32 &P, int N, int r2, float phi0, float ec, float il,
-                                            const float nu0[2], const int64_t *__restrict__ q,
-                                            const float *__restrict__ phi, float &J0, float &J1, float &gs) {
-  const float nu2[2] = {__fmul_rn(P.s[0], ll2f(q[r2])), __fmul_rn(P.s[1], ll2f(q[N + r2]))};
-  link_salt11_nu(P, phi0, phi[r2], ec, il, nu0, nu2, J0, J1, gs);
+// the 64-bit amount of two sums after net = (#added - #subtracted) terms
+__device__ __forceinline__ long long acc_value(unsigned ah, unsigned al, int net) {
+  const unsigned off = (unsigned)net * kMagicBits;
+  return (long long)(int)(ah - off) * 4194304LL + (long long)(int)(al - off);
 }
 
-// The quantised solute update and the force of link i (1:1 salt) from its
-// flux terms: dq_k -= round(J_k kq_k), F += c_i gs.
-__device__ __forceinline__ void link_apply(const P32 &P, int i, float J0, float J1, float gs, long long dq[2],
-                                           float &Fx, float &Fy, float &Fz, bool &over) {
-  const float jq0 = __fmul_rn(J0, c2_of(i) == 1 ? P.kq1[0] : P.kq2[0]);
-  const float jq1 = __fmul_rn(J1, c2_of(i) == 1 ? P.kq1[1] : P.kq2[1]);
-  over |= fabsf(jq0) > 1.0e17f;
-  over |= fabsf(jq1) > 1.0e17f;
-  dq[0] -= f2ll_rn(jq0);
-  dq[1] -= f2ll_rn(jq1);
-  Fx += cx_of(i) * gs;
-  Fy += cy_of(i) * gs;
-  Fz += cz_of(i) * gs;
-}
-
-// Ion part of the step at one fluid node: quantised link fluxes -> dq, and
-// the solvent force from the link excess fluxes.
-template <bool QUANT, bool SALT11>
+// Ion part of the step at one fluid node, any salt (the general form; a 1:1
+// salt takes sweep_node_lf): link fluxes evaluated at both ends with a fixed
+// rounding sequence (the potential difference is exactly antisymmetric and
+// em1_pair(-x) = (M, P) for em1_pair(x) = (P, M)), quantised (QUANT) into dq,
+// and the solvent force from the link excess fluxes.
+template <bool QUANT>
 __device__ __forceinline__ void ion_links(const P32 &P, int N, int r, const Offs &o, uint32_t m,
                                           const int64_t *__restrict__ q, const float *__restrict__ phi,
                                           const long long q0[LBE_MAX_SPECIES], const float q0f[LBE_MAX_SPECIES],  // q0f: nu
                                           long long dq[LBE_MAX_SPECIES], float F[3], bool &over) {
   const float phi0 = phi[r];
   float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-  if (SALT11 && QUANT) {
-    const float nu0[2] = {q0f[0], q0f[1]};
-#pragma unroll
-    for (int i = 1; i < kQ; ++i) {
-      if (!(m & (1u << (i - 1)))) continue;
-      float J0, J1, gs;
-      link_salt11(P, N, nb_of(o, r, i), phi0, P.ec[i], (float)invlen_of(i), nu0, q, phi, J0, J1, gs);
-      link_apply(P, i, J0, J1, gs, dq, Fx, Fy, Fz, over);
-    }
-    F[0] = Fx * P.inv_2a0;
-    F[1] = Fy * P.inv_2a0;
-    F[2] = Fz * P.inv_2a0;
-    return;
-  }
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     if (!(m & (1u << (i - 1)))) continue;
@@ -151,13 +172,10 @@ __device__ __forceinline__ void ion_links(const P32 &P, int N, int r, const Offs
     const float il = (float)invlen_of(i);
     float gs = 0.f;
 #pragma unroll
-    for (int k = 0; k < (SALT11 ? 2 : LBE_MAX_SPECIES); ++k) {
-      if (!SALT11 && k >= P.ns) break;
+    for (int k = 0; k < LBE_MAX_SPECIES; ++k) {
+      if (k >= P.ns) break;
       float Pk, Mk;
-      if (SALT11) {  // z = +1, -1
-        Pk = k == 0 ? P1 : M1;
-        Mk = k == 0 ? M1 : P1;
-      } else if (P.zi[k] == 1) {
+      if (P.zi[k] == 1) {
         Pk = P1;
         Mk = M1;
       } else if (P.zi[k] == -1) {
@@ -171,7 +189,7 @@ __device__ __forceinline__ void ion_links(const P32 &P, int N, int r, const Offs
       const float J = __fsub_rn(tterm(a1, nu1), tterm(a0, q0f[k]));  // t1 - t0, exactly odd under link reversal
       if (QUANT) {
         const float jq = __fmul_rn(J, c2_of(i) == 1 ? P.kq1[k] : P.kq2[k]);
-        over |= fabsf(jq) > 1.0e17f;
+        over |= !(fabsf(jq) <= 1.0e17f);  // also catches NaN
         dq[k] -= f2ll_rn(jq);
       }
       // link excess flux g = j/d + (n' - n)/|c| = -(n' (e^mu - 1) - n (e^-mu - 1))/(2|c|)
@@ -206,14 +224,34 @@ __device__ __forceinline__ long long share(float totf, float ux, float uy, float
 }
 
 
+// Velocity record of a fluid node for the advection: (ux, uy, uz, code),
+// code holding which components are positive (bits 0, 2, 4 for x, y, z)
+// and negative (bits 1, 3, 5).  A node's displaced cell reaches its
+// neighbour at offset s exactly when every nonzero s_a has the sign of u_a
+// (|u| < 1), i.e. when code contains cell_bits(s).
+__device__ __forceinline__ int octant_code(float ux, float uy, float uz) {
+  return (ux > 0.f) | ((ux < 0.f) << 1) | ((uy > 0.f) << 2) | ((uy < 0.f) << 3) | ((uz > 0.f) << 4) |
+         ((uz < 0.f) << 5);
+}
+__host__ __device__ constexpr int cell_bits(int dx, int dy, int dz) {
+  return (dx > 0 ? 1 : 0) | (dx < 0 ? 2 : 0) | (dy > 0 ? 4 : 0) | (dy < 0 ? 8 : 0) | (dz > 0 ? 16 : 0) |
+         (dz < 0 ? 32 : 0);
+}
+
 // BGK + Guo collision and pull streaming with halfway bounce-back at one
-// fluid node, given the solvent force F; the velocity is stored
-template <bool WIDE>
+// fluid node, given the solvent force F; the velocity is stored.  A density
+// deviation of 1/2 or more (or a non-finite one) raises the range flag.
+// In deviations df = f - w (Eq. LBpop with the second-order equilibrium and
+// Guo's source, reading R4), c_{i+9} = -c_i pairs share the even parts:
+//   df'_i = (1 - omega) df_i + E_even +- E_odd,
+//   E_even = w [omega (drho + rho (4.5 cu^2 - 1.5 uu)) + guo (9 cu cF - 3 uF)]
+//   E_odd  = w [3 omega rho cu + 3 guo cF]
+template <bool WIDE, bool ALL = false>
 __device__ __forceinline__ void lb_node(const P32 &P, int N, int r, const Offs &o, uint32_t m,
                                         const float *__restrict__ fin, float *__restrict__ fout,
-                                        float *__restrict__ u, const float F[3]) {
+                                        float4 *__restrict__ u, const float F[3], bool &over) {
   float f[kQ];
-  gather32<WIDE>(N, r, o, m, fin, f);
+  gather32<WIDE, ALL>(N, r, o, m, fin, f);
   float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
@@ -222,44 +260,39 @@ __device__ __forceinline__ void lb_node(const P32 &P, int N, int r, const Offs &
     jy += cy_of(i) * f[i];
     jz += cz_of(i) * f[i];
   }
+  over |= !(fabsf(drho) < 0.5f);
   const float rho = 1.f + drho;
   const float inv_rho = 1.f / rho;
   const float ux = (jx + 0.5f * F[0]) * inv_rho, uy = (jy + 0.5f * F[1]) * inv_rho, uz = (jz + 0.5f * F[2]) * inv_rho;
-  u[r] = ux;
-  u[N + r] = uy;
-  u[2 * N + r] = uz;
+  u[r] = make_float4(ux, uy, uz, __int_as_float(octant_code(ux, uy, uz)));
   const float uu = ux * ux + uy * uy + uz * uz;
   const float uF = ux * F[0] + uy * F[1] + uz * F[2];
-  // BGK + Guo forcing; c_{i+9} = -c_i, so each opposite pair shares the even
-  // part of the equilibrium and of the source and flips the odd part
-  {
-    const float w = (float)w_of(0);
-    const float eq = w * (drho - rho * 1.5f * uu);
-    const float src = -P.guo * w * 3.f * uF;
-    fout[r] = f[0] - P.omega * (f[0] - eq) + src;
-  }
+  const float om = P.omega, g = P.guo, keep = 1.f - om;
+  // w-independent parts per node
+  const float base = om * (drho - 1.5f * rho * uu) - 3.f * g * uF;  // E_even / w at cu = cF = 0
+  const float b2 = 4.5f * om * rho, d2 = 3.f * om * rho;
+  fout[r] = keep * f[0] + (float)w_of(0) * base;
 #pragma unroll
   for (int i = 1; i <= 9; ++i) {
     const float w = (float)w_of(i);
     const float cu = cx_of(i) * ux + cy_of(i) * uy + cz_of(i) * uz;
     const float cF = cx_of(i) * F[0] + cy_of(i) * F[1] + cz_of(i) * F[2];
-    const float eq_even = w * (drho + rho * (4.5f * cu * cu - 1.5f * uu));
-    const float eq_odd = w * rho * 3.f * cu;
-    const float src_even = P.guo * w * (9.f * cu * cF - 3.f * uF);
-    const float src_odd = P.guo * w * 3.f * cF;
+    const float ee = w * (base + cu * (b2 * cu + 9.f * g * cF));
+    const float eo = w * (d2 * cu + 3.f * g * cF);
     const int io = i + 9;
-    fout[(PopIdx<WIDE>)i * N + r] = f[i] - P.omega * (f[i] - (eq_even + eq_odd)) + (src_even + src_odd);
-    fout[(PopIdx<WIDE>)io * N + r] = f[io] - P.omega * (f[io] - (eq_even - eq_odd)) + (src_even - src_odd);
+    fout[(PopIdx<WIDE>)i * N + r] = keep * f[i] + (ee + eo);
+    fout[(PopIdx<WIDE>)io * N + r] = keep * f[io] + (ee - eo);
   }
 }
 
-// Fused step at one fluid node: quantised link fluxes and q* = q - sum Jq,
-// solvent force, and (FLOW) BGK + Guo collision with pull streaming.
-template <bool FLOW, bool SALT11, bool WIDE>
+// Fused step at one fluid node, any salt: quantised link fluxes and
+// q* = q - sum Jq, solvent force, and (FLOW) BGK + Guo collision with pull
+// streaming.
+template <bool FLOW, bool WIDE>
 __device__ __forceinline__ void sweep_node(const P32 &P, int N, int r, const Offs &o, uint32_t m,
                                            const float *__restrict__ fin, float *__restrict__ fout,
                                            const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
-                                           const float *__restrict__ phi, float *__restrict__ u, bool &over) {
+                                           const float *__restrict__ phi, float4 *__restrict__ u, bool &over) {
   long long q0[LBE_MAX_SPECIES], dq[LBE_MAX_SPECIES];
   float q0f[LBE_MAX_SPECIES];
 #pragma unroll
@@ -269,19 +302,85 @@ __device__ __forceinline__ void sweep_node(const P32 &P, int N, int r, const Off
     dq[k] = 0;
   }
   float F[3];
-  ion_links<true, SALT11>(P, N, r, o, m, q, phi, q0, q0f, dq, F, over);
+  ion_links<true>(P, N, r, o, m, q, phi, q0, q0f, dq, F, over);
   // compile-time species indices keep q0/dq in registers
 #pragma unroll
-  for (int k = 0; k < (SALT11 ? 2 : LBE_MAX_SPECIES); ++k)
-    if (SALT11 || k < P.ns) qstar[k * N + r] = q0[k] + dq[k];
-  if (FLOW) lb_node<WIDE>(P, N, r, o, m, fin, fout, u, F);
+  for (int k = 0; k < LBE_MAX_SPECIES; ++k)
+    if (k < P.ns) qstar[k * N + r] = q0[k] + dq[k];
+  if (FLOW) lb_node<WIDE>(P, N, r, o, m, fin, fout, u, F, over);
 }
 
-// Cell-overlap advection at one fluid node (see k_advect32).
+// Fused step at one fluid node of a 1:1 salt from the link records lf
+// (link_record): per link the flux terms of both species (link_pair, in the
+// link's one orientation), their fixed-point rounding (owner end subtracts,
+// the other end adds: exact conservation), the force from the link excess
+// fluxes, then (FLOW) BGK + Guo collision with pull streaming.
+template <bool FLOW, bool WIDE, bool ALL>
+__device__ __forceinline__ void sweep_node_lf_(const P32 &P, int N, int r, const Offs &o, uint32_t m,
+                                              const float *__restrict__ fin, float *__restrict__ fout,
+                                              const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
+                                              const float4 *__restrict__ lf, float4 *__restrict__ u, bool &over) {
+  const float4 self = lf[(PopIdx<WIDE>)r];
+  unsigned ah0 = 0u, al0 = 0u, ah1 = 0u, al1 = 0u;
+  float sabs = 0.f, Fx = 0.f, Fy = 0.f, Fz = 0.f;
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    if (!ALL && !(m & (1u << (i - 1)))) continue;
+    const float4 nb = lf[(PopIdx<WIDE>)nb_of(o, r, i)];
+    const bool mine = i <= 9;  // this node owns the link (c_i among c_1..c_9)
+    const int d = mine ? i : opp_of(i);
+    float Jp, Ap, Jm, Am;
+    link_pair(P, mine ? self : nb, mine ? nb : self, P.ec[d], Jp, Ap, Jm, Am);
+    const float jq0 = __fmul_rn(Jp, c2_of(d) == 1 ? P.kq1[0] : P.kq2[0]);
+    const float jq1 = __fmul_rn(Jm, c2_of(d) == 1 ? P.kq1[1] : P.kq2[1]);
+    sabs += fabsf(jq0) + fabsf(jq1);
+    if (mine) {
+      acc_round<-1>(jq0, ah0, al0);
+      acc_round<-1>(jq1, ah1, al1);
+    } else {
+      acc_round<1>(jq0, ah0, al0);
+      acc_round<1>(jq1, ah1, al1);
+    }
+    if (FLOW) {
+      // link excess flux g = -(A_+ + A_-)/(2|c|) along c_d; both ends take
+      // c_d g (from b it is -g along -c_d)
+      const float gs = (-0.5f * (float)invlen_of(d)) * (Ap + Am);
+      Fx += cx_of(d) * gs;
+      Fy += cy_of(d) * gs;
+      Fz += cz_of(d) * gs;
+    }
+  }
+  over |= !(sabs < 8.0e12f);  // |x| < 2^43 per link keeps acc_round exact; catches NaN
+  const int net = __popc(m & 0x3FE00u) - __popc(m & 0x1FFu);  // received - owned links
+  qstar[r] = q[r] + acc_value(ah0, al0, net);
+  qstar[N + r] = q[N + r] + acc_value(ah1, al1, net);
+  if (FLOW) {
+    const float F[3] = {Fx * P.inv_2a0, Fy * P.inv_2a0, Fz * P.inv_2a0};
+    lb_node<WIDE, ALL>(P, N, r, o, m, fin, fout, u, F, over);
+  }
+}
+// the same; a node whose 18 links all join fluid (most of a lattice) takes
+// a form without the per-link mask tests
+template <bool FLOW, bool WIDE>
+__device__ __forceinline__ void sweep_node_lf(const P32 &P, int N, int r, const Offs &o, uint32_t m,
+                                              const float *__restrict__ fin, float *__restrict__ fout,
+                                              const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
+                                              const float4 *__restrict__ lf, float4 *__restrict__ u, bool &over) {
+  if ((m & 0x3FFFFu) == 0x3FFFFu)
+    sweep_node_lf_<FLOW, WIDE, true>(P, N, r, o, m, fin, fout, q, qstar, lf, u, over);
+  else
+    sweep_node_lf_<FLOW, WIDE, false>(P, N, r, o, m, fin, fout, q, qstar, lf, u, over);
+}
+
+// Cell-overlap advection at one fluid node (see k_advect32), from the
+// velocity records (octant_code): a neighbour's record is read once and its
+// code tells whether its displaced cell reaches this node; only those
+// neighbours' solute is read and shared.
 __device__ __forceinline__ void advect_node(int ns, int N, int r, const Offs &o, uint32_t m,
-                                            const int64_t *__restrict__ qin, const float *__restrict__ u,
+                                            const int64_t *__restrict__ qin, const float4 *__restrict__ u,
                                             int64_t *__restrict__ qout) {
-  const float ux = u[r], uy = u[N + r], uz = u[2 * N + r];
+  const float4 v0 = u[r];
+  const int code0 = __float_as_int(v0.w);
   const long long base = 1LL << kFixBits;
   // species loops run to the compile-time bound (guarded by ns) so that acc
   // and totf stay in registers
@@ -298,10 +397,10 @@ __device__ __forceinline__ void advect_node(int ns, int N, int r, const Offs &o,
   for (int d = 0; d < 27; ++d) {
     const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
     if (d == 13 || !(m & (1u << dir_bit(dx, dy, dz)))) continue;
-    if ((dx && dx * ux <= 0.f) || (dy && dy * uy <= 0.f) || (dz && dz * uz <= 0.f)) continue;
+    if ((code0 & cell_bits(dx, dy, dz)) != cell_bits(dx, dy, dz)) continue;
 #pragma unroll
     for (int k = 0; k < LBE_MAX_SPECIES; ++k)
-      if (k < ns) acc[k] -= share(totf[k], ux, uy, uz, dx, dy, dz);
+      if (k < ns) acc[k] -= share(totf[k], v0.x, v0.y, v0.z, dx, dy, dz);
   }
   // incoming from every fluid neighbour whose cell reaches r: the source at
   // r - s gives along +s
@@ -310,12 +409,11 @@ __device__ __forceinline__ void advect_node(int ns, int N, int r, const Offs &o,
     const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
     if (d == 13 || !(m & (1u << dir_bit(-dx, -dy, -dz)))) continue;
     const int s = r + o.at(-dx, -dy, -dz);
-    const float vx = u[s], vy = u[N + s], vz = u[2 * N + s];
-    const float w = ov(dx, vx) * ov(dy, vy) * ov(dz, vz);
-    if (w == 0.f) continue;
+    const float4 v = u[s];
+    if ((__float_as_int(v.w) & cell_bits(dx, dy, dz)) != cell_bits(dx, dy, dz)) continue;
 #pragma unroll
     for (int k = 0; k < LBE_MAX_SPECIES; ++k)
-      if (k < ns) acc[k] += share(ll2f(base + qin[k * N + s]), vx, vy, vz, dx, dy, dz);
+      if (k < ns) acc[k] += share(ll2f(base + qin[k * N + s]), v.x, v.y, v.z, dx, dy, dz);
   }
 #pragma unroll
   for (int k = 0; k < LBE_MAX_SPECIES; ++k)

@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(kBlock) k_charge_partial(const Geo g, const Ph
     const double p0 = phi[r];
     double s = 0.0;
     for (int i = 1; i < kQ; ++i)
-      if (m & (1u << (i - 1))) s += lapc_of(i) * 2.0 * (phi[nbr_i(g, x, y, z, i)] - p0);
+      if (m & (1u << (i - 1))) s += lapc_of(i) * P.solid_factor * (phi[nbr_i(g, x, y, z, i)] - p0);
     for (int k = 0; k < n_elec; ++k)
       if (k == e - 1) acc[k] += -P.eps * s;
   }
@@ -330,7 +330,7 @@ __global__ void k_charge_node(const Geo g, const Phys P, const uint8_t *__restri
   coords(g, r, x, y, z);
   double s = 0.0;
   for (int i = 1; i < kQ; ++i)
-    if (m & (1u << (i - 1))) s += lapc_of(i) * 2.0 * (phi[nbr_i(g, x, y, z, i)] - phi[r]);
+    if (m & (1u << (i - 1))) s += lapc_of(i) * P.solid_factor * (phi[nbr_i(g, x, y, z, i)] - phi[r]);
   out[r] = -P.eps * s;
 }
 

@@ -42,7 +42,7 @@ bool fp32(const lbe_handle *h) { return h->prm.precision == LBE_FP32; }
 
 void free_all(lbe_handle *h) {
   void *ptrs[] = {h->id, h->mask, h->f[0], h->f[1], h->n, h->nstar, h->phi, h->u, h->qpart, h->qout, h->psi_dev,
-                  h->f32[0], h->f32[1], h->q, h->qstar, h->phi32, h->phi_lo, h->u32, h->flag};
+                  h->f32[0], h->f32[1], h->q, h->qstar, h->phi32, h->phi_lo, h->u32, h->flag, h->lf};
   for (void *p : ptrs) cudaFree(p);
   if (h->qhost) cudaFreeHost(h->qhost);
   lbe::poisson_free(h);
@@ -102,6 +102,8 @@ void fill_constants(lbe_handle *h) {
                       (lbe::cz_of(i) == 0 || p->nz == 1);
     if (self) P.selfmask |= 1u << (i - 1);
   }
+  if (p->boundary_rule == LBE_RULE_NODE) P.selfmask |= lbe::kPlainLaplacian;
+  P.solid_factor = p->boundary_rule == LBE_RULE_NODE ? 1.0 : 2.0;
   // FP32 form
   lbe::P32 &Q = h->p32;
   memset(&Q, 0, sizeof(Q));
@@ -161,6 +163,9 @@ int lbe_create(const lbe_params *p, void *cuda_stream, lbe_handle **out) {
   if (!(p->tau > 0.5) || !(p->bjerrum > 0.0)) return LBE_ERR_ARG;
   if (p->precision != LBE_FP64 && p->precision != LBE_FP32) return LBE_ERR_ARG;
   if (!(p->poisson_tol > 0.0) || p->poisson_max_iter < 1) return LBE_ERR_ARG;
+  if (p->boundary_rule != LBE_RULE_MIDPLANE && p->boundary_rule != LBE_RULE_NODE) return LBE_ERR_ARG;
+  // the FP32 form's multigrid and float-float stencils build in the doubling
+  if (p->boundary_rule == LBE_RULE_NODE && p->precision != LBE_FP64) return LBE_ERR_ARG;
   const long long N = (long long)p->nx * p->ny * p->nz;
   if (N >= (1LL << 31)) return LBE_ERR_ARG;  // 32-bit node indices in the kernels
   // FP32 kernels offset solute and velocity components in 32 bits
@@ -206,9 +211,10 @@ int lbe_create(const lbe_params *p, void *cuda_stream, lbe_handle **out) {
     alloc((void **)&h->qstar, sizeof(int64_t) * (size_t)N * p->nspecies);
     alloc((void **)&h->phi32, nf);
     alloc((void **)&h->phi_lo, nf);
-    alloc((void **)&h->u32, nf * 3);
+    alloc((void **)&h->u32, sizeof(float4) * (size_t)N);
     alloc((void **)&h->flag, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->u32, 0, nf * 3, h->stream);
+    if (h->p32.salt11) alloc((void **)&h->lf, sizeof(float4) * (size_t)N);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->u32, 0, sizeof(float4) * (size_t)N, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
   } else {
     alloc((void **)&h->f[0], nd * lbe::kQ);
@@ -343,7 +349,9 @@ static int flag_result(lbe_handle *h) {
   if (!fp32(h)) return LBE_OK;
   int flag = 0;
   memcpy(&flag, h->qhost, sizeof(int));
-  if (flag) return fail(h, LBE_ERR_NONFINITE, "fixed-point solute range exceeded (|link flux| or |n| too large)");
+  if (flag)
+    return fail(h, LBE_ERR_NONFINITE,
+                "state out of range: fixed-point solute (|link flux| or |n| too large), solvent density or a NaN");
   return LBE_OK;
 }
 static int check_flags(lbe_handle *h) {
@@ -386,6 +394,12 @@ int lbe_step(lbe_handle *h, int nsteps) {
     int rc = lbe::poisson_enqueue(h, true, fused_extrapolation);
     LBE_CK(h, mark(h));
     if (rc != LBE_OK) return rc;
+    // a long call reads the solves' status now and then, so that a failed
+    // solve ends it instead of every later step repeating the failure
+    if ((s + 1) % 1024 == 0 && s + 1 < nsteps) {
+      rc = lbe::poisson_status(h, nullptr, nullptr);
+      if (rc != LBE_OK) return rc;
+    }
   }
   // the solves ran without host synchronisation; their status and counts
   // are read once here, with the range flag, under one synchronisation (a
@@ -400,8 +414,9 @@ int lbe_step(lbe_handle *h, int nsteps) {
     h->prof_solves += h->stats.poisson_solves;
     h->prof_steps += nsteps;
   }
-  if (rc != LBE_OK) return rc;
-  return flag_result(h);
+  // a state out of range (range flag) explains a solve that failed after it
+  const int frc2 = flag_result(h);
+  return frc2 != LBE_OK ? frc2 : rc;
 }
 
 int lbe_induced_charge(lbe_handle *h, double *q_out, int out_on_device) {
@@ -504,7 +519,7 @@ int lbe_set_state(lbe_handle *h, const double *n, const double *phi, int on_devi
 }
 
 // blob: header | populations (19N) | solute (ns N) | phi (N doubles) |
-// velocity (3N) | phi of the previous kHist steps (kHist N doubles, warm
+// velocity (3N doubles, or N float4 records in the FP32 form) | phi of the previous kHist steps (kHist N doubles, warm
 // start of the next solve; header.history of them valid); populations,
 // solute and velocity in the form's own types
 struct BlobHeader {
@@ -512,7 +527,7 @@ struct BlobHeader {
   int64_t N;
   int32_t ns, flow, precision, history;
 };
-static const uint64_t kMagic = 0x4c42457374763130ULL + lbe::kHist;  // format 1, history length
+static const uint64_t kMagic = 0x4c42457374763230ULL + lbe::kHist;  // format 2, history length
 
 static void blob_sizes(const lbe_handle *h, size_t *fb, size_t *nb, size_t *pb, size_t *ub) {
   const size_t N = (size_t)h->geo.N;
@@ -520,7 +535,7 @@ static void blob_sizes(const lbe_handle *h, size_t *fb, size_t *nb, size_t *pb, 
   *fb = N * lbe::kQ * (f32 ? sizeof(float) : sizeof(double));
   *nb = N * h->prm.nspecies * (f32 ? sizeof(int64_t) : sizeof(double));
   *pb = N * sizeof(double);
-  *ub = N * 3 * (f32 ? sizeof(float) : sizeof(double)) + lbe::kHist * N * sizeof(double);
+  *ub = N * (f32 ? sizeof(float4) : 3 * sizeof(double)) + lbe::kHist * N * sizeof(double);
 }
 
 int lbe_save_state(lbe_handle *h, void *blob, size_t *size) {

@@ -164,8 +164,13 @@ struct Phys {
   double four_pi_lb;
   double eps;                     // 1/(4 pi l_B)
   double inv_2a0;                 // 1/(2 A0)
-  uint32_t selfmask;              // links that join a node to itself
+  uint32_t selfmask;              // links that join a node to itself (| kPlainLaplacian)
+  double solid_factor;            // factor of the links to solid: 2 (Eq. DiscreteLaplacianModif) or 1
 };
+// Flag kept in Phys::selfmask (above the 18 link bits) by the first-order
+// boundary rule: the Poisson stencils then leave the links to solid
+// undoubled (LBE_RULE_NODE; FP64 form only).
+constexpr uint32_t kPlainLaplacian = 1u << 30;
 
 // Constants of the FP32 form.  Solute amounts are int64 fixed point:
 // n_k = rho_k^bulk + s_k q_k with s_k = rho_k^bulk 2^-kFixBits (solid nodes
@@ -181,8 +186,6 @@ struct P32 {
   double rbd[LBE_MAX_SPECIES], sd[LBE_MAX_SPECIES];
   float kq1[LBE_MAX_SPECIES], kq2[LBE_MAX_SPECIES];  // -d_k/(2|c| s_k), |c| = 1, sqrt 2
   float ec[kQ];                                      // E_app . c_i, ec[opp] = -ec
-  float kem[kQ], kep[kQ];                            // e^{-E.c_i} - 1, e^{E.c_i} - 1 (link factors)
-  int field;                                         // E_app != 0
   float omega, guo, inv_2a0;
   int salt11;  // two species, z = +1 and -1, equal bulk concentrations
 };
@@ -288,9 +291,9 @@ struct lbe_handle {
   int64_t *qstar = nullptr;
   float *phi32 = nullptr;              // FP32 copy of phi (its high part)
   float *phi_lo = nullptr;             // low part: phi = phi32 + phi_lo to ~2^-48
-  float *u32 = nullptr;                // velocity of the last collision
+  float4 *u32 = nullptr;               // velocity of the last collision (fp32::octant_code records)
   int *flag = nullptr;                 // device error flags (fixed-point range)
-  float4 *lf = nullptr;                // 1:1 salt link records, 2 per node (fp32::link_factors)
+  float4 *lf = nullptr;                // 1:1 salt link records, one per node (fp32::link_record)
   float *pw32 = nullptr;               // FP32 Poisson work: res, p, q, e [4][N]
 
   // profiling (lbe_profile_begin/end): events [sweep start, sweep end,

@@ -63,26 +63,12 @@ __global__ void k_galerkin(const MgLevel F, const float *__restrict__ AF, const 
 
 // --- V-cycle kernels ---------------------------------------------------------
 // Restriction with 8 threads per coarse node (one per child) and a fixed-order
-// shuffle sum of the children's pre-smoothed residuals.  The coarse node's
-// residual rc and its pre-smoothed iterate zc = omega rc/diag are stored.
-// Work item w (8 per coarse node); a block strides over the items in steps of
-// the grid, the same number of steps for all its threads (the shuffle sum).
-__device__ __forceinline__ void coarse_of_item(const MgLevel &C, long long w, int &I, int &X, int &Y, int &Z,
-                                               int &ch) {
-  I = (int)(w >> 3);
-  ch = (int)(w & 7);
-  X = Y = Z = 0;
-  if (I < C.N) level_coords(C, I, X, Y, Z);
-}
+// shuffle sum of the children's pre-smoothed residuals (coarse_of_item,
+// store_coarse in mg_device.cuh).  Work item w (8 per coarse node); a block
+// strides over the items in steps of the grid, the same number of steps for
+// all its threads (the shuffle sum).
 __device__ __forceinline__ void coarse_of_thread(const MgLevel &C, int &I, int &X, int &Y, int &Z, int &ch) {
   coarse_of_item(C, (long long)blockIdx.x * blockDim.x + threadIdx.x, I, X, Y, Z, ch);
-}
-
-__device__ __forceinline__ void store_coarse(const MgLevel &C, int I, float v, const float *__restrict__ AC,
-                                             float *__restrict__ rc, float *__restrict__ zc) {
-  const float d = AC[13 * C.S + I];
-  rc[I] = v;
-  zc[I] = d != 0.f ? kOmega * v / d : 0.f;
 }
 
 // level 1: a fluid child's pre-smoothed residual is r - omega A u, u = r/diag

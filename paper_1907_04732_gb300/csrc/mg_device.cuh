@@ -216,6 +216,24 @@ __device__ __forceinline__ void coarsest_solve(const MgLevel &L, const float *__
 }
 
 
+// restriction work item w: coarse node I = w/8 and its child ch = w%8
+__device__ __forceinline__ void coarse_of_item(const MgLevel &C, long long w, int &I, int &X, int &Y, int &Z,
+                                               int &ch) {
+  I = (int)(w >> 3);
+  ch = (int)(w & 7);
+  X = Y = Z = 0;
+  if (I < C.N) level_coords(C, I, X, Y, Z);
+}
+
+// a coarse node's restricted residual rc and pre-smoothed iterate
+// zc = omega rc/diag
+__device__ __forceinline__ void store_coarse(const MgLevel &C, int I, float v, const float *__restrict__ AC,
+                                             float *__restrict__ rc, float *__restrict__ zc) {
+  const float d = AC[13 * C.S + I];
+  rc[I] = v;
+  zc[I] = d != 0.f ? kOmega * v / d : 0.f;
+}
+
 // --- forms with integer link weights and a stored pre-smoothed iterate -------
 // The modified Laplacian's link weights 1/3 (axis) and 1/6 (diagonal) are
 // 2/6 and 1/6: sums of weights are integers over 6, and a node's diagonal
@@ -240,17 +258,17 @@ __device__ __forceinline__ int diag6(uint32_t m, uint32_t selfmask) {
   return 2 * (2 * __popc(ax) + __popc(dg)) - (2 * __popc(m & ax) + __popc(m & dg));
 }
 
-// 6 * sum over fluid links of weight * v[neighbour]
+// 6 * sum over fluid links of weight * v[neighbour]; every neighbour is
+// read (a zero weight drops it) so that the loads do not wait for the mask
 __device__ __forceinline__ float nbsum6(uint32_t m, uint32_t selfmask, const Offs &o, int i,
                                         const float *__restrict__ v) {
   float s = 0.f;
 #pragma unroll
   for (int l = 1; l < kQ; ++l) {
     const uint32_t b = 1u << (l - 1);
-    if ((m & b) && !(selfmask & b)) {
-      const float vj = v[i + o.at(cx_of(l), cy_of(l), cz_of(l))];
-      s = c2_of(l) == 1 ? fmaf(2.f, vj, s) : s + vj;
-    }
+    const float vj = v[i + o.at(cx_of(l), cy_of(l), cz_of(l))];
+    const float wl = ((m & b) && !(selfmask & b)) ? (c2_of(l) == 1 ? 2.f : 1.f) : 0.f;
+    s = fmaf(wl, vj, s);
   }
   return s;
 }
@@ -264,9 +282,8 @@ __device__ __forceinline__ float presmoothed_res_z(const MgLevel &L, const float
   if (A[13 * L.S + I] == 0.f) return 0.f;
   float s = 0.f;
 #pragma unroll
-  for (int d = 0; d < 27; ++d) {
+  for (int d = 0; d < 27; ++d) {  // a zero coefficient adds nothing; no branch
     const float a = A[d * L.S + I];
-    if (a == 0.f) continue;
     const int jx = wrap(X + d % 3 - 1, L.nx), jy = wrap(Y + (d / 3) % 3 - 1, L.ny), jz = wrap(Z + d / 9 - 1, L.nz);
     s = fmaf(a, z[jx + L.nx * (jy + L.ny * jz)], s);
   }
@@ -283,9 +300,8 @@ __device__ __forceinline__ float post_value_z(const MgLevel &L, const float *__r
   if (d == 0.f) return 0.f;
   float s = 0.f;
 #pragma unroll
-  for (int q = 0; q < 27; ++q) {
+  for (int q = 0; q < 27; ++q) {  // a zero coefficient adds nothing; no branch
     const float a = A[q * L.S + I];
-    if (a == 0.f) continue;
     const int jx = wrap(X + q % 3 - 1, L.nx), jy = wrap(Y + (q / 3) % 3 - 1, L.ny), jz = wrap(Z + q / 9 - 1, L.nz);
     const float ej = fmaf(kAlpha, ec[agg_index(C, jx, jy, jz)], z[jx + L.nx * (jy + L.ny * jz)]);
     s = fmaf(a, ej, s);

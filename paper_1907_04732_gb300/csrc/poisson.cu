@@ -52,28 +52,31 @@ constexpr uint32_t kNN = nn_bits();
 constexpr uint32_t kNNN = ((1u << 18) - 1) & ~kNN;
 
 // diagonal of -lap_mod at a fluid node: 1/3 per nearest and 1/6 per
-// next-nearest link, doubled towards solid; links joining a node to itself
-// (boxes one node wide) cancel and are left out.
+// next-nearest link, doubled towards solid (not under the first-order rule,
+// kPlainLaplacian); links joining a node to itself (boxes one node wide)
+// cancel and are left out.
 template <typename T>
 __device__ __forceinline__ T diag_t(uint32_t m, uint32_t selfmask) {
   const uint32_t nself = ~selfmask;
-  const int nn = __popc(kNN & nself), nns = __popc(kNN & nself & ~m);
-  const int mm = __popc(kNNN & nself), mms = __popc(kNNN & nself & ~m);
+  const int dbl = (selfmask & kPlainLaplacian) ? 0 : 1;
+  const int nn = __popc(kNN & nself), nns = dbl * __popc(kNN & nself & ~m);
+  const int mm = __popc(kNNN & nself), mms = dbl * __popc(kNNN & nself & ~m);
   return (T)(2 * (nn + nns) + (mm + mms)) * (T)(1.0 / 6.0);
 }
 
 // lap_mod(v)(r) at a fluid node, FP64.  With the link weights scaled by 6
-// (2 nearest, 1 next-nearest, doubled towards solid) the sum needs one FP64
-// add per link: 6 lap = sum_i w_i v_i - (sum_i w_i) v0, w_i in {1, 2, 4}.
+// (2 nearest, 1 next-nearest, doubled towards solid unless dbl is false:
+// the first-order rule) the sum needs one FP64 add per link:
+// 6 lap = sum_i w_i v_i - (sum_i w_i) v0, w_i in {1, 2, 4}.
 __device__ __forceinline__ double lap_at(const Geo &g, int r, int x, int y, int z, uint32_t m,
-                                         const double *__restrict__ v) {
+                                         const double *__restrict__ v, bool dbl = true) {
   const Offs o = offsets_of(g, x, y, z);
   double s1 = 0.0, s2 = 0.0, s4 = 0.0;
   int wsum = 0;
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     const double vi = v[r + o.at(cx_of(i), cy_of(i), cz_of(i))];
-    const int w = (c2_of(i) == 1 ? 2 : 1) * ((m & (1u << (i - 1))) ? 1 : 2);
+    const int w = (c2_of(i) == 1 ? 2 : 1) * ((m & (1u << (i - 1))) || !dbl ? 1 : 2);
     if (w == 1) s1 += vi;
     else if (w == 2) s2 += vi;
     else s4 += vi;
@@ -137,9 +140,13 @@ __device__ __forceinline__ void reduce_partials(const double *part, int nblk, do
 }
 
 // outer test of a refinement round (thread 0 of the last block of k_res):
-// converged, out of rounds or out of iterations?
+// converged, out of rounds or out of iterations?  A round that did not
+// halve the residual means the tolerance lies below what the arithmetic
+// resolves: the solve stops there (LBE_ERR_NOCONVERGE) instead of repeating
+// rounds that cannot help.
 __device__ void outer_check(PoissonCtl *c, double m, double tol, int maxit, cudaGraphConditionalHandle hout,
                             cudaGraphConditionalHandle hin, int use_cond, int set_hin) {
+  const double prev = c->res;
   c->res = m;
   int done = 0;
   if (m <= tol) {
@@ -147,7 +154,7 @@ __device__ void outer_check(PoissonCtl *c, double m, double tol, int maxit, cuda
   } else if (!(m == m) || m > 1e300) {
     done = 1;
     c->status = LBE_ERR_NONFINITE;
-  } else if (c->rounds >= kMaxOuter || c->solve_iters >= maxit) {
+  } else if (c->rounds >= kMaxOuter || c->solve_iters >= maxit || (c->rounds >= 1 && m > 0.5 * prev)) {
     done = 1;
     c->status = LBE_ERR_NOCONVERGE;
   }
@@ -290,7 +297,7 @@ __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys
         q += P.z[k] * (MODE == R_FIXED ? P3.rbd[k] + P3.sd[k] * (double)nq[k * g.N + i] : n64[k * g.N + i]);
       b = P.four_pi_lb * q;
     }
-    const double rr = b + lap_at(g, (int)i, X, Y, Z, m, phi);
+    const double rr = b + lap_at(g, (int)i, X, Y, Z, m, phi, !(P.selfmask & kPlainLaplacian));
     const T rt = (T)rr;
     const T dinv = (T)1 / diag_t<T>(m, P.selfmask);
     r[i] = rt;
@@ -342,10 +349,10 @@ __global__ void __launch_bounds__(kBlock) k_cg_b(const Geo g, int zpt, uint32_t 
     const int ii = (int)i;
     T sum = 0;
 #pragma unroll
-    for (int l = 1; l < kQ; ++l) {
+    for (int l = 1; l < kQ; ++l) {  // every neighbour read; a zero weight drops it
       const uint32_t b = 1u << (l - 1);
-      if ((selfmask & b) || !(m & b)) continue;
-      sum += (T)lapc_of(l) * u[ii + o.at(cx_of(l), cy_of(l), cz_of(l))];
+      const T ul = u[ii + o.at(cx_of(l), cy_of(l), cz_of(l))];
+      sum += ((selfmask & b) || !(m & b) ? (T)0 : (T)lapc_of(l)) * ul;
     }
     const T wv = diag_t<T>(m, selfmask) * u0 - sum;
     w[i] = wv;
@@ -500,8 +507,11 @@ void fill_args(lbe_handle *h, Args &A) {
   A.selfmask = h->phys.selfmask;
   A.tol = h->prm.poisson_tol;
   A.eta = sizeof(T) == 4 ? 1e-4 : 1e-9;
-  // an inner solve need not go below a fraction of the outer tolerance
-  A.tol_inner = 0.25 * A.tol;
+  // an inner solve need not go below a fraction of the outer tolerance:
+  // 0.8 measured 2.15 CG iterations per step on the 64x64x256
+  // electro-osmosis lattice against 2.9 at 0.25 and 2.4 at 0.5, with no
+  // extra refinement round (the outer test still decides convergence)
+  A.tol_inner = 0.8 * A.tol;
   A.mask = h->mask;
   A.n64 = h->n;
   A.nq = h->q;

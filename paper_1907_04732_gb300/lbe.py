@@ -26,6 +26,7 @@ LBE_ERR_NONFINITE = -4
 LBE_ERR_STATE = -5
 LBE_ERR_GEOMETRY = -6
 LBE_FP64, LBE_FP32 = 0, 1
+LBE_RULE_MIDPLANE, LBE_RULE_NODE = 0, 1
 LBE_MAX_SPECIES = 4
 LBE_MAX_ELECTRODES = 16
 FIELD_PHI, FIELD_N, FIELD_RHO, FIELD_U, FIELD_F, FIELD_QNODE = 0, 1, 2, 3, 4, 5
@@ -41,7 +42,7 @@ EXPORTED = ["lbe_default_params", "lbe_create", "lbe_destroy", "lbe_last_error",
             "lbe_batch_set_voltage", "lbe_batch_init", "lbe_batch_step", "lbe_batch_charge",
             "lbe_batch_fields", "lbe_batch_get_stats", "lbe_batch_tuning",
             "lbe_batch_profile_begin", "lbe_batch_profile_end",
-            "lbe_adjoint_forward", "lbe_adjoint_backward"]
+            "lbe_adjoint_forward", "lbe_adjoint_forward_budget", "lbe_adjoint_backward"]
 LBE_BATCH_MAX_ELECTRODES = 4
 LBE_BATCH_TUNE_CANDIDATES = 6
 
@@ -52,7 +53,8 @@ class lbe_params(ctypes.Structure):
                 ("nspecies", ctypes.c_int), ("z", ctypes.c_double * LBE_MAX_SPECIES),
                 ("D", ctypes.c_double * LBE_MAX_SPECIES), ("rho_bulk", ctypes.c_double * LBE_MAX_SPECIES),
                 ("e_app", ctypes.c_double * 3), ("flow", ctypes.c_int), ("precision", ctypes.c_int),
-                ("poisson_tol", ctypes.c_double), ("poisson_max_iter", ctypes.c_int)]
+                ("poisson_tol", ctypes.c_double), ("poisson_max_iter", ctypes.c_int),
+                ("boundary_rule", ctypes.c_int)]
 
 
 class lbe_stats(ctypes.Structure):
@@ -125,6 +127,7 @@ def load(path: str = LIB_PATH):
     lib.lbe_batch_get_stats.argtypes = [vp, ctypes.POINTER(lbe_stats)]
     lib.lbe_batch_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp]
     lib.lbe_adjoint_forward.argtypes = [vp, ip, ip, dp]
+    lib.lbe_adjoint_forward_budget.argtypes = [vp, ip, ctypes.c_size_t, dp]
     lib.lbe_adjoint_backward.argtypes = [vp, dp, ip, ctypes.POINTER(lbe_adjoint_grad), vp, ip]
     lib.lbe_batch_profile_begin.argtypes = [vp]
     lib.lbe_batch_profile_end.argtypes = [vp, ctypes.POINTER(lbe_profile)]
@@ -228,6 +231,10 @@ def lbe_adjoint_forward(h, nsteps: int, every: int, q_out=None):
     return _check(h, load().lbe_adjoint_forward(h, int(nsteps), int(every), q_out))
 
 
+def lbe_adjoint_forward_budget(h, nsteps: int, device_bytes: int, q_out=None):
+    return _check(h, load().lbe_adjoint_forward_budget(h, int(nsteps), int(device_bytes), q_out))
+
+
 def lbe_adjoint_backward(h, dq, soft_electrode: int, dchi_ptr, dchi_on_device: bool) -> lbe_adjoint_grad:
     g = lbe_adjoint_grad()
     arr = (ctypes.c_double * max(len(dq), 1))(*[float(v) for v in dq])
@@ -305,8 +312,9 @@ def lbe_batch_tuning(b):
 
 
 # --- convenience wrapper ---------------------------------------------------
-def params_for(workload, *, precision=LBE_FP64, tol=1e-13, maxit=100000, flow=None) -> lbe_params:
-    """lbe_params for a ``workloads.Workload``."""
+def params_for(workload, *, precision=LBE_FP64, tol=1e-13, maxit=100000, flow=None,
+               rule=LBE_RULE_MIDPLANE) -> lbe_params:
+    """lbe_params for a ``workloads.Workload`` (rule: lbe_params.boundary_rule)."""
     p = lbe_default_params()
     p.nx, p.ny, p.nz = workload.shape
     for a in range(3):
@@ -323,6 +331,7 @@ def params_for(workload, *, precision=LBE_FP64, tol=1e-13, maxit=100000, flow=No
     p.precision = precision
     p.poisson_tol = tol
     p.poisson_max_iter = maxit
+    p.boundary_rule = rule
     return p
 
 
@@ -447,6 +456,13 @@ class Lattice:
         """lbe_init + nsteps steps with checkpoints; returns Q(T)."""
         q = np.zeros(max(self.n_elec, 1))
         lbe_adjoint_forward(self.h, nsteps, every, q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return q[: self.n_elec]
+
+    def adjoint_forward_budget(self, nsteps: int, device_bytes: int) -> np.ndarray:
+        """lbe_init + nsteps steps with revolve checkpoints in device_bytes;
+        returns Q(T)."""
+        q = np.zeros(max(self.n_elec, 1))
+        lbe_adjoint_forward_budget(self.h, nsteps, device_bytes, q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         return q[: self.n_elec]
 
     def adjoint_backward(self, dq, soft_electrode: int = 1, dchi=None):
