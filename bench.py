@@ -92,37 +92,57 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-# bytes per node moved by each kernel (algorithmic: every array element read
-# or written once; neighbour re-reads come from cache)
+# Algorithmic bytes per fluid node (the method's own data, each element read
+# or written once; neighbour re-reads come from cache).  The fused sweep of
+# the FP32 deviation form moves 19 populations in and out (152 B), the two
+# solute amounts (16 B at 32 bits each), the potential (4 B), the geometry
+# (1 B) and writes the velocity for the advection (12 B): 185 B.  The
+# implementation moves more (64-bit solute amounts, a 16 B velocity record,
+# the link records of the prep kernel): IMPL_BYTES.
 BYTES = {}
 BYTES["fp64"] = {
     # 19 populations read + 19 written, n_k read + n*_k written, phi read,
-    # u written (3), link mask read
-    "sweep": lambda ns: 8 * (19 + 19 + 2 * ns + 1 + 3) + 4,
-    # n*_k read, n_k written, u read (3), link mask
-    "advect": lambda ns: 8 * (2 * ns + 3) + 4,
-    # one CG iteration: matvec (p read, q write), update (phi, res, p, q read;
-    # phi, res write), direction (res, p read; p write), mask read thrice
-    "cg_iter": lambda ns: 8 * (2 + 6 + 3) + 3 * 4,
+    # u written (3), geometry
+    "sweep": lambda ns: 8 * (19 + 19 + 2 * ns + 1 + 3) + 1,
+    # n*_k read, n_k written, u read (3)
+    "advect": lambda ns: 8 * (2 * ns + 3),
+    # one Jacobi-preconditioned CG iteration: matvec (p read, q write),
+    # update (phi, res, p, q read; phi, res write), direction (res, p read;
+    # p write)
+    "cg_iter": lambda ns: 8 * (2 + 6 + 3),
 }
 BYTES["fp32"] = {
-    # 19 FP32 deviations read + 19 written, int64 q_k read + q*_k written,
-    # FP32 phi read, FP32 u written (3), link mask
-    "sweep": lambda ns: 4 * (19 + 19 + 1 + 3) + 8 * 2 * ns + 4,
-    # int64 q*_k read, q_k written, u read (3), mask; plus the next solve's
-    # warm start fused into this kernel: phi and its three previous values
-    # read and written (FP64, cubic extrapolation), the FP32 split written
-    "advect": lambda ns: 8 * 2 * ns + 4 * 3 + 4 + 8 * 8 + 4 * 2,
-    # one FP32 CG iteration of the inner correction solve: matvec (p read,
-    # q write), update (e, res, p, q read; e, res write), direction (res, p
-    # read; p write), mask read thrice
-    "cg_iter": lambda ns: 4 * (2 + 6 + 3) + 3 * 4,
+    "sweep": lambda ns: 4 * (19 + 19) + 4 * 2 * ns + 4 + 1 + 4 * 3,
+    # solute read and written (32 bits each), velocity read (3 x 4 B)
+    "advect": lambda ns: 4 * 2 * ns + 4 * 3,
+    # one multigrid-preconditioned CG iteration, level 0 (4 B vectors):
+    # update (u, p, w, s, x, r read; p, s, x, r, u written: 44 B),
+    # restriction (r, u: 8 B), prolongation (u read, t written: 8 B),
+    # post-smoothing (r, t read, u written: 12 B), stencil and dot products
+    # (u, r read, w written: 12 B) = 84 B; coarse levels (27-point operator,
+    # 1/8 of the nodes per level): about 16 B per fine node
+    "cg_iter": lambda ns: 84 + 16,
 }
-BYTES_FP64 = BYTES["fp64"]
+IMPL_BYTES = {
+    # prep (mask, potential, two 64-bit amounts read; 16 B record written) +
+    # sweep (populations, record, mask, amounts read and written, 16 B
+    # velocity record)
+    "fp32": {"sweep": lambda ns: (4 + 4 + 16 + 16) + (152 + 16 + 4 + 32 + 16),
+             "advect": lambda ns: 32 + 16 + 8 * 8 + 8},
+}
 
-# DRAM bytes per launch of the fused sweep from an ncu capture of the same
-# kernel code (profiles/), or absent when the kernel changed since
-SWEEP_TRAFFIC = {("fp32", "eof_64x64x256"): 104150016 + 64849920}  # profiles/fp32_eof64x64x256_k_sweep32_ncu_full.md
+# DRAM bytes per launch of the fused sweep from an ncu capture, valid only
+# for the kernel source it was taken from (a hash of the sweep's sources)
+SWEEP_TRAFFIC = {}
+
+
+def sweep_source_hash() -> str:
+    import hashlib
+    hsh = hashlib.sha256()
+    for f in ("fp32_device.cuh", "kernels_fp32.cu", "lbe_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1907_04732_gb300", "csrc", f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()[:16]
 
 
 class ClockSampler:
@@ -209,17 +229,18 @@ def cpu_baseline(w, tol, budget_s=15.0):
                       f"periodic section of {w.name} after its init ({dt:.1f} s, OpenMP)"}
 
 
-def cpu_baseline_single_thread(w, tol, budget_s=5.0):
-    """The same oracle timing on one host thread (a child process with
-    OMP_NUM_THREADS=1); None if it cannot run."""
+def cpu_baseline_child(workload: str, tol, budget_s, threads=None):
+    """cpu_baseline in a child process (the GPU process never loads the
+    oracle), on all host cores or on `threads` threads; None if it fails."""
     code = ("import json, sys; sys.path.insert(0, %r); import bench; "
-            "from paper_1907_04732_gb300 import workloads as wl; "
-            "w = [x for x in [wl.eof_plates()] if x.name == %r]; "
-            "print(json.dumps(bench.cpu_baseline(w[0], %r, %r)['value']) if w else 'null')"
-            % (os.path.dirname(os.path.abspath(__file__)), w.name, tol, budget_s))
+            "print(json.dumps(bench.cpu_baseline(bench.make_workload(%r), %r, %r)))"
+            % (ROOT, workload, tol, budget_s))
+    env = dict(os.environ)
+    if threads:
+        env["OMP_NUM_THREADS"] = str(threads)
     try:
-        p = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, OMP_NUM_THREADS="1"),
-                           capture_output=True, text=True, timeout=120)
+        p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=120 + 4 * budget_s)
         return json.loads(p.stdout.strip().splitlines()[-1]) if p.returncode == 0 else None
     except Exception:
         return None
@@ -345,10 +366,11 @@ def batch_leg(args, lbe, torch, stream, peak):
 
 def adjoint_leg(args, lbe, torch, stream):
     """Gradient of the induced charge after T steps on the 256x256x128
-    porous electrode (solvent at rest): FP32 forward with checkpoints every
-    K steps, then the reverse sweep (recomputation, adjoint Poisson solves),
-    timed with CUDA events; the plain FP64 forward step on the same lattice
-    for comparison."""
+    porous electrode (solvent at rest): FP32 forward with checkpoints placed
+    by the binomial (revolve) schedule within a device-memory budget (or
+    every K steps with --adjoint-every), then the reverse sweep
+    (recomputation, adjoint Poisson solves), timed with CUDA events; the
+    plain FP64 forward step on the same lattice for comparison."""
     import numpy as np
     w = wl.porous_electrode()
     p = lbe.params_for(w, tol=args.tol, precision=lbe.LBE_FP32)
@@ -358,7 +380,18 @@ def adjoint_leg(args, lbe, torch, stream):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     torch.cuda.synchronize()
     ev[0].record(stream)
-    q = lat.adjoint_forward(args.adjoint_steps, args.adjoint_every)
+    per_slot = 48 * w.nodes  # solute (2 x 8 B), potential and its 3 earlier values (FP64)
+    if args.adjoint_every > 0:
+        q = lat.adjoint_forward(args.adjoint_steps, args.adjoint_every)
+        slots = -(-args.adjoint_steps // args.adjoint_every) + 1
+        ck_bytes, seg_bytes = slots * per_slot, args.adjoint_every * 20 * w.nodes
+        schedule = "uniform, every %d steps" % args.adjoint_every
+    else:
+        budget = int(args.adjoint_budget_gb * 1e9)
+        q = lat.adjoint_forward_budget(args.adjoint_steps, budget)
+        slots = min(budget // per_slot, args.adjoint_steps + 2)
+        ck_bytes, seg_bytes = slots * per_slot, 0
+        schedule = "binomial (revolve), %d slots within %.1f GB" % (slots, args.adjoint_budget_gb)
     ev[1].record(stream)
     g, dchi = lat.adjoint_backward([1.0, 0.0], 1)
     ev[2].record(stream)
@@ -366,7 +399,6 @@ def adjoint_leg(args, lbe, torch, stream):
     fwd_ms, bwd_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     lat.close()
     T = args.adjoint_steps
-    nseg = -(-T // args.adjoint_every)
     # plain FP64 forward on the same lattice
     ms64 = None
     if args.compare_steps > 0:
@@ -385,7 +417,7 @@ def adjoint_leg(args, lbe, torch, stream):
         l64.close()
     node_steps = w.nodes * T
     return {"workload": w.name + " (200 seeded spheres r 6-12 on a backing plate, counter plate; flow off)",
-            "objective": "Q_1 after T steps", "steps": T, "checkpoint_every": args.adjoint_every,
+            "objective": "Q_1 after T steps", "steps": T, "checkpoint_schedule": schedule,
             "forward_ms": fwd_ms, "backward_ms": bwd_ms,
             "forward_mlups": node_steps / (fwd_ms * 1e-3) / 1e6,
             "gradient_mlups": node_steps / ((fwd_ms + bwd_ms) * 1e-3) / 1e6,
@@ -393,7 +425,8 @@ def adjoint_leg(args, lbe, torch, stream):
             "recomputed_steps": int(g.recomputed_steps), "adjoint_cg_iters": int(g.poisson_iters),
             "backward_phases_ms": {"recompute": g.recompute_ms, "flux_transpose": g.flux_ms,
                                    "adjoint_solves": g.solve_ms},
-            "checkpoint_bytes": (nseg + 1) * 48 * w.nodes, "segment_bytes": args.adjoint_every * 20 * w.nodes,
+            "checkpoint_bytes": ck_bytes, "segment_bytes": seg_bytes,
+            "recomputed_per_step": g.recomputed_steps / max(T, 1),
             "Q": [float(v) for v in q], "dQ1_dpsi": [float(v) for v in g.dpsi[:2]],
             "dQ1_drho_bulk": float(g.drho_bulk), "dQ1_dD": [float(v) for v in g.dD[:2]],
             "dQ1_dchi_absmax": float(np.abs(dchi).max()),
@@ -420,7 +453,9 @@ def main():
     ap.add_argument("--batch-warmup", type=int, default=3)
     ap.add_argument("--adjoint-steps", type=int, default=2000,
                     help="steps of the porous-electrode gradient run (0 = skip)")
-    ap.add_argument("--adjoint-every", type=int, default=100)
+    ap.add_argument("--adjoint-every", type=int, default=0,
+                    help="uniform checkpoints every K steps (0: the binomial schedule within --adjoint-budget-gb)")
+    ap.add_argument("--adjoint-budget-gb", type=float, default=8.0)
     args = ap.parse_args()
     w = make_workload(args.workload)
     if args.impl == "reference":
@@ -492,28 +527,29 @@ def main():
 
     peak, peak_kind = load_peaks()
     ns = len(w.z)
-    BYTES_FP64 = BYTES[args.precision]
+    B = BYTES[args.precision]
     iters = prof.poisson_iters / max(prof.poisson_solves, 1)
     phases = {"sweep": prof.sweep_ms / max(prof.sweep_launches, 1),
               "advect": prof.advect_ms / max(prof.advect_launches, 1),
               "poisson": prof.poisson_ms / max(prof.poisson_solves, 1)}
-    sweep_bytes = BYTES_FP64["sweep"](ns) * fluid
+    sweep_bytes = B["sweep"](ns) * fluid
     sweep_gbs = sweep_bytes / (phases["sweep"] * 1e-3) / 1e9
-    adv_bytes = BYTES_FP64["advect"](ns) * fluid
+    adv_bytes = B["advect"](ns) * fluid if w.flow else 0
+    pois_bytes = B["cg_iter"](ns) * iters * fluid
     step_ms = ms_step
     shares = {k: v / step_ms for k, v in phases.items()}
-    # The fused LBE sweep is the kernel the HBM roofline is reported for
-    # (its algorithmic bytes / its live CUDA-event time).  The Poisson phase
-    # is a CUDA graph of many small kernels (multigrid levels, CG vectors);
-    # its share of the step is reported beside it.
-    roof = {"kernel": "k_sweep32 (fused link flux + force + BGK/Guo collide + stream)"
+    # The fused LBE sweep (its prep kernel included) is the kernel the HBM
+    # roofline is reported for: algorithmic bytes / live CUDA-event time.
+    traffic = SWEEP_TRAFFIC.get((args.precision, w.name, sweep_source_hash()))
+    roof = {"kernel": "k_prep32 + k_sweep32 (fused link flux + force + BGK/Guo collide + stream)"
             if args.precision == "fp32" else "k_sweep (FP64 fused sweep)",
             "bound": "hbm", "achieved": sweep_gbs, "peak": peak, "unit": "GB/s", "frac": sweep_gbs / peak,
-            "traffic": SWEEP_TRAFFIC.get((args.precision, w.name)),
-            "bytes_per_node": BYTES_FP64["sweep"](ns), "units_per_launch": fluid,
+            "traffic": traffic,
+            "bytes_per_node": B["sweep"](ns), "units_per_launch": fluid,
+            "impl_bytes_per_node": IMPL_BYTES.get(args.precision, B)["sweep"](ns),
             "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
             "share_of_step": shares["sweep"]}
-    step_bytes = sweep_bytes + adv_bytes
+    step_bytes = sweep_bytes + adv_bytes + pois_bytes
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "value_fluid_nodes": whole_job_mlups(world, fluid, args.steps, ms * 1e-3),
@@ -527,8 +563,16 @@ def main():
         "roofline": roof,
         "phases_ms": phases, "phase_shares": shares,
         "poisson": {"ms_per_step": phases["poisson"], "cg_iters_per_step": iters,
-                    "note": "refinement on a float-float residual, multigrid-preconditioned FP32 CG, cubic warm start in time, one CUDA graph"},
-        "lb_part_hbm_frac": step_bytes / ((phases["sweep"] + phases["advect"]) * 1e-3) / 1e9 / peak,
+                    "bytes_per_node_per_cg_iter": B["cg_iter"](ns),
+                    "gbs": pois_bytes / (phases["poisson"] * 1e-3) / 1e9,
+                    "hbm_frac": pois_bytes / (phases["poisson"] * 1e-3) / 1e9 / peak,
+                    "note": "refinement on a float-float residual, multigrid-preconditioned FP32 CG, cubic warm "
+                            "start in time; one persistent cooperative launch per solve (graph path when not "
+                            "available); its vectors stay in L2, so the fraction is of effective bandwidth"},
+        "step": {"bytes_per_node": step_bytes / fluid, "gbs": step_bytes / (step_ms * 1e-3) / 1e9,
+                 "hbm_frac": step_bytes / (step_ms * 1e-3) / 1e9 / peak,
+                 "parts": "fused sweep + advection + Poisson CG iterations (algorithmic bytes)"},
+        "lb_part_hbm_frac": (sweep_bytes + adv_bytes) / ((phases["sweep"] + phases["advect"]) * 1e-3) / 1e9 / peak,
         "advect_gbs": adv_bytes / (phases["advect"] * 1e-3) / 1e9 if phases["advect"] > 0 else None,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * w.n_elec,
                 "d2h_bytes_per_step": 8 * w.n_elec},
@@ -559,8 +603,12 @@ def main():
     if args.adjoint_steps > 0:
         line["adjoint"] = adjoint_leg(args, lbe, torch, stream)
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, args.tol)
-        line["cpu_baseline"]["single_thread_value"] = cpu_baseline_single_thread(w, args.tol)
+        cb = cpu_baseline_child(args.workload, args.tol, 15.0)
+        if cb is not None:
+            one = cpu_baseline_child(args.workload, args.tol, 5.0, threads=1)
+            cb["single_thread_value"] = one["value"] if one else None
+            cb["process"] = "child processes (the GPU process does not load the oracle)"
+        line["cpu_baseline"] = cb
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:

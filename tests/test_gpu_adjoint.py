@@ -179,3 +179,34 @@ def test_adjoint_porous_crop_2000_steps_vs_stored_tangent(lbe):
     for key in ("chi_fluid_node", "chi_interface_node"):
         assert abs(dchi[ref[key]] - dQ[key]) <= TOL * np.abs(dchi).max(), key
     assert g.recomputed_steps == 2000 - 20
+
+
+@pytest.mark.parametrize("slots", [2, 3, 5, 9])
+def test_revolve_schedule_matches_uniform_checkpoints(lbe, slots):
+    """Binomial ("revolve") checkpointing within a memory budget of `slots`
+    checkpoints reproduces the uniform-checkpoint gradient bit for bit, with
+    each forward step recomputed at most r times (r the smallest with
+    C(s + r, s) >= T, s = slots - 2); two slots recompute from the start for
+    every step."""
+    w = crop_case()
+    steps, dq = 60, np.array([1.0, 0.3])
+    _, dpsi, ddebye, dD, dchi, g, lat = gpu_grad(lbe, w, steps, 7, dq)
+    per_slot = w.nodes * (2 * 8 + 8 + 3 * 8)
+    q2 = lat.adjoint_forward_budget(steps, slots * per_slot + per_slot // 2)
+    g2, dchi2 = lat.adjoint_backward(dq, 1)
+    np.testing.assert_array_equal(np.array(g2.dpsi[:2]), dpsi)
+    np.testing.assert_array_equal(np.array(g2.dD[:2]), dD)
+    assert g2.drho_bulk == g.drho_bulk
+    np.testing.assert_array_equal(dchi2, dchi)
+    s = slots - 2
+    if s > 0:
+        r = 0
+        while math.comb(s + r, s) < steps:
+            r += 1
+        assert g2.recomputed_steps <= (r + 1) * steps
+    else:
+        assert g2.recomputed_steps <= steps * steps // 2
+    print("revolve: %d slots, %d recomputed steps for %d steps" % (slots, g2.recomputed_steps, steps))
+    with pytest.raises(lbe.LBEError) as e:
+        lat.adjoint_forward_budget(steps, per_slot)  # one slot
+    assert e.value.code == lbe.LBE_ERR_ARG

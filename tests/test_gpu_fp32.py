@@ -209,3 +209,4 @@ def test_periodic_box_without_electrodes(lbe):
     assert np.all(np.isfinite(g.phi()))
     assert np.abs(g.phi()).max() <= 1e-12
     g.close()
+

@@ -203,3 +203,33 @@ def test_charge_map_sums_to_electrode_charges(lbe, precision):
     n = g.n()
     ionic = (n[0] - n[1]).sum()
     assert abs(qmap.sum() + ionic) <= 1e-9 * np.abs(q).max()
+
+
+def test_first_order_rule_matches_oracle(lbe):
+    """The first-order boundary rule (LBE_RULE_NODE: plain Laplacian, solid
+    nodes at their potential) against the oracle's same rule, element by
+    element, with flow, field and two electrodes."""
+    from oracle import Oracle
+    ids = wl.random_blobs(21, 19, 17, 2, 0.2, seed=17)
+    w = wl.Workload("blob", ids, 2, (1, 1, 1), (0.0, 0.25), 1.1, 2.5, e_app=(2e-3, -1e-3, 5e-4))
+    o = Oracle(w.shape, w.periodic, tau=w.tau, bjerrum=w.bjerrum, z=w.z, D=w.D, rho_bulk=w.rho_bulk,
+               e_app=w.e_app, flow=True, tol=TOL)
+    o.set_geometry(w.ids, w.n_elec)
+    o.set_voltage(w.psi)
+    o.set_boundary_rule(1)
+    o.init()
+    g = lbe.Lattice.from_workload(w, tol=TOL, rule=lbe.LBE_RULE_NODE)
+    g.init()
+    o.step(12)
+    g.step(12)
+    compare(o, g, 0.25, lbe)
+    # Gauss: the induced charges still balance the ionic charge exactly
+    n = g.n()
+    assert abs(g.charge().sum() + (n[0] - n[1]).sum()) < 1e-12 * np.abs(g.charge()).max()
+
+
+def test_first_order_rule_needs_fp64(lbe):
+    p = lbe.params_for(wl.plate_capacitor(2, 2, 8), precision=lbe.LBE_FP32, rule=lbe.LBE_RULE_NODE)
+    with pytest.raises(lbe.LBEError) as e:
+        lbe.Lattice(p)
+    assert e.value.code == lbe.LBE_ERR_ARG

@@ -155,3 +155,64 @@ def test_time_dependent_voltage(lbe):
     assert np.abs(g.phi() - o.phi()).max() <= 1e-6 * 0.15
     qo = o.charge()
     assert np.all(np.abs(g.charge() - qo) <= 1e-5 * np.abs(qo).max())
+
+
+def _plate_capacitance_error(lbe, lam, L, lB, precision, rule=0, dV=0.01, D=0.2):
+    """Relative deviation of a plate column's steady capacitance from
+    Eq. SLITcapaDH (finite-L form): Q(t) sampled over four charging times
+    tau = L lambda/(2D) from the uncharged start, Q_inf from an exponential
+    fit over the last three (as the paper takes C from Q_inf)."""
+    from scipy.optimize import curve_fit
+    w = wl.plate_capacitor(1, 1, L + 2, debye=lam, bjerrum=lB, psi=(0.0, dV), flow=False, D=(D, D))
+    tol = 1e-13 if precision == lbe.LBE_FP64 else 1e-12
+    g = lbe.Lattice.from_workload(w, precision=precision, tol=tol, rule=rule)
+    g.init()
+    tau = L * lam / (2 * D)
+    dt = max(1, int(tau / 10))
+    t, q = [], []
+    for k in range(40):
+        g.step(dt)
+        t.append(dt * (k + 1))
+        q.append(g.charge()[1])
+    g.close()
+    t, q = np.array(t, float), np.array(q)
+    f = lambda t, qi, b, tt: qi - b * np.exp(-t / tt)
+    sel = t >= tau
+    p, _ = curve_fit(f, t[sel], q[sel], p0=(q[-1], q[-1] - q[sel][0], tau))
+    qdh = an.dh_plate_charge_per_area(an.eps_of(lB), 1.0 / lam, L, dV)
+    return (p[0] - qdh) / qdh
+
+
+def test_boundary_rule_convergence_orders(lbe):
+    """Ablation of the boundary rule (Sec. "Imposing conducting boundary
+    conditions"): on plate columns with L = 8 lambda_D and lambda_D/dx = 2,
+    4, 8, the capacitance error of the first-order rule (LBE_RULE_NODE)
+    falls as dx/lambda_D, that of the paper's modified Laplacian as
+    (dx/lambda_D)^2 (FP64 form)."""
+    lams = [2.0, 4.0, 8.0]
+    out = {}
+    for rule in (lbe.LBE_RULE_NODE, lbe.LBE_RULE_MIDPLANE):
+        errs = [_plate_capacitance_error(lbe, lam, int(8 * lam), 1.0, lbe.LBE_FP64, rule) for lam in lams]
+        slope = np.polyfit(np.log(1.0 / np.array(lams)), np.log(np.abs(errs)), 1)[0]
+        out[rule] = (errs, slope)
+    errs1, s1 = out[lbe.LBE_RULE_NODE]
+    errs2, s2 = out[lbe.LBE_RULE_MIDPLANE]
+    assert 0.8 < s1 < 1.25, out
+    assert 1.75 < s2 < 2.25, out
+    assert all(abs(a) > 4 * abs(b) for a, b in zip(errs1, errs2)), out
+
+
+def test_fig4b_second_order_at_fixed_L_over_lB(lbe):
+    """Fig. 4b: at L/l_B = 52.5, for two salt concentrations (lambda_D/l_B =
+    1 and 2), the capacitance error of the FP32 form against Debye-Hueckel
+    falls as (dx/lambda_D)^2 when the lattice is refined (l_B/dx = 2, 4, 6,
+    i.e. L = 105, 210, 315 nodes)."""
+    for ratio in (1.0, 2.0):
+        xs, errs = [], []
+        for b in (2, 4, 6):
+            lam, L = ratio * b, int(round(52.5 * b))
+            errs.append(_plate_capacitance_error(lbe, lam, L, float(b), lbe.LBE_FP32))
+            xs.append(1.0 / lam)
+        slope = np.polyfit(np.log(xs), np.log(np.abs(errs)), 1)[0]
+        assert 1.8 < slope < 2.2, (ratio, errs, slope)
+        assert np.all(np.array(errs) < 0), errs  # the lattice capacitor is slightly too small
