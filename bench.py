@@ -567,8 +567,8 @@ def main():
                     "gbs": pois_bytes / (phases["poisson"] * 1e-3) / 1e9,
                     "hbm_frac": pois_bytes / (phases["poisson"] * 1e-3) / 1e9 / peak,
                     "note": "refinement on a float-float residual, multigrid-preconditioned FP32 CG, cubic warm "
-                            "start in time; one persistent cooperative launch per solve (graph path when not "
-                            "available); its vectors stay in L2, so the fraction is of effective bandwidth"},
+                            "start in time; one CUDA graph launch per solve (conditional while nodes for the refinement "
+                            "and CG loops); its vectors stay in L2, so the fraction is of effective bandwidth"},
         "step": {"bytes_per_node": step_bytes / fluid, "gbs": step_bytes / (step_ms * 1e-3) / 1e9,
                  "hbm_frac": step_bytes / (step_ms * 1e-3) / 1e9 / peak,
                  "parts": "fused sweep + advection + Poisson CG iterations (algorithmic bytes)"},

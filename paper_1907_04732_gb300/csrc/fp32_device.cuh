@@ -246,12 +246,9 @@ __host__ __device__ constexpr int cell_bits(int dx, int dy, int dz) {
 //   df'_i = (1 - omega) df_i + E_even +- E_odd,
 //   E_even = w [omega (drho + rho (4.5 cu^2 - 1.5 uu)) + guo (9 cu cF - 3 uF)]
 //   E_odd  = w [3 omega rho cu + 3 guo cF]
-template <bool WIDE, bool ALL = false>
-__device__ __forceinline__ void lb_node(const P32 &P, int N, int r, const Offs &o, uint32_t m,
-                                        const float *__restrict__ fin, float *__restrict__ fout,
-                                        float4 *__restrict__ u, const float F[3], bool &over) {
-  float f[kQ];
-  gather32<WIDE, ALL>(N, r, o, m, fin, f);
+template <bool WIDE>
+__device__ __forceinline__ void lb_collide(const P32 &P, int N, int r, const float f[kQ], float *__restrict__ fout,
+                                           float4 *__restrict__ u, const float F[3], bool &over) {
   float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
@@ -284,6 +281,14 @@ __device__ __forceinline__ void lb_node(const P32 &P, int N, int r, const Offs &
     fout[(PopIdx<WIDE>)io * N + r] = keep * f[io] + (ee - eo);
   }
 }
+template <bool WIDE, bool ALL = false>
+__device__ __forceinline__ void lb_node(const P32 &P, int N, int r, const Offs &o, uint32_t m,
+                                        const float *__restrict__ fin, float *__restrict__ fout,
+                                        float4 *__restrict__ u, const float F[3], bool &over) {
+  float f[kQ];
+  gather32<WIDE, ALL>(N, r, o, m, fin, f);
+  lb_collide<WIDE>(P, N, r, f, fout, u, F, over);
+}
 
 // Fused step at one fluid node, any salt: quantised link fluxes and
 // q* = q - sum Jq, solvent force, and (FLOW) BGK + Guo collision with pull
@@ -314,12 +319,16 @@ __device__ __forceinline__ void sweep_node(const P32 &P, int N, int r, const Off
 // (link_record): per link the flux terms of both species (link_pair, in the
 // link's one orientation), their fixed-point rounding (owner end subtracts,
 // the other end adds: exact conservation), the force from the link excess
-// fluxes, then (FLOW) BGK + Guo collision with pull streaming.
+// fluxes, then (FLOW) BGK + Guo collision with pull streaming.  The
+// populations are read before the link loop, so that their loads are in
+// flight during the link arithmetic (19 registers held across it).
 template <bool FLOW, bool WIDE, bool ALL>
 __device__ __forceinline__ void sweep_node_lf_(const P32 &P, int N, int r, const Offs &o, uint32_t m,
                                               const float *__restrict__ fin, float *__restrict__ fout,
                                               const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
                                               const float4 *__restrict__ lf, float4 *__restrict__ u, bool &over) {
+  float f[kQ];
+  if (FLOW) gather32<WIDE, ALL>(N, r, o, m, fin, f);
   const float4 self = lf[(PopIdx<WIDE>)r];
   unsigned ah0 = 0u, al0 = 0u, ah1 = 0u, al1 = 0u;
   float sabs = 0.f, Fx = 0.f, Fy = 0.f, Fz = 0.f;
@@ -356,7 +365,7 @@ __device__ __forceinline__ void sweep_node_lf_(const P32 &P, int N, int r, const
   qstar[N + r] = q[N + r] + acc_value(ah1, al1, net);
   if (FLOW) {
     const float F[3] = {Fx * P.inv_2a0, Fy * P.inv_2a0, Fz * P.inv_2a0};
-    lb_node<WIDE, ALL>(P, N, r, o, m, fin, fout, u, F, over);
+    lb_collide<WIDE>(P, N, r, f, fout, u, F, over);
   }
 }
 // the same; a node whose 18 links all join fluid (most of a lattice) takes

@@ -48,9 +48,11 @@ __global__ void __launch_bounds__(kBlock) k_prep32(const Geo g, const P32 P, con
 // Fused step kernel of a 1:1 salt: link fluxes from the link records
 // (quantised, exactly conserving), solute update q* = q - sum Jq, solvent
 // force, and (FLOW) BGK + Guo collision and pull streaming with halfway
-// bounce-back, all in FP32 deviations.
+// bounce-back, all in FP32 deviations.  Capped at 64 registers (four blocks
+// per SM), with the populations read before the link loop: the fastest of
+// the uncapped, capped, early- and late-read forms measured.
 template <bool FLOW, bool WIDE>
-__global__ void __launch_bounds__(kBlock) k_sweep32(const Geo g, const P32 P, const uint32_t *__restrict__ mask,
+__global__ void __launch_bounds__(kBlock, 4) k_sweep32(const Geo g, const P32 P, const uint32_t *__restrict__ mask,
                                                     const float *__restrict__ fin, float *__restrict__ fout,
                                                     const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
                                                     const float4 *__restrict__ lf, float4 *__restrict__ u,
