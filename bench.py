@@ -566,9 +566,12 @@ def main():
                     "bytes_per_node_per_cg_iter": B["cg_iter"](ns),
                     "gbs": pois_bytes / (phases["poisson"] * 1e-3) / 1e9,
                     "hbm_frac": pois_bytes / (phases["poisson"] * 1e-3) / 1e9 / peak,
-                    "note": "refinement on a float-float residual, multigrid-preconditioned FP32 CG, cubic warm "
-                            "start in time; one CUDA graph launch per solve (conditional while nodes for the refinement "
-                            "and CG loops); its vectors stay in L2, so the fraction is of effective bandwidth"},
+                    "note": ("refinement on a float-float residual, multigrid-preconditioned FP32 CG, cubic warm "
+                             "start in time; one CUDA graph launch per solve (conditional while nodes for the "
+                             "refinement and CG loops); its vectors stay in L2, so the fraction is of effective "
+                             "bandwidth") if args.precision == "fp32" else
+                            ("FP64 Jacobi-preconditioned CG in one CUDA graph launch per solve, cubic warm start "
+                             "in time")},
         "step": {"bytes_per_node": step_bytes / fluid, "gbs": step_bytes / (step_ms * 1e-3) / 1e9,
                  "hbm_frac": step_bytes / (step_ms * 1e-3) / 1e9 / peak,
                  "parts": "fused sweep + advection + Poisson CG iterations (algorithmic bytes)"},

@@ -478,17 +478,16 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 // is split exactly (two_sum), the low parts and the rounding errors go to the
 // error word.  Returns S + E ~ 6 lap to ~2^-46 of the terms; the FP64 form
 // of lap_at needs 18 FP64 adds, which are slow on this GPU.
-__device__ __forceinline__ void lap6_ff(const Geo &g, int r, int x, int y, int z, uint32_t m,
-                                        const float *__restrict__ hi, const float *__restrict__ lo, float &S,
-                                        float &E) {
-  const Offs o = offsets_of(g, x, y, z);
+template <bool ALL>
+__device__ __forceinline__ void lap6_ff_(const Offs &o, int r, uint32_t m, const float *__restrict__ hi,
+                                         const float *__restrict__ lo, float &S, float &E) {
   const float h0 = hi[r], l0 = lo[r];
   S = 0.f;
   E = 0.f;
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     const int j = r + o.at(cx_of(i), cy_of(i), cz_of(i));
-    const float w = (float)((c2_of(i) == 1 ? 2 : 1) * ((m & (1u << (i - 1))) ? 1 : 2));
+    const float w = (float)((c2_of(i) == 1 ? 2 : 1) * ((ALL || (m & (1u << (i - 1)))) ? 1 : 2));
     float d, de;
     two_sum(hi[j], -h0, d, de);  // d + de = hi_j - hi_r exactly
     float t, te;
@@ -496,6 +495,16 @@ __device__ __forceinline__ void lap6_ff(const Geo &g, int r, int x, int y, int z
     S = t;
     E += te + w * (de + (lo[j] - l0));
   }
+}
+// (a node whose links all join fluid takes constant weights)
+__device__ __forceinline__ void lap6_ff(const Geo &g, int r, int x, int y, int z, uint32_t m,
+                                        const float *__restrict__ hi, const float *__restrict__ lo, float &S,
+                                        float &E) {
+  const Offs o = offsets_of(g, x, y, z);
+  if ((m & kLinkBits) == kLinkBits)
+    lap6_ff_<true>(o, r, m, hi, lo, S, E);
+  else
+    lap6_ff_<false>(o, r, m, hi, lo, S, E);
 }
 
 }  // namespace fp32

@@ -47,6 +47,7 @@ __host__ __device__ constexpr double invlen_of(int i) {
 // cube corners (+-1,+-1,+-1), corner index 18 + (sx>0) + 2(sy>0) + 4(sz>0);
 // bit 31 set when r itself is fluid.
 constexpr uint32_t kFluidBit = 1u << 31;
+constexpr uint32_t kLinkBits = 0x3FFFFu;  // the 18 link bits
 __host__ __device__ constexpr int corner_bit(int sx, int sy, int sz) {
   return 18 + (sx > 0) + 2 * (sy > 0) + 4 * (sz > 0);
 }
@@ -122,6 +123,13 @@ __device__ __forceinline__ bool node_of(const Geo &g, int zpt, int kz, int &x, i
 // neighbour at (dx,dy,dz) in {-1,0,1}^3 is r + off(dx,dy,dz).  32-bit: the
 // library limits a lattice to fewer than 2^31 nodes.  On a non-periodic face
 // the wrapped offset is never used by fluid nodes (those faces are solid).
+// true when every link of a node joins a fluid node other than itself
+// (most nodes of a lattice): the Laplacian's link weights are then
+// constants, with no per-link tests
+__device__ __forceinline__ bool all_links(uint32_t m, uint32_t selfmask) {
+  return (m & kLinkBits) == kLinkBits && !(selfmask & kLinkBits);
+}
+
 struct Offs {
   int xm, xp, ym, yp, zm, zp;
   __device__ __forceinline__ int at(int dx, int dy, int dz) const {

@@ -63,28 +63,30 @@ __global__ void k_galerkin(const MgLevel F, const float *__restrict__ AF, const 
 
 // --- V-cycle kernels ---------------------------------------------------------
 // Restriction with 8 threads per coarse node (one per child) and a fixed-order
-// shuffle sum of the children's pre-smoothed residuals (coarse_of_item,
-// store_coarse in mg_device.cuh).  Work item w (8 per coarse node); a block
-// strides over the items in steps of the grid, the same number of steps for
-// all its threads (the shuffle sum).
-__device__ __forceinline__ void coarse_of_thread(const MgLevel &C, int &I, int &X, int &Y, int &Z, int &ch) {
-  coarse_of_item(C, (long long)blockIdx.x * blockDim.x + threadIdx.x, I, X, Y, Z, ch);
-}
+// shuffle sum of the children's pre-smoothed residuals (store_coarse in
+// mg_device.cuh).
 
 // level 1: a fluid child's pre-smoothed residual is r - omega A u, u = r/diag
-// being the Jacobi vector the CG formed
+// being the Jacobi vector the CG formed.  A block covers a tile of 32 coarse
+// nodes (2^txl along X, the rest along Y; lanes 8k..8k+7 the children of one
+// coarse node, child index = lane % 8 as in child_of) on zpb consecutive
+// coarse planes: coordinates come from the block and lane indices, with no
+// division, and every lane runs the same iterations (the shuffle sum).
 __global__ void __launch_bounds__(256) k_restrict0(const Geo g, uint32_t selfmask, const uint32_t *__restrict__ mask,
                                                    const float *__restrict__ r, const float *__restrict__ u,
                                                    const MgLevel C, const float *__restrict__ AC,
-                                                   float *__restrict__ rc, float *__restrict__ zc,
+                                                   float *__restrict__ rc, float *__restrict__ zc, int txl, int zpb,
                                                    const PoissonCtl *c) {
   if (c->inner_done) return;
-  const long long items = 8LL * C.N, stride = (long long)gridDim.x * blockDim.x;
-  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w - threadIdx.x < items; w += stride) {
-    int I, X, Y, Z, ch, x, y, z;
-    coarse_of_item(C, w, I, X, Y, Z, ch);
+  const int ch = threadIdx.x & 7, j = threadIdx.x >> 3;
+  const int X = (blockIdx.x << txl) + (j & ((1 << txl) - 1));
+  const int Y = blockIdx.y * (32 >> txl) + (j >> txl);
+  for (int kz = 0; kz < zpb; ++kz) {
+    const int Z = blockIdx.z * zpb + kz;
+    const bool own = X < C.nx && Y < C.ny && Z < C.nz;
+    int x, y, z;
     float v = 0.f;
-    if (I < C.N && child_of(C, X, Y, Z, ch, g.nx, g.ny, g.nz, x, y, z)) {
+    if (own && child_of(C, X, Y, Z, ch, g.nx, g.ny, g.nz, x, y, z)) {
       const int i = x + g.nx * (y + g.ny * z);
       const uint32_t m = mask[i];
       if (m & kFluidBit) {
@@ -93,22 +95,26 @@ __global__ void __launch_bounds__(256) k_restrict0(const Geo g, uint32_t selfmas
       }
     }
     v = sum8(v);
-    if (ch == 0 && I < C.N) store_coarse(C, I, v, AC, rc, zc);
+    if (ch == 0 && own) store_coarse(C, X + C.nx * (Y + C.ny * Z), v, AC, rc, zc);
   }
 }
 
 __global__ void __launch_bounds__(256) k_restrict(const MgLevel F, const float *__restrict__ AF,
                                                   const float *__restrict__ r, const float *__restrict__ zf,
                                                   const MgLevel C, const float *__restrict__ AC,
-                                                  float *__restrict__ rc, float *__restrict__ zc,
+                                                  float *__restrict__ rc, float *__restrict__ zc, int txl,
                                                   const PoissonCtl *c) {
   if (c->inner_done) return;
-  int I, X, Y, Z, ch, x, y, z;
-  coarse_of_thread(C, I, X, Y, Z, ch);
+  // the tile mapping of k_restrict0, one coarse plane per block
+  const int ch = threadIdx.x & 7, j = threadIdx.x >> 3;
+  const int X = (blockIdx.x << txl) + (j & ((1 << txl) - 1));
+  const int Y = blockIdx.y * (32 >> txl) + (j >> txl), Z = blockIdx.z;
+  const bool own = X < C.nx && Y < C.ny;
+  int x, y, z;
   float v = 0.f;
-  if (I < C.N && child_of(C, X, Y, Z, ch, F.nx, F.ny, F.nz, x, y, z)) v = presmoothed_res_z(F, AF, r, zf, x, y, z);
+  if (own && child_of(C, X, Y, Z, ch, F.nx, F.ny, F.nz, x, y, z)) v = presmoothed_res_z(F, AF, r, zf, x, y, z);
   v = sum8(v);
-  if (ch == 0 && I < C.N) store_coarse(C, I, v, AC, rc, zc);
+  if (ch == 0 && own) store_coarse(C, X + C.nx * (Y + C.ny * Z), v, AC, rc, zc);
 }
 
 // fused prolongation + post-smoothing on a 27-point level
@@ -370,16 +376,27 @@ cudaError_t mg_vcycle(lbe_handle *h, const float *r0, float *u0, const PoissonCt
   };
   for (int l = 1; l < nl; ++l) lv[l] = level_dev(mg.lv[l]);
   const void *pg = &g, *psm = &sm;
-  auto cgrid = [](const MgLevel &C) { return dim3((unsigned)((C.N * 8 + 255) / 256)); };
   // down: restrictions (pre-smoothing on the fly)
-  const dim3 g1 = cgrid(lv[1]);
-  nodes.push_back(Node{(void *)k_restrict0, dim3(g1.x < (unsigned)kSolveBlocks ? g1.x : (unsigned)kSolveBlocks), dim3(256),
+  // restrictions: tiles of 32 coarse nodes per block, 2^txl along X (at
+  // most 32) and the rest along Y; level 1 with zpb coarse planes per block
+  // (at most kSolveBlocks blocks), the others one plane per block
+  int txl[kMaxLevels];
+  dim3 rgrid[kMaxLevels];
+  for (int l = 1; l < nl; ++l) {
+    txl[l] = 0;
+    while ((1 << txl[l]) < mg.lv[l].nx && txl[l] < 5) ++txl[l];
+    rgrid[l] = dim3((unsigned)((mg.lv[l].nx + (1 << txl[l]) - 1) >> txl[l]),
+                    (unsigned)((mg.lv[l].ny + (32 >> txl[l]) - 1) / (32 >> txl[l])), (unsigned)mg.lv[l].nz);
+  }
+  int zpb = (int)(((long long)rgrid[1].x * rgrid[1].y * mg.lv[1].nz + kSolveBlocks - 1) / kSolveBlocks);
+  rgrid[1].z = (unsigned)((mg.lv[1].nz + zpb - 1) / zpb);
+  nodes.push_back(Node{(void *)k_restrict0, rgrid[1], dim3(256),
                        {(void *)pg, (void *)psm, P(h->mask), P(r0), P(u0), &lv[1], P(mg.lv[1].A), P(mg.lv[1].r),
-                        P(mg.lv[1].z), P(c)}});
+                        P(mg.lv[1].z), &txl[1], &zpb, P(c)}});
   for (int l = 1; l < nl - 1; ++l)
-    nodes.push_back(Node{(void *)k_restrict, cgrid(lv[l + 1]), dim3(256),
+    nodes.push_back(Node{(void *)k_restrict, rgrid[l + 1], dim3(256),
                          {&lv[l], P(mg.lv[l].A), P(mg.lv[l].r), P(mg.lv[l].z), &lv[l + 1], P(mg.lv[l + 1].A),
-                          P(mg.lv[l + 1].r), P(mg.lv[l + 1].z), P(c)}});
+                          P(mg.lv[l + 1].r), P(mg.lv[l + 1].z), &txl[l + 1], P(c)}});
   // coarsest: exact (inverse) or Jacobi sweeps
   int ncoarse = (int)mg.lv[nl - 1].N;
   if (mg.cinv)

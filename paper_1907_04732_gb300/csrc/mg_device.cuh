@@ -216,15 +216,6 @@ __device__ __forceinline__ void coarsest_solve(const MgLevel &L, const float *__
 }
 
 
-// restriction work item w: coarse node I = w/8 and its child ch = w%8
-__device__ __forceinline__ void coarse_of_item(const MgLevel &C, long long w, int &I, int &X, int &Y, int &Z,
-                                               int &ch) {
-  I = (int)(w >> 3);
-  ch = (int)(w & 7);
-  X = Y = Z = 0;
-  if (I < C.N) level_coords(C, I, X, Y, Z);
-}
-
 // a coarse node's restricted residual rc and pre-smoothed iterate
 // zc = omega rc/diag
 __device__ __forceinline__ void store_coarse(const MgLevel &C, int I, float v, const float *__restrict__ AC,
@@ -259,14 +250,22 @@ __device__ __forceinline__ int diag6(uint32_t m, uint32_t selfmask) {
 }
 
 // 6 * sum over fluid links of weight * v[neighbour]; every neighbour is
-// read (a zero weight drops it) so that the loads do not wait for the mask
+// read (a zero weight drops it) so that the loads do not wait for the mask.
+// A node with all links fluid takes the same fmaf sequence without the
+// per-link weight tests.
 __device__ __forceinline__ float nbsum6(uint32_t m, uint32_t selfmask, const Offs &o, int i,
                                         const float *__restrict__ v) {
+  const float *__restrict__ vi = v + i;
   float s = 0.f;
+  if (all_links(m, selfmask)) {
+#pragma unroll
+    for (int l = 1; l < kQ; ++l) s = fmaf(c2_of(l) == 1 ? 2.f : 1.f, vi[o.at(cx_of(l), cy_of(l), cz_of(l))], s);
+    return s;
+  }
 #pragma unroll
   for (int l = 1; l < kQ; ++l) {
     const uint32_t b = 1u << (l - 1);
-    const float vj = v[i + o.at(cx_of(l), cy_of(l), cz_of(l))];
+    const float vj = vi[o.at(cx_of(l), cy_of(l), cz_of(l))];
     const float wl = ((m & b) && !(selfmask & b)) ? (c2_of(l) == 1 ? 2.f : 1.f) : 0.f;
     s = fmaf(wl, vj, s);
   }

@@ -346,13 +346,18 @@ __global__ void __launch_bounds__(kBlock) k_cg_b(const Geo g, int zpt, uint32_t 
     if (!(m & kFluidBit)) continue;
     const T u0 = u[i];
     const Offs o = offsets_of(g, X, Y, Z);
-    const int ii = (int)i;
+    const T *__restrict__ ui = u + i;
     T sum = 0;
+    if (all_links(m, selfmask)) {  // the same sum without the weight tests
 #pragma unroll
-    for (int l = 1; l < kQ; ++l) {  // every neighbour read; a zero weight drops it
-      const uint32_t b = 1u << (l - 1);
-      const T ul = u[ii + o.at(cx_of(l), cy_of(l), cz_of(l))];
-      sum += ((selfmask & b) || !(m & b) ? (T)0 : (T)lapc_of(l)) * ul;
+      for (int l = 1; l < kQ; ++l) sum += (T)lapc_of(l) * ui[o.at(cx_of(l), cy_of(l), cz_of(l))];
+    } else {
+#pragma unroll
+      for (int l = 1; l < kQ; ++l) {  // every neighbour read; a zero weight drops it
+        const uint32_t b = 1u << (l - 1);
+        const T ul = ui[o.at(cx_of(l), cy_of(l), cz_of(l))];
+        sum += ((selfmask & b) || !(m & b) ? (T)0 : (T)lapc_of(l)) * ul;
+      }
     }
     const T wv = diag_t<T>(m, selfmask) * u0 - sum;
     w[i] = wv;
