@@ -45,8 +45,9 @@ extern "C" {
 
 #define LBE_FP64 0 /* all state and arithmetic in FP64 */
 #define LBE_FP32 1 /* FP32 deviations from the rest state, int64 fixed-point
-                      solute, FP64 potential refined on a float-float
-                      residual, FP64 reductions */
+                      solute and potential (units rho_b 2^-40 and 2^-48;
+                      |potential| < 100), the Poisson residual summed
+                      exactly in integers, FP64 reductions */
 
 #define LBE_RULE_MIDPLANE 0 /* lbe_params.boundary_rule */
 #define LBE_RULE_NODE 1
@@ -127,7 +128,9 @@ int lbe_set_geometry(lbe_handle *h, const uint8_t *node_id, int n_electrodes, in
  * Only differences matter (Sec. "Parallel plate capacitor").  After lbe_init
  * the potential is re-solved at once so that the state stays consistent;
  * potentials equal to the current ones are uploaded and nothing else is done
- * (the state is already consistent). */
+ * (the state is already consistent).  Non-finite values, and in the FP32
+ * form values of magnitude 100 or more (its fixed-point range), fail with
+ * LBE_ERR_ARG. */
 int lbe_set_voltage(lbe_handle *h, const double *psi);
 
 /* Initial state (Sec. "Potential and concentration profiles"): uncharged
@@ -160,14 +163,17 @@ int lbe_fields(lbe_handle *h, int which, void *out, int out_on_device);
 
 /* Overwrite the solute amounts (nspecies*N doubles) and/or the potential
  * (N doubles) of an initialised lattice; either pointer may be NULL.  The
- * potential on solid nodes is reset to the electrode potentials. */
+ * potential on solid nodes is reset to the electrode potentials.  In the
+ * FP32 form, amounts and potentials outside its fixed-point ranges (or
+ * non-finite) return LBE_ERR_NONFINITE. */
 int lbe_set_state(lbe_handle *h, const double *n, const double *phi, int on_device);
 
 /* Checkpoint: the complete dynamic state (including the earlier potentials
- * the next solve extrapolates from) as an opaque blob.  With blob NULL,
- * *size receives the needed size.  lbe_load_state restores a blob written by
- * a handle with the same parameters and geometry, built with the same
- * extrapolation order. */
+ * the next solve extrapolates from) as an opaque blob, every array in the
+ * form's own types, so that a restart continues bit for bit.  With blob
+ * NULL, *size receives the needed size.  lbe_load_state restores a blob
+ * written by a handle with the same parameters and geometry, built with the
+ * same extrapolation order and blob format. */
 int lbe_save_state(lbe_handle *h, void *blob, size_t *size);
 int lbe_load_state(lbe_handle *h, const void *blob, size_t size);
 

@@ -51,7 +51,7 @@ struct AdjWork {
   // slot nseg the final state); 0 = uniform checkpoints
   int revolve_slots = 0;
   int64_t *ck_q = nullptr;  // checkpoints [nseg + 1][2N] (the last: time T)
-  double *ck_phi = nullptr;   // [nseg + 1][N]
+  double *ck_phi = nullptr;   // [nseg + 1][N] (the fixed-point potential's 8 bytes per node)
   double *ck_prev = nullptr;  // [nseg + 1][kHist N]: the warm start's history
   std::vector<char> ck_hist;
   int64_t *st_q = nullptr;  // states of one segment [every][2N]
@@ -429,7 +429,8 @@ int save_ck(lbe_handle *h, int k) {
   const long long N = h->geo.N;
   ACK(h, cudaMemcpyAsync(a->ck_q + (size_t)k * 2 * N, h->q, sizeof(int64_t) * 2 * N, cudaMemcpyDeviceToDevice,
                          h->stream));
-  ACK(h, cudaMemcpyAsync(a->ck_phi + (size_t)k * N, h->phi, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+  ACK(h, cudaMemcpyAsync(a->ck_phi + (size_t)k * N, h->phifx, sizeof(int64_t) * N, cudaMemcpyDeviceToDevice,
+                         h->stream));
   ACK(h, cudaMemcpyAsync(a->ck_prev + (size_t)k * kHist * N, h->pw.phi_prev, sizeof(double) * kHist * N,
                          cudaMemcpyDeviceToDevice, h->stream));
   a->ck_hist[k] = (char)h->pw.history;
@@ -441,11 +442,12 @@ int load_ck(lbe_handle *h, int k) {
   const long long N = h->geo.N;
   ACK(h, cudaMemcpyAsync(h->q, a->ck_q + (size_t)k * 2 * N, sizeof(int64_t) * 2 * N, cudaMemcpyDeviceToDevice,
                          h->stream));
-  ACK(h, cudaMemcpyAsync(h->phi, a->ck_phi + (size_t)k * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+  ACK(h, cudaMemcpyAsync(h->phifx, a->ck_phi + (size_t)k * N, sizeof(int64_t) * N, cudaMemcpyDeviceToDevice,
+                         h->stream));
   ACK(h, cudaMemcpyAsync(h->pw.phi_prev, a->ck_prev + (size_t)k * kHist * N, sizeof(double) * kHist * N,
                          cudaMemcpyDeviceToDevice, h->stream));
   h->pw.history = a->ck_hist[k];
-  ACK(h, launch_phi32_sync(h));
+  ACK(h, launch_phi32_from_fx(h));
   return LBE_OK;
 }
 

@@ -466,6 +466,37 @@ __device__ __forceinline__ void extrapolate_node(long long N, long long i, doubl
   prev[i] = v;
 }
 
+// The potential in fixed point (the FP32 form's master copy): value =
+// v 2^-kPhiFixBits.  Its nearest float (ll2f rounds once; the scaling is
+// exact).
+constexpr float kPhiUnitF = 1.0f / 281474976710656.0f;  // 2^-48
+static_assert(kPhiFixBits == 48, "kPhiUnitF is 2^-kPhiFixBits");
+__device__ __forceinline__ float fx_to_f(long long v) { return __fmul_rn(ll2f(v), kPhiUnitF); }
+
+// The warm start of extrapolate_node on the fixed-point potential: the same
+// polynomials in exact integer arithmetic (no FP64 operation), the float
+// copy refreshed, the history (fixed point too) shifted.
+__device__ __forceinline__ void extrapolate_fx(long long N, long long i, int64_t *__restrict__ phifx,
+                                               int64_t *__restrict__ prev, float *__restrict__ phi32, int history) {
+  const long long v = phifx[i], p1 = prev[i];
+  if (history > 0) {
+    long long e;
+    if (history == 1) {
+      e = 2 * v - p1;
+    } else if (history == 2) {
+      e = prev[N + i] + 3 * (v - p1);
+    } else {
+      const long long p2 = prev[N + i], p3 = prev[2 * N + i];
+      e = v + 3 * (v - p1) - 3 * (p1 - p2) + (p2 - p3);
+    }
+    phifx[i] = e;
+    phi32[i] = fx_to_f(e);
+  }
+#pragma unroll
+  for (int k = kHist - 1; k >= 1; --k) prev[k * N + i] = prev[(k - 1) * N + i];
+  prev[i] = v;
+}
+
 // Error-free sum (Knuth): s + e = a + b exactly, s = fl(a + b).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   s = __fadd_rn(a, b);
@@ -505,6 +536,28 @@ __device__ __forceinline__ void lap6_ff(const Geo &g, int r, int x, int y, int z
     lap6_ff_<true>(o, r, m, hi, lo, S, E);
   else
     lap6_ff_<false>(o, r, m, hi, lo, S, E);
+}
+
+// 6 lap_mod(phi)(r) of the fixed-point potential, exactly: the weighted link
+// differences (weights 2 axis, 1 diagonal, doubled towards solid) summed in
+// 64-bit integers.  |phi| < kPhiMax keeps the sum far below 2^63.
+template <bool ALL>
+__device__ __forceinline__ long long lap6_fx_(const Offs &o, int r, uint32_t m, const int64_t *__restrict__ v) {
+  const long long v0 = v[r];
+  const int64_t *__restrict__ vr = v + r;
+  long long s = 0;
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    const long long d = vr[o.at(cx_of(i), cy_of(i), cz_of(i))] - v0;
+    const int w = (c2_of(i) == 1 ? 2 : 1) * ((ALL || (m & (1u << (i - 1)))) ? 1 : 2);
+    s += w == 1 ? d : (w == 2 ? 2 * d : 4 * d);
+  }
+  return s;
+}
+__device__ __forceinline__ long long lap6_fx(const Geo &g, int r, int x, int y, int z, uint32_t m,
+                                             const int64_t *__restrict__ v) {
+  const Offs o = offsets_of(g, x, y, z);
+  return (m & kLinkBits) == kLinkBits ? lap6_fx_<true>(o, r, m, v) : lap6_fx_<false>(o, r, m, v);
 }
 
 }  // namespace fp32

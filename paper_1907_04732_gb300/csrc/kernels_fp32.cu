@@ -95,9 +95,9 @@ __global__ void __launch_bounds__(kBlock) k_sweep32_gen(const Geo g, const P32 P
 // velocity points at it.
 __global__ void __launch_bounds__(kBlock) k_advect32(const Geo g, int ns, const uint32_t *__restrict__ mask,
                                                      const int64_t *__restrict__ qin, const float4 *__restrict__ u,
-                                                     int64_t *__restrict__ qout, double *__restrict__ phi,
-                                                     double *__restrict__ prev, float *__restrict__ phi32,
-                                                     float *__restrict__ phi_lo, int history) {
+                                                     int64_t *__restrict__ qout, int64_t *__restrict__ phifx,
+                                                     int64_t *__restrict__ prev, float *__restrict__ phi32,
+                                                     int history) {
   int x, y, z;
   long long rl;
   if (!node_of(g, 1, 0, x, y, z, rl)) return;
@@ -108,8 +108,37 @@ __global__ void __launch_bounds__(kBlock) k_advect32(const Geo g, int ns, const 
     return;
   }
   advect_node(ns, N, r, offsets_of(g, x, y, z), m, qin, u, qout);
-  // the next solve's warm start (phi is not read by the advection)
-  if (phi) extrapolate_node(N, r, phi, prev, phi32, phi_lo, history);
+  // the next solve's warm start (the potential is not read by the advection)
+  if (phifx) extrapolate_fx(N, r, phifx, prev, phi32, history);
+}
+
+// The FP64 potential (as the API set it) -> fixed point and its float, every
+// node; a non-finite value or one beyond kPhiMax raises range flag 4
+__global__ void k_phi_from64(const Geo g, const double *__restrict__ phi, int64_t *__restrict__ phifx,
+                             float *__restrict__ phi32, int *__restrict__ flag) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= g.N) return;
+  double v = phi[r];
+  if (!(fabs(v) < kPhiMax)) {
+    atomicOr(flag, 4);
+    v = 0.0;
+  }
+  const long long f = __double2ll_rn(v * 281474976710656.0);  // 2^kPhiFixBits
+  phifx[r] = f;
+  phi32[r] = fx_to_f(f);
+}
+
+// fixed point -> the FP64 copy (exact while |phi| < 2^5, to FP64 rounding beyond)
+__global__ void k_phi_to64(const Geo g, const int64_t *__restrict__ phifx, double *__restrict__ phi) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= g.N) return;
+  phi[r] = (double)phifx[r] * (1.0 / 281474976710656.0);
+}
+
+__global__ void k_phi32_from_fx(const Geo g, const int64_t *__restrict__ phifx, float *__restrict__ phi32) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= g.N) return;
+  phi32[r] = fx_to_f(phifx[r]);
 }
 
 __global__ void k_n_to_double(const Geo g, const P32 P, const int64_t *__restrict__ q, const uint32_t *__restrict__ mask,
@@ -230,8 +259,28 @@ cudaError_t launch_sweep32(lbe_handle *h) {
 
 cudaError_t launch_advect32(lbe_handle *h, bool extrapolate) {
   k_advect32<<<LAUNCH3(h), 0, h->stream>>>(h->geo, h->prm.nspecies, h->mask, h->qstar, h->u32, h->q,
-                                           extrapolate ? h->phi : nullptr, h->pw.phi_prev, h->phi32, h->phi_lo,
+                                           extrapolate ? h->phifx : nullptr, (int64_t *)h->pw.phi_prev, h->phi32,
                                            h->pw.history);
+  if (extrapolate) h->phi64_stale = true;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phi_from64(lbe_handle *h) {
+  k_phi_from64<<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->phi, h->phifx, h->phi32, h->flag);
+  h->phi64_stale = false;
+  return cudaGetLastError();
+}
+
+cudaError_t sync_phi64(lbe_handle *h) {
+  if (h->prm.precision != LBE_FP32 || !h->phi64_stale) return cudaSuccess;
+  k_phi_to64<<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->phifx, h->phi);
+  h->phi64_stale = false;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phi32_from_fx(lbe_handle *h) {
+  k_phi32_from_fx<<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->phifx, h->phi32);
+  h->phi64_stale = true;
   return cudaGetLastError();
 }
 

@@ -42,7 +42,7 @@ bool fp32(const lbe_handle *h) { return h->prm.precision == LBE_FP32; }
 
 void free_all(lbe_handle *h) {
   void *ptrs[] = {h->id, h->mask, h->f[0], h->f[1], h->n, h->nstar, h->phi, h->u, h->qpart, h->qout, h->psi_dev,
-                  h->f32[0], h->f32[1], h->q, h->qstar, h->phi32, h->phi_lo, h->u32, h->flag, h->lf};
+                  h->f32[0], h->f32[1], h->q, h->qstar, h->phifx, h->phi32, h->u32, h->flag, h->lf};
   for (void *p : ptrs) cudaFree(p);
   if (h->qhost) cudaFreeHost(h->qhost);
   lbe::poisson_free(h);
@@ -209,8 +209,8 @@ int lbe_create(const lbe_params *p, void *cuda_stream, lbe_handle **out) {
     if (p->flow) alloc((void **)&h->f32[1], nf * lbe::kQ);
     alloc((void **)&h->q, sizeof(int64_t) * (size_t)N * p->nspecies);
     alloc((void **)&h->qstar, sizeof(int64_t) * (size_t)N * p->nspecies);
+    alloc((void **)&h->phifx, sizeof(int64_t) * (size_t)N);
     alloc((void **)&h->phi32, nf);
-    alloc((void **)&h->phi_lo, nf);
     alloc((void **)&h->u32, sizeof(float4) * (size_t)N);
     alloc((void **)&h->flag, sizeof(int));
     if (h->p32.salt11) alloc((void **)&h->lf, sizeof(float4) * (size_t)N);
@@ -298,8 +298,11 @@ int lbe_set_voltage(lbe_handle *h, const double *psi) {
   if (!h->have_geometry) return fail(h, LBE_ERR_STATE, "set_voltage: no geometry");
   if (!psi && h->n_elec > 0) return fail(h, LBE_ERR_ARG, "set_voltage: NULL psi");
   StreamGuard sg{h, h->owns_stream};
-  for (int e = 0; e < h->n_elec; ++e)
+  for (int e = 0; e < h->n_elec; ++e) {
     if (!isfinite(psi[e])) return fail(h, LBE_ERR_ARG, "set_voltage: non-finite potential");
+    if (fp32(h) && !(fabs(psi[e]) < lbe::kPhiMax))
+      return fail(h, LBE_ERR_ARG, "set_voltage: the FP32 form holds potentials below 100 in magnitude");
+  }
   bool same = h->initialised;
   for (int e = 0; e < h->n_elec; ++e) {
     same = same && h->psi[e] == psi[e];
@@ -314,8 +317,11 @@ int lbe_set_voltage(lbe_handle *h, const double *psi) {
   h->gen += 1;
   if (!h->initialised) return LBE_OK;
   h->stats = lbe_stats{};
+  // the FP32 form: the FP64 copy brought up to date, the electrodes set in
+  // it, the whole of it back to fixed point
+  LBE_CK(h, lbe::sync_phi64(h));
   LBE_CK(h, lbe::launch_set_solid_phi(h));
-  if (fp32(h)) LBE_CK(h, lbe::launch_phi32_sync(h));
+  if (fp32(h)) LBE_CK(h, lbe::launch_phi_from64(h));
   return solve_now(h);
 }
 
@@ -329,7 +335,7 @@ int lbe_init(lbe_handle *h) {
   if (fp32(h)) {
     LBE_CK(h, lbe::launch_init32(h));
     LBE_CK(h, lbe::launch_init_phi(h));
-    LBE_CK(h, lbe::launch_phi32_sync(h));
+    LBE_CK(h, lbe::launch_phi_from64(h));
   } else {
     LBE_CK(h, lbe::launch_init_state(h));
   }
@@ -351,7 +357,8 @@ static int flag_result(lbe_handle *h) {
   memcpy(&flag, h->qhost, sizeof(int));
   if (flag)
     return fail(h, LBE_ERR_NONFINITE,
-                "state out of range: fixed-point solute (|link flux| or |n| too large), solvent density or a NaN");
+                "state out of range: fixed-point solute (|link flux| or |n| too large), potential (|phi| >= 100), "
+                "solvent density or a NaN");
   return LBE_OK;
 }
 static int check_flags(lbe_handle *h) {
@@ -425,6 +432,7 @@ int lbe_induced_charge(lbe_handle *h, double *q_out, int out_on_device) {
   if (!q_out) return fail(h, LBE_ERR_ARG, "induced_charge: NULL output");
   StreamGuard sg{h, h->owns_stream};
   if (h->n_elec == 0) return LBE_OK;
+  LBE_CK(h, lbe::sync_phi64(h));
   LBE_CK(h, lbe::launch_charge(h));
   const size_t bytes = sizeof(double) * h->n_elec;
   if (out_on_device) {
@@ -460,9 +468,9 @@ int lbe_fields(lbe_handle *h, int which, void *out, int out_on_device) {
     LBE_CK(h, cudaMalloc(&tmp, bytes));
     dst = tmp;
   }
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = lbe::sync_phi64(h);  // the potential and the node charges read the FP64 copy
   const bool f32 = fp32(h);
-  switch (which) {
+  if (e == cudaSuccess) switch (which) {
     case LBE_FIELD_PHI: e = cudaMemcpyAsync(dst, h->phi, bytes, cudaMemcpyDeviceToDevice, h->stream); break;
     case LBE_FIELD_N:
       e = f32 ? lbe::launch_n_to_double(h, dst)
@@ -512,22 +520,23 @@ int lbe_set_state(lbe_handle *h, const double *n, const double *phi, int on_devi
   if (phi) {
     LBE_CK(h, cudaMemcpyAsync(h->phi, phi, sizeof(double) * N, kind, h->stream));
     LBE_CK(h, lbe::launch_set_solid_phi(h));
-    if (fp32(h)) LBE_CK(h, lbe::launch_phi32_sync(h));
+    if (fp32(h)) LBE_CK(h, lbe::launch_phi_from64(h));
   }
   if (!on_device) LBE_CK(h, cudaStreamSynchronize(h->stream));
   return check_flags(h);
 }
 
-// blob: header | populations (19N) | solute (ns N) | phi (N doubles) |
-// velocity (3N doubles, or N float4 records in the FP32 form) | phi of the previous kHist steps (kHist N doubles, warm
-// start of the next solve; header.history of them valid); populations,
-// solute and velocity in the form's own types
+// blob: header | populations (19N) | solute (ns N) | phi (N) | velocity (3N
+// doubles, or N float4 records in the FP32 form) | phi of the previous kHist
+// steps (kHist N, warm start of the next solve; header.history of them
+// valid); every array in the form's own type (the FP32 form's potentials
+// in its 64-bit fixed point), so that a restart is exact
 struct BlobHeader {
   uint64_t magic;
   int64_t N;
   int32_t ns, flow, precision, history;
 };
-static const uint64_t kMagic = 0x4c42457374763230ULL + lbe::kHist;  // format 2, history length
+static const uint64_t kMagic = 0x4c42457374763330ULL + lbe::kHist;  // format 3, history length
 
 static void blob_sizes(const lbe_handle *h, size_t *fb, size_t *nb, size_t *pb, size_t *ub) {
   const size_t N = (size_t)h->geo.N;
@@ -560,7 +569,7 @@ int lbe_save_state(lbe_handle *h, void *blob, size_t *size) {
   p += fb;
   LBE_CK(h, cudaMemcpyAsync(p, f32 ? (void *)h->q : (void *)h->n, nb, cudaMemcpyDeviceToHost, h->stream));
   p += nb;
-  LBE_CK(h, cudaMemcpyAsync(p, h->phi, pb, cudaMemcpyDeviceToHost, h->stream));
+  LBE_CK(h, cudaMemcpyAsync(p, f32 ? (void *)h->phifx : (void *)h->phi, pb, cudaMemcpyDeviceToHost, h->stream));
   p += pb;
   const size_t vb = ub - lbe::kHist * (size_t)h->geo.N * sizeof(double);
   LBE_CK(h, cudaMemcpyAsync(p, f32 ? (void *)h->u32 : (void *)h->u, vb, cudaMemcpyDeviceToHost, h->stream));
@@ -594,7 +603,7 @@ int lbe_load_state(lbe_handle *h, const void *blob, size_t size) {
   p += fb;
   LBE_CK(h, cudaMemcpyAsync(f32 ? (void *)h->q : (void *)h->n, p, nb, cudaMemcpyHostToDevice, h->stream));
   p += nb;
-  LBE_CK(h, cudaMemcpyAsync(h->phi, p, pb, cudaMemcpyHostToDevice, h->stream));
+  LBE_CK(h, cudaMemcpyAsync(f32 ? (void *)h->phifx : (void *)h->phi, p, pb, cudaMemcpyHostToDevice, h->stream));
   p += pb;
   const size_t vb = ub - lbe::kHist * (size_t)h->geo.N * sizeof(double);
   LBE_CK(h, cudaMemcpyAsync(f32 ? (void *)h->u32 : (void *)h->u, p, vb, cudaMemcpyHostToDevice, h->stream));
@@ -602,7 +611,7 @@ int lbe_load_state(lbe_handle *h, const void *blob, size_t size) {
   LBE_CK(h, cudaMemcpyAsync(h->pw.phi_prev, p, lbe::kHist * (size_t)h->geo.N * sizeof(double), cudaMemcpyHostToDevice,
                             h->stream));
   h->pw.history = hd.history < 0 ? 0 : (hd.history > lbe::kHist ? lbe::kHist : hd.history);
-  if (f32) LBE_CK(h, lbe::launch_phi32_sync(h));
+  if (f32) LBE_CK(h, lbe::launch_phi32_from_fx(h));
   LBE_CK(h, cudaStreamSynchronize(h->stream));
   h->initialised = true;
   return LBE_OK;

@@ -220,7 +220,8 @@ struct PoissonWork {
   cudaGraphExec_t exec_lin = nullptr;  // linear solve A x = rhs (adjoint)
   const void *lin_key[3] = {nullptr, nullptr, nullptr};
   bool graph_ok = false;
-  double *phi_prev = nullptr;  // [kHist][N]: phi of the previous kHist steps (warm start)
+  double *phi_prev = nullptr;  // [kHist][N]: phi of the previous kHist steps (warm start;
+                               // the FP32 form keeps fixed-point values, int64, in it)
   int history = 0;             // how many of them hold a solution (0..kHist)
 };
 constexpr int kMaxPartials = 2048;
@@ -230,6 +231,12 @@ constexpr int kMaxPartials = 2048;
 #define LBE_EXTRAP_ORDER 3
 #endif
 constexpr int kHist = LBE_EXTRAP_ORDER;
+// The FP32 form's potential in fixed point: phi = phifx * 2^-kPhiFixBits.
+// The unit 2^-48 (3.6e-15) lies far below the solve tolerance; |phi| below
+// kPhiMax keeps every integer sum of the solve (18 weighted link
+// differences, the cubic warm start) far from 2^63.
+constexpr int kPhiFixBits = 48;
+constexpr double kPhiMax = 100.0;
 static_assert(kHist >= 1 && kHist <= 3, "extrapolation order 1..3");
 // Launch size of the solve's lattice kernels: each thread handles zpt nodes
 // along z so that a kernel has at most this many blocks.  On this GPU a
@@ -297,8 +304,9 @@ struct lbe_handle {
   float *f32[2] = {nullptr, nullptr};  // population deviations f_i - w_i
   int64_t *q = nullptr;                // fixed-point solute amounts [k][r]
   int64_t *qstar = nullptr;
-  float *phi32 = nullptr;              // FP32 copy of phi (its high part)
-  float *phi_lo = nullptr;             // low part: phi = phi32 + phi_lo to ~2^-48
+  int64_t *phifx = nullptr;            // the potential in fixed point (kPhiFixBits), the master copy
+  float *phi32 = nullptr;              // nearest float of phifx (the sweep's link records)
+  bool phi64_stale = false;            // phi (FP64, the API's copy) lags phifx
   float4 *u32 = nullptr;               // velocity of the last collision (fp32::octant_code records)
   int *flag = nullptr;                 // device error flags (fixed-point range)
   float4 *lf = nullptr;                // 1:1 salt link records, one per node (fp32::link_record)
@@ -375,5 +383,12 @@ void mg_free(lbe_handle *h);
 cudaError_t mg_vcycle(lbe_handle *h, const float *r0, float *u0, const PoissonCtl *c, cudaGraph_t gr,
                       cudaGraphNode_t *last, cudaStream_t st);
 int mg_kernels_per_cycle(const lbe_handle *h);
-cudaError_t launch_phi32_sync(lbe_handle *h);
+// FP32 form: the FP64 potential (set by the API) -> the fixed-point master
+// and its float copy, every node (a potential beyond kPhiMax or non-finite
+// raises the range flag)
+cudaError_t launch_phi_from64(lbe_handle *h);
+// FP32 form: the FP64 copy refreshed from the fixed-point master when stale
+cudaError_t sync_phi64(lbe_handle *h);
+// FP32 form: the float copy from the fixed-point master, every node
+cudaError_t launch_phi32_from_fx(lbe_handle *h);
 }  // namespace lbe

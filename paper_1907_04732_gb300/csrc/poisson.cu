@@ -218,20 +218,25 @@ __global__ void k_solve_reset(PoissonCtl *c) {
   c->solves += 1;
 }
 
-// FP64 residual of the current potential; seeds the inner solve:
+// Residual of the current potential; seeds the inner solve:
 // r = (T)res, u = r/diag, x = p = s = 0.  Partial max |res|/diag.
-// MODE: 0 charge density from FP64 n, 1 from fixed-point q, 2 a given rhs
-// (linear solve A x = rhs; its relative test also needs max |rhs|/diag,
-// kept in the otherwise idle (r,u) partial slots), 3 = 1 for a 1:1 salt in
-// float-float arithmetic, 4 = 2 in float-float arithmetic (rhs values that
-// are floats, x also held as two floats).
-enum { R_N64 = 0, R_FIXED = 1, R_RHS = 2, R_FF = 3, R_RHS_FF = 4 };
+// MODE: R_N64 the FP64 form (FP64 potential and n); R_FX the FP32 form for
+// a 1:1 salt: the fixed-point potential's Laplacian summed exactly in
+// integers, the charge term from the fixed-point solute, both combined in
+// float-float arithmetic; R_FXG the FP32 form for other salts (the exact
+// Laplacian and the charge density in FP64); R_RHS a given rhs (linear
+// solve A x = rhs with an FP64 iterate; its relative test also needs
+// max |rhs|/diag, kept in the otherwise idle (r,u) partial slots); R_RHS_FF
+// the same in float-float arithmetic (rhs values that are floats, x held as
+// two floats).
+enum { R_N64 = 0, R_FXG = 1, R_RHS = 2, R_FX = 3, R_RHS_FF = 4 };
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys P, const P32 P3,
                                                 const uint32_t *__restrict__ mask, const double *__restrict__ n64,
                                                 const int64_t *__restrict__ nq, const double *__restrict__ rhs,
                                                 const double *__restrict__ phi, const float *__restrict__ phi_hi,
-                                                const float *__restrict__ phi_lo, float c6_hi, float c6_lo,
+                                                const float *__restrict__ phi_lo, const int64_t *__restrict__ phifx,
+                                                float c6_hi, float c6_lo,
                                                 T *__restrict__ r,
                                                 T *__restrict__ u, T *__restrict__ x, T *__restrict__ p,
                                                 T *__restrict__ s, double *__restrict__ part, int nblk,
@@ -249,10 +254,15 @@ __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys
       r[i] = u[i] = x[i] = p[i] = s[i] = (T)0;
       continue;
     }
-    if (MODE == R_FF) {
-      // 6 res = 6 lap + 6 (4 pi l_B s) (q+ - q-), both in float-float
-      float S, E;
-      fp32::lap6_ff(g, (int)i, X, Y, Z, m, phi_hi, phi_lo, S, E);
+    if (MODE == R_FX) {
+      // 6 res = 6 lap + 6 (4 pi l_B s) (q+ - q-): 6 lap exact in fixed
+      // point, split into float-float (the nearest float of the integer sum
+      // and the float of its exact remainder), the charge term in
+      // float-float too
+      const long long L6 = fp32::lap6_fx(g, (int)i, X, Y, Z, m, phifx);
+      const float Lh = fp32::ll2f(L6);
+      const float Ll = fp32::ll2f(L6 - fp32::f2ll_rn(Lh));
+      const float S = __fmul_rn(Lh, fp32::kPhiUnitF), E = __fmul_rn(Ll, fp32::kPhiUnitF);
       const long long dq = nq[i] - nq[g.N + i];
       const float dq_hi = fp32::ll2f(dq);
       const float dq_lo = fp32::ll2f(dq - fp32::f2ll_rn(dq_hi));  // exact remainder
@@ -288,16 +298,16 @@ __global__ void __launch_bounds__(kBlock) k_res(const Geo g, int zpt, const Phys
     double b;
     if (MODE == R_RHS) {
       b = rhs[i];
-    } else if (MODE == R_FIXED && P3.salt11) {
-      // 1:1 salt with one bulk value: rho_el = s (q+ - q-), exact integer difference
-      b = P.four_pi_lb * (P3.sd[0] * (double)(nq[i] - nq[g.N + i]));
     } else {
       double q = 0.0;
       for (int k = 0; k < P.ns; ++k)
-        q += P.z[k] * (MODE == R_FIXED ? P3.rbd[k] + P3.sd[k] * (double)nq[k * g.N + i] : n64[k * g.N + i]);
+        q += P.z[k] * (MODE == R_FXG ? P3.rbd[k] + P3.sd[k] * (double)nq[k * g.N + i] : n64[k * g.N + i]);
       b = P.four_pi_lb * q;
     }
-    const double rr = b + lap_at(g, (int)i, X, Y, Z, m, phi, !(P.selfmask & kPlainLaplacian));
+    const double lap = MODE == R_FXG
+                           ? (double)fp32::lap6_fx(g, (int)i, X, Y, Z, m, phifx) * (1.0 / 281474976710656.0 / 6.0)
+                           : lap_at(g, (int)i, X, Y, Z, m, phi, !(P.selfmask & kPlainLaplacian));
+    const double rr = b + lap;
     const T rt = (T)rr;
     const T dinv = (T)1 / diag_t<T>(m, P.selfmask);
     r[i] = rt;
@@ -424,7 +434,45 @@ __global__ void k_extrapolate(const Geo g, int zpt, const uint32_t *__restrict__
   }
 }
 
-// phi64 += e on fluid nodes; the FP32 form refreshes its FP32 copy
+// FP32 form: the fixed-point potential += e (rounded to the fixed-point
+// unit) on fluid nodes and its float copy; |phi| reaching kPhiMax raises
+// range flag 4
+__global__ void k_correct_fx(const Geo g, int zpt, const uint32_t *__restrict__ mask, const float *__restrict__ e,
+                             int64_t *__restrict__ phifx, float *__restrict__ phi32, int *__restrict__ flag) {
+  constexpr float kMaxFx = (float)(kPhiMax * 281474976710656.0);  // kPhiMax 2^kPhiFixBits
+  bool over = false;
+  for (int kz = 0; kz < zpt; ++kz) {
+    int X, Y, Z;
+    long long i;
+    if (!node_of(g, zpt, kz, X, Y, Z, i)) continue;
+    if (!(mask[i] & kFluidBit)) continue;
+    const float d = __fmul_rn(e[i], 281474976710656.0f);  // e 2^kPhiFixBits, exact
+    if (!(fabsf(d) < kMaxFx)) {  // also NaN
+      over = true;
+      continue;
+    }
+    const long long v = phifx[i] + fp32::f2ll_rn(d);
+    over |= !(fabsf(fp32::ll2f(v)) < kMaxFx);
+    phifx[i] = v;
+    phi32[i] = fp32::fx_to_f(v);
+  }
+  if (over) atomicOr(flag, 4);
+}
+
+// FP32 form without flow (no advection kernel to carry it): the warm start
+// on the fixed-point potential
+__global__ void k_extrapolate_fx(const Geo g, int zpt, const uint32_t *__restrict__ mask, int64_t *__restrict__ phifx,
+                                 int64_t *__restrict__ prev, float *__restrict__ phi32, int history) {
+  for (int kz = 0; kz < zpt; ++kz) {
+    int X, Y, Z;
+    long long i;
+    if (!node_of(g, zpt, kz, X, Y, Z, i)) continue;
+    if (mask[i] & kFluidBit) fp32::extrapolate_fx(g.N, i, phifx, prev, phi32, history);
+  }
+}
+
+// phi64 += e on fluid nodes; with phi32 given its float split follows
+// (the FP64 form, and the linear solves' FP64 iterates)
 template <typename T>
 __global__ void k_correct(const Geo g, int zpt, const uint32_t *__restrict__ mask, const T *__restrict__ e,
                           double *__restrict__ phi, float *__restrict__ phi32, float *__restrict__ phi_lo) {
@@ -460,7 +508,9 @@ struct Args {
   const double *rhs = nullptr;
   double *phi;
   float *phi32, *phi_lo = nullptr;
-  float c6_hi = 0.f, c6_lo = 0.f;  // 6 * 4 pi l_B * s, as two floats (R_FF)
+  float c6_hi = 0.f, c6_lo = 0.f;  // 6 * 4 pi l_B * s, as two floats (R_FX)
+  int64_t *phifx = nullptr;        // the FP32 form's fixed-point potential
+  int *flag = nullptr;             // the FP32 form's range flags
   void *r, *u, *w, *x, *p, *s;
   double *part;
   PoissonCtl *c;
@@ -522,7 +572,8 @@ void fill_args(lbe_handle *h, Args &A) {
   A.nq = h->q;
   A.phi = h->phi;
   A.phi32 = h->phi32;
-  A.phi_lo = h->phi_lo;
+  A.phifx = h->phifx;
+  A.flag = h->flag;
   {
     const double c6 = 6.0 * h->phys.four_pi_lb * h->p32.sd[0];
     A.c6_hi = (float)c6;
@@ -543,9 +594,12 @@ cudaError_t build_graph(lbe_handle *h, Args &A, cudaGraphExec_t *exec) {
   const Launch &L = h->pw.L;
   const dim3 one(1);
   const bool fixed = h->prm.precision == LBE_FP32;
-  const bool ff = fixed && sizeof(T) == 4 && h->p32.salt11 && A.phi_lo && !A.rhs;
   void *f_res = A.rhs ? (A.phi32 && A.phi_lo ? (void *)k_res<T, R_RHS_FF> : (void *)k_res<T, R_RHS>)
-                      : (ff ? (void *)k_res<T, R_FF> : (fixed ? (void *)k_res<T, R_FIXED> : (void *)k_res<T, R_N64>));
+                      : (fixed ? (h->p32.salt11 ? (void *)k_res<T, R_FX> : (void *)k_res<T, R_FXG>)
+                               : (void *)k_res<T, R_N64>);
+  // the FP32 form's own solve corrects its fixed-point potential; the FP64
+  // form and the linear solves correct an FP64 iterate
+  const bool corr_fx = fixed && !A.rhs;
   cudaGraph_t G = nullptr;
   cudaError_t e = cudaGraphCreate(&G, 0);
   if (e != cudaSuccess) return e;
@@ -554,13 +608,13 @@ cudaError_t build_graph(lbe_handle *h, Args &A, cudaGraphExec_t *exec) {
   void *a_reset[] = {&A.c};
   // the residual before the round loop must not touch the inner loop's
   // condition (it belongs to the loop body); the one closing a round does
-  void *a_res0[] = {&A.g,     &A.zpt,   &A.P,      &A.P3,      &A.mask,  &A.n64, &A.nq, &A.rhs,
-                    &A.phi,   &A.phi32, &A.phi_lo, &A.c6_hi,   &A.c6_lo, &A.r,   &A.u,  &A.x,
-                    &A.p,     &A.s,     &A.part,   &A.nblk,    &A.c,     &A.tol, &A.tol_rel,
+  void *a_res0[] = {&A.g,     &A.zpt,   &A.P,      &A.P3,    &A.mask,    &A.n64,   &A.nq, &A.rhs,
+                    &A.phi,   &A.phi32, &A.phi_lo, &A.phifx, &A.c6_hi,   &A.c6_lo, &A.r,  &A.u,
+                    &A.x,     &A.p,     &A.s,      &A.part,  &A.nblk,    &A.c,     &A.tol, &A.tol_rel,
                     &A.maxit, &A.hout,  &A.hin,    &A.use_cond, &A.hin_no};
-  void *a_res[] = {&A.g,     &A.zpt,   &A.P,      &A.P3,      &A.mask,  &A.n64, &A.nq, &A.rhs,
-                   &A.phi,   &A.phi32, &A.phi_lo, &A.c6_hi,   &A.c6_lo, &A.r,   &A.u,  &A.x,
-                   &A.p,     &A.s,     &A.part,   &A.nblk,    &A.c,     &A.tol, &A.tol_rel,
+  void *a_res[] = {&A.g,     &A.zpt,   &A.P,      &A.P3,    &A.mask,    &A.n64,   &A.nq, &A.rhs,
+                   &A.phi,   &A.phi32, &A.phi_lo, &A.phifx, &A.c6_hi,   &A.c6_lo, &A.r,  &A.u,
+                   &A.x,     &A.p,     &A.s,      &A.part,  &A.nblk,    &A.c,     &A.tol, &A.tol_rel,
                    &A.maxit, &A.hout,  &A.hin,    &A.use_cond, &A.hin_yes};
   void *a_bi[] = {&A.g, &A.zpt, &A.selfmask, &A.mask, &A.u, &A.r, &A.w, &A.part, &A.nblk, &A.c,
                   &A.eta, &A.tol_inner, &A.maxit, &A.mode_init, &A.hin, &A.use_cond};
@@ -568,6 +622,7 @@ cudaError_t build_graph(lbe_handle *h, Args &A, cudaGraphExec_t *exec) {
                   &A.eta, &A.tol_inner, &A.maxit, &A.mode_iter, &A.hin, &A.use_cond};
   void *a_a[] = {&A.g, &A.zpt, &A.selfmask, &A.mask, &A.x, &A.r, &A.u, &A.w, &A.p, &A.s, &A.part, &A.nblk, &A.c};
   void *a_cor[] = {&A.g, &A.zpt, &A.mask, &A.x, &A.phi, &A.phi32, &A.phi_lo};
+  void *a_corfx[] = {&A.g, &A.zpt, &A.mask, &A.x, &A.phifx, &A.phi32, &A.flag};
   // reset -> residual test -> while (not converged) { V-cycle -> CG -> correct
   // -> residual test }: a converged test ends the solve without running the
   // rest of a round
@@ -583,7 +638,9 @@ cudaError_t build_graph(lbe_handle *h, Args &A, cudaGraphExec_t *exec) {
   if (e == cudaSuccess) e = add_kernel(body_in, &li, (void *)k_cg_a<T>, L.grid, L.block, a_a);
   if (e == cudaSuccess && mg) e = mg_vcycle(h, (const float *)A.r, (float *)A.u, A.c, body_in, &li, nullptr);
   if (e == cudaSuccess) e = add_kernel(body_in, &li, (void *)k_cg_b<T>, L.grid, L.block, a_bt);
-  if (e == cudaSuccess) e = add_kernel(body_out, &lo, (void *)k_correct<T>, L.grid, L.block, a_cor);
+  if (e == cudaSuccess)
+    e = corr_fx ? add_kernel(body_out, &lo, (void *)k_correct_fx, L.grid, L.block, a_corfx)
+                : add_kernel(body_out, &lo, (void *)k_correct<T>, L.grid, L.block, a_cor);
   if (e == cudaSuccess) e = add_kernel(body_out, &lo, f_res, L.grid, L.block, a_res);
   if (e == cudaSuccess) e = cudaGraphInstantiate(exec, G, 0);
   cudaGraphDestroy(G);
@@ -602,12 +659,11 @@ int solve_polled(lbe_handle *h, Args &A) {
   h->launches += 1;
   for (int round = 0; round <= kMaxOuter; ++round) {
     {
-      const bool ff = fixed && sizeof(T) == 4 && h->p32.salt11 && A.phi_lo && !A.rhs;
       auto kres = A.rhs ? (A.phi32 && A.phi_lo ? k_res<T, R_RHS_FF> : k_res<T, R_RHS>)
-                        : (ff ? k_res<T, R_FF> : (fixed ? k_res<T, R_FIXED> : k_res<T, R_N64>));
+                        : (fixed ? (h->p32.salt11 ? k_res<T, R_FX> : k_res<T, R_FXG>) : k_res<T, R_N64>);
       kres<<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.P, A.P3, A.mask, A.n64, A.nq, A.rhs, A.phi, A.phi32, A.phi_lo,
-                                        A.c6_hi, A.c6_lo, (T *)A.r, (T *)A.u, (T *)A.x, (T *)A.p, (T *)A.s, A.part,
-                                        A.nblk, A.c, A.tol, A.tol_rel, A.maxit, 0, 0, 0, 0);
+                                        A.phifx, A.c6_hi, A.c6_lo, (T *)A.r, (T *)A.u, (T *)A.x, (T *)A.p,
+                                        (T *)A.s, A.part, A.nblk, A.c, A.tol, A.tol_rel, A.maxit, 0, 0, 0, 0);
     }
     const bool mg = sizeof(T) == 4 && h->mg.nlev >= 2;
     if (mg && mg_vcycle(h, (const float *)A.r, (float *)A.u, A.c, nullptr, nullptr, st) != cudaSuccess)
@@ -634,7 +690,10 @@ int solve_polled(lbe_handle *h, Args &A) {
       }
       h->launches += 2 * kChunk;
     }
-    k_correct<T><<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.mask, (const T *)A.x, A.phi, A.phi32, A.phi_lo);
+    if (fixed && !A.rhs)
+      k_correct_fx<<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.mask, (const float *)A.x, A.phifx, A.phi32, A.flag);
+    else
+      k_correct<T><<<L.grid, L.block, 0, st>>>(A.g, A.zpt, A.mask, (const T *)A.x, A.phi, A.phi32, A.phi_lo);
     h->launches += 1;
     if (w.ctl_host->outer_done) break;
   }
@@ -770,17 +829,23 @@ int poisson_enqueue(lbe_handle *h, bool extrapolate, bool extrapolated) {
   PoissonWork &w = h->pw;
   if (extrapolate) {
     if (!extrapolated) {
-      k_extrapolate<<<w.L.grid, w.L.block, 0, h->stream>>>(h->geo, w.L.zpt, h->mask, h->phi, w.phi_prev,
-                                                         h->prm.precision == LBE_FP32 ? h->phi32 : nullptr,
-                                                         h->prm.precision == LBE_FP32 ? h->phi_lo : nullptr,
-                                                         w.history);
+      if (h->prm.precision == LBE_FP32)
+        k_extrapolate_fx<<<w.L.grid, w.L.block, 0, h->stream>>>(h->geo, w.L.zpt, h->mask, h->phifx,
+                                                                (int64_t *)w.phi_prev, h->phi32, w.history);
+      else
+        k_extrapolate<<<w.L.grid, w.L.block, 0, h->stream>>>(h->geo, w.L.zpt, h->mask, h->phi, w.phi_prev, nullptr,
+                                                           nullptr, w.history);
       h->launches += 1;
     }
     if (w.history < kHist) w.history += 1;
   } else {
     w.history = 0;
   }
-  return h->prm.precision == LBE_FP32 ? solve_t<float>(h) : solve_t<double>(h);
+  if (h->prm.precision == LBE_FP32) {
+    h->phi64_stale = true;  // the solve moves the fixed-point potential
+    return solve_t<float>(h);
+  }
+  return solve_t<double>(h);
 }
 
 int poisson_status(lbe_handle *h, lbe_stats *st, long long *kernels) {
@@ -820,10 +885,5 @@ int poisson_status(lbe_handle *h, lbe_stats *st, long long *kernels) {
 
 cudaError_t poisson_reset_stats(lbe_handle *h) { return cudaMemsetAsync(h->pw.ctl, 0, sizeof(PoissonCtl), h->stream); }
 
-cudaError_t launch_phi32_sync(lbe_handle *h) {
-  const Launch L = make_launch(h->geo);
-  k_correct<float><<<L.grid, L.block, 0, h->stream>>>(h->geo, 1, h->mask, nullptr, h->phi, h->phi32, h->phi_lo);
-  return cudaGetLastError();
-}
 
 }  // namespace lbe

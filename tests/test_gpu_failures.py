@@ -47,14 +47,32 @@ def test_nan_solute_is_reported(lbe, precision):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_nan_potential_is_reported(lbe, precision):
-    """A NaN potential at one fluid node: the next step's flux, force and
-    Poisson residual meet it; lbe_step returns LBE_ERR_NONFINITE."""
+    """A NaN potential at one fluid node.  The FP64 form takes it, and the
+    next step's flux, force and Poisson residual meet it: lbe_step returns
+    LBE_ERR_NONFINITE.  The FP32 form converts the potential to its fixed
+    point at once and lbe_set_state itself returns LBE_ERR_NONFINITE."""
     g, w = _lattice(lbe, precision)
     phi = g.phi()
     phi[tuple(_fluid_node(w))] = np.nan
-    g.set_state(phi=phi)
     with pytest.raises(lbe.LBEError) as e:
+        g.set_state(phi=phi)
         g.step(1)
+    assert e.value.code == lbe.LBE_ERR_NONFINITE, e.value
+    g.close()
+
+
+def test_potential_beyond_fixed_point_range(lbe):
+    """The FP32 form holds |potential| < 100: a larger electrode potential is
+    refused (LBE_ERR_ARG) and a larger node value handed to lbe_set_state
+    raises the range flag (LBE_ERR_NONFINITE)."""
+    g, w = _lattice(lbe, "fp32")
+    with pytest.raises(lbe.LBEError) as e:
+        g.set_voltage((0.0, 150.0))
+    assert e.value.code == lbe.LBE_ERR_ARG, e.value
+    phi = g.phi()
+    phi[tuple(_fluid_node(w))] = 120.0
+    with pytest.raises(lbe.LBEError) as e:
+        g.set_state(phi=phi)
     assert e.value.code == lbe.LBE_ERR_NONFINITE, e.value
     g.close()
 
