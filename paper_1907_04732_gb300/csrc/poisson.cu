@@ -126,17 +126,71 @@ __device__ __forceinline__ bool last_block(PoissonCtl *c, int nblk) {
   return last;
 }
 
-// sums/max of the partials in block order (every thread of the block calls)
+// two sums and a max over the block in one pass (the order of block_reduce
+// for each value, with one pair of barriers); results valid in thread 0
+__device__ __forceinline__ void block_reduce3(double &a, double &b, double &m) {
+  __shared__ double sh[3][kBlock / 32];
+  const int t = flat_tid(), lane = t & 31, wid = t >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ua = __shfl_down_sync(0xffffffffu, a, o), ub = __shfl_down_sync(0xffffffffu, b, o),
+                 um = __shfl_down_sync(0xffffffffu, m, o);
+    a += ua;
+    b += ub;
+    m = fmax(m, um);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    sh[0][wid] = a;
+    sh[1][wid] = b;
+    sh[2][wid] = m;
+  }
+  __syncthreads();
+  if (t == 0) {
+    a = sh[0][0];
+    b = sh[1][0];
+    m = sh[2][0];
+    for (int w = 1; w < kBlock / 32; ++w) {
+      a += sh[0][w];
+      b += sh[1][w];
+      m = fmax(m, sh[2][w]);
+    }
+  }
+}
+
+// sums/max of the partials in block order (every thread of the block calls).
+// All of a thread's partials are loaded before any is added (one L2 latency
+// instead of one per stride of the block), then summed in the same order.
 __device__ __forceinline__ void reduce_partials(const double *part, int nblk, double *ru, double *wu, double *mx) {
+  constexpr int kPer = (kSolveBlocks + kBlock - 1) / kBlock;  // the solve launches at most kSolveBlocks blocks
+  double pa[kPer], pb[kPer], pm[kPer];
+  const int t = flat_tid();
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int i = t + k * kBlock;
+    const bool in = i < nblk;
+    pa[k] = in ? __ldcg(part + S_RU * nblk + i) : 0.0;
+    pb[k] = in ? __ldcg(part + S_WU * nblk + i) : 0.0;
+    pm[k] = in ? __ldcg(part + S_MAX * nblk + i) : 0.0;
+  }
   double a = 0.0, b = 0.0, m = 0.0;
-  for (int i = flat_tid(); i < nblk; i += kBlock) {
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    if (t + k * kBlock < nblk) {
+      a += pa[k];
+      b += pb[k];
+      m = fmax(m, pm[k]);
+    }
+  }
+  for (int i = t + kPer * kBlock; i < nblk; i += kBlock) {  // a larger launch (not used by the solve)
     a += __ldcg(part + S_RU * nblk + i);
     b += __ldcg(part + S_WU * nblk + i);
     m = fmax(m, __ldcg(part + S_MAX * nblk + i));
   }
-  *ru = block_reduce<false>(a);
-  *wu = block_reduce<false>(b);
-  *mx = block_reduce<true>(m);
+  block_reduce3(a, b, m);
+  *ru = a;
+  *wu = b;
+  *mx = m;
 }
 
 // outer test of a refinement round (thread 0 of the last block of k_res):
