@@ -557,8 +557,12 @@ def main():
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": w.name, "lattice": list(w.shape), "nodes": w.nodes, "fluid_nodes": fluid,
                    "precision": args.precision, "poisson_tol": args.tol,
-                   "l2": "inputs larger than L2 (populations, two buffers: %.0f MB)"
-                         % (w.nodes * 19 * (4 if args.precision == "fp32" else 8) * 2 / 1e6),
+                   "l2": ("inputs larger than L2 (129 MB): the sweep alone touches %.0f MB (populations "
+                          "%s %.0f MB, link records, solute in and out, velocity records, mask)"
+                          % (w.nodes * ((19 * 4 + 16 + 32 + 16 + 4) if args.precision == "fp32"
+                                        else (19 * 8 * 2 + 8 + 32 + 24 + 4)) / 1e6,
+                             "in place" if args.precision == "fp32" else "two buffers",
+                             w.nodes * 19 * (4 if args.precision == "fp32" else 16) / 1e6)),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,
         "phases_ms": phases, "phase_shares": shares,
@@ -566,10 +570,11 @@ def main():
                     "bytes_per_node_per_cg_iter": B["cg_iter"](ns),
                     "gbs": pois_bytes / (phases["poisson"] * 1e-3) / 1e9,
                     "hbm_frac": pois_bytes / (phases["poisson"] * 1e-3) / 1e9 / peak,
-                    "note": ("refinement on a float-float residual, multigrid-preconditioned FP32 CG, cubic warm "
-                             "start in time; one CUDA graph launch per solve (conditional while nodes for the "
-                             "refinement and CG loops); its vectors stay in L2, so the fraction is of effective "
-                             "bandwidth") if args.precision == "fp32" else
+                    "note": ("refinement on the fixed-point potential (exact integer Laplacian, float-float "
+                             "charge term), multigrid-preconditioned FP32 CG, cubic warm start in time; one CUDA "
+                             "graph launch per solve (conditional while nodes for the refinement and CG loops); "
+                             "its vectors stay in L2, so the fraction is of effective bandwidth")
+                            if args.precision == "fp32" else
                             ("FP64 Jacobi-preconditioned CG in one CUDA graph launch per solve, cubic warm start "
                              "in time")},
         "step": {"bytes_per_node": step_bytes / fluid, "gbs": step_bytes / (step_ms * 1e-3) / 1e9,

@@ -58,18 +58,50 @@ __device__ __forceinline__ int nb_of(const Offs &o, int r, int i) { return r + o
 template <bool WIDE>
 using PopIdx = typename std::conditional<WIDE, long long, int>::type;
 
-// pull streaming with halfway bounce-back (see kernels_fp64.cu); ALL: every
-// link joins fluid (no bounce-back to select)
-template <bool WIDE, bool ALL = false>
+// Population layouts of a step, with halfway bounce-back at links to solid
+// (bit i-1 of the node mask m clear: x + c_i is solid or outside the box).
+//   POP_PULL: two buffers; the step reads the previous step's post-collision
+//     values, f_i(x) = fin[i][x - c_i] (bounced back: fin[opp i][x]), and
+//     writes its own to fout[i][x] (the batched form).
+//   POP_AA_EVEN / POP_AA_ODD: one buffer A updated in place, two kinds of
+//     step in turn (the AA pattern of Bailey, Myre, Walsh, Lilja and Saad,
+//     2009).  An even step reads f_i(x) = A[i][x] and writes f*_i to
+//     A[opp i][x]; an odd step reads f_i(x) = A[opp i][x - c_i] (bounced
+//     back: A[i][x]) and writes f*_i to A[i][x + c_i] (bounced back:
+//     A[opp i][x]).  Each slot is read, then written, by one node of a step.
+// ALL: every link joins fluid (no bounce-back to select).
+enum PopLayout { POP_PULL = 0, POP_AA_EVEN = 1, POP_AA_ODD = 2 };
+
+template <bool WIDE, bool ALL = false, int LAYOUT = POP_PULL>
 __device__ __forceinline__ void gather32(int N, int r, const Offs &o, uint32_t m, const float *__restrict__ fin,
                                          float f[kQ]) {
   f[0] = fin[r];
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     const int io = opp_of(i);
-    f[i] = (ALL || (m & (1u << (io - 1)))) ? fin[(PopIdx<WIDE>)i * N + nb_of(o, r, io)]
-                                           : fin[(PopIdx<WIDE>)io * N + r];
+    const bool in = ALL || (m & (1u << (io - 1)));  // x - c_i is fluid
+    if (LAYOUT == POP_PULL)
+      f[i] = in ? fin[(PopIdx<WIDE>)i * N + nb_of(o, r, io)] : fin[(PopIdx<WIDE>)io * N + r];
+    else if (LAYOUT == POP_AA_EVEN)
+      f[i] = fin[(PopIdx<WIDE>)i * N + r];
+    else
+      f[i] = in ? fin[(PopIdx<WIDE>)io * N + nb_of(o, r, io)] : fin[(PopIdx<WIDE>)i * N + r];
   }
+}
+
+// where post-collision population i of node r goes (i >= 1)
+template <bool WIDE, bool ALL, int LAYOUT>
+__device__ __forceinline__ void put32(int N, int r, const Offs &o, uint32_t m, int i, float v,
+                                      float *__restrict__ fout) {
+  const int io = opp_of(i);
+  if (LAYOUT == POP_PULL)
+    fout[(PopIdx<WIDE>)i * N + r] = v;
+  else if (LAYOUT == POP_AA_EVEN)
+    fout[(PopIdx<WIDE>)io * N + r] = v;
+  else if (ALL || (m & (1u << (i - 1))))
+    fout[(PopIdx<WIDE>)i * N + nb_of(o, r, i)] = v;
+  else
+    fout[(PopIdx<WIDE>)io * N + r] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -246,9 +278,10 @@ __host__ __device__ constexpr int cell_bits(int dx, int dy, int dz) {
 //   df'_i = (1 - omega) df_i + E_even +- E_odd,
 //   E_even = w [omega (drho + rho (4.5 cu^2 - 1.5 uu)) + guo (9 cu cF - 3 uF)]
 //   E_odd  = w [3 omega rho cu + 3 guo cF]
-template <bool WIDE>
-__device__ __forceinline__ void lb_collide(const P32 &P, int N, int r, const float f[kQ], float *__restrict__ fout,
-                                           float4 *__restrict__ u, const float F[3], bool &over) {
+template <bool WIDE, bool ALL = false, int LAYOUT = POP_PULL>
+__device__ __forceinline__ void lb_collide(const P32 &P, int N, int r, const Offs &o, uint32_t m, const float f[kQ],
+                                           float *__restrict__ fout, float4 *__restrict__ u, const float F[3],
+                                           bool &over) {
   float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
@@ -277,23 +310,23 @@ __device__ __forceinline__ void lb_collide(const P32 &P, int N, int r, const flo
     const float ee = w * (base + cu * (b2 * cu + 9.f * g * cF));
     const float eo = w * (d2 * cu + 3.f * g * cF);
     const int io = i + 9;
-    fout[(PopIdx<WIDE>)i * N + r] = keep * f[i] + (ee + eo);
-    fout[(PopIdx<WIDE>)io * N + r] = keep * f[io] + (ee - eo);
+    put32<WIDE, ALL, LAYOUT>(N, r, o, m, i, keep * f[i] + (ee + eo), fout);
+    put32<WIDE, ALL, LAYOUT>(N, r, o, m, io, keep * f[io] + (ee - eo), fout);
   }
 }
-template <bool WIDE, bool ALL = false>
+template <bool WIDE, bool ALL = false, int LAYOUT = POP_PULL>
 __device__ __forceinline__ void lb_node(const P32 &P, int N, int r, const Offs &o, uint32_t m,
                                         const float *__restrict__ fin, float *__restrict__ fout,
                                         float4 *__restrict__ u, const float F[3], bool &over) {
   float f[kQ];
-  gather32<WIDE, ALL>(N, r, o, m, fin, f);
-  lb_collide<WIDE>(P, N, r, f, fout, u, F, over);
+  gather32<WIDE, ALL, LAYOUT>(N, r, o, m, fin, f);
+  lb_collide<WIDE, ALL, LAYOUT>(P, N, r, o, m, f, fout, u, F, over);
 }
 
 // Fused step at one fluid node, any salt: quantised link fluxes and
 // q* = q - sum Jq, solvent force, and (FLOW) BGK + Guo collision with pull
 // streaming.
-template <bool FLOW, bool WIDE>
+template <bool FLOW, bool WIDE, int LAYOUT = POP_PULL>
 __device__ __forceinline__ void sweep_node(const P32 &P, int N, int r, const Offs &o, uint32_t m,
                                            const float *__restrict__ fin, float *__restrict__ fout,
                                            const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
@@ -312,23 +345,27 @@ __device__ __forceinline__ void sweep_node(const P32 &P, int N, int r, const Off
 #pragma unroll
   for (int k = 0; k < LBE_MAX_SPECIES; ++k)
     if (k < P.ns) qstar[k * N + r] = q0[k] + dq[k];
-  if (FLOW) lb_node<WIDE>(P, N, r, o, m, fin, fout, u, F, over);
+  if (FLOW) lb_node<WIDE, false, LAYOUT>(P, N, r, o, m, fin, fout, u, F, over);
 }
 
 // Fused step at one fluid node of a 1:1 salt from the link records lf
 // (link_record): per link the flux terms of both species (link_pair, in the
 // link's one orientation), their fixed-point rounding (owner end subtracts,
 // the other end adds: exact conservation), the force from the link excess
-// fluxes, then (FLOW) BGK + Guo collision with pull streaming.  The
-// populations are read before the link loop, so that their loads are in
-// flight during the link arithmetic (19 registers held across it).
-template <bool FLOW, bool WIDE, bool ALL>
+// fluxes, then (FLOW) BGK + Guo collision with streaming in the given
+// population layout.
+template <bool FLOW, bool WIDE, bool ALL, int LAYOUT>
 __device__ __forceinline__ void sweep_node_lf_(const P32 &P, int N, int r, const Offs &o, uint32_t m,
                                               const float *__restrict__ fin, float *__restrict__ fout,
                                               const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
                                               const float4 *__restrict__ lf, float4 *__restrict__ u, bool &over) {
+  // PULL (the batched form) reads the populations before the link loop, so
+  // that their loads are in flight during the link arithmetic; the in-place
+  // layouts read them after it (measured: the early read spills 56-112 B
+  // under the 64-register cap and took 0.077 ms against 0.065)
+  constexpr bool kEarly = LAYOUT == POP_PULL;
   float f[kQ];
-  if (FLOW) gather32<WIDE, ALL>(N, r, o, m, fin, f);
+  if (FLOW && kEarly) gather32<WIDE, ALL, LAYOUT>(N, r, o, m, fin, f);
   const float4 self = lf[(PopIdx<WIDE>)r];
   unsigned ah0 = 0u, al0 = 0u, ah1 = 0u, al1 = 0u;
   float sabs = 0.f, Fx = 0.f, Fy = 0.f, Fz = 0.f;
@@ -365,20 +402,21 @@ __device__ __forceinline__ void sweep_node_lf_(const P32 &P, int N, int r, const
   qstar[N + r] = q[N + r] + acc_value(ah1, al1, net);
   if (FLOW) {
     const float F[3] = {Fx * P.inv_2a0, Fy * P.inv_2a0, Fz * P.inv_2a0};
-    lb_collide<WIDE>(P, N, r, f, fout, u, F, over);
+    if (!kEarly) gather32<WIDE, ALL, LAYOUT>(N, r, o, m, fin, f);
+    lb_collide<WIDE, ALL, LAYOUT>(P, N, r, o, m, f, fout, u, F, over);
   }
 }
 // the same; a node whose 18 links all join fluid (most of a lattice) takes
 // a form without the per-link mask tests
-template <bool FLOW, bool WIDE>
+template <bool FLOW, bool WIDE, int LAYOUT = POP_PULL>
 __device__ __forceinline__ void sweep_node_lf(const P32 &P, int N, int r, const Offs &o, uint32_t m,
                                               const float *__restrict__ fin, float *__restrict__ fout,
                                               const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
                                               const float4 *__restrict__ lf, float4 *__restrict__ u, bool &over) {
   if ((m & 0x3FFFFu) == 0x3FFFFu)
-    sweep_node_lf_<FLOW, WIDE, true>(P, N, r, o, m, fin, fout, q, qstar, lf, u, over);
+    sweep_node_lf_<FLOW, WIDE, true, LAYOUT>(P, N, r, o, m, fin, fout, q, qstar, lf, u, over);
   else
-    sweep_node_lf_<FLOW, WIDE, false>(P, N, r, o, m, fin, fout, q, qstar, lf, u, over);
+    sweep_node_lf_<FLOW, WIDE, false, LAYOUT>(P, N, r, o, m, fin, fout, q, qstar, lf, u, over);
 }
 
 // Cell-overlap advection at one fluid node (see k_advect32), from the

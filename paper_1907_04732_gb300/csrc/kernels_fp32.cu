@@ -48,10 +48,12 @@ __global__ void __launch_bounds__(kBlock) k_prep32(const Geo g, const P32 P, con
 // Fused step kernel of a 1:1 salt: link fluxes from the link records
 // (quantised, exactly conserving), solute update q* = q - sum Jq, solvent
 // force, and (FLOW) BGK + Guo collision and pull streaming with halfway
-// bounce-back, all in FP32 deviations.  Capped at 64 registers (four blocks
-// per SM), with the populations read before the link loop: the fastest of
-// the uncapped, capped, early- and late-read forms measured.
-template <bool FLOW, bool WIDE>
+// bounce-back, all in FP32 deviations, the populations updated in place
+// (one buffer, fin == fout; LAYOUT = POP_AA_EVEN or POP_AA_ODD, the AA
+// pattern of fp32_device.cuh: every population slot is read and then
+// written by a single node, so the two pointers may alias).  Capped at 64
+// registers (four blocks per SM).
+template <bool FLOW, bool WIDE, int LAYOUT>
 __global__ void __launch_bounds__(kBlock, 4) k_sweep32(const Geo g, const P32 P, const uint32_t *__restrict__ mask,
                                                     const float *__restrict__ fin, float *__restrict__ fout,
                                                     const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
@@ -64,13 +66,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_sweep32(const Geo g, const P32 P,
   const uint32_t m = mask[r];
   if (!(m & kFluidBit)) return;
   bool over = false;
-  sweep_node_lf<FLOW, WIDE>(P, N, r, offsets_of(g, x, y, z), m, fin, fout, q, qstar, lf, u, over);
+  sweep_node_lf<FLOW, WIDE, LAYOUT>(P, N, r, offsets_of(g, x, y, z), m, fin, fout, q, qstar, lf, u, over);
   if (over) atomicOr(flag, 1);
 }
 
 // The same for any other salt (several species, valences other than +-1):
 // each link evaluated at both ends with a fixed rounding sequence.
-template <bool FLOW, bool WIDE>
+template <bool FLOW, bool WIDE, int LAYOUT>
 __global__ void __launch_bounds__(kBlock) k_sweep32_gen(const Geo g, const P32 P, const uint32_t *__restrict__ mask,
                                                         const float *__restrict__ fin, float *__restrict__ fout,
                                                         const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
@@ -83,7 +85,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep32_gen(const Geo g, const P32 P
   const uint32_t m = mask[r];
   if (!(m & kFluidBit)) return;
   bool over = false;
-  sweep_node<FLOW, WIDE>(P, N, r, offsets_of(g, x, y, z), m, fin, fout, q, qstar, phi, u, over);
+  sweep_node<FLOW, WIDE, LAYOUT>(P, N, r, offsets_of(g, x, y, z), m, fin, fout, q, qstar, phi, u, over);
   if (over) atomicOr(flag, 1);
 }
 
@@ -171,6 +173,7 @@ __global__ void k_n_from_double(const Geo g, const P32 P, const double *__restri
 }
 
 // density, velocity (current state) or populations, as FP64
+template <int LAYOUT>
 __global__ void k_moments32(const Geo g, const P32 P, int flow, const uint32_t *__restrict__ mask,
                             const float *__restrict__ fin, const int64_t *__restrict__ q,
                             const float *__restrict__ phi, double *__restrict__ rho_out,
@@ -189,7 +192,7 @@ __global__ void k_moments32(const Geo g, const P32 P, int flow, const uint32_t *
   }
   const Offs o = offsets_of(g, x, y, z);
   float f[kQ];
-  gather32<true>(N, r, o, m, fin, f);
+  gather32<true, false, LAYOUT>(N, r, o, m, fin, f);  // what the next step's collision reads
   if (f_out) {
     for (int i = 0; i < kQ; ++i) f_out[(long long)i * N + r] = w_of(i) + (double)f[i];
     return;
@@ -227,33 +230,37 @@ inline unsigned grid_for(long long N) { return (unsigned)((N + kBlock - 1) / kBl
 }  // namespace
 
 cudaError_t launch_init32(lbe_handle *h) {
-  k_init32<<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->p32, h->id, h->f32[h->cur], h->q, h->u32);
+  k_init32<<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, h->p32, h->id, h->f32[0], h->q, h->u32);
+  h->aa_odd = false;
   return cudaGetLastError();
 }
 
 cudaError_t launch_sweep32(lbe_handle *h) {
-  const int nxt = h->cur ^ 1;
   const P32 &P = h->p32;
   // 32-bit population offsets while the 19 components fit
   const bool wide = (long long)kQ * h->geo.N >= (1LL << 31);
   const bool flow = h->prm.flow != 0;
+  const bool odd = flow && h->aa_odd;  // the populations' in-place step kind
+  float *pop = h->f32[0];
   if (P.salt11) {
     k_prep32<<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, P, h->phi32, h->q, h->lf);
     using Kern = void (*)(const Geo, const P32, const uint32_t *, const float *, float *, const int64_t *, int64_t *,
                           const float4 *, float4 *, int *);
-    const Kern k[2][2] = {{k_sweep32<false, false>, k_sweep32<false, true>},
-                          {k_sweep32<true, false>, k_sweep32<true, true>}};
-    k[flow][wide]<<<LAUNCH3(h), 0, h->stream>>>(h->geo, P, h->mask, h->f32[h->cur], h->f32[nxt],
-                                                                h->q, h->qstar, h->lf, h->u32, h->flag);
+    const Kern k[3][2] = {{k_sweep32<false, false, POP_AA_EVEN>, k_sweep32<false, true, POP_AA_EVEN>},
+                          {k_sweep32<true, false, POP_AA_EVEN>, k_sweep32<true, true, POP_AA_EVEN>},
+                          {k_sweep32<true, false, POP_AA_ODD>, k_sweep32<true, true, POP_AA_ODD>}};
+    k[flow + odd][wide]<<<LAUNCH3(h), 0, h->stream>>>(h->geo, P, h->mask, pop, pop, h->q, h->qstar, h->lf, h->u32,
+                                                      h->flag);
   } else {
     using Kern = void (*)(const Geo, const P32, const uint32_t *, const float *, float *, const int64_t *, int64_t *,
                           const float *, float4 *, int *);
-    const Kern k[2][2] = {{k_sweep32_gen<false, false>, k_sweep32_gen<false, true>},
-                          {k_sweep32_gen<true, false>, k_sweep32_gen<true, true>}};
-    k[flow][wide]<<<LAUNCH3(h), 0, h->stream>>>(h->geo, P, h->mask, h->f32[h->cur], h->f32[nxt], h->q, h->qstar,
-                                                 h->phi32, h->u32, h->flag);
+    const Kern k[3][2] = {{k_sweep32_gen<false, false, POP_AA_EVEN>, k_sweep32_gen<false, true, POP_AA_EVEN>},
+                          {k_sweep32_gen<true, false, POP_AA_EVEN>, k_sweep32_gen<true, true, POP_AA_EVEN>},
+                          {k_sweep32_gen<true, false, POP_AA_ODD>, k_sweep32_gen<true, true, POP_AA_ODD>}};
+    k[flow + odd][wide]<<<LAUNCH3(h), 0, h->stream>>>(h->geo, P, h->mask, pop, pop, h->q, h->qstar, h->phi32,
+                                                      h->u32, h->flag);
   }
-  if (flow) h->cur = nxt;
+  if (flow) h->aa_odd = !h->aa_odd;
   return cudaGetLastError();
 }
 
@@ -295,8 +302,8 @@ cudaError_t launch_n_from_double(lbe_handle *h, const double *n) {
 }
 
 cudaError_t launch_moments32(lbe_handle *h, double *rho_out, double *u_out, double *f_out) {
-  k_moments32<<<LAUNCH3(h), 0, h->stream>>>(h->geo, h->p32, h->prm.flow, h->mask, h->f32[h->cur],
-                                                             h->q, h->phi32, rho_out, u_out, f_out);
+  (h->aa_odd ? k_moments32<POP_AA_ODD> : k_moments32<POP_AA_EVEN>)<<<LAUNCH3(h), 0, h->stream>>>(
+      h->geo, h->p32, h->prm.flow, h->mask, h->f32[0], h->q, h->phi32, rho_out, u_out, f_out);
   return cudaGetLastError();
 }
 

@@ -205,8 +205,7 @@ int lbe_create(const lbe_params *p, void *cuda_stream, lbe_handle **out) {
   alloc((void **)&h->phi, nd);
   alloc((void **)&h->psi_dev, sizeof(double) * (LBE_MAX_ELECTRODES + 1));
   if (fp32(h)) {
-    alloc((void **)&h->f32[0], nf * lbe::kQ);
-    if (p->flow) alloc((void **)&h->f32[1], nf * lbe::kQ);
+    alloc((void **)&h->f32[0], nf * lbe::kQ);  // one buffer: the populations are updated in place
     alloc((void **)&h->q, sizeof(int64_t) * (size_t)N * p->nspecies);
     alloc((void **)&h->qstar, sizeof(int64_t) * (size_t)N * p->nspecies);
     alloc((void **)&h->phifx, sizeof(int64_t) * (size_t)N);
@@ -535,8 +534,9 @@ struct BlobHeader {
   uint64_t magic;
   int64_t N;
   int32_t ns, flow, precision, history;
+  int32_t aa_odd, pad;  // FP32 form: the kind of the next in-place step
 };
-static const uint64_t kMagic = 0x4c42457374763330ULL + lbe::kHist;  // format 3, history length
+static const uint64_t kMagic = 0x4c42457374763430ULL + lbe::kHist;  // format 4, history length
 
 static void blob_sizes(const lbe_handle *h, size_t *fb, size_t *nb, size_t *pb, size_t *ub) {
   const size_t N = (size_t)h->geo.N;
@@ -560,11 +560,12 @@ int lbe_save_state(lbe_handle *h, void *blob, size_t *size) {
   if (*size < need) return fail(h, LBE_ERR_ARG, "save_state: blob too small");
   StreamGuard sg{h, h->owns_stream};
   const bool f32 = fp32(h);
-  BlobHeader hd{kMagic, h->geo.N, h->prm.nspecies, h->prm.flow, h->prm.precision, h->pw.history};
+  BlobHeader hd{kMagic, h->geo.N, h->prm.nspecies, h->prm.flow, h->prm.precision, h->pw.history, h->aa_odd ? 1 : 0,
+                0};
   char *p = (char *)blob;
   memcpy(p, &hd, sizeof(hd));
   p += sizeof(hd);
-  LBE_CK(h, cudaMemcpyAsync(p, f32 ? (void *)h->f32[h->cur] : (void *)h->f[h->cur], fb, cudaMemcpyDeviceToHost,
+  LBE_CK(h, cudaMemcpyAsync(p, f32 ? (void *)h->f32[0] : (void *)h->f[h->cur], fb, cudaMemcpyDeviceToHost,
                             h->stream));
   p += fb;
   LBE_CK(h, cudaMemcpyAsync(p, f32 ? (void *)h->q : (void *)h->n, nb, cudaMemcpyDeviceToHost, h->stream));
@@ -598,6 +599,7 @@ int lbe_load_state(lbe_handle *h, const void *blob, size_t size) {
   const bool f32 = fp32(h);
   const char *p = (const char *)blob + sizeof(hd);
   h->cur = 0;
+  h->aa_odd = hd.aa_odd != 0;
   h->pw.history = 0;
   LBE_CK(h, cudaMemcpyAsync(f32 ? (void *)h->f32[0] : (void *)h->f[0], p, fb, cudaMemcpyHostToDevice, h->stream));
   p += fb;

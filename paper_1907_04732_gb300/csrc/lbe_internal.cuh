@@ -301,7 +301,8 @@ struct lbe_handle {
   lbe::MGWork mg;
 
   // FP32 form state
-  float *f32[2] = {nullptr, nullptr};  // population deviations f_i - w_i
+  float *f32[2] = {nullptr, nullptr};  // population deviations f_i - w_i: f32[0], updated in place
+  bool aa_odd = false;                 // the next step is an odd one of the AA pattern (fp32::PopLayout)
   int64_t *q = nullptr;                // fixed-point solute amounts [k][r]
   int64_t *qstar = nullptr;
   int64_t *phifx = nullptr;            // the potential in fixed point (kPhiFixBits), the master copy

@@ -111,7 +111,7 @@ def test_nan_population_in_loaded_state_is_reported(lbe, precision):
     velocity carries it into the solute and the Poisson residual)."""
     g, w = _lattice(lbe, precision)
     blob = bytearray(g.save_state())
-    header = struct.calcsize("<QqiiII")  # magic, N, ns, flow, precision, history
+    header = struct.calcsize("<QqiiIIii")  # magic, N, ns, flow, precision, history, step kind, pad
     N = w.nodes
     z, y, x = _fluid_node(w)
     r = x + w.shape[0] * (y + w.shape[1] * z)
