@@ -133,7 +133,12 @@ IMPL_BYTES = {
 
 # DRAM bytes per launch of the fused sweep from an ncu capture, valid only
 # for the kernel source it was taken from (a hash of the sweep's sources)
-SWEEP_TRAFFIC = {}
+SWEEP_TRAFFIC = {
+    # k_prep32 + k_sweep32 (odd in-place step), one launch each, from an ncu
+    # --set full capture of these sources on GB300: 20.974592 + 116.62208 MB
+    # read, 53.335808 MB written
+    ("fp32", "eof_64x64x256", "fcc14d5a5ce33f02"): 190932480,
+}
 
 
 def sweep_source_hash() -> str:
