@@ -156,10 +156,12 @@ struct lbe_batch {
   uint32_t *mask = nullptr;
   float *f[2] = {nullptr, nullptr};
   int64_t *q = nullptr, *qstar = nullptr;
-  double *phi = nullptr, *phi_prev = nullptr;  // phi_prev [kHist][Ntot]: the previous solutions
-  float *phi32 = nullptr;
-  float4 *u = nullptr;      // velocity records (fp32::octant_code)
-  float *phi_lo = nullptr;  // phi = phi32 + phi_lo to ~2^-48 (float-float residual)
+  double *phi = nullptr;          // FP64 copy of the potential (charges, fields), refreshed when read
+  int64_t *phifx = nullptr;       // the potential in fixed point (unit 2^-kPhiFixBits), the master copy
+  int64_t *phi_prev = nullptr;    // [kHist][Ntot]: the previous solutions, fixed point
+  bool phi64_stale = false;       // phi lags phifx
+  float *phi32 = nullptr;         // nearest float of phifx
+  float4 *u = nullptr;            // velocity records (fp32::octant_code)
   float4 *lf = nullptr;     // link records, one per node (fp32::link_record)
   float *vec = nullptr;     // CG vectors [6][Ntot]
   double *part = nullptr;   // per-tile partials [3][T]
@@ -332,8 +334,8 @@ __global__ void __launch_bounds__(kBlock) kb_init(const InstDev *__restrict__ in
                                                   int T, long long Ntot, const uint8_t *__restrict__ id,
                                                   const double *__restrict__ psi, float *__restrict__ f,
                                                   int64_t *__restrict__ q, double *__restrict__ phi,
-                                                  float *__restrict__ phi32, float *__restrict__ phi_lo,
-                                                  double *__restrict__ phi_prev,
+                                                  float *__restrict__ phi32, int64_t *__restrict__ phifx,
+                                                  int64_t *__restrict__ phi_prev,
                                                   float4 *__restrict__ u) {
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
     const int ii = tile_inst[t];
@@ -346,10 +348,11 @@ __global__ void __launch_bounds__(kBlock) kb_init(const InstDev *__restrict__ in
       for (int i = 0; i < kQ; ++i) f[i * Ntot + r] = 0.f;
       for (int s = 0; s < 2; ++s) q[s * Ntot + r] = e ? -(1LL << kFixBits) : 0;
       const double p = e ? psi[ii * (kBE + 1) + e] : 0.0;
+      const long long pf = __double2ll_rn(p * 281474976710656.0);  // 2^kPhiFixBits
       phi[r] = p;
-      phi32[r] = (float)p;
-      phi_lo[r] = (float)(p - (double)(float)p);
-      for (int k = 0; k < kHist; ++k) phi_prev[k * Ntot + r] = p;
+      phifx[r] = pf;
+      phi32[r] = fx_to_f(pf);
+      for (int k = 0; k < kHist; ++k) phi_prev[k * Ntot + r] = pf;
       u[r] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
@@ -423,9 +426,9 @@ inline PrepKern prep_kernel(long long Ntot) { return wide_batch(Ntot) ? kb_prep<
 __global__ void __launch_bounds__(kBlock) kb_advect(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
                                                     int T, int Ntot, const uint32_t *__restrict__ mask,
                                                     const int64_t *__restrict__ qin, const float4 *__restrict__ u,
-                                                    int64_t *__restrict__ qout, double *__restrict__ phi,
-                                                    double *__restrict__ prev, float *__restrict__ phi32,
-                                                    float *__restrict__ phi_lo, const int *__restrict__ hist) {
+                                                    int64_t *__restrict__ qout, int64_t *__restrict__ phifx,
+                                                    int64_t *__restrict__ prev, float *__restrict__ phi32,
+                                                    const int *__restrict__ hist) {
   const int have = *hist;  // the next solve's warm start rides along (phi is not read here)
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
     const InstDev &I = inst[tile_inst[t]];
@@ -441,17 +444,16 @@ __global__ void __launch_bounds__(kBlock) kb_advect(const InstDev *__restrict__ 
         continue;
       }
       advect_node(2, Ntot, r, offsets_of(I.g, x, y, z), m, qin, u, qout);
-      extrapolate_node(Ntot, r, phi, prev, phi32, phi_lo, have);
+      extrapolate_fx(Ntot, r, phifx, prev, phi32, have);
     }
   }
 }
 
 // warm start on fluid nodes (all instances) from the *hist previous
-// solutions (fp32::extrapolate_node; with flow, kb_advect does this)
+// solutions (fp32::extrapolate_fx; with flow, kb_advect does this)
 __global__ void kb_extrapolate(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst, int T,
-                               int Ntot, const uint32_t *__restrict__ mask, double *__restrict__ phi,
-                               double *__restrict__ prev, float *__restrict__ phi32, float *__restrict__ phi_lo,
-                               const int *__restrict__ hist) {
+                               int Ntot, const uint32_t *__restrict__ mask, int64_t *__restrict__ phifx,
+                               int64_t *__restrict__ prev, float *__restrict__ phi32, const int *__restrict__ hist) {
   const int have = *hist;
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
     const InstDev &I = inst[tile_inst[t]];
@@ -460,7 +462,7 @@ __global__ void kb_extrapolate(const InstDev *__restrict__ inst, const int *__re
       if (lo >= I.g.N) break;
       const int r = I.off + lo;
       if (!(mask[r] & kFluidBit)) continue;
-      extrapolate_node(Ntot, r, phi, prev, phi32, phi_lo, have);
+      extrapolate_fx(Ntot, r, phifx, prev, phi32, have);
     }
   }
 }
@@ -486,8 +488,8 @@ __global__ void kb_solve_reset(int n, InstCtl *c, BatchCtl *b, int *hist, int se
 // seeds their CG (r, u = r/diag, x = p = s = 0); per-tile max |r|/diag
 __global__ void __launch_bounds__(kBlock) kb_res(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
                                                  int T, int Ntot, const uint32_t *__restrict__ mask,
-                                                 const int64_t *__restrict__ qn, const float *__restrict__ phi_hi,
-                                                 const float *__restrict__ phi_lo, const CgVec v,
+                                                 const int64_t *__restrict__ qn, const int64_t *__restrict__ phifx,
+                                                 const CgVec v,
                                                  double *__restrict__ part, const InstCtl *__restrict__ c) {
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
     const int ii = tile_inst[t];
@@ -505,10 +507,12 @@ __global__ void __launch_bounds__(kBlock) kb_res(const InstDev *__restrict__ ins
         v.r[r] = v.u[r] = v.x[r] = v.p[r] = v.s[r] = 0.f;
         continue;
       }
-      // 6 res = 6 lap(phi) + 6 (4 pi l_B s)(q+ - q-) in float-float (phi =
-      // hi + lo; FP64 adds are slow on this GPU)
-      float S, E;
-      fp32::lap6_ff(I.g, r, x, y, z, m, phi_hi, phi_lo, S, E);
+      // 6 res = 6 lap(phi) + 6 (4 pi l_B s)(q+ - q-): 6 lap exact in fixed
+      // point, split into float-float and added to the charge term in
+      // float-float (as the single lattice's residual)
+      const long long L6 = fp32::lap6_fx(I.g, r, x, y, z, m, phifx);
+      const float Lh = ll2f(L6);
+      const float S = __fmul_rn(Lh, fp32::kPhiUnitF), E = __fmul_rn(ll2f(L6 - f2ll_rn(Lh)), fp32::kPhiUnitF);
       const long long dq = qn[r] - qn[Ntot + r];  // 1:1 salt, one bulk value
       const float dq_hi = ll2f(dq), dq_lo = ll2f(dq - f2ll_rn(dq_hi));
       const float Bv = I.c6_hi * dq_hi;
@@ -709,11 +713,15 @@ __global__ void __launch_bounds__(kBlock) kb_cg_a(const InstDev *__restrict__ in
   }
 }
 
-// phi64 += x for instances that solved this round; FP32 copy refreshed
+// the fixed-point potential += x (rounded to its unit) for instances that
+// solved this round, its float copy refreshed; |phi| reaching kPhiMax raises
+// range flag 4
 __global__ void kb_correct(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst, int T,
                            const uint32_t *__restrict__ mask, const float *__restrict__ x_,
-                           double *__restrict__ phi, float *__restrict__ phi32, float *__restrict__ phi_lo,
+                           int64_t *__restrict__ phifx, float *__restrict__ phi32, int *__restrict__ flag,
                            const InstCtl *__restrict__ c) {
+  constexpr float kMaxFx = (float)(kPhiMax * 281474976710656.0);
+  bool over = false;
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
     const int ii = tile_inst[t];
     if (!c[ii].solving) continue;
@@ -722,15 +730,25 @@ __global__ void kb_correct(const InstDev *__restrict__ inst, const int *__restri
       const int lo = (t - I.tile0) * kTile + k * kBlock + threadIdx.x;
       if (lo >= I.g.N) break;
       const int r = I.off + lo;
-      double v = phi[r];
-      if (mask[r] & kFluidBit) {
-        v += (double)x_[r];
-        phi[r] = v;
+      if (!(mask[r] & kFluidBit)) continue;
+      const float d = __fmul_rn(x_[r], 281474976710656.0f);  // x 2^kPhiFixBits, exact
+      if (!(fabsf(d) < kMaxFx)) {  // also NaN
+        over = true;
+        continue;
       }
-      phi32[r] = (float)v;
-      phi_lo[r] = (float)(v - (double)(float)v);
+      const long long v = phifx[r] + f2ll_rn(d);
+      over |= !(fabsf(ll2f(v)) < kMaxFx);
+      phifx[r] = v;
+      phi32[r] = fx_to_f(v);
     }
   }
+  if (over) atomicOr(flag, 4);
+}
+
+// fixed point -> the FP64 copy, every node of the batch
+__global__ void kb_phi_to64(long long Ntot, const int64_t *__restrict__ phifx, double *__restrict__ phi) {
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < Ntot; r += (long long)gridDim.x * blockDim.x)
+    phi[r] = (double)phifx[r] * (1.0 / 281474976710656.0);
 }
 
 // induced charge per instance and electrode (Eq. Qelec), FP64, fixed order
@@ -1041,7 +1059,7 @@ void mg_release(lbe_batch *b) {
 
 void bfree(lbe_batch *b) {
   void *ptrs[] = {b->inst_d, b->tile_inst, b->id,   b->mask, b->f[0],  b->f[1], b->q,    b->qstar, b->phi,
-                  b->phi_prev, b->phi32,  b->phi_lo, b->u, b->vec, b->part, b->psi_d, b->ictl, b->bctl, b->qpart,
+                  b->phi_prev, b->phi32,  b->phifx, b->u, b->vec, b->part, b->psi_d, b->ictl, b->bctl, b->qpart,
                   b->qout,
                   b->flag,     b->hist,   b->lf};
   for (void *p : ptrs) cudaFree(p);
@@ -1325,8 +1343,8 @@ struct SolveArgs {
   const float *fin;
   float *fout;
   int64_t *qin, *qmid, *qsolve;
-  double *phi, *phi_prev;
-  float *phi32, *phi_lo;
+  int64_t *phifx, *phi_prev;
+  float *phi32;
   float4 *u, *lf;
   lbe::CgVec v;
   const float *vr, *vu, *vx;
@@ -1359,10 +1377,9 @@ void solve_args(lbe_batch *b, bool step, const float *fin, float *fout, int64_t 
   // the solve reads the solute after the step: advected back into qin with
   // flow, the flux-updated copy without
   A.qsolve = !step ? qin : (b->flow ? qin : qmid);
-  A.phi = b->phi;
+  A.phifx = b->phifx;
   A.phi_prev = b->phi_prev;
   A.phi32 = b->phi32;
-  A.phi_lo = b->phi_lo;
   A.u = b->u;
   A.lf = b->lf;
   A.v = b->cg();
@@ -1397,11 +1414,11 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   void *a_prep[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.phi32, &A.qin, &A.lf};
   void *a_sw[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.fin, &A.fout, &A.qin, &A.qmid, &A.lf, &A.u,
                   &A.flag};
-  void *a_adv[] = {&A.inst, &A.tile_inst, &A.T,      &A.Ntot,  &A.mask, &A.qmid,
-                   &A.u,    &A.qin,       &A.phi, &A.phi_prev, &A.phi32, &A.phi_lo, &A.hist};
-  void *a_ext[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.phi, &A.phi_prev, &A.phi32, &A.phi_lo, &A.hist};
+  void *a_adv[] = {&A.inst, &A.tile_inst, &A.T,     &A.Ntot,     &A.mask,  &A.qmid,
+                   &A.u,    &A.qin,       &A.phifx, &A.phi_prev, &A.phi32, &A.hist};
+  void *a_ext[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.phifx, &A.phi_prev, &A.phi32, &A.hist};
   void *a_reset[] = {&A.n, &A.c, &A.bc, &A.hist, &A.set_hist};
-  void *a_res[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.qsolve, &A.phi32, &A.phi_lo, &A.v, &A.part, &A.c};
+  void *a_res[] = {&A.inst, &A.tile_inst, &A.T, &A.Ntot, &A.mask, &A.qsolve, &A.phifx, &A.v, &A.part, &A.c};
   // the test before the round loop must not touch the inner loop's
   // condition (it belongs to the loop body); the one closing a round does
   void *a_out0[] = {&A.inst, &A.n,    &A.T,       &A.part,     &A.c,    &A.bc,  &A.tol,
@@ -1414,7 +1431,7 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   void *a_st[] = {&A.inst, &A.n,     &A.T,    &A.part,    &A.c,        &A.bc,  &A.eta, &A.tol_abs,
                   &A.maxit, &A.init0, &A.nfam, &A.fam_cnt, &A.fam_pref, &A.hin, &A.use};
   void *a_a[] = {&A.inst, &A.n, &A.pref0, &A.T, &A.mask, &A.v, &A.part, &A.c};
-  void *a_cor[] = {&A.inst, &A.tile_inst, &A.T, &A.mask, &A.vx, &A.phi, &A.phi32, &A.phi_lo, &A.c};
+  void *a_cor[] = {&A.inst, &A.tile_inst, &A.T, &A.mask, &A.vx, &A.phifx, &A.phi32, &A.flag, &A.c};
   if (step) {
     void *sweep = (void *)sweep_kernel(b->flow, b->Ntot);
     if (prof) e = add_event(g, &last, b->ev[0]);
@@ -1476,12 +1493,12 @@ int run_polled(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *
                                                                    fout, qin, qmid, A.lf, A.u, A.flag);
     BCK(b, rec(1));
     if (b->flow)  // the advection applies the warm start as well
-      kb_advect<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, qmid, A.u, qin, A.phi, A.phi_prev,
-                                      A.phi32, A.phi_lo, A.hist);
+      kb_advect<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, qmid, A.u, qin, A.phifx, A.phi_prev,
+                                      A.phi32, A.hist);
     BCK(b, rec(2));
     if (!b->flow)
-      kb_extrapolate<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, A.phi, A.phi_prev, A.phi32,
-                                           A.phi_lo, A.hist);
+      kb_extrapolate<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, A.phifx, A.phi_prev, A.phi32,
+                                           A.hist);
     nl += 3;
   }
   kb_solve_reset<<<(n + 255) / 256, 256, 0, st>>>(n, A.c, A.bc, A.hist, A.set_hist);
@@ -1508,8 +1525,7 @@ int run_polled(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *
   const cudaGraphConditionalHandle h0 = 0;
   int any_outer = 1;
   while (any_outer && err == cudaSuccess) {
-    kb_res<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, A.qsolve, A.phi32, A.phi_lo, A.v,
-                                 A.part, A.c);
+    kb_res<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, A.qsolve, A.phifx, A.v, A.part, A.c);
     kb_outer<<<n, kBlock, 0, st>>>(A.inst, n, A.T, A.part, A.c, A.bc, A.tol, A.maxit, A.nfam, A.fam_cnt, A.fam_pref,
                                    h0, h0, 0, 0);
     nl += 2;
@@ -1531,7 +1547,7 @@ int run_polled(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *
       nl += 3;
       flags(nullptr, &any_inner);
     }
-    kb_correct<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.mask, A.vx, A.phi, A.phi32, A.phi_lo, A.c);
+    kb_correct<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.mask, A.vx, A.phifx, A.phi32, A.flag, A.c);
     nl += 1;
   }
   if (vc) cudaGraphExecDestroy(vc);
@@ -1553,9 +1569,18 @@ int profile_collect(lbe_batch *b) {
   return LBE_OK;
 }
 
+// the FP64 copy of the potential brought up to date (charges, fields)
+cudaError_t sync_phi64(lbe_batch *b) {
+  if (!b->phi64_stale) return cudaSuccess;
+  lbe::kb_phi_to64<<<b->grid > 0 ? b->grid : 1024, lbe::kBlock, 0, b->stream>>>(b->Ntot, b->phifx, b->phi);
+  b->phi64_stale = false;
+  return cudaGetLastError();
+}
+
 // launch one step (or, step = false, one solve): one graph launch, or the
 // host-polled sequence
 int launch_step(lbe_batch *b, bool step) {
+  b->phi64_stale = true;  // the solve (and the warm start) move the fixed-point potential
   const float *fin = b->f[b->cur];
   float *fout = b->flow ? b->f[b->cur ^ 1] : b->f[b->cur];
   if (b->polled) {
@@ -1771,7 +1796,7 @@ int lbe_batch_create(const lbe_params *params, int n, void *cuda_stream, lbe_bat
   alloc((void **)&b->phi_prev, 8 * lbe::kHist * N);
   alloc((void **)&b->phi32, 4 * N);
   alloc((void **)&b->lf, sizeof(float4) * N);
-  alloc((void **)&b->phi_lo, 4 * N);
+  alloc((void **)&b->phifx, 8 * N);
   alloc((void **)&b->u, sizeof(float4) * N);
   alloc((void **)&b->vec, 4 * N * 6);
   alloc((void **)&b->part, sizeof(double) * 3 * T);
@@ -1844,6 +1869,8 @@ int lbe_batch_set_voltage(lbe_batch *b, int i, const double *psi) {
   if (b->initialised) return bfail(b, LBE_ERR_STATE, "batch set_voltage: set voltages before lbe_batch_init");
   for (int e = 0; e < b->inst[i].n_elec; ++e) {
     if (!isfinite(psi[e])) return bfail(b, LBE_ERR_ARG, "batch set_voltage: non-finite potential");
+    if (!(fabs(psi[e]) < lbe::kPhiMax))
+      return bfail(b, LBE_ERR_ARG, "batch set_voltage: potentials are held below 100 in magnitude");
     b->psi[(size_t)i * (kBE + 1) + e + 1] = psi[e];
   }
   return LBE_OK;
@@ -1865,7 +1892,7 @@ int lbe_batch_init(lbe_batch *b) {
   BCK(b, cudaMemcpyAsync(b->psi_d, b->psi.data(), sizeof(double) * b->psi.size(), cudaMemcpyHostToDevice, b->stream));
   b->cur = 0;
   kb_init<<<b->grid, kBlock, 0, b->stream>>>(b->inst_d, b->tile_inst, b->T, b->Ntot, b->id, b->psi_d, b->f[0], b->q,
-                                             b->phi, b->phi32, b->phi_lo, b->phi_prev, b->u);
+                                             b->phi, b->phi32, b->phifx, b->phi_prev, b->u);
   BCK(b, cudaGetLastError());
   BCK(b, cudaMemsetAsync(b->hist, 0, sizeof(int), b->stream));
   BCK(b, cudaStreamSynchronize(b->stream));
@@ -1906,6 +1933,7 @@ int lbe_batch_charge(lbe_batch *b, double *q_out, int out_on_device) {
   if (!b) return LBE_ERR_ARG;
   if (!b->initialised) return bfail(b, LBE_ERR_STATE, "batch charge: call lbe_batch_init first");
   if (!q_out) return bfail(b, LBE_ERR_ARG, "batch charge: NULL output");
+  BCK(b, sync_phi64(b));
   kb_charge<<<b->grid, kBlock, 0, b->stream>>>(b->inst_d, b->tile_inst, b->T, b->id, b->mask, b->phi, b->qpart);
   kb_charge_final<<<b->n, 32, 0, b->stream>>>(b->inst_d, b->T, b->qpart, b->qout);
   BCK(b, cudaGetLastError());
@@ -1935,7 +1963,9 @@ int lbe_batch_fields(lbe_batch *b, int i, int which, double *out, int out_on_dev
   }
   cudaError_t e;
   if (which == LBE_FIELD_PHI) {
-    e = cudaMemcpyAsync(dst, b->phi + I.off, sizeof(double) * I.g.N, cudaMemcpyDeviceToDevice, b->stream);
+    e = sync_phi64(b);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dst, b->phi + I.off, sizeof(double) * I.g.N, cudaMemcpyDeviceToDevice, b->stream);
   } else {
     kb_n_to_double<<<(unsigned)((I.g.N + 255) / 256), 256, 0, b->stream>>>(b->inst_d, i, b->Ntot, b->q, b->mask, dst);
     e = cudaGetLastError();

@@ -126,12 +126,18 @@ def test_nan_population_in_loaded_state_is_reported(lbe, precision):
 
 
 def test_batch_voltage_spike_raises_range_flag(lbe):
-    """The batched form: an instance at 100 kT/e across a gap of 4 nodes (a
-    finite, accepted potential: 25 kT/e per link, link fluxes e^25 times the
-    bulk) overflows the fixed-point unit in the first sweep; lbe_batch_step
-    reports LBE_ERR_NONFINITE, and the error names the range flag."""
+    """The batched form: an instance at 96 kT/e across a gap of 4 nodes (a
+    finite, accepted potential, below the fixed-point potential's bound of
+    100: 24 kT/e per link, link fluxes e^24 times the bulk) overflows the
+    solute's fixed-point unit in the first sweep; lbe_batch_step reports
+    LBE_ERR_NONFINITE, and the error names the range flag.  A potential of
+    100 or more is refused when it is set."""
+    big = wl.plate_capacitor(4, 4, 6, debye=4.0, bjerrum=1.44, psi=(0.0, 100.0))
+    with pytest.raises(lbe.LBEError) as e:
+        lbe.Batch([big], tol=1e-12)
+    assert e.value.code == lbe.LBE_ERR_ARG, e.value
     ws = [wl.plate_capacitor(4, 4, 20, debye=4.0, bjerrum=1.44, psi=(0.0, 0.1)),
-          wl.plate_capacitor(4, 4, 6, debye=4.0, bjerrum=1.44, psi=(0.0, 100.0))]
+          wl.plate_capacitor(4, 4, 6, debye=4.0, bjerrum=1.44, psi=(0.0, 96.0))]
     b = lbe.Batch(ws, tol=1e-12)
     b.init()
     with pytest.raises(lbe.LBEError) as e:
