@@ -2,8 +2,9 @@
 //
 // Storage: populations as FP32 deviations df_i = f_i - w_i from the rest
 // state (rho = 1, u = 0); solute amounts as int64 fixed point
-// n_k = rho_k^bulk + s_k q_k with s_k = rho_k^bulk 2^-40; the potential as an
-// FP64 master copy (Poisson) plus an FP32 copy read here.
+// n_k = rho_k^bulk + s_k q_k with s_k = rho_k^bulk 2^-40; the potential in
+// int64 fixed point (unit 2^-48, the Poisson solve's master copy) plus its
+// nearest float, read here.
 //
 // Arithmetic is FP32.  The link flux of Eq. LF2 is evaluated so that the
 // value computed at either end of a link is exactly opposite, and is then

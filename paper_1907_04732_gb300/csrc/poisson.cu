@@ -7,15 +7,18 @@
 // reached by iterative refinement:
 //
 //   round:  res = 4 pi l_B rho_el + lap_mod(phi)      (FP64 in the FP64 form;
-//           in the FP32 form float-float arithmetic on phi = hi + lo)
+//           in the FP32 form lap_mod of the fixed-point potential summed
+//           exactly in integers, the sum added to the charge term in
+//           float-float arithmetic)
 //           stop when max_r |res(r)|/diag(r) <= poisson_tol
 //           solve A e = res approximately by preconditioned conjugate
 //           gradients (FP64 and Jacobi in the FP64 form; FP32 and the
 //           multigrid V-cycle of mg.cu in the FP32 form)
-//           phi += e                                  (FP64)
+//           phi += e                (FP64; FP32 form: e rounded to the
+//                                    fixed-point unit, an integer add)
 //
 // Each step starts from the extrapolation in time of the previous solutions
-// (fp32::extrapolate_node).  The CG is the Chronopoulos-Gear variant: both
+// (fp32::extrapolate_node, fp32::extrapolate_fx).  The CG is the Chronopoulos-Gear variant: both
 // inner products of an iteration come from one reduction phase, so an
 // iteration is the vector update (k_cg_a), the preconditioner, and the
 // stencil with the dot products (k_cg_b, whose last block runs the scalar

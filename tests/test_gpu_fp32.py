@@ -1,6 +1,6 @@
-"""FP32 form (FP32 deviations, int64 fixed-point solute in units of
-rho_b 2^-40, FP64 potential refined on a float-float residual) against the
-FP64 oracle.
+"""FP32 form (FP32 deviations streamed in place, int64 fixed-point solute in
+units of rho_b 2^-40, int64 fixed-point potential in units of 2^-48 refined
+on an exact-Laplacian residual) against the FP64 oracle.
 
 Tolerances (relative): potential 1e-6 of the voltage, induced charge 1e-5,
 velocity 1e-5 of the largest velocity; total solute amount of each species
