@@ -148,13 +148,13 @@ struct lbe_batch {
   lbe_stats stats{};
   int grid = 0;  // persistent grid (blocks), picked by the autotuner
   double tuned_ms[LBE_BATCH_TUNE_CANDIDATES] = {};
-  int cur = 0;
   // device
   lbe::InstDev *inst_d = nullptr;
   int *tile_inst = nullptr;
   uint8_t *id = nullptr;
   uint32_t *mask = nullptr;
-  float *f[2] = {nullptr, nullptr};
+  float *f[2] = {nullptr, nullptr};  // populations: f[0], updated in place
+  bool aa_odd = false;                // the next step is an odd one of the AA pattern
   int64_t *q = nullptr, *qstar = nullptr;
   double *phi = nullptr;          // FP64 copy of the potential (charges, fields), refreshed when read
   int64_t *phifx = nullptr;       // the potential in fixed point (unit 2^-kPhiFixBits), the master copy
@@ -186,10 +186,11 @@ struct lbe_batch {
   float *mg_t0 = nullptr;
   float *mg_cinv = nullptr;          // inverses of the coarsest operators, concatenated
   long long *mg_cinv_off = nullptr;  // device [n]: an instance's inverse (-1: Jacobi sweeps)
-  // step graphs keyed by (populations read, solute read); [4] = solve only;
-  // [5..8] step graphs with profiling events
+  // step graphs keyed by (in-place step kind, solute read); [4] = solve
+  // only; [5..8] step graphs with profiling events
   cudaGraphExec_t exec[9] = {};
-  const void *key_f[9] = {}, *key_q[9] = {};
+  int key_odd[9] = {};
+  const void *key_q[9] = {};
   bool polled = false;  // LBE_POISSON_GRAPH=0: solve loops driven by the host
   // profiling (lbe_batch_profile_begin/end): events around the phases
   bool profiling = false;
@@ -375,10 +376,9 @@ __global__ void __launch_bounds__(kBlock) kb_prep(const InstDev *__restrict__ in
   }
 }
 
-// populations read before the link loop: faster (12.8 against 13.3 ms on
-// the 256-instance sweep) although the early read spills a few registers
-// under the 64-register cap
-template <bool FLOW, bool WIDE>
+// the populations are updated in place (fin == fout; LAYOUT POP_AA_EVEN or
+// POP_AA_ODD, the AA pattern of fp32_device.cuh)
+template <bool FLOW, bool WIDE, int LAYOUT>
 __global__ void __launch_bounds__(kBlock, 4) kb_sweep(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
                                                    int T, int Ntot, const uint32_t *__restrict__ mask,
                                                    const float *__restrict__ fin, float *__restrict__ fout,
@@ -405,7 +405,8 @@ __global__ void __launch_bounds__(kBlock, 4) kb_sweep(const InstDev *__restrict_
       const int r = I.off + lo;
       const uint32_t m = mask[r];
       if (!(m & kFluidBit)) continue;
-      sweep_node_lf<FLOW, WIDE>(I.P, Ntot, r, offsets_of(I.g, x, y, z), m, fin, fout, q, qstar, lf, u, over);
+      sweep_node_lf<FLOW, WIDE, LAYOUT>(I.P, Ntot, r, offsets_of(I.g, x, y, z), m, fin, fout, q, qstar, lf, u,
+                                        over);
     }
   }
   if (over) atomicOr(flag, 1);
@@ -416,10 +417,12 @@ using SweepKern = void (*)(const InstDev *, const int *, int, int, const uint32_
 using PrepKern = void (*)(const InstDev *, const int *, int, int, const float *, const int64_t *, float4 *);
 // 64-bit population and record offsets when 19 components pass 2^31
 inline bool wide_batch(long long Ntot) { return (long long)kQ * Ntot >= (1LL << 31); }
-// the sweep for the batch's flow mode and size
-inline SweepKern sweep_kernel(bool flow, long long Ntot) {
-  const SweepKern k[2][2] = {{kb_sweep<false, false>, kb_sweep<false, true>}, {kb_sweep<true, false>, kb_sweep<true, true>}};
-  return k[flow][wide_batch(Ntot)];
+// the sweep for the batch's flow mode, size and in-place step kind
+inline SweepKern sweep_kernel(bool flow, long long Ntot, bool odd) {
+  const SweepKern k[3][2] = {{kb_sweep<false, false, POP_AA_EVEN>, kb_sweep<false, true, POP_AA_EVEN>},
+                             {kb_sweep<true, false, POP_AA_EVEN>, kb_sweep<true, true, POP_AA_EVEN>},
+                             {kb_sweep<true, false, POP_AA_ODD>, kb_sweep<true, true, POP_AA_ODD>}};
+  return k[flow ? (odd ? 2 : 1) : 0][wide_batch(Ntot)];
 }
 inline PrepKern prep_kernel(long long Ntot) { return wide_batch(Ntot) ? kb_prep<true> : kb_prep<false>; }
 
@@ -1433,7 +1436,7 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   void *a_a[] = {&A.inst, &A.n, &A.pref0, &A.T, &A.mask, &A.v, &A.part, &A.c};
   void *a_cor[] = {&A.inst, &A.tile_inst, &A.T, &A.mask, &A.vx, &A.phifx, &A.phi32, &A.flag, &A.c};
   if (step) {
-    void *sweep = (void *)sweep_kernel(b->flow, b->Ntot);
+    void *sweep = (void *)sweep_kernel(b->flow, b->Ntot, b->aa_odd);
     if (prof) e = add_event(g, &last, b->ev[0]);
     if (e == cudaSuccess) e = add_node(g, &last, (void *)prep_kernel(b->Ntot), G, B, a_prep);
     if (e == cudaSuccess) e = add_node(g, &last, sweep, G, B, a_sw);
@@ -1471,7 +1474,8 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
 void drop_graphs(lbe_batch *b) {
   for (int k = 0; k < 9; ++k) {
     if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]), b->exec[k] = nullptr;
-    b->key_f[k] = b->key_q[k] = nullptr;
+    b->key_odd[k] = 0;
+    b->key_q[k] = nullptr;
   }
 }
 
@@ -1489,8 +1493,8 @@ int run_polled(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *
   if (step) {
     BCK(b, rec(0));
     prep_kernel(b->Ntot)<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.phi32, qin, A.lf);
-    sweep_kernel(b->flow, b->Ntot)<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, fin,
-                                                                   fout, qin, qmid, A.lf, A.u, A.flag);
+    sweep_kernel(b->flow, b->Ntot, b->aa_odd)<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, fin,
+                                                                    fout, qin, qmid, A.lf, A.u, A.flag);
     BCK(b, rec(1));
     if (b->flow)  // the advection applies the warm start as well
       kb_advect<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, qmid, A.u, qin, A.phifx, A.phi_prev,
@@ -1581,8 +1585,8 @@ cudaError_t sync_phi64(lbe_batch *b) {
 // host-polled sequence
 int launch_step(lbe_batch *b, bool step) {
   b->phi64_stale = true;  // the solve (and the warm start) move the fixed-point potential
-  const float *fin = b->f[b->cur];
-  float *fout = b->flow ? b->f[b->cur ^ 1] : b->f[b->cur];
+  const float *fin = b->f[0];
+  float *fout = b->f[0];
   if (b->polled) {
     const int rc = run_polled(b, step, fin, fout, b->q, b->qstar);
     if (rc != LBE_OK) return rc;
@@ -1594,13 +1598,13 @@ int launch_step(lbe_batch *b, bool step) {
     const int base = b->profiling ? 5 : 0;
     int slot = -1, empty = -1;
     for (int k = base; k < base + 4; ++k) {
-      if (b->exec[k] && b->key_f[k] == fin && b->key_q[k] == b->q) slot = k;
+      if (b->exec[k] && b->key_odd[k] == (int)b->aa_odd && b->key_q[k] == b->q) slot = k;
       if (!b->exec[k] && empty < 0) empty = k;
     }
     if (slot < 0) {
       if (empty < 0) return bfail(b, LBE_ERR_STATE, "batch: graph cache full");
       BCK(b, build_graph(b, true, fin, fout, b->q, b->qstar, &b->exec[empty], b->profiling));
-      b->key_f[empty] = fin;
+      b->key_odd[empty] = (int)b->aa_odd;
       b->key_q[empty] = b->q;
       slot = empty;
     }
@@ -1608,7 +1612,7 @@ int launch_step(lbe_batch *b, bool step) {
   }
   if (!step) return LBE_OK;
   if (b->flow) {
-    b->cur ^= 1;
+    b->aa_odd = !b->aa_odd;
   } else {
     int64_t *t = b->q;
     b->q = b->qstar;
@@ -1664,8 +1668,9 @@ int autotune(lbe_batch *b) {
   BCK(b, cudaEventCreate(&e1));
   float best = 1e30f;
   int best_grid = 4 * sms;
-  float *fout = b->flow ? b->f[b->cur ^ 1] : b->f[b->cur];
-  // the sweep reads the link records of the current state
+  // the sweep reads the link records of the current state; the trial sweeps
+  // update the populations in place, which are put back to rest (the state
+  // kb_init left) afterwards
   prep_kernel(b->Ntot)<<<4 * sms, kBlock, 0, b->stream>>>(b->inst_d, b->tile_inst, b->T, (int)b->Ntot, b->phi32,
                                                          b->q, b->lf);
   cudaError_t err = cudaGetLastError();
@@ -1674,8 +1679,8 @@ int autotune(lbe_batch *b) {
     float ms = 0.f;
     for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
       err = cudaEventRecord(e0, b->stream);
-      sweep_kernel(b->flow, b->Ntot)<<<grid, kBlock, 0, b->stream>>>(
-          b->inst_d, b->tile_inst, b->T, (int)b->Ntot, b->mask, b->f[b->cur], fout, b->q, b->qstar, b->lf, b->u,
+      sweep_kernel(b->flow, b->Ntot, false)<<<grid, kBlock, 0, b->stream>>>(
+          b->inst_d, b->tile_inst, b->T, (int)b->Ntot, b->mask, b->f[0], b->f[0], b->q, b->qstar, b->lf, b->u,
           b->flag);
       if (err == cudaSuccess) err = cudaGetLastError();
       if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
@@ -1693,6 +1698,9 @@ int autotune(lbe_batch *b) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   BCK(b, err);
+  BCK(b, cudaMemsetAsync(b->f[0], 0, sizeof(float) * lbe::kQ * b->Ntot, b->stream));  // rest: zero deviations
+  BCK(b, cudaMemsetAsync(b->u, 0, sizeof(float4) * b->Ntot, b->stream));
+  b->aa_odd = false;
   b->grid = best_grid;
   return LBE_OK;
 }
@@ -1788,8 +1796,7 @@ int lbe_batch_create(const lbe_params *params, int n, void *cuda_stream, lbe_bat
   alloc((void **)&b->tile_inst, sizeof(int) * T);
   alloc((void **)&b->id, N);
   alloc((void **)&b->mask, 4 * N);
-  alloc((void **)&b->f[0], 4 * N * lbe::kQ);
-  if (b->flow) alloc((void **)&b->f[1], 4 * N * lbe::kQ);
+  alloc((void **)&b->f[0], 4 * N * lbe::kQ);  // one buffer: the populations are updated in place
   alloc((void **)&b->q, 8 * N * 2);
   alloc((void **)&b->qstar, 8 * N * 2);
   alloc((void **)&b->phi, 8 * N);
@@ -1890,7 +1897,7 @@ int lbe_batch_init(lbe_batch *b) {
   int rc = mg_setup(b);  // also uploads the instance table
   if (rc != LBE_OK) return rc;
   BCK(b, cudaMemcpyAsync(b->psi_d, b->psi.data(), sizeof(double) * b->psi.size(), cudaMemcpyHostToDevice, b->stream));
-  b->cur = 0;
+  b->aa_odd = false;
   kb_init<<<b->grid, kBlock, 0, b->stream>>>(b->inst_d, b->tile_inst, b->T, b->Ntot, b->id, b->psi_d, b->f[0], b->q,
                                              b->phi, b->phi32, b->phifx, b->phi_prev, b->u);
   BCK(b, cudaGetLastError());
