@@ -106,12 +106,29 @@ __device__ __forceinline__ void put32(int N, int r, const Offs &o, uint32_t m, i
 
 // ---------------------------------------------------------------------------
 // Link records of a 1:1 salt (z = +1, -1): one float4 per fluid node,
-// (phi, nu_+, nu_-, 0) with nu = s q, written before each sweep so that the
+// (nu_+, nu_-, phi, 0) with nu = s q, written before each sweep so that the
 // link loop reads one record per neighbour instead of converting its 64-bit
-// solute amounts.
+// solute amounts.  The two species' values come first, as one aligned pair
+// of registers for the paired arithmetic of link_pair.
 __device__ __forceinline__ float4 link_record(const P32 &P, float phi, long long q0, long long q1) {
-  return make_float4(phi, __fmul_rn(P.s[0], ll2f(q0)), __fmul_rn(P.s[1], ll2f(q1)), 0.f);
+  return make_float4(__fmul_rn(P.s[0], ll2f(q0)), __fmul_rn(P.s[1], ll2f(q1)), phi, 0.f);
 }
+
+// Paired FP32 arithmetic (one instruction for two lanes on this GPU), each
+// lane rounded exactly as the scalar __fadd_rn / __fmul_rn / __fmaf_rn: the
+// two species of a 1:1 salt go through a link's flux terms together.
+__device__ __forceinline__ float2 sub2_rn(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+      "mov.b64 pa, {%2, %3};\n\t"
+      "mov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pd, pa, pb;\n\t"
+      "mov.b64 {%0, %1}, pd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 lo_pair(const float4 &v) { return make_float2(v.x, v.y); }
 
 // sinh x and cosh x - 1 from expm1f, for the rare link with |x| > 1/4 (a
 // call, so that the common path does not carry it)
@@ -130,9 +147,11 @@ static __device__ __noinline__ float2 shch_wide(float x) {
 // below 5e-8) and from expm1f beyond.  Every link is evaluated in this one
 // orientation (a = the end from which it points along one of c_1..c_9), by
 // both of its end nodes from the same records: the two are bitwise equal.
-__device__ __forceinline__ void link_pair(const P32 &P, const float4 &ra, const float4 &rb, float ec, float &Jp,
-                                          float &Ap, float &Jm, float &Am) {
-  const float x = __fsub_rn(__fsub_rn(rb.x, ra.x), ec);
+// The species (+, -) are the two lanes of J = (J_+, J_-) and A = (A_+, A_-);
+// rb2 = (2 rho_b+, 2 rho_b-).
+__device__ __forceinline__ void link_pair(float2 rb2, const float4 &ra, const float4 &rb, float ec, float2 &J,
+                                          float2 &A) {
+  const float x = __fsub_rn(__fsub_rn(rb.z, ra.z), ec);
   float sh, ch;
   if (fabsf(x) <= 0.25f) {
     const float x2 = __fmul_rn(x, x);
@@ -143,36 +162,41 @@ __device__ __forceinline__ void link_pair(const P32 &P, const float4 &ra, const 
     sh = w.x;
     ch = w.y;
   }
-  const float Dp = __fsub_rn(rb.y, ra.y), Dm = __fsub_rn(rb.z, ra.z);
-  const float Sp = __fadd_rn(2.f * P.rb[0], __fadd_rn(ra.y, rb.y));
-  const float Sm = __fadd_rn(2.f * P.rb[1], __fadd_rn(ra.z, rb.z));
-  Ap = __fmaf_rn(Sp, sh, __fmul_rn(Dp, ch));
-  Am = __fmaf_rn(-Sm, sh, __fmul_rn(Dm, ch));
-  Jp = __fmaf_rn(2.f, Dp, Ap);
-  Jm = __fmaf_rn(2.f, Dm, Am);
+  const float2 na = lo_pair(ra), nb = lo_pair(rb);
+  const float2 D = sub2_rn(nb, na);
+  const float2 S = __fadd2_rn(rb2, __fadd2_rn(na, nb));
+  // A_+ = S_+ sh + D_+ ch, A_- = -S_- sh + D_- ch (z = -1 flips dmu)
+  A = __ffma2_rn(S, make_float2(sh, -sh), __fmul2_rn(D, make_float2(ch, ch)));
+  J = __ffma2_rn(make_float2(2.f, 2.f), D, A);
 }
 
-// Rounding a link's flux x (fixed-point units, |x| < 2^44) to an integer and
-// adding it to (SIGN > 0) or subtracting it from (SIGN < 0) a 64-bit amount
-// kept as two 32-bit sums hi 2^22 + lo, with FP32 and integer adds only (no
-// conversion instructions): h = round(x 2^-22) read off the float grid of
-// unit spacing at 1.5 2^23 (kMagic), lo = x - h 2^22 (exact), l = round(lo)
+// Rounding a link's fluxes x = (x_0, x_1) of the two species (fixed-point
+// units, |x| < 2^44) to integers and adding them to (SIGN > 0) or
+// subtracting them from (SIGN < 0) two 64-bit amounts, each kept as two
+// 32-bit sums hi 2^22 + lo, with FP32 and integer adds only (no conversion
+// instructions): per lane h = round(x 2^-22) read off the float grid of unit
+// spacing at 1.5 2^23 (kMagic), lo = x - h 2^22 (exact), l = round(lo)
 // likewise.  The sums carry kMagicBits per term, removed once per node
 // (mod 2^32).  Both roundings are round-half-even, an odd function of x, so
 // a link's two ends move exactly opposite amounts.
 constexpr float kMagic = 12582912.f;  // 1.5 * 2^23
 constexpr unsigned kMagicBits = 0x4B400000u;
 template <int SIGN>
-__device__ __forceinline__ void acc_round(float x, unsigned &ah, unsigned &al) {
-  const float h = __fmaf_rn(x, 2.384185791015625e-07f, kMagic);  // 2^-22
-  const float lo = __fmaf_rn(-__fsub_rn(h, kMagic), 4194304.f, x);  // 2^22
-  const float l = __fadd_rn(lo, kMagic);
+__device__ __forceinline__ void acc_round(float2 x, unsigned &ah0, unsigned &al0, unsigned &ah1, unsigned &al1) {
+  const float2 mg = make_float2(kMagic, kMagic);
+  const float2 h = __ffma2_rn(x, make_float2(2.384185791015625e-07f, 2.384185791015625e-07f), mg);  // 2^-22
+  const float2 lo = __ffma2_rn(sub2_rn(h, mg), make_float2(-4194304.f, -4194304.f), x);  // x - (h - M) 2^22
+  const float2 l = __fadd2_rn(lo, mg);
   if (SIGN > 0) {
-    ah += (unsigned)__float_as_int(h);
-    al += (unsigned)__float_as_int(l);
+    ah0 += (unsigned)__float_as_int(h.x);
+    ah1 += (unsigned)__float_as_int(h.y);
+    al0 += (unsigned)__float_as_int(l.x);
+    al1 += (unsigned)__float_as_int(l.y);
   } else {
-    ah -= (unsigned)__float_as_int(h);
-    al -= (unsigned)__float_as_int(l);
+    ah0 -= (unsigned)__float_as_int(h.x);
+    ah1 -= (unsigned)__float_as_int(h.y);
+    al0 -= (unsigned)__float_as_int(l.x);
+    al1 -= (unsigned)__float_as_int(l.y);
   }
 }
 // the 64-bit amount of two sums after net = (#added - #subtracted) terms
@@ -367,36 +391,37 @@ __device__ __forceinline__ void sweep_node_lf_(const P32 &P, int N, int r, const
   float f[kQ];
   if (FLOW && kEarly) gather32<WIDE, ALL, LAYOUT>(N, r, o, m, fin, f);
   const float4 self = lf[(PopIdx<WIDE>)r];
+  const float2 rb2 = make_float2(2.f * P.rb[0], 2.f * P.rb[1]);
+  const float2 kq1 = make_float2(P.kq1[0], P.kq1[1]), kq2 = make_float2(P.kq2[0], P.kq2[1]);
   unsigned ah0 = 0u, al0 = 0u, ah1 = 0u, al1 = 0u;
-  float sabs = 0.f, Fx = 0.f, Fy = 0.f, Fz = 0.f;
+  float2 sq = make_float2(0.f, 0.f);
+  float Fx = 0.f, Fy = 0.f, Fz = 0.f;
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     if (!ALL && !(m & (1u << (i - 1)))) continue;
     const float4 nb = lf[(PopIdx<WIDE>)nb_of(o, r, i)];
     const bool mine = i <= 9;  // this node owns the link (c_i among c_1..c_9)
     const int d = mine ? i : opp_of(i);
-    float Jp, Ap, Jm, Am;
-    link_pair(P, mine ? self : nb, mine ? nb : self, P.ec[d], Jp, Ap, Jm, Am);
-    const float jq0 = __fmul_rn(Jp, c2_of(d) == 1 ? P.kq1[0] : P.kq2[0]);
-    const float jq1 = __fmul_rn(Jm, c2_of(d) == 1 ? P.kq1[1] : P.kq2[1]);
-    sabs += fabsf(jq0) + fabsf(jq1);
-    if (mine) {
-      acc_round<-1>(jq0, ah0, al0);
-      acc_round<-1>(jq1, ah1, al1);
-    } else {
-      acc_round<1>(jq0, ah0, al0);
-      acc_round<1>(jq1, ah1, al1);
-    }
+    float2 J, A;
+    link_pair(rb2, mine ? self : nb, mine ? nb : self, P.ec[d], J, A);
+    const float2 jq = __fmul2_rn(J, c2_of(d) == 1 ? kq1 : kq2);
+    sq = __ffma2_rn(jq, jq, sq);
+    if (mine)
+      acc_round<-1>(jq, ah0, al0, ah1, al1);
+    else
+      acc_round<1>(jq, ah0, al0, ah1, al1);
     if (FLOW) {
       // link excess flux g = -(A_+ + A_-)/(2|c|) along c_d; both ends take
       // c_d g (from b it is -g along -c_d)
-      const float gs = (-0.5f * (float)invlen_of(d)) * (Ap + Am);
+      const float gs = (-0.5f * (float)invlen_of(d)) * (A.x + A.y);
       Fx += cx_of(d) * gs;
       Fy += cy_of(d) * gs;
       Fz += cz_of(d) * gs;
     }
   }
-  over |= !(sabs < 8.0e12f);  // |x| < 2^43 per link keeps acc_round exact; catches NaN
+  // every |x| < 2^43 keeps acc_round exact (the sum of squares bounds each
+  // link's value); a NaN fails the test too
+  over |= !(sq.x + sq.y < 6.4e25f);
   const int net = __popc(m & 0x3FE00u) - __popc(m & 0x1FFu);  // received - owned links
   qstar[r] = q[r] + acc_value(ah0, al0, net);
   qstar[N + r] = q[N + r] + acc_value(ah1, al1, net);
@@ -597,6 +622,5 @@ __device__ __forceinline__ long long lap6_fx(const Geo &g, int r, int x, int y, 
   const Offs o = offsets_of(g, x, y, z);
   return (m & kLinkBits) == kLinkBits ? lap6_fx_<true>(o, r, m, v) : lap6_fx_<false>(o, r, m, v);
 }
-
 }  // namespace fp32
 }  // namespace lbe
