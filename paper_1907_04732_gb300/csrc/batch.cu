@@ -426,7 +426,7 @@ inline SweepKern sweep_kernel(bool flow, long long Ntot, bool odd) {
 }
 inline PrepKern prep_kernel(long long Ntot) { return wide_batch(Ntot) ? kb_prep<true> : kb_prep<false>; }
 
-__global__ void __launch_bounds__(kBlock) kb_advect(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
+__global__ void __launch_bounds__(kBlock, 5) kb_advect(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
                                                     int T, int Ntot, const uint32_t *__restrict__ mask,
                                                     const int64_t *__restrict__ qin, const float4 *__restrict__ u,
                                                     int64_t *__restrict__ qout, int64_t *__restrict__ phifx,
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(kBlock) kb_advect(const InstDev *__restrict__ 
         qout[Ntot + r] = qin[Ntot + r];
         continue;
       }
-      advect_node(2, Ntot, r, offsets_of(I.g, x, y, z), m, qin, u, qout);
+      advect_node2(Ntot, r, offsets_of(I.g, x, y, z), m, qin, u, qout);
       extrapolate_fx(Ntot, r, phifx, prev, phi32, have);
     }
   }

@@ -492,6 +492,67 @@ __device__ __forceinline__ void advect_node(int ns, int N, int r, const Offs &o,
     if (k < ns) qout[k * N + r] = acc[k] - base;
 }
 
+// advect_node for two species (out of line: the rare case of advect_node2)
+static __device__ __noinline__ void advect_node2_wide(int N, int r, Offs o, uint32_t m,
+                                                      const int64_t *__restrict__ qin, const float4 *__restrict__ u,
+                                                      int64_t *__restrict__ qout);
+
+// advect_node for two species, each share rounded by acc_round for both
+// species at once (no conversion instructions; the same integers as share:
+// round-half-even of w tot).  acc_round is exact while |w tot| < 2^43, i.e.
+// while the node and its sources hold less than 8 times the bulk amount;
+// otherwise (a node near overflow) the node is done again by advect_node.
+__device__ __forceinline__ void advect_node2(int N, int r, const Offs &o, uint32_t m,
+                                             const int64_t *__restrict__ qin, const float4 *__restrict__ u,
+                                             int64_t *__restrict__ qout) {
+  constexpr float kFast = 8796093022208.f;  // 2^43
+  const float4 v0 = u[r];
+  const int code0 = __float_as_int(v0.w);
+  const long long base = 1LL << kFixBits;
+  const long long acc0 = base + qin[r], acc1 = base + qin[N + r];
+  const float2 tot = make_float2(ll2f(acc0), ll2f(acc1));
+  bool fast = fabsf(tot.x) < kFast && fabsf(tot.y) < kFast;
+  unsigned ah0 = 0u, al0 = 0u, ah1 = 0u, al1 = 0u;
+  int net = 0;  // acc_round terms added - subtracted
+  // outgoing (the share is zero outside the octant of u); shares bound for
+  // solid neighbours stay
+#pragma unroll
+  for (int d = 0; d < 27; ++d) {
+    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+    if (d == 13 || !(m & (1u << dir_bit(dx, dy, dz)))) continue;
+    if ((code0 & cell_bits(dx, dy, dz)) != cell_bits(dx, dy, dz)) continue;
+    const float w = ov(dx, v0.x) * ov(dy, v0.y) * ov(dz, v0.z);
+    acc_round<-1>(__fmul2_rn(make_float2(w, w), tot), ah0, al0, ah1, al1);
+    --net;
+  }
+  // incoming from every fluid neighbour whose cell reaches r: the source at
+  // r - s gives along +s
+#pragma unroll
+  for (int d = 0; d < 27; ++d) {
+    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+    if (d == 13 || !(m & (1u << dir_bit(-dx, -dy, -dz)))) continue;
+    const int s = r + o.at(-dx, -dy, -dz);
+    const float4 v = u[s];
+    if ((__float_as_int(v.w) & cell_bits(dx, dy, dz)) != cell_bits(dx, dy, dz)) continue;
+    const float2 ts = make_float2(ll2f(base + qin[s]), ll2f(base + qin[N + s]));
+    fast &= fabsf(ts.x) < kFast && fabsf(ts.y) < kFast;
+    const float w = ov(dx, v.x) * ov(dy, v.y) * ov(dz, v.z);
+    acc_round<1>(__fmul2_rn(make_float2(w, w), ts), ah0, al0, ah1, al1);
+    ++net;
+  }
+  if (fast) {
+    qout[r] = acc0 + acc_value(ah0, al0, net) - base;
+    qout[N + r] = acc1 + acc_value(ah1, al1, net) - base;
+  } else {
+    advect_node2_wide(N, r, o, m, qin, u, qout);
+  }
+}
+static __device__ __noinline__ void advect_node2_wide(int N, int r, Offs o, uint32_t m,
+                                                      const int64_t *__restrict__ qin, const float4 *__restrict__ u,
+                                                      int64_t *__restrict__ qout) {
+  advect_node(2, N, r, o, m, qin, u, qout);
+}
+
 // Warm start of the next solve at fluid node i: the polynomial in time
 // through the last history + 1 solutions, one step ahead,
 //   history 3: phi <- 4 phi(t) - 6 phi(t-1) + 4 phi(t-2) - phi(t-3)
