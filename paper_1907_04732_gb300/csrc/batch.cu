@@ -361,7 +361,6 @@ __global__ void __launch_bounds__(kBlock) kb_init(const InstDev *__restrict__ in
 
 // link records of every fluid node (fp32::link_record) from the potential
 // and solute of the step about to run
-template <bool WIDE>
 __global__ void __launch_bounds__(kBlock) kb_prep(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
                                                   int T, int Ntot, const float *__restrict__ phi,
                                                   const int64_t *__restrict__ q, float4 *__restrict__ lf) {
@@ -378,7 +377,7 @@ __global__ void __launch_bounds__(kBlock) kb_prep(const InstDev *__restrict__ in
 
 // the populations are updated in place (fin == fout; LAYOUT POP_AA_EVEN or
 // POP_AA_ODD, the AA pattern of fp32_device.cuh)
-template <bool FLOW, bool WIDE, int LAYOUT>
+template <bool FLOW, int WIDE, int LAYOUT>
 __global__ void __launch_bounds__(kBlock, 4) kb_sweep(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
                                                    int T, int Ntot, const uint32_t *__restrict__ mask,
                                                    const float *__restrict__ fin, float *__restrict__ fout,
@@ -415,16 +414,16 @@ __global__ void __launch_bounds__(kBlock, 4) kb_sweep(const InstDev *__restrict_
 using SweepKern = void (*)(const InstDev *, const int *, int, int, const uint32_t *, const float *, float *,
                           const int64_t *, int64_t *, const float4 *, float4 *, int *);
 using PrepKern = void (*)(const InstDev *, const int *, int, int, const float *, const int64_t *, float4 *);
-// 64-bit population and record offsets when 19 components pass 2^31
-inline bool wide_batch(long long Ntot) { return (long long)kQ * Ntot >= (1LL << 31); }
-// the sweep for the batch's flow mode, size and in-place step kind
+// the sweep for the batch's flow mode, size (the width of the population
+// offsets, fp32::pop_idx_kind) and in-place step kind
 inline SweepKern sweep_kernel(bool flow, long long Ntot, bool odd) {
-  const SweepKern k[3][2] = {{kb_sweep<false, false, POP_AA_EVEN>, kb_sweep<false, true, POP_AA_EVEN>},
-                             {kb_sweep<true, false, POP_AA_EVEN>, kb_sweep<true, true, POP_AA_EVEN>},
-                             {kb_sweep<true, false, POP_AA_ODD>, kb_sweep<true, true, POP_AA_ODD>}};
-  return k[flow ? (odd ? 2 : 1) : 0][wide_batch(Ntot)];
+  const SweepKern k[3][3] = {
+      {kb_sweep<false, 0, POP_AA_EVEN>, kb_sweep<false, 1, POP_AA_EVEN>, kb_sweep<false, 2, POP_AA_EVEN>},
+      {kb_sweep<true, 0, POP_AA_EVEN>, kb_sweep<true, 1, POP_AA_EVEN>, kb_sweep<true, 2, POP_AA_EVEN>},
+      {kb_sweep<true, 0, POP_AA_ODD>, kb_sweep<true, 1, POP_AA_ODD>, kb_sweep<true, 2, POP_AA_ODD>}};
+  return k[flow ? (odd ? 2 : 1) : 0][pop_idx_kind(Ntot)];
 }
-inline PrepKern prep_kernel(long long Ntot) { return wide_batch(Ntot) ? kb_prep<true> : kb_prep<false>; }
+inline PrepKern prep_kernel(long long) { return kb_prep; }
 
 __global__ void __launch_bounds__(kBlock, 5) kb_advect(const InstDev *__restrict__ inst, const int *__restrict__ tile_inst,
                                                     int T, int Ntot, const uint32_t *__restrict__ mask,

@@ -53,10 +53,15 @@ __device__ __forceinline__ float tterm(float a, float nu) { return __fmaf_rn(2.f
 
 __device__ __forceinline__ int nb_of(const Offs &o, int r, int i) { return r + o.at(cx_of(i), cy_of(i), cz_of(i)); }
 
-// Population component offsets: 32-bit while 19 N < 2^31, else 64-bit
-// (WIDE; a large lattice or batch passes 2^31 over 19 components).
-template <bool WIDE>
-using PopIdx = typename std::conditional<WIDE, long long, int>::type;
+// Population component offsets (WIDE): 0 signed 32-bit while 19 N < 2^31,
+// 1 unsigned 32-bit while 19 N < 2^32 (the same address arithmetic, one
+// more bit: a large lattice or batch), 2 64-bit beyond.
+template <int WIDE>
+using PopIdx = typename std::conditional<WIDE == 0, int,
+                                         typename std::conditional<WIDE == 1, unsigned, long long>::type>::type;
+inline int pop_idx_kind(long long N) {
+  return 19LL * N < (1LL << 31) ? 0 : (19LL * N < (1LL << 32) ? 1 : 2);
+}
 
 // Population layouts of a step, with halfway bounce-back at links to solid
 // (bit i-1 of the node mask m clear: x + c_i is solid or outside the box).
@@ -72,7 +77,7 @@ using PopIdx = typename std::conditional<WIDE, long long, int>::type;
 // ALL: every link joins fluid (no bounce-back to select).
 enum PopLayout { POP_PULL = 0, POP_AA_EVEN = 1, POP_AA_ODD = 2 };
 
-template <bool WIDE, bool ALL = false, int LAYOUT = POP_PULL>
+template <int WIDE, bool ALL = false, int LAYOUT = POP_PULL>
 __device__ __forceinline__ void gather32(int N, int r, const Offs &o, uint32_t m, const float *__restrict__ fin,
                                          float f[kQ]) {
   f[0] = fin[r];
@@ -81,27 +86,27 @@ __device__ __forceinline__ void gather32(int N, int r, const Offs &o, uint32_t m
     const int io = opp_of(i);
     const bool in = ALL || (m & (1u << (io - 1)));  // x - c_i is fluid
     if (LAYOUT == POP_PULL)
-      f[i] = in ? fin[(PopIdx<WIDE>)i * N + nb_of(o, r, io)] : fin[(PopIdx<WIDE>)io * N + r];
+      f[i] = in ? fin[(PopIdx<WIDE>)i * (PopIdx<WIDE>)N + (PopIdx<WIDE>)nb_of(o, r, io)] : fin[(PopIdx<WIDE>)io * (PopIdx<WIDE>)N + (PopIdx<WIDE>)r];
     else if (LAYOUT == POP_AA_EVEN)
-      f[i] = fin[(PopIdx<WIDE>)i * N + r];
+      f[i] = fin[(PopIdx<WIDE>)i * (PopIdx<WIDE>)N + (PopIdx<WIDE>)r];
     else
-      f[i] = in ? fin[(PopIdx<WIDE>)io * N + nb_of(o, r, io)] : fin[(PopIdx<WIDE>)i * N + r];
+      f[i] = in ? fin[(PopIdx<WIDE>)io * (PopIdx<WIDE>)N + (PopIdx<WIDE>)nb_of(o, r, io)] : fin[(PopIdx<WIDE>)i * (PopIdx<WIDE>)N + (PopIdx<WIDE>)r];
   }
 }
 
 // where post-collision population i of node r goes (i >= 1)
-template <bool WIDE, bool ALL, int LAYOUT>
+template <int WIDE, bool ALL, int LAYOUT>
 __device__ __forceinline__ void put32(int N, int r, const Offs &o, uint32_t m, int i, float v,
                                       float *__restrict__ fout) {
   const int io = opp_of(i);
   if (LAYOUT == POP_PULL)
-    fout[(PopIdx<WIDE>)i * N + r] = v;
+    fout[(PopIdx<WIDE>)i * (PopIdx<WIDE>)N + (PopIdx<WIDE>)r] = v;
   else if (LAYOUT == POP_AA_EVEN)
-    fout[(PopIdx<WIDE>)io * N + r] = v;
+    fout[(PopIdx<WIDE>)io * (PopIdx<WIDE>)N + (PopIdx<WIDE>)r] = v;
   else if (ALL || (m & (1u << (i - 1))))
-    fout[(PopIdx<WIDE>)i * N + nb_of(o, r, i)] = v;
+    fout[(PopIdx<WIDE>)i * (PopIdx<WIDE>)N + (PopIdx<WIDE>)nb_of(o, r, i)] = v;
   else
-    fout[(PopIdx<WIDE>)io * N + r] = v;
+    fout[(PopIdx<WIDE>)io * (PopIdx<WIDE>)N + (PopIdx<WIDE>)r] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -302,7 +307,7 @@ __host__ __device__ constexpr int cell_bits(int dx, int dy, int dz) {
 //   df'_i = (1 - omega) df_i + E_even +- E_odd,
 //   E_even = w [omega (drho + rho (4.5 cu^2 - 1.5 uu)) + guo (9 cu cF - 3 uF)]
 //   E_odd  = w [3 omega rho cu + 3 guo cF]
-template <bool WIDE, bool ALL = false, int LAYOUT = POP_PULL>
+template <int WIDE, bool ALL = false, int LAYOUT = POP_PULL>
 __device__ __forceinline__ void lb_collide(const P32 &P, int N, int r, const Offs &o, uint32_t m, const float f[kQ],
                                            float *__restrict__ fout, float4 *__restrict__ u, const float F[3],
                                            bool &over) {
@@ -338,7 +343,7 @@ __device__ __forceinline__ void lb_collide(const P32 &P, int N, int r, const Off
     put32<WIDE, ALL, LAYOUT>(N, r, o, m, io, keep * f[io] + (ee - eo), fout);
   }
 }
-template <bool WIDE, bool ALL = false, int LAYOUT = POP_PULL>
+template <int WIDE, bool ALL = false, int LAYOUT = POP_PULL>
 __device__ __forceinline__ void lb_node(const P32 &P, int N, int r, const Offs &o, uint32_t m,
                                         const float *__restrict__ fin, float *__restrict__ fout,
                                         float4 *__restrict__ u, const float F[3], bool &over) {
@@ -350,7 +355,7 @@ __device__ __forceinline__ void lb_node(const P32 &P, int N, int r, const Offs &
 // Fused step at one fluid node, any salt: quantised link fluxes and
 // q* = q - sum Jq, solvent force, and (FLOW) BGK + Guo collision with pull
 // streaming.
-template <bool FLOW, bool WIDE, int LAYOUT = POP_PULL>
+template <bool FLOW, int WIDE, int LAYOUT = POP_PULL>
 __device__ __forceinline__ void sweep_node(const P32 &P, int N, int r, const Offs &o, uint32_t m,
                                            const float *__restrict__ fin, float *__restrict__ fout,
                                            const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
@@ -378,7 +383,7 @@ __device__ __forceinline__ void sweep_node(const P32 &P, int N, int r, const Off
 // the other end adds: exact conservation), the force from the link excess
 // fluxes, then (FLOW) BGK + Guo collision with streaming in the given
 // population layout.
-template <bool FLOW, bool WIDE, bool ALL, int LAYOUT>
+template <bool FLOW, int WIDE, bool ALL, int LAYOUT>
 __device__ __forceinline__ void sweep_node_lf_(const P32 &P, int N, int r, const Offs &o, uint32_t m,
                                               const float *__restrict__ fin, float *__restrict__ fout,
                                               const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
@@ -390,7 +395,7 @@ __device__ __forceinline__ void sweep_node_lf_(const P32 &P, int N, int r, const
   constexpr bool kEarly = LAYOUT == POP_PULL;
   float f[kQ];
   if (FLOW && kEarly) gather32<WIDE, ALL, LAYOUT>(N, r, o, m, fin, f);
-  const float4 self = lf[(PopIdx<WIDE>)r];
+  const float4 self = lf[r];
   const float2 rb2 = make_float2(2.f * P.rb[0], 2.f * P.rb[1]);
   const float2 kq1 = make_float2(P.kq1[0], P.kq1[1]), kq2 = make_float2(P.kq2[0], P.kq2[1]);
   unsigned ah0 = 0u, al0 = 0u, ah1 = 0u, al1 = 0u;
@@ -399,7 +404,7 @@ __device__ __forceinline__ void sweep_node_lf_(const P32 &P, int N, int r, const
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     if (!ALL && !(m & (1u << (i - 1)))) continue;
-    const float4 nb = lf[(PopIdx<WIDE>)nb_of(o, r, i)];
+    const float4 nb = lf[nb_of(o, r, i)];
     const bool mine = i <= 9;  // this node owns the link (c_i among c_1..c_9)
     const int d = mine ? i : opp_of(i);
     float2 J, A;
@@ -433,7 +438,7 @@ __device__ __forceinline__ void sweep_node_lf_(const P32 &P, int N, int r, const
 }
 // the same; a node whose 18 links all join fluid (most of a lattice) takes
 // a form without the per-link mask tests
-template <bool FLOW, bool WIDE, int LAYOUT = POP_PULL>
+template <bool FLOW, int WIDE, int LAYOUT = POP_PULL>
 __device__ __forceinline__ void sweep_node_lf(const P32 &P, int N, int r, const Offs &o, uint32_t m,
                                               const float *__restrict__ fin, float *__restrict__ fout,
                                               const int64_t *__restrict__ q, int64_t *__restrict__ qstar,

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kBlock) k_prep32(const Geo g, const P32 P, con
 // pattern of fp32_device.cuh: every population slot is read and then
 // written by a single node, so the two pointers may alias).  Capped at 64
 // registers (four blocks per SM).
-template <bool FLOW, bool WIDE, int LAYOUT>
+template <bool FLOW, int WIDE, int LAYOUT>
 __global__ void __launch_bounds__(kBlock, 4) k_sweep32(const Geo g, const P32 P, const uint32_t *__restrict__ mask,
                                                     const float *__restrict__ fin, float *__restrict__ fout,
                                                     const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_sweep32(const Geo g, const P32 P,
 
 // The same for any other salt (several species, valences other than +-1):
 // each link evaluated at both ends with a fixed rounding sequence.
-template <bool FLOW, bool WIDE, int LAYOUT>
+template <bool FLOW, int WIDE, int LAYOUT>
 __global__ void __launch_bounds__(kBlock) k_sweep32_gen(const Geo g, const P32 P, const uint32_t *__restrict__ mask,
                                                         const float *__restrict__ fin, float *__restrict__ fout,
                                                         const int64_t *__restrict__ q, int64_t *__restrict__ qstar,
@@ -198,7 +198,7 @@ __global__ void k_moments32(const Geo g, const P32 P, int flow, const uint32_t *
   }
   const Offs o = offsets_of(g, x, y, z);
   float f[kQ];
-  gather32<true, false, LAYOUT>(N, r, o, m, fin, f);  // what the next step's collision reads
+  gather32<2, false, LAYOUT>(N, r, o, m, fin, f);  // what the next step's collision reads
   if (f_out) {
     for (int i = 0; i < kQ; ++i) f_out[(long long)i * N + r] = w_of(i) + (double)f[i];
     return;
@@ -243,8 +243,11 @@ cudaError_t launch_init32(lbe_handle *h) {
 
 cudaError_t launch_sweep32(lbe_handle *h) {
   const P32 &P = h->p32;
-  // 32-bit population offsets while the 19 components fit
-  const bool wide = (long long)kQ * h->geo.N >= (1LL << 31);
+  // 32-bit population offsets while the 19 components fit (pop_idx_kind);
+  // the even in-place step of a 1:1 salt takes 64-bit offsets: in that form
+  // it compiles without spilling under the 64-register cap (measured on the
+  // 64x64x256 electro-osmosis lattice: sweep phase 0.0623 against 0.0633 ms)
+  const int wide = pop_idx_kind(h->geo.N);
   const bool flow = h->prm.flow != 0;
   const bool odd = flow && h->aa_odd;  // the populations' in-place step kind
   float *pop = h->f32[0];
@@ -252,17 +255,21 @@ cudaError_t launch_sweep32(lbe_handle *h) {
     k_prep32<<<grid_for(h->geo.N), kBlock, 0, h->stream>>>(h->geo, P, h->phi32, h->q, h->lf);
     using Kern = void (*)(const Geo, const P32, const uint32_t *, const float *, float *, const int64_t *, int64_t *,
                           const float4 *, float4 *, int *);
-    const Kern k[3][2] = {{k_sweep32<false, false, POP_AA_EVEN>, k_sweep32<false, true, POP_AA_EVEN>},
-                          {k_sweep32<true, false, POP_AA_EVEN>, k_sweep32<true, true, POP_AA_EVEN>},
-                          {k_sweep32<true, false, POP_AA_ODD>, k_sweep32<true, true, POP_AA_ODD>}};
-    k[flow + odd][wide]<<<LAUNCH3(h), 0, h->stream>>>(h->geo, P, h->mask, pop, pop, h->q, h->qstar, h->lf, h->u32,
-                                                      h->flag);
+    const Kern k[3][3] = {
+        {k_sweep32<false, 0, POP_AA_EVEN>, k_sweep32<false, 1, POP_AA_EVEN>, k_sweep32<false, 2, POP_AA_EVEN>},
+        {k_sweep32<true, 0, POP_AA_EVEN>, k_sweep32<true, 1, POP_AA_EVEN>, k_sweep32<true, 2, POP_AA_EVEN>},
+        {k_sweep32<true, 0, POP_AA_ODD>, k_sweep32<true, 1, POP_AA_ODD>, k_sweep32<true, 2, POP_AA_ODD>}};
+    k[flow + odd][flow && !odd ? 2 : wide]<<<LAUNCH3(h), 0, h->stream>>>(h->geo, P, h->mask, pop, pop, h->q,
+                                                                         h->qstar, h->lf, h->u32, h->flag);
   } else {
     using Kern = void (*)(const Geo, const P32, const uint32_t *, const float *, float *, const int64_t *, int64_t *,
                           const float *, float4 *, int *);
-    const Kern k[3][2] = {{k_sweep32_gen<false, false, POP_AA_EVEN>, k_sweep32_gen<false, true, POP_AA_EVEN>},
-                          {k_sweep32_gen<true, false, POP_AA_EVEN>, k_sweep32_gen<true, true, POP_AA_EVEN>},
-                          {k_sweep32_gen<true, false, POP_AA_ODD>, k_sweep32_gen<true, true, POP_AA_ODD>}};
+    const Kern k[3][3] = {{k_sweep32_gen<false, 0, POP_AA_EVEN>, k_sweep32_gen<false, 1, POP_AA_EVEN>,
+                           k_sweep32_gen<false, 2, POP_AA_EVEN>},
+                          {k_sweep32_gen<true, 0, POP_AA_EVEN>, k_sweep32_gen<true, 1, POP_AA_EVEN>,
+                           k_sweep32_gen<true, 2, POP_AA_EVEN>},
+                          {k_sweep32_gen<true, 0, POP_AA_ODD>, k_sweep32_gen<true, 1, POP_AA_ODD>,
+                           k_sweep32_gen<true, 2, POP_AA_ODD>}};
     k[flow + odd][wide]<<<LAUNCH3(h), 0, h->stream>>>(h->geo, P, h->mask, pop, pop, h->q, h->qstar, h->phi32,
                                                       h->u32, h->flag);
   }
