@@ -135,9 +135,9 @@ IMPL_BYTES = {
 # for the kernel source it was taken from (a hash of the sweep's sources)
 SWEEP_TRAFFIC = {
     # k_prep32 + k_sweep32 (odd in-place step), one launch each, from an ncu
-    # --set full capture of these sources on GB300: 20.976128 + 116.609792 MB
-    # read, 53.0688 MB written
-    ("fp32", "eof_64x64x256", "2ceb4928095ff6da"): 190654720,
+    # --set full capture of these sources on GB300: 20.974592 + 116.611328 MB
+    # read, 53.602816 MB written
+    ("fp32", "eof_64x64x256", "c615e5a71457a79a"): 191188736,
 }
 
 
