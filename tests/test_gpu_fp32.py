@@ -125,6 +125,46 @@ def test_fp32_full_size_eof_vs_oracle_column(lbe):
     g.close()
 
 
+def test_fp32_unsigned_population_offsets_vs_oracle_column(lbe):
+    """A plate lattice of 115,343,360 nodes (256x256x1760): 19 N lies
+    between 2^31 and 2^32, so the odd in-place sweeps index the populations
+    with unsigned 32-bit offsets (the even ones with 64-bit offsets).  Four
+    steps (both step kinds twice) against the oracle on the 1x1x1760 column,
+    on sampled columns of the device fields, with exact fixed-point
+    conservation over the whole lattice summed on the device."""
+    import torch
+    nx, ny, nz = 256, 256, 1760
+    assert 2 ** 31 <= 19 * nx * ny * nz < 2 ** 32
+    full, red = wl.eof_plates(nx, ny, nz), wl.eof_plates(1, 1, nz)
+    o, g = oracle_for(red), gpu_for(lbe, full)
+    fluid = torch.from_numpy(full.ids == 0).to("cuda")
+    rb = torch.tensor(full.rho_bulk, dtype=torch.float64, device="cuda")[:, None, None, None]
+
+    def total_units():
+        n = g.field(lbe.FIELD_N, device=True)
+        q = torch.round((n - rb) / (rb * 2.0 ** -40)).to(torch.int64) * fluid
+        return q.sum(dim=(1, 2, 3)).cpu().numpy()
+
+    q0 = total_units()
+    o.step(4)
+    g.step(4)
+    cols = [(0, 0), (255, 255), (17, 200), (128, 64)]
+    scale = abs(full.psi[1] - full.psi[0])
+    phi = g.field(lbe.FIELD_PHI, device=True)
+    u = g.field(lbe.FIELD_U, device=True)
+    n = g.field(lbe.FIELD_N, device=True)
+    u_o, n_o = o.u()[:, :, 0, 0], o.n()[:, :, 0, 0]
+    for x, y in cols:
+        assert np.abs(phi[:, y, x].cpu().numpy() - o.phi()[:, 0, 0]).max() <= TOL_PHI * scale
+        assert np.abs(u[:, :, y, x].cpu().numpy() - u_o).max() <= TOL_U * np.abs(u_o).max() + 1e-12
+        assert np.abs(n[:, :, y, x].cpu().numpy() - n_o).max() <= 2e-6 * max(full.rho_bulk)
+    del phi, u, n
+    q_o = o.charge() * (nx * ny)
+    assert np.all(np.abs(g.charge() - q_o) <= TOL_Q * np.abs(q_o).max()), (g.charge(), q_o)
+    np.testing.assert_array_equal(total_units(), q0)
+    g.close()
+
+
 @pytest.mark.parametrize("flow", [True, False])
 def test_fp32_large_random_geometry(lbe, flow):
     """A random two-electrode lattice above 262,144 nodes (72x72x64 =
