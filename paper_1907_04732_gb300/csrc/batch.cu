@@ -1265,6 +1265,26 @@ int mg_setup(lbe_batch *b) {
   return coarse_inverses(b, seg);
 }
 
+// Blocks of a persistent kernel other than the sweep: the tuned grid, but at
+// most as many as the GPU holds at once at the kernel's own occupancy.  A
+// block beyond that would start only when a resident one had finished its
+// whole share of the tiles, and the kernel would take up to twice as long
+// (the coarse levels' post-smoothing, at 64 registers, holds four blocks per
+// SM; the tuned grid can have eight).  On the 256-instance sweep: solve 49.7
+// -> 47.3 ms per step.  The advection (48 registers) measured no better
+// capped (9.29 against 9.14 ms) and keeps the tuned grid, as the sweep.
+int resident_grid(const lbe_batch *b, const void *kernel) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0 ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, lbe::kBlock, 0) != cudaSuccess ||
+      per_sm <= 0) {
+    cudaGetLastError();  // clear; the tuned grid
+    return b->grid;
+  }
+  return std::min(b->grid, per_sm * sms);
+}
+
 // u = M r (one V-cycle over every active instance with a hierarchy) as graph
 // nodes after *last; r and u are the CG vectors
 cudaError_t add_vcycle(lbe_batch *b, cudaGraph_t gr, cudaGraphNode_t *last) {
@@ -1288,7 +1308,7 @@ cudaError_t add_vcycle(lbe_batch *b, cudaGraph_t gr, cudaGraphNode_t *last) {
     const float *A1 = P.A[1];
     float *rc = P.r[1], *zc = P.z[1];
     void *a[] = {&inst, &n, &pref, &seg1, &mask, &r0, &uj, &A1, &rc, &zc};
-    e = add_node(gr, last, (void *)kbm_restrict0, G, B, a);
+    e = add_node(gr, last, (void *)kbm_restrict0, dim3(resident_grid(b, (void *)kbm_restrict0)), B, a);
     if (e != cudaSuccess) return e;
   }
   for (int l = 1; l + 1 < L; ++l) {
@@ -1297,7 +1317,7 @@ cudaError_t add_vcycle(lbe_batch *b, cudaGraph_t gr, cudaGraphNode_t *last) {
     const float *AF = P.A[l], *rF = P.r[l], *zF = P.z[l], *AC = P.A[l + 1];
     float *rC = P.r[l + 1], *zC = P.z[l + 1];
     void *a[] = {&n, &pref, &sf, &sc, &AF, &rF, &zF, &AC, &rC, &zC};
-    e = add_node(gr, last, (void *)kbm_restrict, G, B, a);
+    e = add_node(gr, last, (void *)kbm_restrict, dim3(resident_grid(b, (void *)kbm_restrict)), B, a);
     if (e != cudaSuccess) return e;
   }
   {
@@ -1313,7 +1333,7 @@ cudaError_t add_vcycle(lbe_batch *b, cudaGraph_t gr, cudaGraphNode_t *last) {
     const float *A = P.A[l], *r = P.r[l], *z = P.z[l], *ec = P.e[l + 1];
     float *el = P.e[l];
     void *a[] = {&n, &pref, &sl, &sc, &A, &r, &z, &ec, &el};
-    e = add_node(gr, last, (void *)kbm_post, G, B, a);
+    e = add_node(gr, last, (void *)kbm_post, dim3(resident_grid(b, (void *)kbm_post)), B, a);
     if (e != cudaSuccess) return e;
   }
   const int *prefB0 = fam(b, famB(L, 0));
@@ -1321,13 +1341,13 @@ cudaError_t add_vcycle(lbe_batch *b, cudaGraph_t gr, cudaGraphNode_t *last) {
     const LvSeg *seg1 = seg_all + n;
     const float *e1 = P.e[1];
     void *a[] = {&inst, &n, &prefB0, &seg1, &mask, &uj, &e1, &t0};
-    e = add_node(gr, last, (void *)kbm_prolong0, G, B, a);
+    e = add_node(gr, last, (void *)kbm_prolong0, dim3(resident_grid(b, (void *)kbm_prolong0)), B, a);
     if (e != cudaSuccess) return e;
   }
   {
     const float *tc = t0;
     void *a[] = {&inst, &n, &prefB0, &mask, &r0, &tc, &u0};
-    e = add_node(gr, last, (void *)kbm_post0, G, B, a);
+    e = add_node(gr, last, (void *)kbm_post0, dim3(resident_grid(b, (void *)kbm_post0)), B, a);
   }
   return e;
 }
@@ -1408,6 +1428,12 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   SolveArgs A;
   solve_args(b, step, fin, fout, qin, qmid, A);
   const dim3 G(b->grid), B(kBlock), NB(b->n), rb((b->n + 255) / 256);
+  // the sweep and the advection take the tuned grid, the other persistent
+  // kernels at most one resident wave each (resident_grid)
+  const dim3 Gprep(resident_grid(b, (void *)prep_kernel(b->Ntot))), Gadv(b->grid),
+      Gext(resident_grid(b, (void *)kb_extrapolate)), Gres(resident_grid(b, (void *)kb_res)),
+      Gb(resident_grid(b, (void *)kb_cg_b)), Ga(resident_grid(b, (void *)kb_cg_a)),
+      Gcor(resident_grid(b, (void *)kb_correct));
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaGraphCreate(&g, 0);
   if (e != cudaSuccess) return e;
@@ -1437,32 +1463,32 @@ cudaError_t build_graph(lbe_batch *b, bool step, const float *fin, float *fout, 
   if (step) {
     void *sweep = (void *)sweep_kernel(b->flow, b->Ntot, b->aa_odd);
     if (prof) e = add_event(g, &last, b->ev[0]);
-    if (e == cudaSuccess) e = add_node(g, &last, (void *)prep_kernel(b->Ntot), G, B, a_prep);
+    if (e == cudaSuccess) e = add_node(g, &last, (void *)prep_kernel(b->Ntot), Gprep, B, a_prep);
     if (e == cudaSuccess) e = add_node(g, &last, sweep, G, B, a_sw);
     if (e == cudaSuccess && prof) e = add_event(g, &last, b->ev[1]);
-    if (e == cudaSuccess && b->flow) e = add_node(g, &last, (void *)kb_advect, G, B, a_adv);
+    if (e == cudaSuccess && b->flow) e = add_node(g, &last, (void *)kb_advect, Gadv, B, a_adv);
     if (e == cudaSuccess && prof) e = add_event(g, &last, b->ev[2]);
     // with flow the advection applies the warm start (kb_advect)
-    if (e == cudaSuccess && !b->flow) e = add_node(g, &last, (void *)kb_extrapolate, G, B, a_ext);
+    if (e == cudaSuccess && !b->flow) e = add_node(g, &last, (void *)kb_extrapolate, Gext, B, a_ext);
   }
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&A.hout, g, 1, cudaGraphCondAssignDefault);
   // reset -> residual test -> while (any instance unconverged) { V-cycle ->
   // CG -> correct -> residual test }
   if (e == cudaSuccess) e = add_node(g, &last, (void *)kb_solve_reset, rb, dim3(256), a_reset);
-  if (e == cudaSuccess) e = add_node(g, &last, (void *)kb_res, G, B, a_res);
+  if (e == cudaSuccess) e = add_node(g, &last, (void *)kb_res, Gres, B, a_res);
   if (e == cudaSuccess) e = add_node(g, &last, (void *)kb_outer, NB, B, a_out0);
   if (e == cudaSuccess) e = add_while(g, &last, A.hout, &bo);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&A.hin, bo, 0, 0);
   if (e == cudaSuccess) e = add_vcycle(b, bo, &lo);
-  if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_cg_b, G, B, a_b);
+  if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_cg_b, Gb, B, a_b);
   if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_scal, NB, B, a_si);
   if (e == cudaSuccess) e = add_while(bo, &lo, A.hin, &bi);
-  if (e == cudaSuccess) e = add_node(bi, &li, (void *)kb_cg_a, G, B, a_a);
+  if (e == cudaSuccess) e = add_node(bi, &li, (void *)kb_cg_a, Ga, B, a_a);
   if (e == cudaSuccess) e = add_vcycle(b, bi, &li);
-  if (e == cudaSuccess) e = add_node(bi, &li, (void *)kb_cg_b, G, B, a_b);
+  if (e == cudaSuccess) e = add_node(bi, &li, (void *)kb_cg_b, Gb, B, a_b);
   if (e == cudaSuccess) e = add_node(bi, &li, (void *)kb_scal, NB, B, a_st);
-  if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_correct, G, B, a_cor);
-  if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_res, G, B, a_res);
+  if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_correct, Gcor, B, a_cor);
+  if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_res, Gres, B, a_res);
   if (e == cudaSuccess) e = add_node(bo, &lo, (void *)kb_outer, NB, B, a_out);
   if (e == cudaSuccess && prof) e = add_event(g, &last, b->ev[3]);
   if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
@@ -1487,20 +1513,24 @@ int run_polled(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *
   solve_args(b, step, fin, fout, qin, qmid, A);
   cudaStream_t st = b->stream;
   const int G = b->grid, n = b->n;
+  const int Gprep = resident_grid(b, (void *)prep_kernel(b->Ntot)), Gadv = G,
+            Gext = resident_grid(b, (void *)kb_extrapolate), Gres = resident_grid(b, (void *)kb_res),
+            Gb = resident_grid(b, (void *)kb_cg_b), Ga = resident_grid(b, (void *)kb_cg_a),
+            Gcor = resident_grid(b, (void *)kb_correct);
   auto rec = [&](int k) { return b->profiling && step ? cudaEventRecord(b->ev[k], st) : cudaSuccess; };
   long long &nl = b->prof_launches;
   if (step) {
     BCK(b, rec(0));
-    prep_kernel(b->Ntot)<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.phi32, qin, A.lf);
+    prep_kernel(b->Ntot)<<<Gprep, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.phi32, qin, A.lf);
     sweep_kernel(b->flow, b->Ntot, b->aa_odd)<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, fin,
                                                                     fout, qin, qmid, A.lf, A.u, A.flag);
     BCK(b, rec(1));
     if (b->flow)  // the advection applies the warm start as well
-      kb_advect<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, qmid, A.u, qin, A.phifx, A.phi_prev,
+      kb_advect<<<Gadv, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, qmid, A.u, qin, A.phifx, A.phi_prev,
                                       A.phi32, A.hist);
     BCK(b, rec(2));
     if (!b->flow)
-      kb_extrapolate<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, A.phifx, A.phi_prev, A.phi32,
+      kb_extrapolate<<<Gext, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, A.phifx, A.phi_prev, A.phi32,
                                            A.hist);
     nl += 3;
   }
@@ -1528,29 +1558,29 @@ int run_polled(lbe_batch *b, bool step, const float *fin, float *fout, int64_t *
   const cudaGraphConditionalHandle h0 = 0;
   int any_outer = 1;
   while (any_outer && err == cudaSuccess) {
-    kb_res<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, A.qsolve, A.phifx, A.v, A.part, A.c);
+    kb_res<<<Gres, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.Ntot, A.mask, A.qsolve, A.phifx, A.v, A.part, A.c);
     kb_outer<<<n, kBlock, 0, st>>>(A.inst, n, A.T, A.part, A.c, A.bc, A.tol, A.maxit, A.nfam, A.fam_cnt, A.fam_pref,
                                    h0, h0, 0, 0);
     nl += 2;
     flags(&any_outer, nullptr);
     if (!any_outer) break;
     if (vc && err == cudaSuccess) err = cudaGraphLaunch(vc, st), nl += vck;
-    kb_cg_b<<<G, kBlock, 0, st>>>(A.inst, n, A.pref0, A.T, A.mask, A.vr, A.vu, A.vw, A.part);
+    kb_cg_b<<<Gb, kBlock, 0, st>>>(A.inst, n, A.pref0, A.T, A.mask, A.vr, A.vu, A.vw, A.part);
     kb_scal<<<n, kBlock, 0, st>>>(A.inst, n, A.T, A.part, A.c, A.bc, A.eta, A.tol_abs, A.maxit, 1, A.nfam, A.fam_cnt,
                                   A.fam_pref, h0, 0);
     nl += 2;
     int any_inner = 0;
     flags(nullptr, &any_inner);
     while (any_inner && err == cudaSuccess) {
-      kb_cg_a<<<G, kBlock, 0, st>>>(A.inst, n, A.pref0, A.T, A.mask, A.v, A.part, A.c);
+      kb_cg_a<<<Ga, kBlock, 0, st>>>(A.inst, n, A.pref0, A.T, A.mask, A.v, A.part, A.c);
       if (vc) err = cudaGraphLaunch(vc, st), nl += vck;
-      kb_cg_b<<<G, kBlock, 0, st>>>(A.inst, n, A.pref0, A.T, A.mask, A.vr, A.vu, A.vw, A.part);
+      kb_cg_b<<<Gb, kBlock, 0, st>>>(A.inst, n, A.pref0, A.T, A.mask, A.vr, A.vu, A.vw, A.part);
       kb_scal<<<n, kBlock, 0, st>>>(A.inst, n, A.T, A.part, A.c, A.bc, A.eta, A.tol_abs, A.maxit, 0, A.nfam,
                                     A.fam_cnt, A.fam_pref, h0, 0);
       nl += 3;
       flags(nullptr, &any_inner);
     }
-    kb_correct<<<G, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.mask, A.vx, A.phifx, A.phi32, A.flag, A.c);
+    kb_correct<<<Gcor, kBlock, 0, st>>>(A.inst, A.tile_inst, A.T, A.mask, A.vx, A.phifx, A.phi32, A.flag, A.c);
     nl += 1;
   }
   if (vc) cudaGraphExecDestroy(vc);
