@@ -1,7 +1,8 @@
-"""Host logic of the multigrid preconditioner, on the CPU: the inverse of the
-coarsest level's operator that the exact coarsest solve applies
-(mgd::coarse_inverse in csrc/mg.cu), compiled from the library's own source
-into a host program (no GPU call)."""
+"""Host logic of the library, on the CPU, compiled from its own source into
+host programs (no GPU call): the inverse of the multigrid's coarsest-level
+operator that the exact coarsest solve applies (mgd::coarse_inverse in
+csrc/mg.cu), and the width of the FP32 sweep's population offsets
+(fp32::pop_idx_kind in csrc/fp32_device.cuh)."""
 import os
 import re
 import shutil
@@ -32,3 +33,25 @@ def test_coarse_inverse(tmp_path):
     assert float(spd.group(2)) < 1e-5  # A inv = I to FP32 rounding of the inverse
     assert spd.group(3) == "1"        # the zero-diagonal node stays a zero of the correction
     assert re.search(r"singular ok=0", out), out  # a singular operator keeps the Jacobi sweeps
+
+
+def test_population_offset_widths(tmp_path):
+    """Signed 32-bit offsets while 19 N < 2^31, unsigned 32-bit while
+    19 N < 2^32, 64-bit beyond; the largest offset of every case is exact in
+    the width chosen."""
+    nvcc = _nvcc()
+    if not nvcc:
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path / "pop_idx_check")
+    src = os.path.join(HERE, "host", "pop_idx_check.cu")
+    subprocess.run([nvcc, "-std=c++17", "--expt-relaxed-constexpr", "-gencode", "arch=compute_103a,code=sm_103a",
+                    "-w", "-o", exe, src], check=True, capture_output=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    got = {int(n): (int(k), int(e)) for n, k, e in re.findall(r"N=(\d+) kind=(\d) exact=(\d)", out)}
+    assert len(got) == 9, out
+    for n, (kind, exact) in got.items():
+        want = 0 if 19 * n < 2 ** 31 else (1 if 19 * n < 2 ** 32 else 2)
+        assert kind == want, (n, kind, want)
+        assert exact == 1, (n, kind)
+    assert got[113025455][0] == 0 and got[113025456][0] == 1  # 19 N crosses 2^31
+    assert got[226050910][0] == 1 and got[226050911][0] == 2  # 19 N crosses 2^32
